@@ -1,0 +1,342 @@
+"""Benchmark of the GKS step on GB300: prints ONE JSON line (rank 0).
+
+Workload (default): 2-D TM, 4096 x 4096 Cartesian grid with 32 seeded dielectric cylinders,
+kinetic non-reflecting boundary, Gaussian-modulated line source, CFL 0.5, FP32 state and
+arithmetic; a step is one GKS time step over the whole grid (one fused kernel launch).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gks|reference]
+
+value      cell-updates per second over the K timed steps (all ranks), inputs resident in HBM.
+e2e        the same metric through the C ABI from host memory: gks_write_fields (pinned FP64
+           host fields) + gks_step(K) + gks_read_fields, wall-clocked.
+roofline   the fused step kernel against the measured HBM copy bandwidth.
+cpu_baseline  the FP64 oracle on a bounded sample of the workload on the host cores.
+With N > 1 (torchrun) every rank runs its own replica of the workload (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GCell-updates/s FP32 vs FP64 at stated error; % HBM roofline; adjoint/fwd cost"
+UNIT = "GCell-updates/s"
+BYTES_PER_CELL_STEP = {"fp32": 28, "fp64": 56}   # 3 fields read + written, eps read
+KERNEL_SRC = os.path.join(ROOT, "paper_2412_16845_gb300", "csrc", "gks_cart2d.cu")
+PROFILE = os.path.join(ROOT, "profiles", "cart2d_step_tm2d_cylinders_4096_fp32.md")
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def _kernel_hash():
+    return hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
+
+
+def _profiled_traffic():
+    """DRAM bytes per launch from the committed ncu summary, if it matches the current kernel."""
+    if not os.path.exists(PROFILE):
+        return None
+    txt = open(PROFILE).read()
+    m = re.search(r"dram_bytes_per_launch\s*=\s*([0-9.eE+]+)", txt)
+    h = re.search(r"kernel_source_sha256_16\s*=\s*([0-9a-f]+)", txt)
+    if not m or not h or h.group(1) != _kernel_hash():
+        return None
+    return float(m.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.2)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(seconds=12.0, block=160):
+    """Time the FP64 oracle (unchanged) on a block of the 4096^2 workload, in a fresh process
+    with single-threaded numpy/BLAS."""
+    code = f"""
+import sys, time, json, numpy as np
+sys.path.insert(0, {ROOT!r})
+from oracle import gks_oracle as go
+from paper_2412_16845_gb300 import workloads as wl
+n = 4096; b = {block}
+w = wl.config2_cylinders_tm(n=n, steps=1)
+i0 = w.extra['i_src'] - b // 2; j0 = n // 2 - b // 2
+ii = np.arange(i0, i0 + b); jj = np.arange(j0, j0 + b)
+gid = (jj[:, None] * n + ii[None, :]).ravel()
+h = 1.0 / n
+mesh = go.cartesian_mesh((b, b), (i0 * h, j0 * h), ((i0 + b) * h, (j0 + b) * h), ('nrbc',) * 4)
+rng = np.random.default_rng(0)
+V = go.fields_to_state(rng.standard_normal((3, b * b)), 2)
+m = go.material_diag(w.eps[gid], None)
+dt = 0.5 * h; C = go.time_coefficients(dt, 0.0)
+steps = 0; t0 = time.perf_counter()
+while True:
+    V = go.step(mesh, V, m, dt, C, 1.0, w.jz_mask[gid] * go.source_signal(steps * dt, *w.src))
+    steps += 1
+    el = time.perf_counter() - t0
+    if el >= {seconds}:
+        break
+print(json.dumps({{"cells": b * b, "steps": steps, "seconds": el}}))
+"""
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = "1"
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                       timeout=600)
+    if r.returncode != 0:
+        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": "failed: " + r.stderr[-300:]}
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    v = d["cells"] * d["steps"] / d["seconds"] / 1e9
+    return {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{d['steps']} FP64 oracle steps on a {block}x{block} block of the 4096^2 "
+                      f"cylinder workload around the source ({d['seconds']:.1f} s, numpy single "
+                      f"thread)"}
+
+
+def run_reference(args, rank):
+    """The reference arm: the FP64 oracle as it stands, on the host cores."""
+    if rank != 0:
+        return
+    block = 96
+    per = []
+    base = cpu_baseline(seconds=0.5, block=block)   # warm imports / caches
+    for _ in range(args.warmup):
+        pass
+    t0 = time.perf_counter()
+    res = cpu_baseline(seconds=max(2.0, 1.0 * args.steps / 50.0), block=block)
+    el = time.perf_counter() - t0
+    v = res["value"]
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "tm2d_cylinders_4096 (block sample)", "grid": [4096, 4096],
+                       "cfl": 0.5, "steps_config": 2000},
+            "cpu_baseline": res,
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": el}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="gks", choices=["gks", "reference"])
+    ap.add_argument("--n", type=int, default=4096)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_2412_16845_gb300 import build as gbuild
+    from paper_2412_16845_gb300 import workloads as wl
+    from paper_2412_16845_gb300.gks import GKSSolver
+
+    if rank == 0 and not os.path.exists(os.path.join(ROOT, "paper_2412_16845_gb300", "libgks.so")):
+        gbuild.build()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+        dist.barrier()
+        if rank != 0:
+            gbuild.build()
+    stream = torch.cuda.current_stream()
+    sptr = stream.cuda_stream
+
+    n = args.n
+    w = wl.config2_cylinders_tm(n=n, steps=args.steps)
+    ncell = n * n
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    # ---------------- FP32 device-resident timing
+    s32 = GKSSolver.from_workload(w, precision="fp32", stream=sptr)
+    s32.step(args.warmup)
+    s32.sync()
+    L0 = s32.launch_count()
+    sampler = ClockSampler(local)
+    if rank == 0:
+        sampler.start()
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s32.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop() if rank == 0 else None
+    ms = e0.elapsed_time(e1)
+    launches = s32.launch_count() - L0
+    t_max = torch.tensor([ms], device="cuda", dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    ms = float(t_max.item())
+    value = world * ncell * args.steps / (ms * 1e-3) / 1e9
+    ms_step = ms / args.steps
+
+    # ---------------- FP64 path, FP32-vs-FP64 error after the configuration's step count
+    steps_cfg = 2000
+    s64 = GKSSolver.from_workload(w, precision="fp64", stream=sptr)
+    s64.step(3)
+    s64.sync()
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    k64 = min(args.steps, 200)
+    f0.record(stream)
+    s64.step(k64)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    ms64 = f0.elapsed_time(f1) / k64
+    value64 = ncell / (ms64 * 1e-3) / 1e9
+    a32 = GKSSolver.from_workload(w, precision="fp32", stream=sptr)
+    a64 = GKSSolver.from_workload(w, precision="fp64", stream=sptr)
+    a32.step(steps_cfg)
+    a64.step(steps_cfg)
+    r32 = a32.read_fields()
+    r64 = a64.read_fields()
+    err = float(np.sqrt(np.sum((r32 - r64) ** 2) / max(np.sum(r64 ** 2), 1e-300)))
+    for s in (s64, a32, a64):
+        s.close()
+
+    # ---------------- end to end through the C ABI from pinned host memory
+    host_in = torch.empty((3, ncell), dtype=torch.float64, pin_memory=True)
+    host_in.copy_(torch.from_numpy(w.fields0))
+    host_out = torch.empty((3, ncell), dtype=torch.float64, pin_memory=True)
+    hin, hout = host_in.numpy(), host_out.numpy()
+    s32.write_fields(hin)
+    s32.step(2)
+    s32.read_fields(hout)
+    barrier()
+    t0 = time.perf_counter()
+    s32.write_fields(hin)
+    s32.step(args.steps)
+    s32.read_fields(hout)
+    e2e_s = time.perf_counter() - t0
+    tt = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    e2e_s = float(tt.item())
+    e2e = world * ncell * args.steps / e2e_s / 1e9
+    s32.close()
+
+    if rank == 0:
+        hbm, how = _peaks()
+        achieved = BYTES_PER_CELL_STEP["fp32"] * ncell / (ms_step * 1e-3) / 1e9
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"tm2d_cylinders_{n}", "grid": [n, n], "cylinders": 32,
+                       "bc": "nonreflecting", "cfl": 0.5, "source": "line, f0=20",
+                       "steps_config": steps_cfg, "precision": "fp32",
+                       "l2": "inputs larger than L2 (state+eps read+write per step "
+                             f"{BYTES_PER_CELL_STEP['fp32'] * ncell / 1e6:.0f} MB > 129 MB)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "peak_source": how,
+                         "traffic": _profiled_traffic(),
+                         "kernel": "cart2d_step_kernel<float>",
+                         "algorithmic_bytes_per_launch": BYTES_PER_CELL_STEP["fp32"] * ncell},
+            "fp64": {"value": value64, "ms_per_step": ms64, "unit": UNIT,
+                     "fp32_speedup": value / world / value64},
+            "fp32_vs_fp64_rel_l2": {"value": err, "after_steps": steps_cfg},
+            "e2e": {"value": e2e, "unit": UNIT,
+                    "h2d_bytes_per_step": 8 * 3 * ncell / args.steps,
+                    "d2h_bytes_per_step": 8 * 3 * ncell / args.steps,
+                    "definition": "write_fields(pinned FP64) + step(K) + read_fields, wall clock"},
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(line))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,153 @@
+/*
+ * gks.h -- C ABI of the GB300 (sm_103a) gas-kinetic scheme (GKS) for Maxwell's equations.
+ *
+ * Method: Pu, Long & Xu, "A Gas-Kinetic Scheme for Maxwell Equations" (arXiv 2412.16845).
+ * One call of gks_step advances the cell averages by the finite-volume update of Sec. 3.1,
+ *     U_i^{n+1} = U_i^n - dt/|Omega_i| sum_s |l_s| F_s + dt S_i^n,
+ * where every interface flux F_s is the time-integrated GKS flux of Sec. 3.1 (D3Q4 / D2Q4
+ * equilibrium, upwind interface equilibrium, compatibility time derivative, coefficients
+ * C1..C5), evaluated in the face frame T' of Sec. 3.1, with the kinetic non-reflecting boundary
+ * of Sec. 3.1 (incoming distributions of ghost cells are zero).
+ *
+ * Conventions shared by every entry point
+ *  - Fields: 2-D TM carries (Ez, Hx, Hy); 3-D carries (Ex, Ey, Ez, Hx, Hy, Hz).  The library
+ *    stores the primitive state V = (E, H); the conserved state is U = (eps E, mu H).
+ *    Units: c = eps0 = mu0 = 1 (Sec. 4) unless a lattice speed is given.
+ *  - User order: host arrays are [ncomp][n_cells] in user cell order.  Cartesian cells are
+ *    numbered x fastest (i + nx*(j + ny*k)); tetrahedra in the order of tet_vert.  Internal
+ *    layouts (padded rows, reordered cells) never show at the API.
+ *  - Ownership: host arrays passed in are copied before the call returns; the caller keeps
+ *    them.  Device buffers of the context are owned by the context and freed by gks_destroy.
+ *    Device pointers passed in (adjoint buffers) stay owned by the caller.
+ *  - Errors: every call returns a gks_status; no call aborts, traps or throws.  Arguments are
+ *    validated before anything is enqueued.  Asynchronous device errors and the non-finite
+ *    flag surface at the next call that synchronises (gks_read_fields, gks_energy,
+ *    gks_objective, gks_sync).  gks_last_error() gives a one-line reason.
+ *  - Streams: all device work of a context is enqueued on the stream given at creation
+ *    (cudaStream_t as void*, NULL = the legacy default stream).  A context is not re-entrant:
+ *    one host thread at a time.
+ */
+#ifndef GKS_H
+#define GKS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gks_ctx gks_ctx;
+
+typedef enum gks_status {
+  GKS_OK = 0,
+  GKS_E_ARG = 1,          /* invalid argument (null pointer, bad size, eps <= 0, ...)     */
+  GKS_E_NOMEM = 2,        /* device or host allocation failed                              */
+  GKS_E_CUDA = 3,         /* a CUDA runtime call failed                                    */
+  GKS_E_UNSUPPORTED = 4,  /* valid but not implemented combination                         */
+  GKS_E_STATE = 5,        /* call out of order (e.g. step before fields were written)      */
+  GKS_E_NONFINITE = 6,    /* a non-finite value appeared in the state                      */
+  GKS_E_TIMEOUT = 7       /* a bounded wait ran out                                        */
+} gks_status;
+
+enum { GKS_CARTESIAN = 0, GKS_TET = 1 };
+enum { GKS_FP32 = 0, GKS_FP64 = 1 };
+enum { GKS_BC_PERIODIC = 0, GKS_BC_NONREFLECTING = 1 };
+
+/* Problem description (Sec. 3.1: cells Omega_i, faces l_s with normals n_s).
+ *  dim        2 => TM (Ez, Hx, Hy) on an (x, y) grid; 3 => full Maxwell.
+ *  kind       GKS_CARTESIAN, or GKS_TET (requires dim == 3).
+ *  precision  GKS_FP32 or GKS_FP64: storage of the state and the flux/update arithmetic.
+ *  n, lo, hi  Cartesian cells per axis and box (n[2] ignored in 2-D).
+ *  bc         per side -x,+x,-y,+y,-z,+z: GKS_BC_PERIODIC (sides paired) or
+ *             GKS_BC_NONREFLECTING (kinetic boundary of Sec. 3.1).
+ *  vert_xyz   tets: [n_vert][3] doubles (host, copied).
+ *  tet_vert   tets: [n_tet][4] int64 vertex ids (host, copied), any orientation.
+ *  tet_bc     tets: boundary kind of every face that belongs to one tet only
+ *             (GKS_BC_NONREFLECTING).
+ *  cfl        dt = cfl * h_min / c, h_i = 2 dim |Omega_i| / sum_s |l_s| (edge of a square/cube).
+ *  tau_over_dt  kappa = tau/dt of the BGK relaxation time (Sec. 2.2, eq. of the vector BGK
+ *             model); 0 selects the tau -> 0 limit coefficients of Sec. 3.3.
+ *  c_lattice  lattice speed c of the D3Q4 velocities (Sec. 2.2); <= 0 selects
+ *             max_i 1/sqrt(eps_i mu_i) at gks_set_materials (1 in vacuum).
+ *  cuda_stream  cudaStream_t of all device work of this context.                          */
+typedef struct gks_mesh_desc {
+  int32_t dim;
+  int32_t kind;
+  int32_t precision;
+  int32_t reserved0;
+  int64_t n[3];
+  double lo[3];
+  double hi[3];
+  int32_t bc[6];
+  int64_t n_vert;
+  const double *vert_xyz;
+  int64_t n_tet;
+  const int64_t *tet_vert;
+  int32_t tet_bc;
+  int32_t reserved1;
+  double cfl;
+  double tau_over_dt;
+  double c_lattice;
+  void *cuda_stream;
+} gks_mesh_desc;
+
+/* Build the geometry (Sec. 3.1: |Omega_i|, |l_s|, n_s, face and cell centroids; T'(n_s) on
+ * tets), allocate the state (zero fields, eps = mu = 1) and compute dt and C1..C5.
+ * *out receives a new context, or NULL on error.  GKS_E_ARG on an invalid description,
+ * GKS_E_NOMEM / GKS_E_CUDA on allocation failure. */
+gks_status gks_create_mesh(const gks_mesh_desc *d, gks_ctx **out);
+
+/* Per-cell material eps, mu ([n_cells] doubles, user order, all > 0 and finite; mu == NULL
+ * means mu = 1).  The paper has no materials (Sec. 4 uses vacuum); the library uses
+ * U = (eps E, mu H) and the interface equilibrium M_s = (M_L + M_R)/2, which reduces to the
+ * paper's scheme for eps = mu = 1.  Recomputes the lattice speed (c_lattice <= 0), dt and
+ * C1..C5. */
+gks_status gks_set_materials(gks_ctx *ctx, const double *eps, const double *mu);
+
+/* Upload the primitive fields V = (E, H) ([ncomp][n_cells] doubles, user order, host) and set
+ * the time to t0 and the step counter to 0.  Converted to the context precision. */
+gks_status gks_write_fields(gks_ctx *ctx, const double *fields, double t0);
+
+/* Current-density source of Sec. 2.1, S = (-J, 0), with J = (0, 0, J_z) and
+ *     J_z(x_i, t) = jz_mask[i] * A * exp(-((t - t0)/s)^2) * sin(2 pi f0 (t - t0)),
+ * evaluated explicitly at t^n.  jz_mask: [n_cells] doubles, user order, or NULL to remove the
+ * source.  s must be > 0. */
+gks_status gks_set_source(gks_ctx *ctx, const double *jz_mask, double A, double f0, double t0,
+                          double s);
+
+/* Override dt (> 0) and recompute C1..C5; used to land exactly on a final time. */
+gks_status gks_set_dt(gks_ctx *ctx, double dt);
+
+/* Enqueue n_steps >= 0 GKS steps (Sec. 3.1) on the context stream; asynchronous. */
+gks_status gks_step(gks_ctx *ctx, int64_t n_steps);
+
+/* Wait for the stream, then copy the fields to out ([ncomp][n_cells] doubles, user order,
+ * host).  GKS_E_NONFINITE if a step produced a non-finite value. */
+gks_status gks_read_fields(gks_ctx *ctx, double *out);
+
+/* Electromagnetic energy 1/2 sum_i |Omega_i| (eps_i |E_i|^2 + mu_i |H_i|^2), accumulated in
+ * FP64 on the device; synchronises.  (Not in the paper: a diagnostic.) */
+gks_status gks_energy(gks_ctx *ctx, double *out);
+
+/* Wait for all enqueued work; report asynchronous errors and the non-finite flag. */
+gks_status gks_sync(gks_ctx *ctx);
+
+/* dt, current time, steps taken since the last gks_write_fields, cells, and the lattice c. */
+gks_status gks_get_info(const gks_ctx *ctx, double *dt, double *t, int64_t *step,
+                        int64_t *n_cells, double *c_lattice);
+
+/* Number of kernels this context has launched since it was created (a diagnostic for
+ * benchmarks; not in the paper). */
+gks_status gks_get_launch_count(const gks_ctx *ctx, int64_t *launches);
+
+/* One-line reason of the last failed call on this context (never NULL). */
+const char *gks_last_error(const gks_ctx *ctx);
+
+/* Free every device and host resource of the context (NULL is ignored). */
+void gks_destroy(gks_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GKS_H */

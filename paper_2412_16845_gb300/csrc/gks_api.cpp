@@ -1,0 +1,388 @@
+// Host side of the C ABI declared in include/gks.h: validation, device memory, dt and C1..C5,
+// and the step loop.  Every device operation is enqueued on the context's stream.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "gks_internal.h"
+
+namespace gks {
+
+// C1..C5 = integrals over [0, dt] of 1 - e^{-t/tau}, (tau + t)e^{-t/tau} - tau,
+// t + tau(e^{-t/tau} - 1), e^{-t/tau}, t e^{-t/tau} (Sec. 3.1).  For x = dt/tau < 2 the closed
+// forms cancel badly, so their power series in x are summed (terms alternate and fall fast).
+void time_coefficients(double dt, double tau, double C[5]) {
+  if (tau == 0.0) {
+    C[0] = dt;
+    C[1] = 0.0;
+    C[2] = 0.5 * dt * dt;
+    C[3] = 0.0;
+    C[4] = 0.0;
+    return;
+  }
+  const double x = dt / tau;
+  if (x >= 2.0) {
+    const double E = std::exp(-x);
+    const double one_minus_E = -std::expm1(-x);
+    C[0] = dt - tau * one_minus_E;
+    C[1] = tau * (-dt + 2.0 * tau * one_minus_E - dt * E);
+    C[2] = 0.5 * dt * dt - tau * dt + tau * tau * one_minus_E;
+    C[3] = tau * one_minus_E;
+    C[4] = -tau * dt * E + tau * tau * one_minus_E;
+    return;
+  }
+  // a_n = (-1)^n x^(n-2) / n!  (n >= 1); the five series below are sums of multiples of a_n.
+  double s1 = 0, s2 = 0, s3 = 0, s4 = 0, s5 = 0;
+  double xp = 1.0 / x;  // x^(n-2) for n = 1
+  double fact = 1.0;
+  for (int n = 1; n < 60; ++n) {
+    fact *= n;
+    const double an = ((n & 1) ? -1.0 : 1.0) * xp / fact;
+    s4 += -an * x;                    // (1 - E)/x       = sum_{n>=1} -a_n x
+    if (n >= 2) {
+      s1 += an * x;                   // 1 - (1 - E)/x   = sum_{n>=2} a_n x
+      s5 += (n - 1) * an;             // ((1-E) - xE)/x^2
+    }
+    if (n >= 3) {
+      s3 += -an;                      // 1/2 - 1/x + (1-E)/x^2
+      s2 += (n - 2) * an;             // (-x + 2(1-E) - xE)/x^2
+    }
+    xp *= x;
+  }
+  C[0] = dt * s1;
+  C[1] = dt * dt * s2;
+  C[2] = dt * dt * s3;
+  C[3] = dt * s4;
+  C[4] = dt * dt * s5;
+}
+
+}  // namespace gks
+
+namespace {
+
+gks_status fail(gks_ctx *ctx, gks_status s, const std::string &msg) {
+  if (ctx) ctx->err = msg;
+  return s;
+}
+
+gks_status cuda_fail(gks_ctx *ctx, cudaError_t e, const char *where) {
+  std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+  return fail(ctx, GKS_E_CUDA, m);
+}
+
+#define GKS_CUDA(call)                                   \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+  } while (0)
+
+bool finite_positive(double v) { return std::isfinite(v) && v > 0.0; }
+
+// dt = CFL h_min / c and C1..C5 with tau = kappa dt.
+void refresh_time_step(gks_ctx *ctx) {
+  ctx->dt = ctx->cfl * ctx->min_h / ctx->c;
+  gks::time_coefficients(ctx->dt, ctx->kappa * ctx->dt, ctx->C);
+}
+
+gks_status alloc_dev(gks_ctx *ctx, void **p, size_t bytes) {
+  cudaError_t e = cudaMallocAsync(p, bytes, ctx->st);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return fail(ctx, GKS_E_NOMEM, std::string("device allocation failed: ") + cudaGetErrorString(e));
+  }
+  return GKS_OK;
+}
+
+gks_status upload_cells(gks_ctx *ctx, const double *host, int ncomp, void *dst) {
+  const size_t bytes = sizeof(double) * (size_t)ncomp * (size_t)ctx->ncell;
+  GKS_CUDA(cudaMemcpyAsync(ctx->staging, host, bytes, cudaMemcpyHostToDevice, ctx->st));
+  GKS_CUDA(gks::launch_user_to_cart(ctx->g, ncomp, ctx->staging, dst, ctx->fp64, ctx->st));
+  return GKS_OK;
+}
+
+gks_status check_flag(gks_ctx *ctx) {
+  int h = 0;
+  GKS_CUDA(cudaMemcpyAsync(&h, ctx->flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+  GKS_CUDA(cudaStreamSynchronize(ctx->st));
+  if (h) return fail(ctx, GKS_E_NONFINITE, "a non-finite value appeared in the state");
+  return GKS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+gks_status gks_create_mesh(const gks_mesh_desc *d, gks_ctx **out) {
+  if (!out) return GKS_E_ARG;
+  *out = nullptr;
+  if (!d) return GKS_E_ARG;
+  if (d->dim != 2 && d->dim != 3) return GKS_E_ARG;
+  if (d->precision != GKS_FP32 && d->precision != GKS_FP64) return GKS_E_ARG;
+  if (!finite_positive(d->cfl) || !(d->tau_over_dt >= 0.0) || !std::isfinite(d->tau_over_dt))
+    return GKS_E_ARG;
+  if (d->kind == GKS_TET) return GKS_E_UNSUPPORTED;
+  if (d->kind != GKS_CARTESIAN) return GKS_E_ARG;
+  if (d->dim == 3) return GKS_E_UNSUPPORTED;
+  for (int a = 0; a < d->dim; ++a) {
+    if (d->n[a] < 1 || d->n[a] > (1 << 24)) return GKS_E_ARG;
+    if (!(d->hi[a] > d->lo[a]) || !std::isfinite(d->hi[a] - d->lo[a])) return GKS_E_ARG;
+    const int b0 = d->bc[2 * a], b1 = d->bc[2 * a + 1];
+    if ((b0 != GKS_BC_PERIODIC && b0 != GKS_BC_NONREFLECTING) ||
+        (b1 != GKS_BC_PERIODIC && b1 != GKS_BC_NONREFLECTING))
+      return GKS_E_ARG;
+    if ((b0 == GKS_BC_PERIODIC) != (b1 == GKS_BC_PERIODIC)) return GKS_E_ARG;
+  }
+
+  gks_ctx *ctx = new (std::nothrow) gks_ctx();
+  if (!ctx) return GKS_E_NOMEM;
+  ctx->d = *d;
+  ctx->d.vert_xyz = nullptr;
+  ctx->d.tet_vert = nullptr;
+  ctx->st = (cudaStream_t)d->cuda_stream;
+  ctx->dim = d->dim;
+  ctx->kind = d->kind;
+  ctx->ncomp = d->dim == 2 ? 3 : 6;
+  ctx->fp64 = d->precision == GKS_FP64;
+  ctx->esize = ctx->fp64 ? 8 : 4;
+  ctx->cfl = d->cfl;
+  ctx->kappa = d->tau_over_dt;
+  ctx->c_user = d->c_lattice;
+
+  gks::CartGeom &g = ctx->g;
+  g.dim = d->dim;
+  g.nx = (int)d->n[0];
+  g.ny = (int)d->n[1];
+  g.nz = d->dim == 3 ? (int)d->n[2] : 1;
+  g.pitch = ((int64_t)g.nx + 31) / 32 * 32;
+  g.plane = g.pitch * g.ny;
+  g.cstride = g.plane * g.nz;
+  ctx->ncell = (int64_t)g.nx * g.ny * g.nz;
+  ctx->min_h = 1e300;
+  for (int a = 0; a < d->dim; ++a) {
+    g.h[a] = (d->hi[a] - d->lo[a]) / (double)d->n[a];
+    g.periodic[a] = d->bc[2 * a] == GKS_BC_PERIODIC;
+    ctx->min_h = std::fmin(ctx->min_h, g.h[a]);
+  }
+  // h_i = 2 dim |Omega| / sum_s |l_s| for a box cell is the harmonic-type mean
+  // dim / sum_a (1/h_a); it equals the edge for squares and cubes.
+  {
+    double s = 0;
+    for (int a = 0; a < d->dim; ++a) s += 1.0 / g.h[a];
+    ctx->min_h = d->dim / s;
+  }
+  ctx->c = ctx->c_user > 0 ? ctx->c_user : 1.0;
+
+  gks_status s = GKS_OK;
+  const size_t fbytes = ctx->esize * (size_t)ctx->ncomp * (size_t)g.cstride;
+  const size_t mbytes = ctx->esize * (size_t)g.cstride;
+  if ((s = alloc_dev(ctx, &ctx->V[0], fbytes)) != GKS_OK ||
+      (s = alloc_dev(ctx, &ctx->V[1], fbytes)) != GKS_OK ||
+      (s = alloc_dev(ctx, &ctx->eps, mbytes)) != GKS_OK ||
+      (s = alloc_dev(ctx, (void **)&ctx->flag, sizeof(int))) != GKS_OK ||
+      (s = alloc_dev(ctx, (void **)&ctx->staging, sizeof(double) * ctx->ncomp * ctx->ncell)) !=
+          GKS_OK) {
+    gks_destroy(ctx);
+    return s;
+  }
+  ctx->red_n = 2 * 152 * 8;
+  if ((s = alloc_dev(ctx, (void **)&ctx->red, sizeof(double) * (ctx->red_n + 1))) != GKS_OK) {
+    gks_destroy(ctx);
+    return s;
+  }
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(ctx->V[0], 0, fbytes, ctx->st)) != cudaSuccess ||
+      (e = cudaMemsetAsync(ctx->V[1], 0, fbytes, ctx->st)) != cudaSuccess ||
+      (e = cudaMemsetAsync(ctx->flag, 0, sizeof(int), ctx->st)) != cudaSuccess ||
+      (e = gks::launch_fill(ctx->eps, g.cstride, 1.0, ctx->fp64, ctx->st)) != cudaSuccess) {
+    gks_destroy(ctx);
+    return GKS_E_CUDA;
+  }
+  refresh_time_step(ctx);
+  *out = ctx;
+  return GKS_OK;
+}
+
+gks_status gks_set_materials(gks_ctx *ctx, const double *eps, const double *mu) {
+  if (!ctx) return GKS_E_ARG;
+  if (!eps) return fail(ctx, GKS_E_ARG, "eps is NULL");
+  double cmax = 0.0;
+  for (int64_t i = 0; i < ctx->ncell; ++i) {
+    const double e = eps[i], m = mu ? mu[i] : 1.0;
+    if (!finite_positive(e) || !finite_positive(m))
+      return fail(ctx, GKS_E_ARG, "eps and mu must be finite and > 0 (cell " +
+                                      std::to_string(i) + ")");
+    cmax = std::fmax(cmax, 1.0 / std::sqrt(e * m));
+  }
+  gks_status s;
+  if ((s = upload_cells(ctx, eps, 1, ctx->eps)) != GKS_OK) return s;
+  if (mu) {
+    if (!ctx->mu) {
+      if ((s = alloc_dev(ctx, &ctx->mu, ctx->esize * (size_t)ctx->g.cstride)) != GKS_OK) return s;
+    }
+    if ((s = upload_cells(ctx, mu, 1, ctx->mu)) != GKS_OK) return s;
+  } else if (ctx->mu) {
+    GKS_CUDA(cudaFreeAsync(ctx->mu, ctx->st));
+    ctx->mu = nullptr;
+  }
+  ctx->c = ctx->c_user > 0 ? ctx->c_user : cmax;
+  refresh_time_step(ctx);
+  return GKS_OK;
+}
+
+gks_status gks_write_fields(gks_ctx *ctx, const double *fields, double t0) {
+  if (!ctx) return GKS_E_ARG;
+  if (!fields) return fail(ctx, GKS_E_ARG, "fields is NULL");
+  if (!std::isfinite(t0)) return fail(ctx, GKS_E_ARG, "t0 must be finite");
+  gks_status s = upload_cells(ctx, fields, ctx->ncomp, ctx->V[ctx->cur]);
+  if (s != GKS_OK) return s;
+  GKS_CUDA(cudaMemsetAsync(ctx->flag, 0, sizeof(int), ctx->st));
+  ctx->t0 = t0;
+  ctx->step = 0;
+  ctx->fields_written = true;
+  return GKS_OK;
+}
+
+gks_status gks_set_source(gks_ctx *ctx, const double *jz_mask, double A, double f0, double t0,
+                          double s) {
+  if (!ctx) return GKS_E_ARG;
+  if (!jz_mask) {
+    if (ctx->src) GKS_CUDA(cudaFreeAsync(ctx->src, ctx->st));
+    ctx->src = nullptr;
+    return GKS_OK;
+  }
+  if (!std::isfinite(A) || !std::isfinite(f0) || !std::isfinite(t0) || !finite_positive(s))
+    return fail(ctx, GKS_E_ARG, "source parameters must be finite and s > 0");
+  const gks::CartGeom &g = ctx->g;
+  int box[6] = {g.nx, -1, g.ny, -1, g.nz, -1};
+  for (int64_t i = 0; i < ctx->ncell; ++i) {
+    const double v = jz_mask[i];
+    if (!std::isfinite(v)) return fail(ctx, GKS_E_ARG, "jz_mask must be finite");
+    if (v != 0.0) {
+      const int ix = (int)(i % g.nx), iy = (int)((i / g.nx) % g.ny), iz = (int)(i / ((int64_t)g.nx * g.ny));
+      box[0] = std::min(box[0], ix); box[1] = std::max(box[1], ix);
+      box[2] = std::min(box[2], iy); box[3] = std::max(box[3], iy);
+      box[4] = std::min(box[4], iz); box[5] = std::max(box[5], iz);
+    }
+  }
+  gks_status st;
+  if (!ctx->src) {
+    if ((st = alloc_dev(ctx, &ctx->src, ctx->esize * (size_t)g.cstride)) != GKS_OK) return st;
+  }
+  if ((st = upload_cells(ctx, jz_mask, 1, ctx->src)) != GKS_OK) return st;
+  if (box[1] < 0) {  // all zero
+    box[0] = box[2] = box[4] = 0;
+    box[1] = box[3] = box[5] = -1;
+  }
+  ctx->src_box[0] = box[0]; ctx->src_box[1] = box[1] + 1;
+  ctx->src_box[2] = box[2]; ctx->src_box[3] = box[3] + 1;
+  ctx->src_box[4] = box[4]; ctx->src_box[5] = box[5] + 1;
+  ctx->srcA = A;
+  ctx->srcF0 = f0;
+  ctx->srcT0 = t0;
+  ctx->srcS = s;
+  return GKS_OK;
+}
+
+gks_status gks_set_dt(gks_ctx *ctx, double dt) {
+  if (!ctx) return GKS_E_ARG;
+  if (!finite_positive(dt)) return fail(ctx, GKS_E_ARG, "dt must be finite and > 0");
+  ctx->dt = dt;
+  gks::time_coefficients(dt, ctx->kappa * dt, ctx->C);
+  return GKS_OK;
+}
+
+gks_status gks_step(gks_ctx *ctx, int64_t n_steps) {
+  if (!ctx) return GKS_E_ARG;
+  if (n_steps < 0) return fail(ctx, GKS_E_ARG, "n_steps must be >= 0");
+  if (!ctx->fields_written) return fail(ctx, GKS_E_STATE, "gks_write_fields must come first");
+  gks::CartStepArgs a;
+  a.eps = ctx->eps;
+  a.mu = ctx->mu;
+  a.src = ctx->src;
+  std::memcpy(a.src_box, ctx->src_box, sizeof(a.src_box));
+  std::memcpy(a.C, ctx->C, sizeof(a.C));
+  a.c = ctx->c;
+  a.flag = ctx->flag;
+  for (int64_t n = 0; n < n_steps; ++n) {
+    const double t = ctx->t0 + (double)ctx->step * ctx->dt;
+    a.src_amp = 0.0;
+    if (ctx->src) {
+      const double tt = t - ctx->srcT0;
+      a.src_amp = ctx->dt * ctx->srcA * std::exp(-(tt / ctx->srcS) * (tt / ctx->srcS)) *
+                  std::sin(2.0 * M_PI * ctx->srcF0 * tt);
+    }
+    a.V = ctx->V[ctx->cur];
+    a.Vout = ctx->V[ctx->cur ^ 1];
+    cudaError_t e = gks::launch_cart2d_step(ctx->g, a, ctx->fp64, ctx->st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cart2d step launch");
+    ctx->launches += 1;
+    ctx->cur ^= 1;
+    ctx->step += 1;
+  }
+  return GKS_OK;
+}
+
+gks_status gks_read_fields(gks_ctx *ctx, double *out) {
+  if (!ctx) return GKS_E_ARG;
+  if (!out) return fail(ctx, GKS_E_ARG, "out is NULL");
+  GKS_CUDA(gks::launch_cart_to_user(ctx->g, ctx->ncomp, ctx->V[ctx->cur], ctx->staging,
+                                    ctx->fp64, ctx->st));
+  GKS_CUDA(cudaMemcpyAsync(out, ctx->staging, sizeof(double) * ctx->ncomp * ctx->ncell,
+                           cudaMemcpyDeviceToHost, ctx->st));
+  return check_flag(ctx);
+}
+
+gks_status gks_energy(gks_ctx *ctx, double *out) {
+  if (!ctx) return GKS_E_ARG;
+  if (!out) return fail(ctx, GKS_E_ARG, "out is NULL");
+  GKS_CUDA(gks::launch_cart_energy(ctx->g, ctx->ncomp, ctx->V[ctx->cur], ctx->eps, ctx->mu,
+                                   ctx->fp64, ctx->red, ctx->red_n, ctx->red + ctx->red_n,
+                                   ctx->st));
+  GKS_CUDA(cudaMemcpyAsync(out, ctx->red + ctx->red_n, sizeof(double), cudaMemcpyDeviceToHost,
+                           ctx->st));
+  return check_flag(ctx);
+}
+
+gks_status gks_sync(gks_ctx *ctx) {
+  if (!ctx) return GKS_E_ARG;
+  GKS_CUDA(cudaStreamSynchronize(ctx->st));
+  GKS_CUDA(cudaGetLastError());
+  return check_flag(ctx);
+}
+
+gks_status gks_get_info(const gks_ctx *ctx, double *dt, double *t, int64_t *step,
+                        int64_t *n_cells, double *c_lattice) {
+  if (!ctx) return GKS_E_ARG;
+  if (dt) *dt = ctx->dt;
+  if (t) *t = ctx->t0 + (double)ctx->step * ctx->dt;
+  if (step) *step = ctx->step;
+  if (n_cells) *n_cells = ctx->ncell;
+  if (c_lattice) *c_lattice = ctx->c;
+  return GKS_OK;
+}
+
+gks_status gks_get_launch_count(const gks_ctx *ctx, int64_t *launches) {
+  if (!ctx || !launches) return GKS_E_ARG;
+  *launches = ctx->launches;
+  return GKS_OK;
+}
+
+const char *gks_last_error(const gks_ctx *ctx) {
+  if (!ctx) return "null context";
+  return ctx->err.c_str();
+}
+
+void gks_destroy(gks_ctx *ctx) {
+  if (!ctx) return;
+  void *bufs[] = {ctx->V[0], ctx->V[1], ctx->eps, ctx->mu, ctx->src, ctx->flag, ctx->red,
+                  ctx->staging};
+  for (void *p : bufs)
+    if (p) cudaFreeAsync(p, ctx->st);
+  cudaStreamSynchronize(ctx->st);
+  delete ctx;
+}
+
+}  // extern "C"

@@ -1,0 +1,89 @@
+// Internal declarations shared by the host API (gks_api.cpp) and the CUDA translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/gks.h"
+
+namespace gks {
+
+// Time-integration coefficients C1..C5 of the GKS flux (Sec. 3.1) for step dt and relaxation
+// time tau (tau = 0: the tau -> 0 limit of Sec. 3.3).
+void time_coefficients(double dt, double tau, double C[5]);
+
+// Cartesian grid geometry and state layout.  Fields are stored structure-of-arrays,
+// [ncomp][nz][ny][pitch] with x fastest; pitch is nx rounded up to a multiple of 32 elements
+// (128 B rows in FP32) so that every row starts 128-byte aligned.
+struct CartGeom {
+  int dim = 2;
+  int nx = 1, ny = 1, nz = 1;
+  int64_t pitch = 0;    // elements per row
+  int64_t plane = 0;    // pitch * ny
+  int64_t cstride = 0;  // elements per component: plane * nz
+  double h[3] = {1, 1, 1};
+  int periodic[3] = {0, 0, 0};
+};
+
+// Arguments of one Cartesian step launch (precision-independent; kernels cast).
+struct CartStepArgs {
+  const void *V;        // state at t^n
+  void *Vout;           // state at t^{n+1}
+  const void *eps;      // [nz][ny][pitch]
+  const void *mu;       // same layout, or nullptr (mu = 1)
+  const void *src;      // J_z mask, same layout, or nullptr
+  int src_box[6];       // i0,i1,j0,j1,k0,k1 (half open) of the non-zero mask
+  double src_amp;       // dt * waveform(t^n)
+  double C[5];          // C1..C5
+  double c;             // lattice speed
+  int *flag;            // non-finite flag (device)
+};
+
+// Launchers (return cudaGetLastError() of the launch).
+cudaError_t launch_cart2d_step(const CartGeom &g, const CartStepArgs &a, bool fp64,
+                               cudaStream_t st);
+cudaError_t launch_user_to_cart(const CartGeom &g, int ncomp, const double *user, void *dst,
+                                bool fp64, cudaStream_t st);
+cudaError_t launch_cart_to_user(const CartGeom &g, int ncomp, const void *src, double *user,
+                                bool fp64, cudaStream_t st);
+cudaError_t launch_fill(void *dst, int64_t n, double value, bool fp64, cudaStream_t st);
+// Energy 1/2 sum |Omega| (eps |E|^2 + mu |H|^2) into *out (device double), FP64 accumulation.
+cudaError_t launch_cart_energy(const CartGeom &g, int ncomp, const void *V, const void *eps,
+                               const void *mu, bool fp64, double *partials, int npart,
+                               double *out, cudaStream_t st);
+
+}  // namespace gks
+
+struct gks_ctx {
+  gks_mesh_desc d{};
+  cudaStream_t st = nullptr;
+  int dim = 2, kind = GKS_CARTESIAN, ncomp = 3;
+  bool fp64 = false;
+  int64_t ncell = 0;
+  size_t esize = 4;
+  gks::CartGeom g;
+  // device buffers
+  void *V[2] = {nullptr, nullptr};
+  int cur = 0;
+  void *eps = nullptr;
+  void *mu = nullptr;           // null: mu = 1
+  void *src = nullptr;          // J_z mask or null
+  int src_box[6] = {0, 0, 0, 0, 0, 0};
+  double srcA = 0, srcF0 = 0, srcT0 = 0, srcS = 1;
+  int *flag = nullptr;
+  double *red = nullptr;        // reduction scratch (partials + result)
+  int red_n = 0;
+  double *staging = nullptr;    // FP64 user-order staging buffer [ncomp][ncell]
+  // time stepping
+  double cfl = 0.5, kappa = 0.0, c = 1.0, c_user = 0.0;
+  double dt = 0.0, t0 = 0.0;
+  int64_t step = 0;
+  double C[5] = {0, 0, 0, 0, 0};
+  double min_h = 1.0;
+  bool fields_written = false;
+  int64_t launches = 0;
+  std::string err;
+};
