@@ -1,13 +1,12 @@
 // Fused 2-D TM GKS step on a Cartesian grid: cell gradients, face reconstruction, the GKS
 // interface flux and the finite-volume update in one pass over the state (Sec. 3.1).
 //
-// Row-marching scheme.  A CTA of NT threads owns a strip of W = 2 NT - 4 columns and a chunk of
-// rows, and walks up the rows with one barrier per row.  Thread t owns the column pair
-// (X, X+1), X = x0 - 2 + 2t, and keeps its own columns of the state, eps, gradients and the
-// y-face flux in registers; shared memory holds the current rows only for the x-neighbours.
-// Every gradient and every face is evaluated once: per row a thread evaluates the gradient pair
-// of row j+1, the x-face pair (X+1/2, X+3/2) and the y-face pair (j+1/2) and updates its two
-// cells of row j.  FP32 pairs run on the packed FP32x2 pipe (FFMA2 / FADD2 / FMUL2).
+// Row-marching scheme.  A CTA of NT threads owns a strip of W = NT - 2 columns and a chunk of
+// rows, and walks up the rows with one barrier per row.  Thread t owns column X = x0 - 1 + t
+// and keeps its own column of the state, eps, central differences and the y-face flux in
+// registers; shared memory holds the current rows only for the x-neighbours.  Every gradient
+// and every face is evaluated once: per row a thread forms the differences of row j+1, the
+// x-face X - 1/2 and the y-face j + 1/2, and updates its cell of row j.
 //
 // Face frames (Sec. 3.1, T'(n)): an x-face uses n = e_x (T' = I); a y-face n = e_y with local
 // axes (x', y') = (y, -x); the low boundary faces use the outward normals -e_x (T' =
@@ -20,37 +19,15 @@
 namespace gks {
 namespace {
 
-constexpr int NT = 64;             // threads per CTA
-constexpr int W = 2 * NT - 4;      // columns updated per CTA
-constexpr int NCOL = 2 * NT + 2;   // staged columns: x0-3 .. x0+W+2
+constexpr int NT = 128;            // threads per CTA, one column each
+constexpr int W = NT - 2;          // columns updated per CTA
 constexpr int ROWS = 64;           // rows per CTA
 
-// ------------------------------------------------------------------ pair arithmetic
-__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 vsub(float2 a, float2 b) {
-  return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
-}
-__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ float2 vbc(float s) { return make_float2(s, s); }
-__device__ __forceinline__ float2 vrcp(float2 a) {
-  return make_float2(__fdividef(1.f, a.x), __fdividef(1.f, a.y));
-}
-__device__ __forceinline__ float2 vmk(float a, float b) { return make_float2(a, b); }
-
-__device__ __forceinline__ double2 vadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ double2 vsub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ double2 vmul(double2 a, double2 b) { return make_double2(a.x * b.x, a.y * b.y); }
-__device__ __forceinline__ double2 vfma(double2 a, double2 b, double2 c) {
-  return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
-}
-__device__ __forceinline__ double2 vbc(double s) { return make_double2(s, s); }
-__device__ __forceinline__ double2 vrcp(double2 a) { return make_double2(1.0 / a.x, 1.0 / a.y); }
-__device__ __forceinline__ double2 vmk(double a, double b) { return make_double2(a, b); }
-
-template <typename T> struct PairOf;
-template <> struct PairOf<float> { using type = float2; };
-template <> struct PairOf<double> { using type = double2; };
+// Reciprocals: FP32 uses the fast hardware reciprocal (about 1 ulp), FP64 divides.
+__device__ __forceinline__ float rcp1(float x) { return __fdividef(1.f, x); }
+__device__ __forceinline__ double rcp1(double x) { return 1.0 / x; }
+__device__ __forceinline__ float rcp2(float x) { return __fdividef(2.f, x); }
+__device__ __forceinline__ double rcp2(double x) { return 2.0 / x; }
 
 // ------------------------------------------------------------------ flux coefficients
 // Combined constants of one face orientation (K_i = C_i / h_normal, c the lattice speed,
@@ -131,71 +108,55 @@ __device__ __forceinline__ void tm_face_flux(const Side<T> &L, const Side<T> &R,
   fb = ob + K.k4 * t4b - K.k5 * t5b;
 }
 
-// One side of an interior face pair in global components: e = Ez, hn = normal H, ht =
-// tangential H (reconstructed at the face), their normal derivatives en, hnn, htn, the
-// tangential derivatives at = d_t(hn), et = d_t(Ez), and the material.
-template <typename P>
-struct PSide {
-  P e, hn, ht, en, hnn, htn, at, et, eps, mu;
+// One side of an interior face in global components: e = Ez, hn = normal H, ht =
+// tangential H (reconstructed at the face), the raw central differences along the normal of
+// (Ez, Hn, Ht) (dn_* = V_{+1} - V_{-1}), the raw tangential differences of Hn and Ez, and the
+// material.
+template <typename T>
+struct FSide {
+  T e, hn, ht, den, dhn, dht, dat, det, eps, mu;
 };
 
-// Interior face flux for a pair of faces (times dt/h), in global components:
+// Interior face flux (times dt/h), global components, from raw differences:
 //   Phi_E  = im (a1 S_UB + a2 D_e) + g (S_Uxe/2 + a3 D_xB) + a4 S_B - q2 D_Ue - q3 S_Uxe
 //            + a5 D_At + a6 D_xB
 //   Phi_Hn = q5 S_Uxa - q2 D_Ua + b1 D_Et
 //   Phi_Ht = ie (c1 S_Ue + c2 D_B) + g (S_UxB/2 + c3 D_ex) + c4 ie im S_UAt + c5 S_e - q2 D_UB
 //            - q3 S_UxB + c6 D_ex
 // with S_* = l + r sums, D_* = r - l differences, U* = M V, ie = 1/eps_s, im = 1/mu_s and
-// g = g0 - k3 ie im.  This is the closed form of tm_face_flux above with the face-frame signs
-// and the C1..C5 combinations folded into FaceK (see make_face_k).
-template <typename T, typename P, bool HAS_MU>
-__device__ __forceinline__ void face_pair(const PSide<P> &l, const PSide<P> &r,
-                                          const FaceK<T> &k, P &fE, P &fHn, P &fHt) {
-  const P half = vbc(T(0.5));
-  const P Ue_l = vmul(l.eps, l.e), Ue_r = vmul(r.eps, r.e);
-  const P Uxe_l = vmul(l.eps, l.en), Uxe_r = vmul(r.eps, r.en);
-  P UB_l = l.ht, UB_r = r.ht, Ua_l = l.hn, Ua_r = r.hn;
-  P UxB_l = l.htn, UxB_r = r.htn, Uxa_l = l.hnn, Uxa_r = r.hnn, UAt_l = l.at, UAt_r = r.at;
+// g = g0 - k3 ie im.  This is tm_face_flux above rewritten in sums and differences, with the
+// face-frame signs, the C1..C5 combinations and the 1/(2h) of the central differences folded
+// into FaceK (make_face_k).
+template <typename T, bool HAS_MU>
+__device__ __forceinline__ void face_flux(const FSide<T> &l, const FSide<T> &r, const FaceK<T> &k,
+                                          T &fE, T &fHn, T &fHt) {
+  const T Ue_l = l.eps * l.e, Ue_r = r.eps * r.e;
+  const T Uxe_l = l.eps * l.den, Uxe_r = r.eps * r.den;
+  T UB_l = l.ht, UB_r = r.ht, Ua_l = l.hn, Ua_r = r.hn;
+  T UxB_l = l.dht, UxB_r = r.dht, Uxa_l = l.dhn, Uxa_r = r.dhn, UAt_l = l.dat, UAt_r = r.dat;
   if (HAS_MU) {
-    UB_l = vmul(l.mu, l.ht); UB_r = vmul(r.mu, r.ht);
-    Ua_l = vmul(l.mu, l.hn); Ua_r = vmul(r.mu, r.hn);
-    UxB_l = vmul(l.mu, l.htn); UxB_r = vmul(r.mu, r.htn);
-    Uxa_l = vmul(l.mu, l.hnn); Uxa_r = vmul(r.mu, r.hnn);
-    UAt_l = vmul(l.mu, l.at); UAt_r = vmul(r.mu, r.at);
+    UB_l *= l.mu; UB_r *= r.mu; Ua_l *= l.mu; Ua_r *= r.mu;
+    UxB_l *= l.mu; UxB_r *= r.mu; Uxa_l *= l.mu; Uxa_r *= r.mu; UAt_l *= l.mu; UAt_r *= r.mu;
   }
-  const P S_UB = vadd(UB_l, UB_r), D_e = vsub(r.e, l.e);
-  const P S_Uxe = vadd(Uxe_l, Uxe_r), D_xB = vsub(r.htn, l.htn);
-  const P S_B = vadd(l.ht, r.ht), D_Ue = vsub(Ue_r, Ue_l), D_At = vsub(r.at, l.at);
-  const P S_Uxa = vadd(Uxa_l, Uxa_r), D_Ua = vsub(Ua_r, Ua_l), D_Et = vsub(r.et, l.et);
-  const P S_Ue = vadd(Ue_l, Ue_r), D_B = vsub(r.ht, l.ht), S_UxB = vadd(UxB_l, UxB_r);
-  const P D_ex = vsub(r.en, l.en), S_UAt = vadd(UAt_l, UAt_r), S_e = vadd(l.e, r.e);
-  const P D_UB = vsub(UB_r, UB_l);
-  const P ie = vrcp(vmul(half, vadd(l.eps, r.eps)));
-  P im = vbc(T(1));
-  if (HAS_MU) im = vrcp(vmul(half, vadd(l.mu, r.mu)));
-  const P iem = HAS_MU ? vmul(ie, im) : ie;
-  const P g = vfma(vbc(-k.k3), iem, vbc(k.g0));
-  // E flux
-  P t = vfma(vbc(k.a2), D_e, vmul(vbc(k.a1), S_UB));
-  P fe = HAS_MU ? vmul(im, t) : t;
-  fe = vfma(g, vfma(vbc(k.a3), D_xB, vmul(half, S_Uxe)), fe);
-  fe = vfma(vbc(k.a4), S_B, fe);
-  fe = vfma(vbc(-k.q2), D_Ue, fe);
-  fe = vfma(vbc(-k.q3), S_Uxe, fe);
-  fe = vfma(vbc(k.a5), D_At, fe);
-  fe = vfma(vbc(k.a6), D_xB, fe);
-  // normal-H flux
-  P fa = vmul(vbc(k.q5), S_Uxa);
-  fa = vfma(vbc(-k.q2), D_Ua, fa);
-  fa = vfma(vbc(k.b1), D_Et, fa);
-  // tangential-H flux
-  P fb = vmul(ie, vfma(vbc(k.c2), D_B, vmul(vbc(k.c1), S_Ue)));
-  fb = vfma(g, vfma(vbc(k.c3), D_ex, vmul(half, S_UxB)), fb);
-  fb = vfma(vmul(vbc(k.c4), iem), S_UAt, fb);
-  fb = vfma(vbc(k.c5), S_e, fb);
-  fb = vfma(vbc(-k.q2), D_UB, fb);
-  fb = vfma(vbc(-k.q3), S_UxB, fb);
-  fb = vfma(vbc(k.c6), D_ex, fb);
+  const T S_UB = UB_l + UB_r, D_e = r.e - l.e;
+  const T S_Uxe = Uxe_l + Uxe_r, D_xB = r.dht - l.dht;
+  const T S_B = l.ht + r.ht, D_Ue = Ue_r - Ue_l, D_At = r.dat - l.dat;
+  const T S_Uxa = Uxa_l + Uxa_r, D_Ua = Ua_r - Ua_l, D_Et = r.det - l.det;
+  const T S_Ue = Ue_l + Ue_r, D_B = r.ht - l.ht, S_UxB = UxB_l + UxB_r;
+  const T D_ex = r.den - l.den, S_UAt = UAt_l + UAt_r, S_e = l.e + r.e;
+  const T D_UB = UB_r - UB_l;
+  const T ie = rcp2(l.eps + r.eps);                 // 1 / ((eps_l + eps_r)/2)
+  const T im = HAS_MU ? rcp2(l.mu + r.mu) : T(1);
+  const T iem = HAS_MU ? ie * im : ie;
+  const T g = k.g0 - k.k3 * iem;
+  T fe = k.a1 * S_UB + k.a2 * D_e;
+  if (HAS_MU) fe *= im;
+  fe += g * (T(0.5) * S_Uxe + k.a3 * D_xB);
+  fe += k.a4 * S_B - k.q2 * D_Ue - k.q3 * S_Uxe + k.a5 * D_At + k.a6 * D_xB;
+  const T fa = k.q5 * S_Uxa - k.q2 * D_Ua + k.b1 * D_Et;
+  T fb = ie * (k.c1 * S_Ue + k.c2 * D_B);
+  fb += g * (T(0.5) * S_UxB + k.c3 * D_ex);
+  fb += k.c4 * iem * S_UAt + k.c5 * S_e - k.q2 * D_UB - k.q3 * S_UxB + k.c6 * D_ex;
   fE = fe;
   fHn = fa;
   fHt = fb;
@@ -213,7 +174,7 @@ struct Cart2DKernelArgs {
   int nx, ny;
   int64_t pitch, cstride;
   int perx, pery;
-  T inv2hx, inv2hy, halfhx, halfhy;
+  T inv2hx, inv2hy;
   FaceK<T> fx, fy;     // interior x- and y-faces
   Coef<T> Kx, Ky;      // boundary faces (scalar path)
   int *flag;
@@ -227,140 +188,142 @@ __device__ __forceinline__ int wrap_or_clamp(int i, int n, int periodic) {
   return i < 0 ? 0 : (i >= n ? n - 1 : i);
 }
 
+// One row of a thread's column: (Ez, Hx, Hy) and the material.
 template <typename T>
-__device__ __forceinline__ T lane(const typename PairOf<T>::type &p, int k) {
-  return k ? p.y : p.x;
-}
-template <typename T>
-__device__ __forceinline__ void set_lane(typename PairOf<T>::type &p, int k, T v) {
-  if (k) p.y = v; else p.x = v;
-}
-
-// Register state of one row of a thread's column pair.
-template <typename P>
 struct RowV {
-  P ez, hx, hy, eps, mu;
+  T ez, hx, hy, eps, mu;
 };
-// Gradient pair of one row: d/dx and d/dy of (Ez, Hx, Hy).
-template <typename P>
+// Raw central differences of one row: x and y differences of (Ez, Hx, Hy).
+template <typename T>
 struct RowG {
-  P ex, ey, ax, ay, bx, by;
+  T ex, ey, ax, ay, bx, by;
 };
 
-// Load the pair (X, X+1) of row `row` (wrapped or clamped), all components.
-template <typename T, bool HAS_MU>
-__device__ __forceinline__ RowV<typename PairOf<T>::type> load_pair(const Cart2DKernelArgs<T> &p,
-                                                                   int X, int row) {
-  using P = typename PairOf<T>::type;
-  RowV<P> v;
-  const int r = wrap_or_clamp(row, p.ny, p.pery);
-  const int64_t ro = (int64_t)r * p.pitch;
-  if (X >= 0 && X + 1 < p.nx) {
-    const P *b0 = reinterpret_cast<const P *>(p.V + ro + X);
-    v.ez = __ldg(b0);
-    v.hx = __ldg(reinterpret_cast<const P *>(p.V + p.cstride + ro + X));
-    v.hy = __ldg(reinterpret_cast<const P *>(p.V + 2 * p.cstride + ro + X));
-    v.eps = __ldg(reinterpret_cast<const P *>(p.eps + ro + X));
-    if (HAS_MU) v.mu = __ldg(reinterpret_cast<const P *>(p.mu + ro + X));
-  } else {
-    const int c0 = wrap_or_clamp(X, p.nx, p.perx), c1 = wrap_or_clamp(X + 1, p.nx, p.perx);
-    v.ez = vmk(__ldg(p.V + ro + c0), __ldg(p.V + ro + c1));
-    v.hx = vmk(__ldg(p.V + p.cstride + ro + c0), __ldg(p.V + p.cstride + ro + c1));
-    v.hy = vmk(__ldg(p.V + 2 * p.cstride + ro + c0), __ldg(p.V + 2 * p.cstride + ro + c1));
-    v.eps = vmk(__ldg(p.eps + ro + c0), __ldg(p.eps + ro + c1));
-    if (HAS_MU) v.mu = vmk(__ldg(p.mu + ro + c0), __ldg(p.mu + ro + c1));
-  }
-  if (!HAS_MU) v.mu = vbc(T(1));
-  return v;
+// ------------------------------------------------------------------ asynchronous row copies
+__device__ __forceinline__ void cp_async(void *smem, const void *gmem, int bytes) {
+  const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  if (bytes == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem));
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem));
 }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
-// One extra staged column (x-halo of the strip) for shared memory.
-template <typename T, bool HAS_MU>
-__device__ __forceinline__ void load_extra(const Cart2DKernelArgs<T> &p, int col, int row, T out[5]) {
-  const int r = wrap_or_clamp(row, p.ny, p.pery);
-  const int c = wrap_or_clamp(col, p.nx, p.perx);
-  const int64_t o = (int64_t)r * p.pitch + c;
-  out[0] = __ldg(p.V + o);
-  out[1] = __ldg(p.V + p.cstride + o);
-  out[2] = __ldg(p.V + 2 * p.cstride + o);
-  out[3] = __ldg(p.eps + o);
-  out[4] = HAS_MU ? __ldg(p.mu + o) : T(1);
-}
+constexpr int NS = 8;      // row slots in the shared-memory ring
+constexpr int AHEAD = 4;   // rows in flight beyond the ones being used
 
-// Shared memory (per CTA): staged rows sV[3][5][NCOL] (Ez, Hx, Hy, eps, mu; three row slots),
-// gradients sG[2][5][NCOL] (dEz/dx, dHx/dx, dHy/dx, dHx/dy, dEz/dy; two slots), and the
-// second x-face flux of each thread sF[2][3][NT].
+// Shared memory (per CTA): a ring of staged rows V[NS][5][NT+2] (Ez, Hx, Hy, eps, mu of
+// columns x0-2 .. x0+NT-1, filled by cp.async), raw differences G[2][5][NT] (x-differences of
+// Ez, Hx, Hy and y-differences of Hx, Ez of columns x0-1 .. x0+NT-2), and each thread's
+// x-face flux F[2][3][NT].
 template <typename T>
 struct Smem {
-  T V[3][5][NCOL];
-  T G[2][5][NCOL];
+  T V[NS][5][NT + 2];
+  T G[2][5][NT];
   T F[2][3][NT];
 };
 
-template <typename T, typename P, bool HAS_MU>
-__device__ __forceinline__ void stage_row(Smem<T> &s, int slot, int t, const RowV<P> &v) {
-  const int ci = 2 * t + 1;
-  s.V[slot][0][ci] = v.ez.x; s.V[slot][0][ci + 1] = v.ez.y;
-  s.V[slot][1][ci] = v.hx.x; s.V[slot][1][ci + 1] = v.hx.y;
-  s.V[slot][2][ci] = v.hy.x; s.V[slot][2][ci + 1] = v.hy.y;
-  s.V[slot][3][ci] = v.eps.x; s.V[slot][3][ci + 1] = v.eps.y;
-  if (HAS_MU) { s.V[slot][4][ci] = v.mu.x; s.V[slot][4][ci + 1] = v.mu.y; }
+// Issue the copies of row `row` (wrapped or clamped) for the own column and, for threads 0 and
+// NT-1, the extra column, into ring slot row mod NS.
+template <typename T, bool HAS_MU>
+__device__ __forceinline__ void issue_row(Smem<T> &s, const Cart2DKernelArgs<T> &p, int t, int X,
+                                          bool has_extra, int extra_col, int extra_idx, int row) {
+  const int slot = (row + 2 * NS) % NS;
+  const int r = wrap_or_clamp(row, p.ny, p.pery);
+  const int64_t ro = (int64_t)r * p.pitch;
+  {
+    const int c = wrap_or_clamp(X, p.nx, p.perx);
+    const int64_t o = ro + c;
+    cp_async(&s.V[slot][0][t + 1], p.V + o, sizeof(T));
+    cp_async(&s.V[slot][1][t + 1], p.V + p.cstride + o, sizeof(T));
+    cp_async(&s.V[slot][2][t + 1], p.V + 2 * p.cstride + o, sizeof(T));
+    cp_async(&s.V[slot][3][t + 1], p.eps + o, sizeof(T));
+    if (HAS_MU) cp_async(&s.V[slot][4][t + 1], p.mu + o, sizeof(T));
+  }
+  if (has_extra) {
+    const int c = wrap_or_clamp(extra_col, p.nx, p.perx);
+    const int64_t o = ro + c;
+    cp_async(&s.V[slot][0][extra_idx], p.V + o, sizeof(T));
+    cp_async(&s.V[slot][1][extra_idx], p.V + p.cstride + o, sizeof(T));
+    cp_async(&s.V[slot][2][extra_idx], p.V + 2 * p.cstride + o, sizeof(T));
+    cp_async(&s.V[slot][3][extra_idx], p.eps + o, sizeof(T));
+    if (HAS_MU) cp_async(&s.V[slot][4][extra_idx], p.mu + o, sizeof(T));
+  }
+  cp_async_commit();
 }
 
-// Gradient pair of a row: x-neighbours from the staged slot, y-neighbours from registers.
-template <typename T, typename P>
-__device__ __forceinline__ RowG<P> grad_pair(const Smem<T> &s, int slot, int t, const RowV<P> &c,
-                                            const RowV<P> &dn, const RowV<P> &up, T inv2hx,
-                                            T inv2hy) {
-  const int ci = 2 * t + 1;
-  RowG<P> g;
-  const P sx = vbc(inv2hx), sy = vbc(inv2hy);
-  g.ex = vmul(sx, vsub(vmk(c.ez.y, s.V[slot][0][ci + 2]), vmk(s.V[slot][0][ci - 1], c.ez.x)));
-  g.ax = vmul(sx, vsub(vmk(c.hx.y, s.V[slot][1][ci + 2]), vmk(s.V[slot][1][ci - 1], c.hx.x)));
-  g.bx = vmul(sx, vsub(vmk(c.hy.y, s.V[slot][2][ci + 2]), vmk(s.V[slot][2][ci - 1], c.hy.x)));
-  g.ey = vmul(sy, vsub(up.ez, dn.ez));
-  g.ay = vmul(sy, vsub(up.hx, dn.hx));
-  g.by = vmul(sy, vsub(up.hy, dn.hy));
+template <typename T, bool HAS_MU>
+__device__ __forceinline__ RowV<T> own_cell(const Smem<T> &s, int row, int t) {
+  const int slot = (row + 2 * NS) % NS;
+  RowV<T> v;
+  v.ez = s.V[slot][0][t + 1];
+  v.hx = s.V[slot][1][t + 1];
+  v.hy = s.V[slot][2][t + 1];
+  v.eps = s.V[slot][3][t + 1];
+  v.mu = HAS_MU ? s.V[slot][4][t + 1] : T(1);
+  return v;
+}
+
+// Raw central differences of the own column in row `row` (all neighbours staged).
+template <typename T>
+__device__ __forceinline__ RowG<T> grad_row(const Smem<T> &s, int row, int t) {
+  const int sl = (row + 2 * NS) % NS, dn = (row - 1 + 2 * NS) % NS, up = (row + 1 + 2 * NS) % NS;
+  RowG<T> g;
+  g.ex = s.V[sl][0][t + 2] - s.V[sl][0][t];
+  g.ax = s.V[sl][1][t + 2] - s.V[sl][1][t];
+  g.bx = s.V[sl][2][t + 2] - s.V[sl][2][t];
+  g.ey = s.V[up][0][t + 1] - s.V[dn][0][t + 1];
+  g.ay = s.V[up][1][t + 1] - s.V[dn][1][t + 1];
+  g.by = s.V[up][2][t + 1] - s.V[dn][2][t + 1];
   return g;
 }
 
-template <typename T, typename P>
-__device__ __forceinline__ void stage_grad(Smem<T> &s, int slot, int t, const RowG<P> &g) {
-  const int ci = 2 * t + 1;
-  s.G[slot][0][ci] = g.ex.x; s.G[slot][0][ci + 1] = g.ex.y;
-  s.G[slot][1][ci] = g.ax.x; s.G[slot][1][ci + 1] = g.ax.y;
-  s.G[slot][2][ci] = g.bx.x; s.G[slot][2][ci + 1] = g.bx.y;
-  s.G[slot][3][ci] = g.ay.x; s.G[slot][3][ci + 1] = g.ay.y;
-  s.G[slot][4][ci] = g.ey.x; s.G[slot][4][ci + 1] = g.ey.y;
+// x-face side of a cell (normal x: hn = Hx, ht = Hy; tangential derivatives along y),
+// reconstructed by sgn * (h/2) d/dx = sgn * (raw difference)/4.
+template <typename T>
+__device__ __forceinline__ FSide<T> xface_side(const RowV<T> &v, const RowG<T> &g, T sgn4) {
+  FSide<T> s;
+  s.e = v.ez + sgn4 * g.ex; s.hn = v.hx + sgn4 * g.ax; s.ht = v.hy + sgn4 * g.bx;
+  s.den = g.ex; s.dhn = g.ax; s.dht = g.bx; s.dat = g.ay; s.det = g.ey;
+  s.eps = v.eps; s.mu = v.mu;
+  return s;
 }
 
-// Scalar boundary-face sides, built from lane k of a thread's pair.
-template <typename T, typename P>
-__device__ __forceinline__ Side<T> xside(const RowV<P> &v, const RowG<P> &g, int k, T sgn_halfh) {
+// y-face side (normal y: hn = Hy, ht = Hx; tangential derivatives along x).
+template <typename T>
+__device__ __forceinline__ FSide<T> yface_side(const RowV<T> &v, const RowG<T> &g, T sgn4) {
+  FSide<T> s;
+  s.e = v.ez + sgn4 * g.ey; s.hn = v.hy + sgn4 * g.by; s.ht = v.hx + sgn4 * g.ay;
+  s.den = g.ey; s.dhn = g.by; s.dht = g.ay; s.dat = g.bx; s.det = g.ex;
+  s.eps = v.eps; s.mu = v.mu;
+  return s;
+}
+
+// Boundary sides for the scalar path (derivatives scaled to true gradients).
+template <typename T>
+__device__ __forceinline__ Side<T> xside_scalar(const RowV<T> &v, const RowG<T> &g, T sgn4, T sx,
+                                               T sy) {
   Side<T> s;
-  const T ex = lane<T>(g.ex, k), ax = lane<T>(g.ax, k), bx = lane<T>(g.bx, k);
-  s.e = lane<T>(v.ez, k) + sgn_halfh * ex;
-  s.a = lane<T>(v.hx, k) + sgn_halfh * ax;
-  s.b = lane<T>(v.hy, k) + sgn_halfh * bx;
-  s.ex = ex; s.ax = ax; s.bx = bx;
-  s.ay = lane<T>(g.ay, k); s.ey = lane<T>(g.ey, k);
-  s.eps = lane<T>(v.eps, k); s.mu = lane<T>(v.mu, k);
+  s.e = v.ez + sgn4 * g.ex; s.a = v.hx + sgn4 * g.ax; s.b = v.hy + sgn4 * g.bx;
+  s.ex = g.ex * sx; s.ax = g.ax * sx; s.bx = g.bx * sx;
+  s.ay = g.ay * sy; s.ey = g.ey * sy;
+  s.eps = v.eps; s.mu = v.mu;
   return s;
 }
 
 // In the +e_y face frame: e = Ez, a = Hy, b = -Hx; d_x' = d_y, d_y' = -d_x.
-template <typename T, typename P>
-__device__ __forceinline__ Side<T> yside(const RowV<P> &v, const RowG<P> &g, int k, T sgn_halfh) {
+template <typename T>
+__device__ __forceinline__ Side<T> yside_scalar(const RowV<T> &v, const RowG<T> &g, T sgn4, T sx,
+                                               T sy) {
   Side<T> s;
-  const T dEx = lane<T>(g.ex, k), dEy = lane<T>(g.ey, k);
-  const T dHxy = lane<T>(g.ay, k), dHyx = lane<T>(g.bx, k), dHyy = lane<T>(g.by, k);
-  const T ez = lane<T>(v.ez, k) + sgn_halfh * dEy;
-  const T hx = lane<T>(v.hx, k) + sgn_halfh * dHxy;
-  const T hy = lane<T>(v.hy, k) + sgn_halfh * dHyy;
-  s.e = ez; s.a = hy; s.b = -hx;
-  s.ex = dEy; s.ax = dHyy; s.bx = -dHxy;
-  s.ay = -dHyx; s.ey = -dEx;
-  s.eps = lane<T>(v.eps, k); s.mu = lane<T>(v.mu, k);
+  s.e = v.ez + sgn4 * g.ey;
+  s.a = v.hy + sgn4 * g.by;
+  s.b = -(v.hx + sgn4 * g.ay);
+  s.ex = g.ey * sy; s.ax = g.by * sy; s.bx = -g.ay * sy;
+  s.ay = -g.bx * sx; s.ey = -g.ex * sx;
+  s.eps = v.eps; s.mu = v.mu;
   return s;
 }
 
@@ -379,220 +342,144 @@ __device__ __forceinline__ void low_boundary_flux(const Side<T> &s, const Coef<T
   fe = -oe; fa = oa; fb = ob;
 }
 
+// Row loop.  Iteration j (after one barrier) issues the copies of row j+6, completes the
+// update of row j-1, forms the differences of row j+1, the x-face X-1/2 and the y-face j+1/2
+// of row j, and publishes the differences and the x-face for the neighbours.  Rows j-1 .. j+2
+// are read while rows j+3 .. j+6 are in flight (ring of NS = 8 slots).
 template <typename T, bool HAS_MU>
 __global__ void __launch_bounds__(NT) cart2d_step_kernel(const Cart2DKernelArgs<T> p) {
-  using P = typename PairOf<T>::type;
-  __shared__ __align__(16) Smem<T> s;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Smem<T> &s = *reinterpret_cast<Smem<T> *>(smem_raw);
   const int t = threadIdx.x;
   const int x0 = blockIdx.x * W;
   const int y0 = blockIdx.y * ROWS;
   const int y1 = min(y0 + ROWS, p.ny);
-  const int X = x0 - 2 + 2 * t;
-  const int xend = min(x0 + W, p.nx);
-  const bool xlo_nrbc = !p.perx, ylo_nrbc = !p.pery;
-
-  // extra staged columns: ci = 0 (column x0-3) by thread 0, ci = NCOL-1 by thread NT-1
+  const int X = x0 - 1 + t;                         // own column
+  const bool upd = t >= 1 && t <= NT - 2 && X < p.nx;
+  const bool xnr = !p.perx, ynr = !p.pery;
+  const T q4 = T(0.25), mq4 = T(-0.25);
   const bool has_extra = (t == 0) || (t == NT - 1);
-  const int extra_col = (t == 0) ? x0 - 3 : x0 + 2 * NT - 2;
-  const int extra_ci = (t == 0) ? 0 : NCOL - 1;
+  const int extra_col = (t == 0) ? x0 - 2 : x0 + NT - 1;
+  const int extra_idx = (t == 0) ? 0 : NT + 1;
 
-  // ---------------- prologue: rows y0-2 .. y0+2 in registers, rows y0-1 .. y0+1 staged
-  RowV<P> vm2 = load_pair<T, HAS_MU>(p, X, y0 - 2);
-  RowV<P> vm1 = load_pair<T, HAS_MU>(p, X, y0 - 1);
-  RowV<P> v0 = load_pair<T, HAS_MU>(p, X, y0);
-  RowV<P> v1 = load_pair<T, HAS_MU>(p, X, y0 + 1);
-  RowV<P> v2 = load_pair<T, HAS_MU>(p, X, y0 + 2);
-  stage_row<T, P, HAS_MU>(s, (y0 + 2) % 3, t, vm1);
-  stage_row<T, P, HAS_MU>(s, y0 % 3, t, v0);
-  stage_row<T, P, HAS_MU>(s, (y0 + 1) % 3, t, v1);
-  if (has_extra) {
-    T e[5];
-    for (int rr = -1; rr <= 1; ++rr) {
-      load_extra<T, HAS_MU>(p, extra_col, y0 + rr, e);
-      const int sl = (y0 + rr + 3) % 3;
-#pragma unroll
-      for (int c = 0; c < 5; ++c) s.V[sl][c][extra_ci] = e[c];
-    }
-  }
+  // ---------------- prologue: rows y0-2 .. y0+5 in flight, differences of rows y0-1, y0
+#pragma unroll 1
+  for (int r = y0 - 2; r <= y0 + AHEAD + 1; ++r)
+    issue_row<T, HAS_MU>(s, p, t, X, has_extra, extra_col, extra_idx, r);
+  cp_async_wait<AHEAD - 1>();      // rows up to y0+2 landed
   __syncthreads();
-  RowG<P> gm1 = grad_pair<T, P>(s, (y0 + 2) % 3, t, vm1, vm2, v0, p.inv2hx, p.inv2hy);
-  RowG<P> g0 = grad_pair<T, P>(s, y0 % 3, t, v0, vm1, v1, p.inv2hx, p.inv2hy);
-  // y-face below row y0
-  P fbE, fbHx, fbHy;
+  RowG<T> g0 = grad_row<T>(s, y0, t);
+  T fbE, fbHx, fbHy;   // flux along +y through the face below the row being processed
   {
-    if (y0 == 0 && ylo_nrbc) {
-#pragma unroll
-      for (int k = 0; k < 2; ++k) {
-        // outward normal -e_y: in the +e_y frame quantities, local (x', y') = (-y, x)
-        Side<T> sq = yside<T, P>(v0, g0, k, -p.halfhy);
-        Side<T> q;
-        q.e = sq.e; q.a = -sq.a; q.b = -sq.b;
-        q.ex = -sq.ex; q.ax = sq.ax; q.bx = sq.bx;
-        q.ay = sq.ay; q.ey = -sq.ey;
-        q.eps = sq.eps; q.mu = sq.mu;
-        T oe, oa, ob;
-        tm_face_flux<T, true>(q, q, p.Ky, oe, oa, ob);
-        set_lane<T>(fbE, k, -oe); set_lane<T>(fbHx, k, -ob); set_lane<T>(fbHy, k, oa);
-      }
+    const RowV<T> v0 = own_cell<T, HAS_MU>(s, y0, t);
+    if (y0 == 0 && ynr) {
+      // outward normal -e_y: from the +e_y frame quantities, local (x', y') = (-y, x)
+      const Side<T> sq = yside_scalar<T>(v0, g0, mq4, p.inv2hx, p.inv2hy);
+      Side<T> q;
+      q.e = sq.e; q.a = -sq.a; q.b = -sq.b;
+      q.ex = -sq.ex; q.ax = sq.ax; q.bx = sq.bx;
+      q.ay = sq.ay; q.ey = -sq.ey;
+      q.eps = sq.eps; q.mu = sq.mu;
+      T oe, oa, ob;
+      tm_face_flux<T, true>(q, q, p.Ky, oe, oa, ob);
+      fbE = -oe; fbHx = -ob; fbHy = oa;
     } else {
-      PSide<P> l, r;
-      const P hh = vbc(p.halfhy);
-      l.e = vfma(hh, gm1.ey, vm1.ez); l.hn = vfma(hh, gm1.by, vm1.hy); l.ht = vfma(hh, gm1.ay, vm1.hx);
-      l.en = gm1.ey; l.hnn = gm1.by; l.htn = gm1.ay; l.at = gm1.bx; l.et = gm1.ex;
-      l.eps = vm1.eps; l.mu = vm1.mu;
-      r.e = vfma(vbc(-p.halfhy), g0.ey, v0.ez); r.hn = vfma(vbc(-p.halfhy), g0.by, v0.hy);
-      r.ht = vfma(vbc(-p.halfhy), g0.ay, v0.hx);
-      r.en = g0.ey; r.hnn = g0.by; r.htn = g0.ay; r.at = g0.bx; r.et = g0.ex;
-      r.eps = v0.eps; r.mu = v0.mu;
-      face_pair<T, P, HAS_MU>(l, r, p.fy, fbE, fbHy, fbHx);
+      const RowG<T> gm1 = grad_row<T>(s, y0 - 1, t);
+      const RowV<T> vm1 = own_cell<T, HAS_MU>(s, y0 - 1, t);
+      face_flux<T, HAS_MU>(yface_side<T>(vm1, gm1, q4), yface_side<T>(v0, g0, mq4), p.fy, fbE,
+                           fbHy, fbHx);
     }
   }
-  stage_grad<T, P>(s, y0 & 1, t, g0);
-  __syncthreads();
-
-  T ex_next[5];
+  {
+    const int gs = y0 & 1;
+    s.G[gs][0][t] = g0.ex; s.G[gs][1][t] = g0.ax; s.G[gs][2][t] = g0.bx;
+    s.G[gs][3][t] = g0.ay; s.G[gs][4][t] = g0.ey;
+  }
+  // fluxes of the row whose update is pending
+  T pxE = 0, pxHx = 0, pxHy = 0, pbE = 0, pbHx = 0, pbHy = 0, ptE = 0, ptHx = 0, ptHy = 0;
   bool bad = false;
-  for (int j = y0; j < y1; ++j) {
-    // A. prefetch row j+3
-    const RowV<P> pf = load_pair<T, HAS_MU>(p, X, j + 3);
-    if (has_extra) load_extra<T, HAS_MU>(p, extra_col, j + 2, ex_next);
-    // B. gradient pair of row j+1
-    const RowG<P> g1 = grad_pair<T, P>(s, (j + 1) % 3, t, v1, v0, v2, p.inv2hx, p.inv2hy);
-    // C. x-face pair of row j: faces X+1/2 (own cells) and X+3/2 (own X+1, neighbour X+2)
-    P fxE, fxHx, fxHy;
-    {
-      const int sl = j % 3, gs = j & 1, ci = 2 * t + 1;
-      const T rE = s.V[sl][0][ci + 2], rHx = s.V[sl][1][ci + 2], rHy = s.V[sl][2][ci + 2];
-      const T rEps = s.V[sl][3][ci + 2];
-      const T rMu = HAS_MU ? s.V[sl][4][ci + 2] : T(1);
-      const T rgex = s.G[gs][0][ci + 2], rgax = s.G[gs][1][ci + 2], rgbx = s.G[gs][2][ci + 2];
-      const T rgay = s.G[gs][3][ci + 2], rgey = s.G[gs][4][ci + 2];
-      const P hh = vbc(p.halfhx), mh = vbc(-p.halfhx);
-      PSide<P> l, r;
-      l.e = vfma(hh, g0.ex, v0.ez); l.hn = vfma(hh, g0.ax, v0.hx); l.ht = vfma(hh, g0.bx, v0.hy);
-      l.en = g0.ex; l.hnn = g0.ax; l.htn = g0.bx; l.at = g0.ay; l.et = g0.ey;
-      l.eps = v0.eps; l.mu = v0.mu;
-      const P Re = vmk(v0.ez.y, rE), RHx = vmk(v0.hx.y, rHx), RHy = vmk(v0.hy.y, rHy);
-      r.en = vmk(g0.ex.y, rgex); r.hnn = vmk(g0.ax.y, rgax); r.htn = vmk(g0.bx.y, rgbx);
-      r.at = vmk(g0.ay.y, rgay); r.et = vmk(g0.ey.y, rgey);
-      r.e = vfma(mh, r.en, Re); r.hn = vfma(mh, r.hnn, RHx); r.ht = vfma(mh, r.htn, RHy);
-      r.eps = vmk(v0.eps.y, rEps); r.mu = vmk(v0.mu.y, rMu);
-      face_pair<T, P, HAS_MU>(l, r, p.fx, fxE, fxHx, fxHy);
-      if (xlo_nrbc) {
-        // face X+1/2 or X+3/2 on the domain's x boundary
-        if (X == p.nx - 1) {
-          Side<T> q = xside<T, P>(v0, g0, 0, p.halfhx);
-          T e_, a_, b_;
-          tm_face_flux<T, true>(q, q, p.Kx, e_, a_, b_);
-          fxE.x = e_; fxHx.x = a_; fxHy.x = b_;
-        }
-        if (X + 1 == p.nx - 1) {
-          Side<T> q = xside<T, P>(v0, g0, 1, p.halfhx);
-          T e_, a_, b_;
-          tm_face_flux<T, true>(q, q, p.Kx, e_, a_, b_);
-          fxE.y = e_; fxHx.y = a_; fxHy.y = b_;
-        }
-        if (X == -2) {
-          // second face is the low boundary face of column 0: build column 0's side from the
-          // staged neighbour values (column X+2 = 0)
-          Side<T> q;
-          q.ex = rgex; q.ax = rgax; q.bx = rgbx; q.ay = rgay; q.ey = rgey;
-          q.e = rE - p.halfhx * rgex; q.a = rHx - p.halfhx * rgax; q.b = rHy - p.halfhx * rgbx;
-          q.eps = rEps; q.mu = rMu;
-          T e_, a_, b_;
-          low_boundary_flux<T>(q, p.Kx, e_, a_, b_);
-          fxE.y = e_; fxHx.y = a_; fxHy.y = b_;
-        }
-      }
-    }
-    // D. y-face pair between rows j and j+1
-    P ftE, ftHx, ftHy;
-    if (j + 1 == p.ny && ylo_nrbc) {
-#pragma unroll
-      for (int k = 0; k < 2; ++k) {
-        Side<T> q = yside<T, P>(v0, g0, k, p.halfhy);
-        T oe, oa, ob;
-        tm_face_flux<T, true>(q, q, p.Ky, oe, oa, ob);
-        set_lane<T>(ftE, k, oe); set_lane<T>(ftHx, k, -ob); set_lane<T>(ftHy, k, oa);
-      }
-    } else {
-      PSide<P> l, r;
-      const P hh = vbc(p.halfhy), mh = vbc(-p.halfhy);
-      l.e = vfma(hh, g0.ey, v0.ez); l.hn = vfma(hh, g0.by, v0.hy); l.ht = vfma(hh, g0.ay, v0.hx);
-      l.en = g0.ey; l.hnn = g0.by; l.htn = g0.ay; l.at = g0.bx; l.et = g0.ex;
-      l.eps = v0.eps; l.mu = v0.mu;
-      r.e = vfma(mh, g1.ey, v1.ez); r.hn = vfma(mh, g1.by, v1.hy); r.ht = vfma(mh, g1.ay, v1.hx);
-      r.en = g1.ey; r.hnn = g1.by; r.htn = g1.ay; r.at = g1.bx; r.et = g1.ex;
-      r.eps = v1.eps; r.mu = v1.mu;
-      face_pair<T, P, HAS_MU>(l, r, p.fy, ftE, ftHy, ftHx);
-    }
-    // E. stage row j+2, gradient row j+1, and the second x-face for the right neighbour
-    {
-      const int sl = (j + 2) % 3;
-      stage_row<T, P, HAS_MU>(s, sl, t, v2);
-      if (has_extra) {
-#pragma unroll
-        for (int c = 0; c < 5; ++c) s.V[sl][c][extra_ci] = ex_next[c];
-      }
-      stage_grad<T, P>(s, (j + 1) & 1, t, g1);
-      s.F[j & 1][0][t] = fxE.y;
-      s.F[j & 1][1][t] = fxHx.y;
-      s.F[j & 1][2][t] = fxHy.y;
-    }
-    __syncthreads();
-    // G. update the pair of row j: U^{n+1} = U^n - sum of face fluxes (carry dt/h) + dt S
-    {
-      const T lE = t > 0 ? s.F[j & 1][0][t - 1] : T(0);
-      const T lHx = t > 0 ? s.F[j & 1][1][t - 1] : T(0);
-      const T lHy = t > 0 ? s.F[j & 1][2][t - 1] : T(0);
-      // left faces of (X, X+1) = (neighbour's second face, own first face)
-      P dE = vadd(vsub(vmk(lE, fxE.x), fxE), vsub(fbE, ftE));
-      const P dHx = vadd(vsub(vmk(lHx, fxHx.x), fxHx), vsub(fbHx, ftHx));
-      const P dHy = vadd(vsub(vmk(lHy, fxHy.x), fxHy), vsub(fbHy, ftHy));
-      if (p.src && j >= p.sy0 && j < p.sy1) {
-        const int64_t ro = (int64_t)j * p.pitch;
-        if (X >= p.sx0 && X < p.sx1 && X >= 0) dE.x -= p.src_amp * p.src[ro + X];
-        if (X + 1 >= p.sx0 && X + 1 < p.sx1 && X + 1 < p.nx) dE.y -= p.src_amp * p.src[ro + X + 1];
-      }
-      const P ie = vrcp(v0.eps);
-      const P ve = vfma(dE, ie, v0.ez);
-      P vhx, vhy;
+#pragma unroll 1
+  for (int j = y0; j <= y1; ++j) {
+    cp_async_wait<AHEAD - 1>();    // row j+2 landed (this thread's copies)
+    __syncthreads();               // ... and everyone's; G and F of the previous row visible
+    if (j + AHEAD + 2 < y1 + 3) issue_row<T, HAS_MU>(s, p, t, X, has_extra, extra_col, extra_idx,
+                                                    j + AHEAD + 2);
+    else cp_async_commit();        // keep the group count uniform
+    // finish the update of row j-1
+    if (j > y0 && upd) {
+      const int fs = (j - 1) & 1;
+      const RowV<T> v = own_cell<T, HAS_MU>(s, j - 1, t);
+      T dE = (pxE - s.F[fs][0][t + 1]) + (pbE - ptE);
+      const T dHx = (pxHx - s.F[fs][1][t + 1]) + (pbHx - ptHx);
+      const T dHy = (pxHy - s.F[fs][2][t + 1]) + (pbHy - ptHy);
+      const int64_t o = (int64_t)(j - 1) * p.pitch + X;
+      if (p.src && j - 1 >= p.sy0 && j - 1 < p.sy1 && X >= p.sx0 && X < p.sx1)
+        dE -= p.src_amp * p.src[o];
+      const T ve = v.ez + dE * rcp1(v.eps);
+      T vhx, vhy;
       if (HAS_MU) {
-        const P im = vrcp(v0.mu);
-        vhx = vfma(dHx, im, v0.hx);
-        vhy = vfma(dHy, im, v0.hy);
+        const T im = rcp1(v.mu);
+        vhx = v.hx + dHx * im;
+        vhy = v.hy + dHy * im;
       } else {
-        vhx = vadd(v0.hx, dHx);
-        vhy = vadd(v0.hy, dHy);
+        vhx = v.hx + dHx;
+        vhy = v.hy + dHy;
       }
-      const int64_t ro = (int64_t)j * p.pitch;
-      const bool ok0 = X >= x0 && X < xend, ok1 = X + 1 >= x0 && X + 1 < xend;
-      if (ok0 && ok1) {
-        *reinterpret_cast<P *>(p.Vout + ro + X) = ve;
-        *reinterpret_cast<P *>(p.Vout + p.cstride + ro + X) = vhx;
-        *reinterpret_cast<P *>(p.Vout + 2 * p.cstride + ro + X) = vhy;
-        bad |= !(isfinite(ve.x) && isfinite(vhx.x) && isfinite(vhy.x) && isfinite(ve.y) &&
-                 isfinite(vhx.y) && isfinite(vhy.y));
+      p.Vout[o] = ve;
+      p.Vout[p.cstride + o] = vhx;
+      p.Vout[2 * p.cstride + o] = vhy;
+      bad |= !(isfinite(ve) && isfinite(vhx) && isfinite(vhy));
+    }
+    if (j == y1) break;
+    const RowV<T> v0 = own_cell<T, HAS_MU>(s, j, t);
+    const RowG<T> g1 = grad_row<T>(s, j + 1, t);
+    // x-face X - 1/2 of row j (left cell X-1 from shared memory)
+    T fxE = 0, fxHx = 0, fxHy = 0;
+    if (t >= 1) {
+      const int sl = j % NS, gs = j & 1;
+      RowV<T> lv;
+      lv.ez = s.V[sl][0][t]; lv.hx = s.V[sl][1][t]; lv.hy = s.V[sl][2][t];
+      lv.eps = s.V[sl][3][t]; lv.mu = HAS_MU ? s.V[sl][4][t] : T(1);
+      RowG<T> lg;
+      lg.ex = s.G[gs][0][t - 1]; lg.ax = s.G[gs][1][t - 1]; lg.bx = s.G[gs][2][t - 1];
+      lg.ay = s.G[gs][3][t - 1]; lg.ey = s.G[gs][4][t - 1]; lg.by = T(0);
+      if (xnr && X == 0) {
+        low_boundary_flux<T>(xside_scalar<T>(v0, g0, mq4, p.inv2hx, p.inv2hy), p.Kx, fxE, fxHx,
+                             fxHy);
+      } else if (xnr && X == p.nx) {
+        const Side<T> q = xside_scalar<T>(lv, lg, q4, p.inv2hx, p.inv2hy);
+        tm_face_flux<T, true>(q, q, p.Kx, fxE, fxHx, fxHy);
       } else {
-        if (ok0) {
-          p.Vout[ro + X] = ve.x;
-          p.Vout[p.cstride + ro + X] = vhx.x;
-          p.Vout[2 * p.cstride + ro + X] = vhy.x;
-          bad |= !(isfinite(ve.x) && isfinite(vhx.x) && isfinite(vhy.x));
-        }
-        if (ok1) {
-          p.Vout[ro + X + 1] = ve.y;
-          p.Vout[p.cstride + ro + X + 1] = vhx.y;
-          p.Vout[2 * p.cstride + ro + X + 1] = vhy.y;
-          bad |= !(isfinite(ve.y) && isfinite(vhx.y) && isfinite(vhy.y));
-        }
+        face_flux<T, HAS_MU>(xface_side<T>(lv, lg, q4), xface_side<T>(v0, g0, mq4), p.fx, fxE,
+                             fxHx, fxHy);
       }
     }
-    // H. rotate the register window
-    v0 = v1; v1 = v2; v2 = pf;
+    // y-face between rows j and j+1
+    T ftE, ftHx, ftHy;
+    if (j + 1 == p.ny && ynr) {
+      const Side<T> q = yside_scalar<T>(v0, g0, q4, p.inv2hx, p.inv2hy);
+      T oe, oa, ob;
+      tm_face_flux<T, true>(q, q, p.Ky, oe, oa, ob);
+      ftE = oe; ftHx = -ob; ftHy = oa;
+    } else {
+      const RowV<T> v1 = own_cell<T, HAS_MU>(s, j + 1, t);
+      face_flux<T, HAS_MU>(yface_side<T>(v0, g0, q4), yface_side<T>(v1, g1, mq4), p.fy, ftE,
+                           ftHy, ftHx);
+    }
+    // publish differences of row j+1 and this thread's x-face of row j
+    {
+      const int gs = (j + 1) & 1, fs = j & 1;
+      s.G[gs][0][t] = g1.ex; s.G[gs][1][t] = g1.ax; s.G[gs][2][t] = g1.bx;
+      s.G[gs][3][t] = g1.ay; s.G[gs][4][t] = g1.ey;
+      s.F[fs][0][t] = fxE; s.F[fs][1][t] = fxHx; s.F[fs][2][t] = fxHy;
+    }
+    pxE = fxE; pxHx = fxHx; pxHy = fxHy;
+    pbE = fbE; pbHx = fbHx; pbHy = fbHy;
+    ptE = ftE; ptHx = ftHx; ptHy = ftHy;
     g0 = g1;
     fbE = ftE; fbHx = ftHx; fbHy = ftHy;
   }
+  cp_async_wait<0>();
   if (__any_sync(0xffffffffu, bad) && (t & 31) == 0) atomicOr(p.flag, 1);
 }
 
@@ -606,20 +493,22 @@ Coef<T> make_coef(const double C[5], double h, double c) {
   return k;
 }
 
-// Constants of face_pair for a face of normal spacing h whose frame has tangential-H sign sb
-// and tangential-derivative sign st (x-faces: +1, +1; y-faces: -1, -1).
+// Constants of face_flux for a face of normal spacing hn and tangential spacing ht whose frame
+// has tangential-H sign sb and tangential-derivative sign st (x-faces: +1, +1; y-faces: -1, -1).
+// Differences along the normal carry 1/(2 hn), along the tangent 1/(2 ht).
 template <typename T>
-FaceK<T> make_face_k(const double C[5], double h, double c, double sb, double st) {
-  const double K1 = C[0] / h, K2 = C[1] / h, K3 = C[2] / h, K4 = C[3] / h, K5 = C[4] / h;
+FaceK<T> make_face_k(const double C[5], double hn, double ht, double c, double sb, double st) {
+  const double K1 = C[0] / hn, K2 = C[1] / hn, K3 = C[2] / hn, K4 = C[3] / hn, K5 = C[4] / hn;
+  const double sn = 0.5 / hn, stt = 0.5 / ht;
   const double inv2c = 0.5 / c;
   const double q1 = 0.5 * K4, q2 = 0.5 * K4 * c, q3 = 0.5 * K5 * c * c, q4 = 0.5 * K5 * c;
   FaceK<T> k;
   k.a1 = T(-0.5 * K1 * sb); k.a2 = T(-K1 * inv2c); k.a3 = T(sb * inv2c);
-  k.a4 = T(-q1 * sb); k.a5 = T(q4 * st); k.a6 = T(-q4 * sb);
-  k.q2 = T(q2); k.q3 = T(q3); k.q5 = T(0.5 * K2 * c * c - q3); k.b1 = T(q4 * st);
+  k.a4 = T(-q1 * sb); k.a5 = T(q4 * st * stt); k.a6 = T(-q4 * sb * sn);
+  k.q2 = T(q2); k.q3 = T(q3 * sn); k.q5 = T((0.5 * K2 * c * c - q3) * sn); k.b1 = T(q4 * st * stt);
   k.c1 = T(-0.5 * K1 * sb); k.c2 = T(-K1 * inv2c); k.c3 = T(sb * inv2c);
-  k.c4 = T(0.5 * K3 * sb * st); k.c5 = T(-sb * q1); k.c6 = T(-sb * q4);
-  k.g0 = T(K2 * c * c); k.k3 = T(K3);
+  k.c4 = T(0.5 * K3 * sb * st * stt); k.c5 = T(-sb * q1); k.c6 = T(-sb * q4 * sn);
+  k.g0 = T(K2 * c * c * sn); k.k3 = T(K3 * sn);
   return k;
 }
 
@@ -638,17 +527,22 @@ cudaError_t launch_t(const CartGeom &g, const CartStepArgs &a, cudaStream_t st) 
   p.pitch = g.pitch; p.cstride = g.cstride;
   p.perx = g.periodic[0]; p.pery = g.periodic[1];
   p.inv2hx = T(0.5 / g.h[0]); p.inv2hy = T(0.5 / g.h[1]);
-  p.halfhx = T(0.5 * g.h[0]); p.halfhy = T(0.5 * g.h[1]);
-  p.fx = make_face_k<T>(a.C, g.h[0], a.c, 1.0, 1.0);
-  p.fy = make_face_k<T>(a.C, g.h[1], a.c, -1.0, -1.0);
+  p.fx = make_face_k<T>(a.C, g.h[0], g.h[1], a.c, 1.0, 1.0);
+  p.fy = make_face_k<T>(a.C, g.h[1], g.h[0], a.c, -1.0, -1.0);
   p.Kx = make_coef<T>(a.C, g.h[0], a.c);
   p.Ky = make_coef<T>(a.C, g.h[1], a.c);
   p.flag = a.flag;
   dim3 grid((g.nx + W - 1) / W, (g.ny + ROWS - 1) / ROWS);
-  if (a.mu)
-    cart2d_step_kernel<T, true><<<grid, NT, 0, st>>>(p);
-  else
-    cart2d_step_kernel<T, false><<<grid, NT, 0, st>>>(p);
+  const int smem = (int)sizeof(Smem<T>);
+  if (a.mu) {
+    cudaFuncSetAttribute(cart2d_step_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         smem);
+    cart2d_step_kernel<T, true><<<grid, NT, smem, st>>>(p);
+  } else {
+    cudaFuncSetAttribute(cart2d_step_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         smem);
+    cart2d_step_kernel<T, false><<<grid, NT, smem, st>>>(p);
+  }
   return cudaGetLastError();
 }
 
