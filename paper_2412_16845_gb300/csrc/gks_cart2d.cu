@@ -1,12 +1,12 @@
 // Fused 2-D TM GKS step on a Cartesian grid: cell gradients, face reconstruction, the GKS
 // interface flux and the finite-volume update in one pass over the state (Sec. 3.1).
 //
-// Row-marching scheme.  A CTA of NT threads owns a strip of W = NT - 2 columns and a chunk of
-// rows, and walks up the rows with one barrier per row.  Thread t owns column X = x0 - 1 + t
-// and keeps its own column of the state, eps, central differences and the y-face flux in
-// registers; shared memory holds the current rows only for the x-neighbours.  Every gradient
-// and every face is evaluated once: per row a thread forms the differences of row j+1, the
-// x-face X - 1/2 and the y-face j + 1/2, and updates its cell of row j.
+// Warp-strip march.  Each warp owns a strip of 64 columns and a chunk of rows and walks up the
+// rows on its own (no shared memory, no barriers).  Lane l holds columns X = x0-2+2l and X+1
+// of the rows j .. j+2 in registers, with two more rows in flight; x-neighbours come from the
+// adjacent lanes by shuffles.  Every gradient and every face is evaluated once: per row a lane
+// forms the central differences of row j+1, the x-faces X+1/2 and X+3/2 and the y-faces
+// j+1/2 of its two columns, and updates its two cells of row j.
 //
 // Face frames (Sec. 3.1, T'(n)): an x-face uses n = e_x (T' = I); a y-face n = e_y with local
 // axes (x', y') = (y, -x); the low boundary faces use the outward normals -e_x (T' =
@@ -19,9 +19,6 @@
 namespace gks {
 namespace {
 
-constexpr int NT = 128;            // threads per CTA, one column each
-constexpr int W = NT - 2;          // columns updated per CTA
-constexpr int ROWS = 64;           // rows per CTA
 
 // Reciprocals: FP32 uses the fast hardware reciprocal (about 1 ulp), FP64 divides.
 __device__ __forceinline__ float rcp1(float x) { return __fdividef(1.f, x); }
@@ -199,85 +196,62 @@ struct RowG {
   T ex, ey, ax, ay, bx, by;
 };
 
-// ------------------------------------------------------------------ asynchronous row copies
-__device__ __forceinline__ void cp_async(void *smem, const void *gmem, int bytes) {
-  const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
-  if (bytes == 8)
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem));
-  else
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem));
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+// ------------------------------------------------------------------ warp-strip march
+// A warp owns a strip of 64 columns x0-2 .. x0+61 (lane l: columns X = x0-2+2l and X+1) and
+// updates columns x0 .. x0+59 (lanes 1..30).  x-neighbours come from the adjacent lanes by
+// warp shuffles; rows are loaded straight into registers (float2 / double2 per lane, coalesced)
+// two rows ahead of use.  No shared memory and no barriers: warps march independently.
+constexpr int WARPS = 4;             // warps per CTA
+constexpr int WCOLS = 60;            // columns updated per warp
+constexpr unsigned FULL = 0xffffffffu;
 
-constexpr int NS = 8;      // row slots in the shared-memory ring
-constexpr int AHEAD = 4;   // rows in flight beyond the ones being used
+template <typename T> struct Pair2;
+template <> struct Pair2<float> { using type = float2; };
+template <> struct Pair2<double> { using type = double2; };
 
-// Shared memory (per CTA): a ring of staged rows V[NS][5][NT+2] (Ez, Hx, Hy, eps, mu of
-// columns x0-2 .. x0+NT-1, filled by cp.async), raw differences G[2][5][NT] (x-differences of
-// Ez, Hx, Hy and y-differences of Hx, Ez of columns x0-1 .. x0+NT-2), and each thread's
-// x-face flux F[2][3][NT].
+// Two columns of one row: (Ez, Hx, Hy, eps, mu).
 template <typename T>
-struct Smem {
-  T V[NS][5][NT + 2];
-  T G[2][5][NT];
-  T F[2][3][NT];
+struct Row2 {
+  T ez[2], hx[2], hy[2], eps[2], mu[2];
 };
 
-// Issue the copies of row `row` (wrapped or clamped) for the own column and, for threads 0 and
-// NT-1, the extra column, into ring slot row mod NS.
 template <typename T, bool HAS_MU>
-__device__ __forceinline__ void issue_row(Smem<T> &s, const Cart2DKernelArgs<T> &p, int t, int X,
-                                          bool has_extra, int extra_col, int extra_idx, int row) {
-  const int slot = (row + 2 * NS) % NS;
+__device__ __forceinline__ Row2<T> load_row2(const Cart2DKernelArgs<T> &p, int X, int row) {
+  using P = typename Pair2<T>::type;
+  Row2<T> v;
   const int r = wrap_or_clamp(row, p.ny, p.pery);
   const int64_t ro = (int64_t)r * p.pitch;
-  {
-    const int c = wrap_or_clamp(X, p.nx, p.perx);
-    const int64_t o = ro + c;
-    cp_async(&s.V[slot][0][t + 1], p.V + o, sizeof(T));
-    cp_async(&s.V[slot][1][t + 1], p.V + p.cstride + o, sizeof(T));
-    cp_async(&s.V[slot][2][t + 1], p.V + 2 * p.cstride + o, sizeof(T));
-    cp_async(&s.V[slot][3][t + 1], p.eps + o, sizeof(T));
-    if (HAS_MU) cp_async(&s.V[slot][4][t + 1], p.mu + o, sizeof(T));
+  if (X >= 0 && X + 1 < p.nx) {
+    const P a = __ldg(reinterpret_cast<const P *>(p.V + ro + X));
+    const P b = __ldg(reinterpret_cast<const P *>(p.V + p.cstride + ro + X));
+    const P c = __ldg(reinterpret_cast<const P *>(p.V + 2 * p.cstride + ro + X));
+    const P e = __ldg(reinterpret_cast<const P *>(p.eps + ro + X));
+    v.ez[0] = a.x; v.ez[1] = a.y; v.hx[0] = b.x; v.hx[1] = b.y;
+    v.hy[0] = c.x; v.hy[1] = c.y; v.eps[0] = e.x; v.eps[1] = e.y;
+    if (HAS_MU) {
+      const P m = __ldg(reinterpret_cast<const P *>(p.mu + ro + X));
+      v.mu[0] = m.x; v.mu[1] = m.y;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int64_t o = ro + wrap_or_clamp(X + k, p.nx, p.perx);
+      v.ez[k] = __ldg(p.V + o);
+      v.hx[k] = __ldg(p.V + p.cstride + o);
+      v.hy[k] = __ldg(p.V + 2 * p.cstride + o);
+      v.eps[k] = __ldg(p.eps + o);
+      if (HAS_MU) v.mu[k] = __ldg(p.mu + o);
+    }
   }
-  if (has_extra) {
-    const int c = wrap_or_clamp(extra_col, p.nx, p.perx);
-    const int64_t o = ro + c;
-    cp_async(&s.V[slot][0][extra_idx], p.V + o, sizeof(T));
-    cp_async(&s.V[slot][1][extra_idx], p.V + p.cstride + o, sizeof(T));
-    cp_async(&s.V[slot][2][extra_idx], p.V + 2 * p.cstride + o, sizeof(T));
-    cp_async(&s.V[slot][3][extra_idx], p.eps + o, sizeof(T));
-    if (HAS_MU) cp_async(&s.V[slot][4][extra_idx], p.mu + o, sizeof(T));
-  }
-  cp_async_commit();
-}
-
-template <typename T, bool HAS_MU>
-__device__ __forceinline__ RowV<T> own_cell(const Smem<T> &s, int row, int t) {
-  const int slot = (row + 2 * NS) % NS;
-  RowV<T> v;
-  v.ez = s.V[slot][0][t + 1];
-  v.hx = s.V[slot][1][t + 1];
-  v.hy = s.V[slot][2][t + 1];
-  v.eps = s.V[slot][3][t + 1];
-  v.mu = HAS_MU ? s.V[slot][4][t + 1] : T(1);
+  if (!HAS_MU) { v.mu[0] = T(1); v.mu[1] = T(1); }
   return v;
 }
 
-// Raw central differences of the own column in row `row` (all neighbours staged).
 template <typename T>
-__device__ __forceinline__ RowG<T> grad_row(const Smem<T> &s, int row, int t) {
-  const int sl = (row + 2 * NS) % NS, dn = (row - 1 + 2 * NS) % NS, up = (row + 1 + 2 * NS) % NS;
-  RowG<T> g;
-  g.ex = s.V[sl][0][t + 2] - s.V[sl][0][t];
-  g.ax = s.V[sl][1][t + 2] - s.V[sl][1][t];
-  g.bx = s.V[sl][2][t + 2] - s.V[sl][2][t];
-  g.ey = s.V[up][0][t + 1] - s.V[dn][0][t + 1];
-  g.ay = s.V[up][1][t + 1] - s.V[dn][1][t + 1];
-  g.by = s.V[up][2][t + 1] - s.V[dn][2][t + 1];
-  return g;
+__device__ __forceinline__ RowV<T> col_of(const Row2<T> &v, int k) {
+  RowV<T> c;
+  c.ez = v.ez[k]; c.hx = v.hx[k]; c.hy = v.hy[k]; c.eps = v.eps[k]; c.mu = v.mu[k];
+  return c;
 }
 
 // x-face side of a cell (normal x: hn = Hx, ht = Hy; tangential derivatives along y),
@@ -342,145 +316,198 @@ __device__ __forceinline__ void low_boundary_flux(const Side<T> &s, const Coef<T
   fe = -oe; fa = oa; fb = ob;
 }
 
-// Row loop.  Iteration j (after one barrier) issues the copies of row j+6, completes the
-// update of row j-1, forms the differences of row j+1, the x-face X-1/2 and the y-face j+1/2
-// of row j, and publishes the differences and the x-face for the neighbours.  Rows j-1 .. j+2
-// are read while rows j+3 .. j+6 are in flight (ring of NS = 8 slots).
+// Flux along +y of the face below a cell on the low-y boundary (outward normal -e_y).
+template <typename T>
+__device__ __forceinline__ void low_y_boundary_flux(const RowV<T> &v, const RowG<T> &g,
+                                                    const Cart2DKernelArgs<T> &p, T &fE, T &fHx,
+                                                    T &fHy) {
+  const Side<T> sq = yside_scalar<T>(v, g, T(-0.25), p.inv2hx, p.inv2hy);
+  Side<T> q;
+  q.e = sq.e; q.a = -sq.a; q.b = -sq.b;
+  q.ex = -sq.ex; q.ax = sq.ax; q.bx = sq.bx;
+  q.ay = sq.ay; q.ey = -sq.ey;
+  q.eps = sq.eps; q.mu = sq.mu;
+  T oe, oa, ob;
+  tm_face_flux<T, true>(q, q, p.Ky, oe, oa, ob);
+  fE = -oe; fHx = -ob; fHy = oa;
+}
+
+// Raw central differences of the lane's two columns in a row: x-neighbours by shuffle, the rows
+// below and above from registers.  right_* receive column X+2 of this row (reused by the
+// x-face of the row).
+template <typename T>
+__device__ __forceinline__ void diffs2(const Row2<T> &c, const Row2<T> &dn, const Row2<T> &up,
+                                       RowG<T> g[2], T right[3]) {
+  const T lE = __shfl_up_sync(FULL, c.ez[1], 1), rE = __shfl_down_sync(FULL, c.ez[0], 1);
+  const T lA = __shfl_up_sync(FULL, c.hx[1], 1), rA = __shfl_down_sync(FULL, c.hx[0], 1);
+  const T lB = __shfl_up_sync(FULL, c.hy[1], 1), rB = __shfl_down_sync(FULL, c.hy[0], 1);
+  g[0].ex = c.ez[1] - lE; g[1].ex = rE - c.ez[0];
+  g[0].ax = c.hx[1] - lA; g[1].ax = rA - c.hx[0];
+  g[0].bx = c.hy[1] - lB; g[1].bx = rB - c.hy[0];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    g[k].ey = up.ez[k] - dn.ez[k];
+    g[k].ay = up.hx[k] - dn.hx[k];
+    g[k].by = up.hy[k] - dn.hy[k];
+  }
+  right[0] = rE; right[1] = rA; right[2] = rB;
+}
+
 template <typename T, bool HAS_MU>
-__global__ void __launch_bounds__(NT) cart2d_step_kernel(const Cart2DKernelArgs<T> p) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  Smem<T> &s = *reinterpret_cast<Smem<T> *>(smem_raw);
-  const int t = threadIdx.x;
-  const int x0 = blockIdx.x * W;
-  const int y0 = blockIdx.y * ROWS;
-  const int y1 = min(y0 + ROWS, p.ny);
-  const int X = x0 - 1 + t;                         // own column
-  const bool upd = t >= 1 && t <= NT - 2 && X < p.nx;
+__global__ void __launch_bounds__(WARPS * 32) cart2d_step_kernel(const Cart2DKernelArgs<T> p,
+                                                                 int nstrips, int rows) {
+  const int lane = threadIdx.x & 31;
+  const int wid = blockIdx.x * WARPS + (threadIdx.x >> 5);
+  const int strip = wid % nstrips, chunk = wid / nstrips;
+  const int y0 = chunk * rows;
+  if (y0 >= p.ny) return;                             // whole warp leaves together
+  const int y1 = min(y0 + rows, p.ny);
+  const int x0 = strip * WCOLS;
+  const int X = x0 - 2 + 2 * lane;
+  const int xend = min(x0 + WCOLS, p.nx);
   const bool xnr = !p.perx, ynr = !p.pery;
   const T q4 = T(0.25), mq4 = T(-0.25);
-  const bool has_extra = (t == 0) || (t == NT - 1);
-  const int extra_col = (t == 0) ? x0 - 2 : x0 + NT - 1;
-  const int extra_idx = (t == 0) ? 0 : NT + 1;
 
-  // ---------------- prologue: rows y0-2 .. y0+5 in flight, differences of rows y0-1, y0
-#pragma unroll 1
-  for (int r = y0 - 2; r <= y0 + AHEAD + 1; ++r)
-    issue_row<T, HAS_MU>(s, p, t, X, has_extra, extra_col, extra_idx, r);
-  cp_async_wait<AHEAD - 1>();      // rows up to y0+2 landed
-  __syncthreads();
-  RowG<T> g0 = grad_row<T>(s, y0, t);
-  T fbE, fbHx, fbHy;   // flux along +y through the face below the row being processed
-  {
-    const RowV<T> v0 = own_cell<T, HAS_MU>(s, y0, t);
-    if (y0 == 0 && ynr) {
-      // outward normal -e_y: from the +e_y frame quantities, local (x', y') = (-y, x)
-      const Side<T> sq = yside_scalar<T>(v0, g0, mq4, p.inv2hx, p.inv2hy);
-      Side<T> q;
-      q.e = sq.e; q.a = -sq.a; q.b = -sq.b;
-      q.ex = -sq.ex; q.ax = sq.ax; q.bx = sq.bx;
-      q.ay = sq.ay; q.ey = -sq.ey;
-      q.eps = sq.eps; q.mu = sq.mu;
-      T oe, oa, ob;
-      tm_face_flux<T, true>(q, q, p.Ky, oe, oa, ob);
-      fbE = -oe; fbHx = -ob; fbHy = oa;
-    } else {
-      const RowG<T> gm1 = grad_row<T>(s, y0 - 1, t);
-      const RowV<T> vm1 = own_cell<T, HAS_MU>(s, y0 - 1, t);
-      face_flux<T, HAS_MU>(yface_side<T>(vm1, gm1, q4), yface_side<T>(v0, g0, mq4), p.fy, fbE,
-                           fbHy, fbHx);
-    }
+  // ---------------- prologue: rows y0-2 .. y0+3 loaded, differences of rows y0-1, y0
+  Row2<T> vm2 = load_row2<T, HAS_MU>(p, X, y0 - 2);
+  Row2<T> vm1 = load_row2<T, HAS_MU>(p, X, y0 - 1);
+  Row2<T> v0 = load_row2<T, HAS_MU>(p, X, y0);
+  Row2<T> v1 = load_row2<T, HAS_MU>(p, X, y0 + 1);
+  Row2<T> v2 = load_row2<T, HAS_MU>(p, X, y0 + 2);
+  Row2<T> pf = load_row2<T, HAS_MU>(p, X, y0 + 3);
+  RowG<T> g0[2], gm1[2];
+  T r0[3], rm1[3];
+  diffs2<T>(vm1, vm2, v0, gm1, rm1);
+  diffs2<T>(v0, vm1, v1, g0, r0);
+  T fbE[2], fbHx[2], fbHy[2];                         // flux along +y below row j
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    if (y0 == 0 && ynr)
+      low_y_boundary_flux<T>(col_of(v0, k), g0[k], p, fbE[k], fbHx[k], fbHy[k]);
+    else
+      face_flux<T, HAS_MU>(yface_side<T>(col_of(vm1, k), gm1[k], q4),
+                           yface_side<T>(col_of(v0, k), g0[k], mq4), p.fy, fbE[k], fbHy[k],
+                           fbHx[k]);
   }
-  {
-    const int gs = y0 & 1;
-    s.G[gs][0][t] = g0.ex; s.G[gs][1][t] = g0.ax; s.G[gs][2][t] = g0.bx;
-    s.G[gs][3][t] = g0.ay; s.G[gs][4][t] = g0.ey;
-  }
-  // fluxes of the row whose update is pending
-  T pxE = 0, pxHx = 0, pxHy = 0, pbE = 0, pbHx = 0, pbHy = 0, ptE = 0, ptHx = 0, ptHy = 0;
   bool bad = false;
 #pragma unroll 1
-  for (int j = y0; j <= y1; ++j) {
-    cp_async_wait<AHEAD - 1>();    // row j+2 landed (this thread's copies)
-    __syncthreads();               // ... and everyone's; G and F of the previous row visible
-    if (j + AHEAD + 2 < y1 + 3) issue_row<T, HAS_MU>(s, p, t, X, has_extra, extra_col, extra_idx,
-                                                    j + AHEAD + 2);
-    else cp_async_commit();        // keep the group count uniform
-    // finish the update of row j-1
-    if (j > y0 && upd) {
-      const int fs = (j - 1) & 1;
-      const RowV<T> v = own_cell<T, HAS_MU>(s, j - 1, t);
-      T dE = (pxE - s.F[fs][0][t + 1]) + (pbE - ptE);
-      const T dHx = (pxHx - s.F[fs][1][t + 1]) + (pbHx - ptHx);
-      const T dHy = (pxHy - s.F[fs][2][t + 1]) + (pbHy - ptHy);
-      const int64_t o = (int64_t)(j - 1) * p.pitch + X;
-      if (p.src && j - 1 >= p.sy0 && j - 1 < p.sy1 && X >= p.sx0 && X < p.sx1)
-        dE -= p.src_amp * p.src[o];
-      const T ve = v.ez + dE * rcp1(v.eps);
-      T vhx, vhy;
-      if (HAS_MU) {
-        const T im = rcp1(v.mu);
-        vhx = v.hx + dHx * im;
-        vhy = v.hy + dHy * im;
-      } else {
-        vhx = v.hx + dHx;
-        vhy = v.hy + dHy;
-      }
-      p.Vout[o] = ve;
-      p.Vout[p.cstride + o] = vhx;
-      p.Vout[2 * p.cstride + o] = vhy;
-      bad |= !(isfinite(ve) && isfinite(vhx) && isfinite(vhy));
-    }
-    if (j == y1) break;
-    const RowV<T> v0 = own_cell<T, HAS_MU>(s, j, t);
-    const RowG<T> g1 = grad_row<T>(s, j + 1, t);
-    // x-face X - 1/2 of row j (left cell X-1 from shared memory)
-    T fxE = 0, fxHx = 0, fxHy = 0;
-    if (t >= 1) {
-      const int sl = j % NS, gs = j & 1;
-      RowV<T> lv;
-      lv.ez = s.V[sl][0][t]; lv.hx = s.V[sl][1][t]; lv.hy = s.V[sl][2][t];
-      lv.eps = s.V[sl][3][t]; lv.mu = HAS_MU ? s.V[sl][4][t] : T(1);
-      RowG<T> lg;
-      lg.ex = s.G[gs][0][t - 1]; lg.ax = s.G[gs][1][t - 1]; lg.bx = s.G[gs][2][t - 1];
-      lg.ay = s.G[gs][3][t - 1]; lg.ey = s.G[gs][4][t - 1]; lg.by = T(0);
-      if (xnr && X == 0) {
-        low_boundary_flux<T>(xside_scalar<T>(v0, g0, mq4, p.inv2hx, p.inv2hy), p.Kx, fxE, fxHx,
-                             fxHy);
-      } else if (xnr && X == p.nx) {
-        const Side<T> q = xside_scalar<T>(lv, lg, q4, p.inv2hx, p.inv2hy);
-        tm_face_flux<T, true>(q, q, p.Kx, fxE, fxHx, fxHy);
-      } else {
-        face_flux<T, HAS_MU>(xface_side<T>(lv, lg, q4), xface_side<T>(v0, g0, mq4), p.fx, fxE,
-                             fxHx, fxHy);
-      }
-    }
-    // y-face between rows j and j+1
-    T ftE, ftHx, ftHy;
-    if (j + 1 == p.ny && ynr) {
-      const Side<T> q = yside_scalar<T>(v0, g0, q4, p.inv2hx, p.inv2hy);
-      T oe, oa, ob;
-      tm_face_flux<T, true>(q, q, p.Ky, oe, oa, ob);
-      ftE = oe; ftHx = -ob; ftHy = oa;
-    } else {
-      const RowV<T> v1 = own_cell<T, HAS_MU>(s, j + 1, t);
-      face_flux<T, HAS_MU>(yface_side<T>(v0, g0, q4), yface_side<T>(v1, g1, mq4), p.fy, ftE,
-                           ftHy, ftHx);
-    }
-    // publish differences of row j+1 and this thread's x-face of row j
+  for (int j = y0; j < y1; ++j) {
+    const Row2<T> pf2 = load_row2<T, HAS_MU>(p, X, j + 4);   // two rows ahead of use
+    RowG<T> g1[2];
+    T r1[3];
+    diffs2<T>(v1, v0, v2, g1, r1);
+    // x-faces of row j: X+1/2 (own columns) and X+3/2 (own X+1, column X+2 of the next lane)
+    T fxE[2], fxHx[2], fxHy[2];
     {
-      const int gs = (j + 1) & 1, fs = j & 1;
-      s.G[gs][0][t] = g1.ex; s.G[gs][1][t] = g1.ax; s.G[gs][2][t] = g1.bx;
-      s.G[gs][3][t] = g1.ay; s.G[gs][4][t] = g1.ey;
-      s.F[fs][0][t] = fxE; s.F[fs][1][t] = fxHx; s.F[fs][2][t] = fxHy;
+      RowV<T> nb;   // column X+2
+      nb.ez = r0[0]; nb.hx = r0[1]; nb.hy = r0[2];
+      nb.eps = __shfl_down_sync(FULL, v0.eps[0], 1);
+      nb.mu = HAS_MU ? __shfl_down_sync(FULL, v0.mu[0], 1) : T(1);
+      RowG<T> gn;
+      gn.ex = __shfl_down_sync(FULL, g0[0].ex, 1);
+      gn.ax = __shfl_down_sync(FULL, g0[0].ax, 1);
+      gn.bx = __shfl_down_sync(FULL, g0[0].bx, 1);
+      gn.ay = __shfl_down_sync(FULL, g0[0].ay, 1);
+      gn.ey = __shfl_down_sync(FULL, g0[0].ey, 1);
+      gn.by = T(0);
+      const RowV<T> c0 = col_of(v0, 0), c1 = col_of(v0, 1);
+      face_flux<T, HAS_MU>(xface_side<T>(c0, g0[0], q4), xface_side<T>(c1, g0[1], mq4), p.fx,
+                           fxE[0], fxHx[0], fxHy[0]);
+      face_flux<T, HAS_MU>(xface_side<T>(c1, g0[1], q4), xface_side<T>(nb, gn, mq4), p.fx,
+                           fxE[1], fxHx[1], fxHy[1]);
+      if (xnr) {
+        if (X == p.nx - 1) {            // first face on the high-x boundary
+          const Side<T> q = xside_scalar<T>(c0, g0[0], q4, p.inv2hx, p.inv2hy);
+          tm_face_flux<T, true>(q, q, p.Kx, fxE[0], fxHx[0], fxHy[0]);
+        }
+        if (X + 1 == p.nx - 1) {        // second face on the high-x boundary
+          const Side<T> q = xside_scalar<T>(c1, g0[1], q4, p.inv2hx, p.inv2hy);
+          tm_face_flux<T, true>(q, q, p.Kx, fxE[1], fxHx[1], fxHy[1]);
+        }
+        if (X == -2) {                  // second face is the low-x boundary face of column 0
+          low_boundary_flux<T>(xside_scalar<T>(nb, gn, mq4, p.inv2hx, p.inv2hy), p.Kx, fxE[1],
+                               fxHx[1], fxHy[1]);
+        }
+      }
     }
-    pxE = fxE; pxHx = fxHx; pxHy = fxHy;
-    pbE = fbE; pbHx = fbHx; pbHy = fbHy;
-    ptE = ftE; ptHx = ftHx; ptHy = ftHy;
-    g0 = g1;
-    fbE = ftE; fbHx = ftHx; fbHy = ftHy;
+    // y-faces between rows j and j+1
+    T ftE[2], ftHx[2], ftHy[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const RowV<T> c = col_of(v0, k);
+      if (j + 1 == p.ny && ynr) {
+        const Side<T> q = yside_scalar<T>(c, g0[k], q4, p.inv2hx, p.inv2hy);
+        T oe, oa, ob;
+        tm_face_flux<T, true>(q, q, p.Ky, oe, oa, ob);
+        ftE[k] = oe; ftHx[k] = -ob; ftHy[k] = oa;
+      } else {
+        face_flux<T, HAS_MU>(yface_side<T>(c, g0[k], q4), yface_side<T>(col_of(v1, k), g1[k], mq4),
+                             p.fy, ftE[k], ftHy[k], ftHx[k]);
+      }
+    }
+    // update row j: left face of column X is the previous lane's second face
+    {
+      const T lE = __shfl_up_sync(FULL, fxE[1], 1);
+      const T lHx = __shfl_up_sync(FULL, fxHx[1], 1);
+      const T lHy = __shfl_up_sync(FULL, fxHy[1], 1);
+      T dE[2], dHx[2], dHy[2];
+      dE[0] = (lE - fxE[0]) + (fbE[0] - ftE[0]);
+      dHx[0] = (lHx - fxHx[0]) + (fbHx[0] - ftHx[0]);
+      dHy[0] = (lHy - fxHy[0]) + (fbHy[0] - ftHy[0]);
+      dE[1] = (fxE[0] - fxE[1]) + (fbE[1] - ftE[1]);
+      dHx[1] = (fxHx[0] - fxHx[1]) + (fbHx[1] - ftHx[1]);
+      dHy[1] = (fxHy[0] - fxHy[1]) + (fbHy[1] - ftHy[1]);
+      const int64_t ro = (int64_t)j * p.pitch;
+      if (p.src && j >= p.sy0 && j < p.sy1) {
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+          if (X + k >= p.sx0 && X + k < p.sx1) dE[k] -= p.src_amp * p.src[ro + X + k];
+      }
+      T ne[2], nhx[2], nhy[2];
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        ne[k] = v0.ez[k] + dE[k] * rcp1(v0.eps[k]);
+        if (HAS_MU) {
+          const T im = rcp1(v0.mu[k]);
+          nhx[k] = v0.hx[k] + dHx[k] * im;
+          nhy[k] = v0.hy[k] + dHy[k] * im;
+        } else {
+          nhx[k] = v0.hx[k] + dHx[k];
+          nhy[k] = v0.hy[k] + dHy[k];
+        }
+      }
+      const bool ok0 = X >= x0 && X < xend, ok1 = X + 1 >= x0 && X + 1 < xend;
+      using P = typename Pair2<T>::type;
+      if (ok0 && ok1) {
+        P a, b, c;
+        a.x = ne[0]; a.y = ne[1]; b.x = nhx[0]; b.y = nhx[1]; c.x = nhy[0]; c.y = nhy[1];
+        *reinterpret_cast<P *>(p.Vout + ro + X) = a;
+        *reinterpret_cast<P *>(p.Vout + p.cstride + ro + X) = b;
+        *reinterpret_cast<P *>(p.Vout + 2 * p.cstride + ro + X) = c;
+        bad |= !(isfinite(ne[0]) && isfinite(nhx[0]) && isfinite(nhy[0]) && isfinite(ne[1]) &&
+                 isfinite(nhx[1]) && isfinite(nhy[1]));
+      } else {
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          if (k == 0 ? ok0 : ok1) {
+            p.Vout[ro + X + k] = ne[k];
+            p.Vout[p.cstride + ro + X + k] = nhx[k];
+            p.Vout[2 * p.cstride + ro + X + k] = nhy[k];
+            bad |= !(isfinite(ne[k]) && isfinite(nhx[k]) && isfinite(nhy[k]));
+          }
+        }
+      }
+    }
+    // rotate the register window
+    v0 = v1; v1 = v2; v2 = pf; pf = pf2;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      g0[k] = g1[k];
+      fbE[k] = ftE[k]; fbHx[k] = ftHx[k]; fbHy[k] = ftHy[k];
+    }
+    r0[0] = r1[0]; r0[1] = r1[1]; r0[2] = r1[2];
   }
-  cp_async_wait<0>();
-  if (__any_sync(0xffffffffu, bad) && (t & 31) == 0) atomicOr(p.flag, 1);
+  if (__any_sync(FULL, bad) && lane == 0) atomicOr(p.flag, 1);
 }
 
 template <typename T>
@@ -532,17 +559,22 @@ cudaError_t launch_t(const CartGeom &g, const CartStepArgs &a, cudaStream_t st) 
   p.Kx = make_coef<T>(a.C, g.h[0], a.c);
   p.Ky = make_coef<T>(a.C, g.h[1], a.c);
   p.flag = a.flag;
-  dim3 grid((g.nx + W - 1) / W, (g.ny + ROWS - 1) / ROWS);
-  const int smem = (int)sizeof(Smem<T>);
-  if (a.mu) {
-    cudaFuncSetAttribute(cart2d_step_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         smem);
-    cart2d_step_kernel<T, true><<<grid, NT, smem, st>>>(p);
-  } else {
-    cudaFuncSetAttribute(cart2d_step_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         smem);
-    cart2d_step_kernel<T, false><<<grid, NT, smem, st>>>(p);
+  // rows per warp: enough warps to fill the GPU (about 20 resident per SM), at most 256 rows
+  const int nstrips = (g.nx + WCOLS - 1) / WCOLS;
+  int rows = g.ny;
+  const int target = 152 * 24;
+  if ((int64_t)nstrips * 1 < target) {
+    const int chunks = (target + nstrips - 1) / nstrips;
+    rows = (g.ny + chunks - 1) / chunks;
   }
+  rows = rows < 16 ? 16 : (rows > 256 ? 256 : rows);
+  const int nchunks = (g.ny + rows - 1) / rows;
+  const int64_t nwarps = (int64_t)nstrips * nchunks;
+  const int grid = (int)((nwarps + WARPS - 1) / WARPS);
+  if (a.mu)
+    cart2d_step_kernel<T, true><<<grid, WARPS * 32, 0, st>>>(p, nstrips, rows);
+  else
+    cart2d_step_kernel<T, false><<<grid, WARPS * 32, 0, st>>>(p, nstrips, rows);
   return cudaGetLastError();
 }
 
