@@ -194,6 +194,11 @@ def main():
     ap.add_argument("--impl", default="gks", choices=["gks", "reference"])
     ap.add_argument("--n", type=int, default=4096)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--with-3d", dest="with_3d", action="store_true", default=True)
+    ap.add_argument("--no-3d", dest="with_3d", action="store_false")
+    ap.add_argument("--n3", type=int, default=256)
+    ap.add_argument("--steps3", type=int, default=100)
+    ap.add_argument("--no-err3", dest="err3", action="store_false", default=True)
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -301,6 +306,49 @@ def main():
     e2e = world * ncell * args.steps / e2e_s / 1e9
     s32.close()
 
+    # ---------------- 3-D sphere workload (256^3): FP32 and FP64, error after its 500 steps
+    three = None
+    if args.with_3d:
+        w3 = wl.config3_sphere_3d(n=args.n3, steps=500)
+        n3 = w3.ncell
+        t32 = GKSSolver.from_workload(w3, precision="fp32", stream=sptr)
+        t32.step(3)
+        t32.sync()
+        g0 = torch.cuda.Event(enable_timing=True)
+        g1 = torch.cuda.Event(enable_timing=True)
+        k3 = args.steps3
+        g0.record(stream)
+        t32.step(k3)
+        g1.record(stream)
+        torch.cuda.synchronize()
+        ms3 = g0.elapsed_time(g1) / k3
+        t64 = GKSSolver.from_workload(w3, precision="fp64", stream=sptr)
+        t64.step(1)
+        t64.sync()
+        g0.record(stream)
+        t64.step(5)
+        g1.record(stream)
+        torch.cuda.synchronize()
+        ms3_64 = g0.elapsed_time(g1) / 5
+        t32.close()
+        t64.close()
+        err3 = None
+        if args.err3:
+            b32 = GKSSolver.from_workload(w3, precision="fp32", stream=sptr)
+            b64 = GKSSolver.from_workload(w3, precision="fp64", stream=sptr)
+            b32.step(500)
+            b64.step(500)
+            o32, o64 = b32.read_fields(), b64.read_fields()
+            err3 = float(np.sqrt(np.sum((o32 - o64) ** 2) / np.sum(o64 ** 2)))
+            b32.close()
+            b64.close()
+        three = {"workload": f"maxwell3d_sphere_{args.n3}", "steps_timed": k3,
+                 "value_fp32": n3 / (ms3 * 1e-3) / 1e9, "ms_per_step_fp32": ms3,
+                 "value_fp64": n3 / (ms3_64 * 1e-3) / 1e9, "ms_per_step_fp64": ms3_64,
+                 "fp32_speedup": ms3_64 / ms3, "fp32_vs_fp64_rel_l2_after_500": err3,
+                 "hbm_frac_fp32": 52 * n3 / (ms3 * 1e-3) / 1e9 / _peaks()[0],
+                 "algorithmic_bytes_per_cell_step": 52}
+
     if rank == 0:
         hbm, how = _peaks()
         achieved = BYTES_PER_CELL_STEP["fp32"] * ncell / (ms_step * 1e-3) / 1e9
@@ -328,6 +376,7 @@ def main():
                     "d2h_bytes_per_step": 8 * 3 * ncell / args.steps,
                     "definition": "write_fields(pinned FP64) + step(K) + read_fields, wall clock"},
             "gpu_launches": int(launches),
+            "maxwell3d": three,
             "clocks": clocks,
         }
         if not args.no_cpu_baseline:

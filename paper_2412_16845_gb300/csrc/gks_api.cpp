@@ -125,7 +125,6 @@ gks_status gks_create_mesh(const gks_mesh_desc *d, gks_ctx **out) {
     return GKS_E_ARG;
   if (d->kind == GKS_TET) return GKS_E_UNSUPPORTED;
   if (d->kind != GKS_CARTESIAN) return GKS_E_ARG;
-  if (d->dim == 3) return GKS_E_UNSUPPORTED;
   for (int a = 0; a < d->dim; ++a) {
     if (d->n[a] < 1 || d->n[a] > (1 << 24)) return GKS_E_ARG;
     if (!(d->hi[a] > d->lo[a]) || !std::isfinite(d->hi[a] - d->lo[a])) return GKS_E_ARG;
@@ -316,8 +315,9 @@ gks_status gks_step(gks_ctx *ctx, int64_t n_steps) {
     }
     a.V = ctx->V[ctx->cur];
     a.Vout = ctx->V[ctx->cur ^ 1];
-    cudaError_t e = gks::launch_cart2d_step(ctx->g, a, ctx->fp64, ctx->st);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "cart2d step launch");
+    cudaError_t e = ctx->dim == 2 ? gks::launch_cart2d_step(ctx->g, a, ctx->fp64, ctx->st)
+                                  : gks::launch_cart3d_step(ctx->g, a, ctx->fp64, ctx->st);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "Cartesian step launch");
     ctx->launches += 1;
     ctx->cur ^= 1;
     ctx->step += 1;

@@ -202,6 +202,9 @@ struct RowG {
 // warp shuffles; rows are loaded straight into registers (float2 / double2 per lane, coalesced)
 // two rows ahead of use.  No shared memory and no barriers: warps march independently.
 constexpr int WARPS = 4;             // warps per CTA
+#ifndef GKS_CART2D_MINBLOCKS
+#define GKS_CART2D_MINBLOCKS 1           // CTAs per SM the register allocation must allow
+#endif
 constexpr int WCOLS = 60;            // columns updated per warp
 constexpr unsigned FULL = 0xffffffffu;
 
@@ -354,7 +357,7 @@ __device__ __forceinline__ void diffs2(const Row2<T> &c, const Row2<T> &dn, cons
 }
 
 template <typename T, bool HAS_MU>
-__global__ void __launch_bounds__(WARPS * 32) cart2d_step_kernel(const Cart2DKernelArgs<T> p,
+__global__ void __launch_bounds__(WARPS * 32, GKS_CART2D_MINBLOCKS) cart2d_step_kernel(const Cart2DKernelArgs<T> p,
                                                                  int nstrips, int rows) {
   const int lane = threadIdx.x & 31;
   const int wid = blockIdx.x * WARPS + (threadIdx.x >> 5);

@@ -1,0 +1,596 @@
+// Fused 3-D GKS step on a Cartesian grid (fields E, H): cell gradients, face reconstruction,
+// the GKS interface flux and the finite-volume update in one pass (Sec. 3.1).
+//
+// 2.5-D march.  A CTA of BX x BY threads owns the columns x0-1 .. x0+BX-2, y0-1 .. y0+BY-2 of a
+// chunk of z-planes (thread (tx, ty) -> x = x0-1+tx, y = y0-1+ty) and updates the inner
+// (BX-2) x (BY-2) columns; the outer ring of threads supplies the gradients and faces the inner
+// cells need.  Planes are staged in shared memory (x/y neighbours); per plane a thread forms
+// the central differences of plane z+1, the x-face x+1/2, the y-face y+1/2 and the z-face z+1/2
+// of its cell, publishes them, and after one barrier completes the update of plane z.
+//
+// Face frames (Sec. 3.1, T'(n)): interior faces use n = +e_x (frame (x, y, z)), n = +e_y
+// (frame (y, -x, z)) and n = +e_z (frame (z, y, -x)); boundary faces on the low sides use the
+// outward normals -e_x (frame (-x, -y, z)), -e_y (frame (-y, x, z)) and -e_z (frame (-z, y, x)).
+// Every frame is a signed permutation of the axes, so rotations cost nothing.
+#include <cuda_runtime.h>
+
+#include "gks_internal.h"
+
+namespace gks {
+namespace {
+
+constexpr int BX = 32;
+constexpr int BY = 8;
+constexpr int NTH = BX * BY;
+constexpr int PX = BX + 2;            // staged plane: one extra ring around the thread grid
+constexpr int PY = BY + 2;
+constexpr int NV = 8;                 // staged quantities: Ex Ey Ez Hx Hy Hz eps mu
+constexpr int NSLOT = 4;              // staged planes z-1 .. z+2
+
+// Local face quantities of one side (components in the face frame (n, t, w)):
+// V = (En, Et, Ew, Hn, Ht, Hw) reconstructed at the face centre, and its derivatives along
+// n, t and w.
+template <typename T>
+struct Side3 {
+  T v[6], dn[6], dt[6], dw[6];
+  T eps, mu;
+};
+
+template <typename T>
+struct K3 {
+  T k1, k2, k3, k4, k5;  // C_i / h_normal
+  T c, c2, inv2c, halfc, c2half;
+};
+
+enum { EN = 0, ET = 1, EW = 2, HN = 3, HT = 4, HW = 5 };
+
+// F_1 (flux along the face normal) in the face frame: (0, Hw, -Ht, 0, -Ew, Et).
+// Time-integrated GKS flux (Sec. 3.1) in the face frame, times dt/h.  Closed form of the
+// D3Q4 sums (s_k = u_k / c; right-moving pair (1,1,1), (1,-1,-1)):
+//   W0 = (U^l + U^r)/2 + (F_1^l - F_1^r)/(2c),        V0 = W0 / M_s
+//   <u_n g0> = F_1(V0)
+//   <u_n u.grad g0> = c^2 d_n W0 + c (F_3(d_t V0) + F_2(d_w V0))
+//   <u_n g_t> = F_1(V0_t),  V0_t = -(F_1(d_n V0) + F_2(d_t V0) + F_3(d_w V0)) / M_s
+//   free transport = (F_1^l + F_1^r)/2 - (c/2)(U^r - U^l)
+//   free-transport gradient = (c^2/2)(M d_n V^l + M d_n V^r)
+//       + (c/2)[F_1(d_n V^l) + (F_2 + F_3)(d_t V^l + d_w V^l)]
+//       - (c/2)[F_1(d_n V^r) + (F_2 - F_3)(d_t V^r - d_w V^r)]
+// where (F_2 + F_3)(p) = (pHt - pHw, -pHn, pHn, pEw - pEt, pEn, -pEn) and
+// (F_2 - F_3)(q) = (-qHw - qHt, qHn, qHn, qEw + qEt, -qEn, -qEn).
+// GHOST: the r side is a non-reflecting ghost (no distributions; M_s = M_l).
+template <typename T, bool GHOST>
+__device__ __forceinline__ void flux3(const Side3<T> &l, const Side3<T> &r, const K3<T> &K,
+                                      T out[6]) {
+  const T h = T(0.5);
+  // conserved values and normal derivatives of conserved values
+  T Ul[6], Ur[6], Nl[6], Nr[6];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    const T ml = c < 3 ? l.eps : l.mu;
+    Ul[c] = ml * l.v[c];
+    Nl[c] = ml * l.dn[c];
+    if (!GHOST) {
+      const T mr = c < 3 ? r.eps : r.mu;
+      Ur[c] = mr * r.v[c];
+      Nr[c] = mr * r.dn[c];
+    } else {
+      Ur[c] = T(0);
+      Nr[c] = T(0);
+    }
+  }
+  T ie, im;
+  if (GHOST) {
+    ie = T(1) / l.eps;
+    im = T(1) / l.mu;
+  } else {
+    ie = T(2) / (l.eps + r.eps);
+    im = T(2) / (l.mu + r.mu);
+  }
+  // r-side raw values (zero on a ghost face)
+  T rv[6], rdn[6], rdt[6], rdw[6];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    rv[c] = GHOST ? T(0) : r.v[c];
+    rdn[c] = GHOST ? T(0) : r.dn[c];
+    rdt[c] = GHOST ? T(0) : r.dt[c];
+    rdw[c] = GHOST ? T(0) : r.dw[c];
+  }
+  const T rmE = GHOST ? T(0) : r.eps, rmH = GHOST ? T(0) : r.mu;
+  // interface moment W0 (components Et, Ew, Ht, Hw) -> V0
+  const T W_Et = h * (Ul[ET] + Ur[ET]) + (l.v[HW] - rv[HW]) * K.inv2c;
+  const T W_Ew = h * (Ul[EW] + Ur[EW]) + (rv[HT] - l.v[HT]) * K.inv2c;
+  const T W_Ht = h * (Ul[HT] + Ur[HT]) + (rv[EW] - l.v[EW]) * K.inv2c;
+  const T W_Hw = h * (Ul[HW] + Ur[HW]) + (l.v[ET] - rv[ET]) * K.inv2c;
+  // d_n W0 (all six)
+  T Dn[6];
+  Dn[EN] = h * (Nl[EN] + Nr[EN]);
+  Dn[ET] = h * (Nl[ET] + Nr[ET]) + (l.dn[HW] - rdn[HW]) * K.inv2c;
+  Dn[EW] = h * (Nl[EW] + Nr[EW]) + (rdn[HT] - l.dn[HT]) * K.inv2c;
+  Dn[HN] = h * (Nl[HN] + Nr[HN]);
+  Dn[HT] = h * (Nl[HT] + Nr[HT]) + (rdn[EW] - l.dn[EW]) * K.inv2c;
+  Dn[HW] = h * (Nl[HW] + Nr[HW]) + (l.dn[ET] - rdn[ET]) * K.inv2c;
+  // d_t W0 (En, Et, Hn, Ht) and d_w W0 (En, Ew, Hn, Hw)
+  const T Dt_En = h * (l.eps * l.dt[EN] + rmE * rdt[EN]);
+  const T Dt_Et = h * (l.eps * l.dt[ET] + rmE * rdt[ET]) + (l.dt[HW] - rdt[HW]) * K.inv2c;
+  const T Dt_Hn = h * (l.mu * l.dt[HN] + rmH * rdt[HN]);
+  const T Dt_Ht = h * (l.mu * l.dt[HT] + rmH * rdt[HT]) + (rdt[EW] - l.dt[EW]) * K.inv2c;
+  const T Dw_En = h * (l.eps * l.dw[EN] + rmE * rdw[EN]);
+  const T Dw_Ew = h * (l.eps * l.dw[EW] + rmE * rdw[EW]) + (rdw[HT] - l.dw[HT]) * K.inv2c;
+  const T Dw_Hn = h * (l.mu * l.dw[HN] + rmH * rdw[HN]);
+  const T Dw_Hw = h * (l.mu * l.dw[HW] + rmH * rdw[HW]) + (l.dw[ET] - rdw[ET]) * K.inv2c;
+  // derivatives of V0 = W0 / M_s
+  const T aEn = Dt_En * ie, aEt = Dt_Et * ie, aHn = Dt_Hn * im, aHt = Dt_Ht * im;
+  const T bEn = Dw_En * ie, bEw = Dw_Ew * ie, bHn = Dw_Hn * im, bHw = Dw_Hw * im;
+  const T dEt = Dn[ET] * ie, dEw = Dn[EW] * ie, dHt = Dn[HT] * im, dHw = Dn[HW] * im;
+  // term 1: F_1(V0)
+  T t1[6] = {T(0), W_Hw * im, -W_Ht * im, T(0), -W_Ew * ie, W_Et * ie};
+  // term 2: c^2 d_n W0 + c (F_3(a) + F_2(b))
+  T X0[6] = {aHt - bHw, -aHn, bHn, bEw - aEt, aEn, -bEn};
+  // term 3: F_1(V0_t), V0_t = -(F_1(d) + F_2(a) + F_3(b)) / M_s (components Et, Ew, Ht, Hw)
+  const T Vt_Et = -(dHw - bHn) * ie;
+  const T Vt_Ew = -(aHn - dHt) * ie;
+  const T Vt_Ht = -(bEn - dEw) * im;
+  const T Vt_Hw = -(dEt - aEn) * im;
+  T t3[6] = {T(0), Vt_Hw, -Vt_Ht, T(0), -Vt_Ew, Vt_Et};
+  // term 4: (F_1^l + F_1^r)/2 - (c/2)(U^r - U^l)
+  T t4[6];
+  t4[EN] = -K.halfc * (Ur[EN] - Ul[EN]);
+  t4[ET] = h * (l.v[HW] + rv[HW]) - K.halfc * (Ur[ET] - Ul[ET]);
+  t4[EW] = -h * (l.v[HT] + rv[HT]) - K.halfc * (Ur[EW] - Ul[EW]);
+  t4[HN] = -K.halfc * (Ur[HN] - Ul[HN]);
+  t4[HT] = -h * (l.v[EW] + rv[EW]) - K.halfc * (Ur[HT] - Ul[HT]);
+  t4[HW] = h * (l.v[ET] + rv[ET]) - K.halfc * (Ur[HW] - Ul[HW]);
+  // term 5: free-transport gradient
+  T p[6], q[6];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    p[c] = l.dt[c] + l.dw[c];
+    q[c] = rdt[c] - rdw[c];
+  }
+  const T SX_l[6] = {p[HT] - p[HW], -p[HN], p[HN], p[EW] - p[ET], p[EN], -p[EN]};
+  const T SX_r[6] = {-q[HW] - q[HT], q[HN], q[HN], q[EW] + q[ET], -q[EN], -q[EN]};
+  const T F1l[6] = {T(0), l.dn[HW], -l.dn[HT], T(0), -l.dn[EW], l.dn[ET]};
+  const T F1r[6] = {T(0), rdn[HW], -rdn[HT], T(0), -rdn[EW], rdn[ET]};
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    const T t2 = K.c2 * Dn[c] + K.c * X0[c];
+    const T t5 = K.c2half * (Nl[c] + Nr[c]) + K.halfc * ((F1l[c] + SX_l[c]) - (F1r[c] + SX_r[c]));
+    out[c] = K.k1 * t1[c] + K.k2 * t2 + K.k3 * t3[c] + K.k4 * t4[c] - K.k5 * t5;
+  }
+}
+
+// Signed-axis face frame: local axis k is sign S_k times global axis A_k.
+template <int AN, int SN, int AT, int ST, int AW, int SW>
+struct Frame {
+  static constexpr int an = AN, sn = SN, at = AT, st = ST, aw = AW, sw = SW;
+};
+using FrameXp = Frame<0, 1, 1, 1, 2, 1>;
+using FrameYp = Frame<1, 1, 0, -1, 2, 1>;
+using FrameZp = Frame<2, 1, 1, 1, 0, -1>;
+using FrameXm = Frame<0, -1, 1, -1, 2, 1>;
+using FrameYm = Frame<1, -1, 0, 1, 2, 1>;
+using FrameZm = Frame<2, -1, 1, 1, 0, 1>;
+
+// Global data of one cell: V (Ex..Hz), gradients G[axis][comp] (true derivatives), materials.
+template <typename T>
+struct Cell3 {
+  T v[6];
+  T g[3][6];
+  T eps, mu;
+};
+
+// Local side of a cell, reconstructed by `shift` along the face's global normal axis
+// (V + shift * d/d(axis) V; shift = +-h/2).
+template <typename T, typename F>
+__device__ __forceinline__ Side3<T> to_local(const Cell3<T> &c, T shift) {
+  Side3<T> s;
+  const int ax[3] = {F::an, F::at, F::aw};
+  const T sg[3] = {T(F::sn), T(F::st), T(F::sw)};
+#pragma unroll
+  for (int b = 0; b < 2; ++b) {           // E block, H block
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {          // local component n, t, w
+      const int gc = 3 * b + ax[k];
+      const T sgc = sg[k];
+      s.v[3 * b + k] = sgc * (c.v[gc] + shift * c.g[F::an][gc]);
+      s.dn[3 * b + k] = sgc * T(F::sn) * c.g[F::an][gc];
+      s.dt[3 * b + k] = sgc * T(F::st) * c.g[F::at][gc];
+      s.dw[3 * b + k] = sgc * T(F::sw) * c.g[F::aw][gc];
+    }
+  }
+  s.eps = c.eps;
+  s.mu = c.mu;
+  return s;
+}
+
+// Back to global components: Phi_global = T'^T Phi_local.
+template <typename T, typename F>
+__device__ __forceinline__ void to_global(const T loc[6], T glob[6]) {
+  const int ax[3] = {F::an, F::at, F::aw};
+  const T sg[3] = {T(F::sn), T(F::st), T(F::sw)};
+#pragma unroll
+  for (int b = 0; b < 2; ++b)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) glob[3 * b + ax[k]] = sg[k] * loc[3 * b + k];
+}
+
+// Interior face of frame F between cells L (low side) and R (high side), along +axis.
+template <typename T, typename F>
+__device__ __forceinline__ void interior_face(const Cell3<T> &L, const Cell3<T> &R, T halfh,
+                                              const K3<T> &K, T phi[6]) {
+  T loc[6];
+  flux3<T, false>(to_local<T, F>(L, halfh), to_local<T, F>(R, -halfh), K, loc);
+  to_global<T, F>(loc, phi);
+}
+
+// High-side boundary face (outward +axis, l = the cell): flux along +axis.
+template <typename T, typename F>
+__device__ __forceinline__ void high_boundary_face(const Cell3<T> &L, T halfh, const K3<T> &K,
+                                                   T phi[6]) {
+  T loc[6];
+  const Side3<T> s = to_local<T, F>(L, halfh);
+  flux3<T, true>(s, s, K, loc);
+  to_global<T, F>(loc, phi);
+}
+
+// Low-side boundary face (outward -axis, l = the cell): returns the flux along +axis, i.e.
+// minus F.n_out.
+template <typename T, typename F>
+__device__ __forceinline__ void low_boundary_face(const Cell3<T> &R, T halfh, const K3<T> &K,
+                                                  T phi[6]) {
+  T loc[6], g[6];
+  const Side3<T> s = to_local<T, F>(R, -halfh);
+  flux3<T, true>(s, s, K, loc);
+  to_global<T, F>(loc, g);
+#pragma unroll
+  for (int c = 0; c < 6; ++c) phi[c] = -g[c];
+}
+
+template <typename T>
+struct Cart3DArgs {
+  const T *__restrict__ V;
+  T *__restrict__ Vout;
+  const T *__restrict__ eps;
+  const T *__restrict__ mu;
+  const T *__restrict__ src;
+  int sx0, sx1, sy0, sy1, sz0, sz1;
+  T src_amp;
+  int nx, ny, nz;
+  int64_t pitch, plane, cstride;
+  int per[3];
+  T inv2h[3], halfh[3];
+  K3<T> K[3];
+  int zchunk;
+  int *flag;
+};
+
+__device__ __forceinline__ int wrap_clamp(int i, int n, int periodic) {
+  if (periodic) {
+    i %= n;
+    return i < 0 ? i + n : i;
+  }
+  return i < 0 ? 0 : (i >= n ? n - 1 : i);
+}
+
+template <typename T>
+struct Smem3 {
+  T V[NSLOT][NV][PY][PX];       // staged planes with one extra ring
+  T G[2][18][BY][BX];           // gradients (axis-major: x comps, y comps, z comps)
+  T F[2][12][BY][BX];           // x-face (0..5) and y-face (6..11) fluxes at the high side
+};
+
+// Load one staged entry (x, y, z) of all quantities into registers.
+template <typename T, bool HAS_MU>
+__device__ __forceinline__ void load_entry(const Cart3DArgs<T> &p, int x, int y, int z, T out[NV]) {
+  const int xx = wrap_clamp(x, p.nx, p.per[0]);
+  const int yy = wrap_clamp(y, p.ny, p.per[1]);
+  const int zz = wrap_clamp(z, p.nz, p.per[2]);
+  const int64_t o = (int64_t)zz * p.plane + (int64_t)yy * p.pitch + xx;
+#pragma unroll
+  for (int c = 0; c < 6; ++c) out[c] = __ldg(p.V + c * p.cstride + o);
+  out[6] = __ldg(p.eps + o);
+  out[7] = HAS_MU ? __ldg(p.mu + o) : T(1);
+}
+
+template <typename T>
+__device__ __forceinline__ void stage(Smem3<T> &s, int slot, int py, int px, const T v[NV]) {
+#pragma unroll
+  for (int c = 0; c < NV; ++c) s.V[slot][c][py][px] = v[c];
+}
+
+// Gradient of the thread's cell in plane z: x/y neighbours from the staged plane, z neighbours
+// from the staged planes below/above.
+template <typename T>
+__device__ __forceinline__ void gradient(const Smem3<T> &s, int sl, int sdn, int sup, int ty,
+                                         int tx, const Cart3DArgs<T> &p, T g[3][6]) {
+  const int py = ty + 1, px = tx + 1;
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    g[0][c] = (s.V[sl][c][py][px + 1] - s.V[sl][c][py][px - 1]) * p.inv2h[0];
+    g[1][c] = (s.V[sl][c][py + 1][px] - s.V[sl][c][py - 1][px]) * p.inv2h[1];
+    g[2][c] = (s.V[sup][c][py][px] - s.V[sdn][c][py][px]) * p.inv2h[2];
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void cell_from(const Smem3<T> &s, int sl, int py, int px,
+                                          const T g[3][6], Cell3<T> &c) {
+#pragma unroll
+  for (int k = 0; k < 6; ++k) c.v[k] = s.V[sl][k][py][px];
+  c.eps = s.V[sl][6][py][px];
+  c.mu = s.V[sl][7][py][px];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int k = 0; k < 6; ++k) c.g[a][k] = g[a][k];
+}
+
+template <typename T>
+__device__ __forceinline__ void load_grad(const Smem3<T> &s, int gs, int ty, int tx, T g[3][6]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int k = 0; k < 6; ++k) g[a][k] = s.G[gs][6 * a + k][ty][tx];
+}
+
+// FP32: two CTAs per SM (registers capped at 128); FP64 keeps one (its planes fill the SM).
+template <typename T, bool HAS_MU>
+__global__ void __launch_bounds__(NTH, sizeof(T) == 4 ? 2 : 1)
+    cart3d_step_kernel(const Cart3DArgs<T> p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Smem3<T> &s = *reinterpret_cast<Smem3<T> *>(smem_raw);
+  const int tid = threadIdx.x;
+  const int tx = tid % BX, ty = tid / BX;
+  const int x0 = blockIdx.x * (BX - 2), y0 = blockIdx.y * (BY - 2);
+  const int z0 = blockIdx.z * p.zchunk;
+  const int z1 = min(z0 + p.zchunk, p.nz);
+  const int x = x0 - 1 + tx, y = y0 - 1 + ty;
+  const bool inner = tx >= 1 && tx <= BX - 2 && ty >= 1 && ty <= BY - 2 && x < p.nx && y < p.ny;
+  const bool need_xface = ty >= 1 && ty <= BY - 2 && tx <= BX - 2;   // faces x+1/2 of the tile
+  const bool need_yface = tx >= 1 && tx <= BX - 2 && ty <= BY - 2;
+  // ring entries of the staged plane (84 for 32 x 8) are loaded by threads 0 .. 83
+  constexpr int NRING = 2 * PX + 2 * BY;
+  int rpx = 0, rpy = 0;
+  const bool ringer = tid < NRING;
+  if (ringer) {
+    if (tid < PX) { rpy = 0; rpx = tid; }
+    else if (tid < 2 * PX) { rpy = PY - 1; rpx = tid - PX; }
+    else { const int k = tid - 2 * PX; rpy = 1 + (k >> 1); rpx = (k & 1) ? PX - 1 : 0; }
+  }
+  const int rx = x0 - 2 + rpx, ry = y0 - 2 + rpy;
+  const bool xlo = !p.per[0] && x == -1, xhi = !p.per[0] && x == p.nx - 1;
+  const bool ylo = !p.per[1] && y == -1, yhi = !p.per[1] && y == p.ny - 1;
+  const bool znr = !p.per[2];
+
+  T own[NV], ring[NV];
+  // ---------------- prologue: stage planes z0-1, z0, z0+1; gradients of z0-1 and z0
+  T ownm2[NV];
+  load_entry<T, HAS_MU>(p, x, y, z0 - 2, ownm2);
+  for (int dz = -1; dz <= 1; ++dz) {
+    load_entry<T, HAS_MU>(p, x, y, z0 + dz, own);
+    stage<T>(s, (z0 + dz + NSLOT) % NSLOT, ty + 1, tx + 1, own);
+    if (ringer) {
+      load_entry<T, HAS_MU>(p, rx, ry, z0 + dz, ring);
+      stage<T>(s, (z0 + dz + NSLOT) % NSLOT, rpy, rpx, ring);
+    }
+  }
+  T pf[NV], pfr[NV];
+  load_entry<T, HAS_MU>(p, x, y, z0 + 2, pf);
+  if (ringer) load_entry<T, HAS_MU>(p, rx, ry, z0 + 2, pfr);
+  __syncthreads();
+  T fzb[6];     // flux along +z through the face below the plane being processed
+  {
+    const int sm1 = (z0 - 1 + NSLOT) % NSLOT, s0 = z0 % NSLOT, s1 = (z0 + 1) % NSLOT;
+    T gm1[3][6], g0[3][6];
+    // gradient of z0-1: its lower z neighbour is not staged, use the register copy
+    {
+      const int py = ty + 1, px = tx + 1;
+#pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        gm1[0][c] = (s.V[sm1][c][py][px + 1] - s.V[sm1][c][py][px - 1]) * p.inv2h[0];
+        gm1[1][c] = (s.V[sm1][c][py + 1][px] - s.V[sm1][c][py - 1][px]) * p.inv2h[1];
+        gm1[2][c] = (s.V[s0][c][py][px] - ownm2[c]) * p.inv2h[2];
+      }
+    }
+    gradient<T>(s, s0, sm1, s1, ty, tx, p, g0);
+    Cell3<T> cm1, c0;
+    cell_from<T>(s, sm1, ty + 1, tx + 1, gm1, cm1);
+    cell_from<T>(s, s0, ty + 1, tx + 1, g0, c0);
+    if (z0 == 0 && znr)
+      low_boundary_face<T, FrameZm>(c0, p.halfh[2], p.K[2], fzb);
+    else
+      interior_face<T, FrameZp>(cm1, c0, p.halfh[2], p.K[2], fzb);
+    const int gs = z0 & 1;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int k = 0; k < 6; ++k) s.G[gs][6 * a + k][ty][tx] = g0[a][k];
+  }
+  // fluxes of the plane whose update is pending
+  T px_[6], py_[6], pzb[6], pzt[6];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) { px_[c] = py_[c] = pzb[c] = pzt[c] = T(0); }
+  bool bad = false;
+#pragma unroll 1
+  for (int z = z0; z <= z1; ++z) {
+    __syncthreads();
+    // finish the update of plane z-1
+    if (z > z0 && inner) {
+      const int fs = (z - 1) & 1;
+      const int sl = (z - 1 + NSLOT) % NSLOT;
+      const int64_t o = (int64_t)(z - 1) * p.plane + (int64_t)y * p.pitch + x;
+      T d[6];
+#pragma unroll
+      for (int c = 0; c < 6; ++c)
+        d[c] = (s.F[fs][c][ty][tx - 1] - px_[c]) + (s.F[fs][6 + c][ty - 1][tx] - py_[c]) +
+               (pzb[c] - pzt[c]);
+      if (p.src && x >= p.sx0 && x < p.sx1 && y >= p.sy0 && y < p.sy1 && z - 1 >= p.sz0 &&
+          z - 1 < p.sz1)
+        d[2] -= p.src_amp * p.src[o];
+      const T ie = T(1) / s.V[sl][6][ty + 1][tx + 1];
+      const T im = HAS_MU ? T(1) / s.V[sl][7][ty + 1][tx + 1] : T(1);
+      T sum = T(0);
+#pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        const T nv = s.V[sl][c][ty + 1][tx + 1] + d[c] * (c < 3 ? ie : im);
+        p.Vout[c * p.cstride + o] = nv;
+        sum += nv;
+      }
+      bad |= !isfinite(sum);
+    }
+    if (z == z1) break;
+    const int sm = (z - 1 + NSLOT) % NSLOT, s0 = z % NSLOT, s1 = (z + 1) % NSLOT;
+    const int s2 = (z + 2) % NSLOT;
+    // gradient of plane z+1 (its upper neighbour, plane z+2, is still in registers: stage
+    // it first into its slot, which no thread reads before the next barrier except here)
+    T g1[3][6];
+    {
+      const int py = ty + 1, px = tx + 1;
+#pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        g1[0][c] = (s.V[s1][c][py][px + 1] - s.V[s1][c][py][px - 1]) * p.inv2h[0];
+        g1[1][c] = (s.V[s1][c][py + 1][px] - s.V[s1][c][py - 1][px]) * p.inv2h[1];
+        g1[2][c] = (pf[c] - s.V[s0][c][py][px]) * p.inv2h[2];
+      }
+    }
+    // faces of plane z
+    T g0[3][6];
+    load_grad<T>(s, z & 1, ty, tx, g0);
+    Cell3<T> c0;
+    cell_from<T>(s, s0, ty + 1, tx + 1, g0, c0);
+    T fx[6], fy[6], fzt[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) { fx[c] = fy[c] = T(0); }
+    if (need_xface) {
+      if (xhi) {
+        high_boundary_face<T, FrameXp>(c0, p.halfh[0], p.K[0], fx);
+      } else {
+        T gr[3][6];
+        load_grad<T>(s, z & 1, ty, tx + 1, gr);
+        Cell3<T> cr;
+        cell_from<T>(s, s0, ty + 1, tx + 2, gr, cr);
+        if (xlo)
+          low_boundary_face<T, FrameXm>(cr, p.halfh[0], p.K[0], fx);
+        else
+          interior_face<T, FrameXp>(c0, cr, p.halfh[0], p.K[0], fx);
+      }
+    }
+    if (need_yface) {
+      if (yhi) {
+        high_boundary_face<T, FrameYp>(c0, p.halfh[1], p.K[1], fy);
+      } else {
+        T gu[3][6];
+        load_grad<T>(s, z & 1, ty + 1, tx, gu);
+        Cell3<T> cu;
+        cell_from<T>(s, s0, ty + 2, tx + 1, gu, cu);
+        if (ylo)
+          low_boundary_face<T, FrameYm>(cu, p.halfh[1], p.K[1], fy);
+        else
+          interior_face<T, FrameYp>(c0, cu, p.halfh[1], p.K[1], fy);
+      }
+    }
+    if (inner) {
+      if (z + 1 == p.nz && znr) {
+        high_boundary_face<T, FrameZp>(c0, p.halfh[2], p.K[2], fzt);
+      } else {
+        Cell3<T> c1;
+        cell_from<T>(s, s1, ty + 1, tx + 1, g1, c1);
+        interior_face<T, FrameZp>(c0, c1, p.halfh[2], p.K[2], fzt);
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < 6; ++c) fzt[c] = T(0);
+    }
+    // publish gradients of z+1, this thread's x/y faces; stage plane z+2; prefetch plane z+3
+    {
+      const int gs = (z + 1) & 1, fs = z & 1;
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) s.G[gs][6 * a + k][ty][tx] = g1[a][k];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        s.F[fs][c][ty][tx] = fx[c];
+        s.F[fs][6 + c][ty][tx] = fy[c];
+      }
+      stage<T>(s, s2, ty + 1, tx + 1, pf);
+      if (ringer) stage<T>(s, s2, rpy, rpx, pfr);
+      if (z + 3 <= z1 + 1) {
+        load_entry<T, HAS_MU>(p, x, y, z + 3, pf);
+        if (ringer) load_entry<T, HAS_MU>(p, rx, ry, z + 3, pfr);
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      px_[c] = fx[c];
+      py_[c] = fy[c];
+      pzb[c] = fzb[c];
+      pzt[c] = fzt[c];
+      fzb[c] = fzt[c];
+    }
+    (void)sm;
+  }
+  if (__any_sync(0xffffffffu, bad) && (tid & 31) == 0) atomicOr(p.flag, 1);
+}
+
+template <typename T>
+K3<T> make_k3(const double C[5], double h, double c) {
+  K3<T> k;
+  k.k1 = T(C[0] / h); k.k2 = T(C[1] / h); k.k3 = T(C[2] / h);
+  k.k4 = T(C[3] / h); k.k5 = T(C[4] / h);
+  k.c = T(c); k.c2 = T(c * c); k.inv2c = T(0.5 / c); k.halfc = T(0.5 * c);
+  k.c2half = T(0.5 * c * c);
+  return k;
+}
+
+template <typename T>
+cudaError_t launch3_t(const CartGeom &g, const CartStepArgs &a, cudaStream_t st) {
+  Cart3DArgs<T> p;
+  p.V = static_cast<const T *>(a.V);
+  p.Vout = static_cast<T *>(a.Vout);
+  p.eps = static_cast<const T *>(a.eps);
+  p.mu = static_cast<const T *>(a.mu);
+  p.src = static_cast<const T *>(a.src);
+  p.sx0 = a.src_box[0]; p.sx1 = a.src_box[1];
+  p.sy0 = a.src_box[2]; p.sy1 = a.src_box[3];
+  p.sz0 = a.src_box[4]; p.sz1 = a.src_box[5];
+  p.src_amp = T(a.src_amp);
+  p.nx = g.nx; p.ny = g.ny; p.nz = g.nz;
+  p.pitch = g.pitch; p.plane = g.plane; p.cstride = g.cstride;
+  for (int d = 0; d < 3; ++d) {
+    p.per[d] = g.periodic[d];
+    p.inv2h[d] = T(0.5 / g.h[d]);
+    p.halfh[d] = T(0.5 * g.h[d]);
+    p.K[d] = make_k3<T>(a.C, g.h[d], a.c);
+  }
+  p.flag = a.flag;
+  const int gx = (g.nx + BX - 3) / (BX - 2), gy = (g.ny + BY - 3) / (BY - 2);
+  // z chunks: enough CTAs for about two waves of two CTAs per SM
+  int zchunks = (2 * 2 * 152 + gx * gy - 1) / (gx * gy);
+  if (zchunks < 1) zchunks = 1;
+  if (zchunks > g.nz) zchunks = g.nz;
+  p.zchunk = (g.nz + zchunks - 1) / zchunks;
+  if (p.zchunk < 8 && g.nz >= 8) p.zchunk = 8;
+  zchunks = (g.nz + p.zchunk - 1) / p.zchunk;
+  const int smem = (int)sizeof(Smem3<T>);
+  dim3 grid(gx, gy, zchunks);
+  if (a.mu) {
+    cudaFuncSetAttribute(cart3d_step_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         smem);
+    cart3d_step_kernel<T, true><<<grid, NTH, smem, st>>>(p);
+  } else {
+    cudaFuncSetAttribute(cart3d_step_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         smem);
+    cart3d_step_kernel<T, false><<<grid, NTH, smem, st>>>(p);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_cart3d_step(const CartGeom &g, const CartStepArgs &a, bool fp64,
+                               cudaStream_t st) {
+  return fp64 ? launch3_t<double>(g, a, st) : launch3_t<float>(g, a, st);
+}
+
+}  // namespace gks

@@ -45,6 +45,8 @@ struct CartStepArgs {
 // Launchers (return cudaGetLastError() of the launch).
 cudaError_t launch_cart2d_step(const CartGeom &g, const CartStepArgs &a, bool fp64,
                                cudaStream_t st);
+cudaError_t launch_cart3d_step(const CartGeom &g, const CartStepArgs &a, bool fp64,
+                               cudaStream_t st);
 cudaError_t launch_user_to_cart(const CartGeom &g, int ncomp, const double *user, void *dst,
                                 bool fp64, cudaStream_t st);
 cudaError_t launch_cart_to_user(const CartGeom &g, int ncomp, const void *src, double *user,

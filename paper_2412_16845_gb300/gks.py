@@ -220,7 +220,8 @@ class GKSSolver:
     @classmethod
     def from_workload(cls, w, precision="fp32", kappa=0.0, stream=0):
         s = cls(SolverSpec(dim=w.dim, n=w.n, lo=w.lo, hi=w.hi, bc=w.bc, cfl=w.cfl,
-                           precision=precision, kappa=kappa), stream=stream)
+                           precision=precision, kappa=kappa,
+                           c_lattice=getattr(w, "c_lattice", 0.0) or 0.0), stream=stream)
         s.set_materials(w.eps, w.mu)
         s.write_fields(w.fields0)
         if w.jz_mask is not None:

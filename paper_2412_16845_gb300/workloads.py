@@ -121,6 +121,7 @@ class CartWorkload:
     src: tuple = (SRC_A, SRC_F0, SRC_T0, SRC_S)
     probe: np.ndarray | None = None      # int64 cell ids
     design: np.ndarray | None = None     # int64 cell ids
+    c_lattice: float = 1.0               # lattice speed c of the workload (c = 1 in Sec. 4)
     extra: dict = field(default_factory=dict)
 
     @property

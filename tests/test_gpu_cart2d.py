@@ -38,7 +38,7 @@ def _random_workload(nx, ny, bc, seed, with_mu=False, with_src=False, hx=None):
             rng.uniform(-3, 3, max(1, nx * ny // 20))
     return wl.CartWorkload(name="rand", dim=2, n=(nx, ny), lo=(0.0, 0.0), hi=hi, bc=bc,
                            cfl=0.5, steps=0, eps=eps, mu=mu, fields0=f, jz_mask=mask,
-                           src=(1.0, 20.0, 0.02, 0.02))
+                           src=(1.0, 20.0, 0.02, 0.02), c_lattice=0.0)
 
 
 def _gpu_run(w, steps, precision, kappa=0.0, dt=None):
