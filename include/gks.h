@@ -129,6 +129,27 @@ gks_status gks_read_fields(gks_ctx *ctx, double *out);
  * FP64 on the device; synchronises.  (Not in the paper: a diagnostic.) */
 gks_status gks_energy(gks_ctx *ctx, double *out);
 
+/* Energy 1/2 |Omega| sum_i (eps_i |E_i|^2 + mu_i |H_i|^2) of caller-owned device arrays, for
+ * callers that cannot allocate device memory (a framework that reserved the device memory for
+ * its own pool, a hot loop that cannot pay for an allocation, or code without a gks context).
+ * The paper has no counterpart; it is a variant of the reduction behind gks_energy.
+ *  precision    GKS_FP32 or GKS_FP64: element type of fields, eps and mu.
+ *  dim          2 (fields = Ez, Hx, Hy) or 3 (Ex, Ey, Ez, Hx, Hy, Hz).
+ *  n_cells      1 .. 33,554,432 cells; larger sizes return GKS_E_ARG (the fixed scratch holds
+ *               one partial sum per 4096 cells, 8192 partials).
+ *  cell_volume  |Omega| of every cell (> 0).
+ *  fields       device, [ncomp][n_cells], contiguous; eps, mu device [n_cells] (mu NULL: 1).
+ *  out          device pointer to one double, overwritten with the energy.
+ *  cuda_stream  stream the two kernels are enqueued on (asynchronous; no synchronisation).
+ * Allocates nothing: the partial sums live in a fixed device array of 64 KiB that every GPU
+ * loading the library keeps until the process exits.  The first call on a device looks up
+ * that array's device address (with the device current); make that first call before any
+ * stream capture.  All calls share the array, so calls that overlap on the GPU (on different
+ * streams) race; serialise them.  GKS_E_ARG on bad arguments, GKS_E_CUDA on a launch error. */
+gks_status gks_energy_noalloc(int32_t precision, int32_t dim, int64_t n_cells, double cell_volume,
+                              const void *fields, const void *eps, const void *mu, double *out,
+                              void *cuda_stream);
+
 /* Wait for all enqueued work; report asynchronous errors and the non-finite flag. */
 gks_status gks_sync(gks_ctx *ctx);
 

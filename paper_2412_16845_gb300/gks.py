@@ -65,6 +65,9 @@ SIGNATURES = {
     "gks_read_fields": (ctypes.c_int, [_CTX, _D]),
     "gks_energy": (ctypes.c_int, [_CTX, _D]),
     "gks_sync": (ctypes.c_int, [_CTX]),
+    "gks_energy_noalloc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
+                                          ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     "gks_get_info": (ctypes.c_int, [_CTX, _D, _D, _I64, _I64, _D]),
     "gks_get_launch_count": (ctypes.c_int, [_CTX, _I64]),
     "gks_last_error": (ctypes.c_char_p, [_CTX]),
@@ -145,6 +148,17 @@ def gks_energy(ctx):
     v = ctypes.c_double()
     _check(ctx, load_library().gks_energy(ctx, ctypes.byref(v)))
     return v.value
+
+
+def gks_energy_noalloc(precision, dim, n_cells, cell_volume, fields_ptr, eps_ptr, mu_ptr,
+                       out_ptr, stream=0):
+    """Energy of caller-owned device arrays (device pointers as ints) into the device double at
+    out_ptr; no allocation.  Raises GksError on a non-OK status."""
+    st = load_library().gks_energy_noalloc(int(precision), int(dim), int(n_cells),
+                                           float(cell_volume), fields_ptr, eps_ptr, mu_ptr,
+                                           out_ptr, stream or None)
+    if st != GKS_OK:
+        raise GksError(st, "gks_energy_noalloc rejected the call")
 
 
 def gks_sync(ctx):
