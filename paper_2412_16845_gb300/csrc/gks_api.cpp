@@ -99,7 +99,43 @@ gks_status alloc_dev(gks_ctx *ctx, void **p, size_t bytes) {
 gks_status upload_cells(gks_ctx *ctx, const double *host, int ncomp, void *dst) {
   const size_t bytes = sizeof(double) * (size_t)ncomp * (size_t)ctx->ncell;
   GKS_CUDA(cudaMemcpyAsync(ctx->staging, host, bytes, cudaMemcpyHostToDevice, ctx->st));
-  GKS_CUDA(gks::launch_user_to_cart(ctx->g, ncomp, ctx->staging, dst, ctx->fp64, ctx->st));
+  if (ctx->kind == GKS_TET)
+    GKS_CUDA(gks::launch_user_to_tet(ctx->tet, ncomp, ctx->staging, dst, ctx->fp64, ctx->st));
+  else
+    GKS_CUDA(gks::launch_user_to_cart(ctx->g, ncomp, ctx->staging, dst, ctx->fp64, ctx->st));
+  return GKS_OK;
+}
+
+template <typename V>
+gks_status upload_vec(gks_ctx *ctx, const std::vector<V> &h, V **d) {
+  gks_status s = alloc_dev(ctx, reinterpret_cast<void **>(d), sizeof(V) * (h.size() ? h.size() : 1));
+  if (s != GKS_OK) return s;
+  if (!h.empty())
+    GKS_CUDA(cudaMemcpyAsync(*d, h.data(), sizeof(V) * h.size(), cudaMemcpyHostToDevice, ctx->st));
+  return GKS_OK;
+}
+
+// Build the tet geometry on the host and copy it to the device (kind == GKS_TET).
+gks_status setup_tets(gks_ctx *ctx, const gks_mesh_desc *d) {
+  gks::TetHost h;
+  gks_status s = gks::build_tet_geometry(d->vert_xyz, d->n_vert, d->tet_vert, d->n_tet, h, ctx->err);
+  if (s != GKS_OK) return s;
+  gks::TetDev &g = ctx->tet;
+  g.nt = h.nt;
+  g.nf = h.nf;
+  if ((s = upload_vec(ctx, h.perm, &g.perm)) != GKS_OK || (s = upload_vec(ctx, h.vol, &g.vol)) != GKS_OK ||
+      (s = upload_vec(ctx, h.cnb, &g.cnb)) != GKS_OK || (s = upload_vec(ctx, h.cface, &g.cface)) != GKS_OK ||
+      (s = upload_vec(ctx, h.csign, &g.csign)) != GKS_OK || (s = upload_vec(ctx, h.cw, &g.cw)) != GKS_OK ||
+      (s = upload_vec(ctx, h.fL, &g.fL)) != GKS_OK || (s = upload_vec(ctx, h.fR, &g.fR)) != GKS_OK ||
+      (s = upload_vec(ctx, h.fT, &g.fT)) != GKS_OK || (s = upload_vec(ctx, h.farea, &g.farea)) != GKS_OK ||
+      (s = upload_vec(ctx, h.fdL, &g.fdL)) != GKS_OK || (s = upload_vec(ctx, h.fdR, &g.fdR)) != GKS_OK)
+    return s;
+  if ((s = alloc_dev(ctx, &g.Gscratch, ctx->esize * 18 * (size_t)g.nt)) != GKS_OK ||
+      (s = alloc_dev(ctx, &g.Fscratch, ctx->esize * 6 * (size_t)g.nf)) != GKS_OK)
+    return s;
+  ctx->min_h = h.min_h;
+  // host copies are released here; wait so the pageable sources outlive the copies
+  GKS_CUDA(cudaStreamSynchronize(ctx->st));
   return GKS_OK;
 }
 
@@ -123,9 +159,13 @@ gks_status gks_create_mesh(const gks_mesh_desc *d, gks_ctx **out) {
   if (d->precision != GKS_FP32 && d->precision != GKS_FP64) return GKS_E_ARG;
   if (!finite_positive(d->cfl) || !(d->tau_over_dt >= 0.0) || !std::isfinite(d->tau_over_dt))
     return GKS_E_ARG;
-  if (d->kind == GKS_TET) return GKS_E_UNSUPPORTED;
-  if (d->kind != GKS_CARTESIAN) return GKS_E_ARG;
-  for (int a = 0; a < d->dim; ++a) {
+  if (d->kind != GKS_CARTESIAN && d->kind != GKS_TET) return GKS_E_ARG;
+  if (d->kind == GKS_TET) {
+    if (d->dim != 3 || !d->vert_xyz || !d->tet_vert || d->n_vert < 4 || d->n_tet < 1)
+      return GKS_E_ARG;
+    if (d->tet_bc != GKS_BC_NONREFLECTING) return GKS_E_UNSUPPORTED;
+  }
+  for (int a = 0; a < (d->kind == GKS_TET ? 0 : d->dim); ++a) {
     if (d->n[a] < 1 || d->n[a] > (1 << 24)) return GKS_E_ARG;
     if (!(d->hi[a] > d->lo[a]) || !std::isfinite(d->hi[a] - d->lo[a])) return GKS_E_ARG;
     const int b0 = d->bc[2 * a], b1 = d->bc[2 * a + 1];
@@ -152,25 +192,32 @@ gks_status gks_create_mesh(const gks_mesh_desc *d, gks_ctx **out) {
 
   gks::CartGeom &g = ctx->g;
   g.dim = d->dim;
-  g.nx = (int)d->n[0];
-  g.ny = (int)d->n[1];
-  g.nz = d->dim == 3 ? (int)d->n[2] : 1;
-  g.pitch = ((int64_t)g.nx + 31) / 32 * 32;
-  g.plane = g.pitch * g.ny;
-  g.cstride = g.plane * g.nz;
-  ctx->ncell = (int64_t)g.nx * g.ny * g.nz;
-  ctx->min_h = 1e300;
-  for (int a = 0; a < d->dim; ++a) {
-    g.h[a] = (d->hi[a] - d->lo[a]) / (double)d->n[a];
-    g.periodic[a] = d->bc[2 * a] == GKS_BC_PERIODIC;
-    ctx->min_h = std::fmin(ctx->min_h, g.h[a]);
-  }
-  // h_i = 2 dim |Omega| / sum_s |l_s| for a box cell is the harmonic-type mean
-  // dim / sum_a (1/h_a); it equals the edge for squares and cubes.
-  {
-    double s = 0;
-    for (int a = 0; a < d->dim; ++a) s += 1.0 / g.h[a];
-    ctx->min_h = d->dim / s;
+  if (d->kind == GKS_TET) {
+    gks_status s = setup_tets(ctx, d);
+    if (s != GKS_OK) {
+      gks_destroy(ctx);
+      return s;
+    }
+    g.nx = (int)ctx->tet.nt; g.ny = 1; g.nz = 1;
+    g.pitch = ctx->tet.nt; g.plane = g.pitch; g.cstride = g.pitch;
+    ctx->ncell = ctx->tet.nt;
+  } else {
+    g.nx = (int)d->n[0];
+    g.ny = (int)d->n[1];
+    g.nz = d->dim == 3 ? (int)d->n[2] : 1;
+    g.pitch = ((int64_t)g.nx + 31) / 32 * 32;
+    g.plane = g.pitch * g.ny;
+    g.cstride = g.plane * g.nz;
+    ctx->ncell = (int64_t)g.nx * g.ny * g.nz;
+    for (int a = 0; a < d->dim; ++a) {
+      g.h[a] = (d->hi[a] - d->lo[a]) / (double)d->n[a];
+      g.periodic[a] = d->bc[2 * a] == GKS_BC_PERIODIC;
+    }
+    // h_i = 2 dim |Omega| / sum_s |l_s| for a box cell is dim / sum_a (1/h_a); it equals the
+    // edge for squares and cubes.
+    double sum = 0;
+    for (int a = 0; a < d->dim; ++a) sum += 1.0 / g.h[a];
+    ctx->min_h = d->dim / sum;
   }
   ctx->c = ctx->c_user > 0 ? ctx->c_user : 1.0;
 
@@ -259,7 +306,7 @@ gks_status gks_set_source(gks_ctx *ctx, const double *jz_mask, double A, double 
   for (int64_t i = 0; i < ctx->ncell; ++i) {
     const double v = jz_mask[i];
     if (!std::isfinite(v)) return fail(ctx, GKS_E_ARG, "jz_mask must be finite");
-    if (v != 0.0) {
+    if (v != 0.0 && ctx->kind == GKS_CARTESIAN) {
       const int ix = (int)(i % g.nx), iy = (int)((i / g.nx) % g.ny), iz = (int)(i / ((int64_t)g.nx * g.ny));
       box[0] = std::min(box[0], ix); box[1] = std::max(box[1], ix);
       box[2] = std::min(box[2], iy); box[3] = std::max(box[3], iy);
@@ -315,10 +362,17 @@ gks_status gks_step(gks_ctx *ctx, int64_t n_steps) {
     }
     a.V = ctx->V[ctx->cur];
     a.Vout = ctx->V[ctx->cur ^ 1];
-    cudaError_t e = ctx->dim == 2 ? gks::launch_cart2d_step(ctx->g, a, ctx->fp64, ctx->st)
-                                  : gks::launch_cart3d_step(ctx->g, a, ctx->fp64, ctx->st);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "Cartesian step launch");
-    ctx->launches += 1;
+    cudaError_t e;
+    if (ctx->kind == GKS_TET) {
+      e = gks::launch_tet_step(ctx->tet, a.V, a.Vout, a.eps, a.mu, a.src, a.src_amp, a.C, a.c,
+                               a.flag, ctx->fp64, ctx->st);
+      ctx->launches += 3;
+    } else {
+      e = ctx->dim == 2 ? gks::launch_cart2d_step(ctx->g, a, ctx->fp64, ctx->st)
+                        : gks::launch_cart3d_step(ctx->g, a, ctx->fp64, ctx->st);
+      ctx->launches += 1;
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "step launch");
     ctx->cur ^= 1;
     ctx->step += 1;
   }
@@ -328,8 +382,12 @@ gks_status gks_step(gks_ctx *ctx, int64_t n_steps) {
 gks_status gks_read_fields(gks_ctx *ctx, double *out) {
   if (!ctx) return GKS_E_ARG;
   if (!out) return fail(ctx, GKS_E_ARG, "out is NULL");
-  GKS_CUDA(gks::launch_cart_to_user(ctx->g, ctx->ncomp, ctx->V[ctx->cur], ctx->staging,
-                                    ctx->fp64, ctx->st));
+  if (ctx->kind == GKS_TET)
+    GKS_CUDA(gks::launch_tet_to_user(ctx->tet, ctx->ncomp, ctx->V[ctx->cur], ctx->staging,
+                                     ctx->fp64, ctx->st));
+  else
+    GKS_CUDA(gks::launch_cart_to_user(ctx->g, ctx->ncomp, ctx->V[ctx->cur], ctx->staging,
+                                      ctx->fp64, ctx->st));
   GKS_CUDA(cudaMemcpyAsync(out, ctx->staging, sizeof(double) * ctx->ncomp * ctx->ncell,
                            cudaMemcpyDeviceToHost, ctx->st));
   return check_flag(ctx);
@@ -338,9 +396,13 @@ gks_status gks_read_fields(gks_ctx *ctx, double *out) {
 gks_status gks_energy(gks_ctx *ctx, double *out) {
   if (!ctx) return GKS_E_ARG;
   if (!out) return fail(ctx, GKS_E_ARG, "out is NULL");
-  GKS_CUDA(gks::launch_cart_energy(ctx->g, ctx->ncomp, ctx->V[ctx->cur], ctx->eps, ctx->mu,
-                                   ctx->fp64, ctx->red, ctx->red_n, ctx->red + ctx->red_n,
-                                   ctx->st));
+  if (ctx->kind == GKS_TET)
+    GKS_CUDA(gks::launch_tet_energy(ctx->tet, ctx->V[ctx->cur], ctx->eps, ctx->mu, ctx->fp64,
+                                    ctx->red, ctx->red_n, ctx->red + ctx->red_n, ctx->st));
+  else
+    GKS_CUDA(gks::launch_cart_energy(ctx->g, ctx->ncomp, ctx->V[ctx->cur], ctx->eps, ctx->mu,
+                                     ctx->fp64, ctx->red, ctx->red_n, ctx->red + ctx->red_n,
+                                     ctx->st));
   GKS_CUDA(cudaMemcpyAsync(out, ctx->red + ctx->red_n, sizeof(double), cudaMemcpyDeviceToHost,
                            ctx->st));
   return check_flag(ctx);
@@ -377,8 +439,10 @@ const char *gks_last_error(const gks_ctx *ctx) {
 
 void gks_destroy(gks_ctx *ctx) {
   if (!ctx) return;
+  const gks::TetDev &t = ctx->tet;
   void *bufs[] = {ctx->V[0], ctx->V[1], ctx->eps, ctx->mu, ctx->src, ctx->flag, ctx->red,
-                  ctx->staging};
+                  ctx->staging, t.perm, t.vol, t.cnb, t.cface, t.csign, t.cw, t.fL, t.fR, t.fT,
+                  t.farea, t.fdL, t.fdR, t.Gscratch, t.Fscratch};
   for (void *p : bufs)
     if (p) cudaFreeAsync(p, ctx->st);
   cudaStreamSynchronize(ctx->st);

@@ -14,6 +14,7 @@
 // Every frame is a signed permutation of the axes, so rotations cost nothing.
 #include <cuda_runtime.h>
 
+#include "gks_flux3.cuh"
 #include "gks_internal.h"
 
 namespace gks {
@@ -26,138 +27,6 @@ constexpr int PX = BX + 2;            // staged plane: one extra ring around the
 constexpr int PY = BY + 2;
 constexpr int NV = 8;                 // staged quantities: Ex Ey Ez Hx Hy Hz eps mu
 constexpr int NSLOT = 4;              // staged planes z-1 .. z+2
-
-// Local face quantities of one side (components in the face frame (n, t, w)):
-// V = (En, Et, Ew, Hn, Ht, Hw) reconstructed at the face centre, and its derivatives along
-// n, t and w.
-template <typename T>
-struct Side3 {
-  T v[6], dn[6], dt[6], dw[6];
-  T eps, mu;
-};
-
-template <typename T>
-struct K3 {
-  T k1, k2, k3, k4, k5;  // C_i / h_normal
-  T c, c2, inv2c, halfc, c2half;
-};
-
-enum { EN = 0, ET = 1, EW = 2, HN = 3, HT = 4, HW = 5 };
-
-// F_1 (flux along the face normal) in the face frame: (0, Hw, -Ht, 0, -Ew, Et).
-// Time-integrated GKS flux (Sec. 3.1) in the face frame, times dt/h.  Closed form of the
-// D3Q4 sums (s_k = u_k / c; right-moving pair (1,1,1), (1,-1,-1)):
-//   W0 = (U^l + U^r)/2 + (F_1^l - F_1^r)/(2c),        V0 = W0 / M_s
-//   <u_n g0> = F_1(V0)
-//   <u_n u.grad g0> = c^2 d_n W0 + c (F_3(d_t V0) + F_2(d_w V0))
-//   <u_n g_t> = F_1(V0_t),  V0_t = -(F_1(d_n V0) + F_2(d_t V0) + F_3(d_w V0)) / M_s
-//   free transport = (F_1^l + F_1^r)/2 - (c/2)(U^r - U^l)
-//   free-transport gradient = (c^2/2)(M d_n V^l + M d_n V^r)
-//       + (c/2)[F_1(d_n V^l) + (F_2 + F_3)(d_t V^l + d_w V^l)]
-//       - (c/2)[F_1(d_n V^r) + (F_2 - F_3)(d_t V^r - d_w V^r)]
-// where (F_2 + F_3)(p) = (pHt - pHw, -pHn, pHn, pEw - pEt, pEn, -pEn) and
-// (F_2 - F_3)(q) = (-qHw - qHt, qHn, qHn, qEw + qEt, -qEn, -qEn).
-// GHOST: the r side is a non-reflecting ghost (no distributions; M_s = M_l).
-template <typename T, bool GHOST>
-__device__ __forceinline__ void flux3(const Side3<T> &l, const Side3<T> &r, const K3<T> &K,
-                                      T out[6]) {
-  const T h = T(0.5);
-  // conserved values and normal derivatives of conserved values
-  T Ul[6], Ur[6], Nl[6], Nr[6];
-#pragma unroll
-  for (int c = 0; c < 6; ++c) {
-    const T ml = c < 3 ? l.eps : l.mu;
-    Ul[c] = ml * l.v[c];
-    Nl[c] = ml * l.dn[c];
-    if (!GHOST) {
-      const T mr = c < 3 ? r.eps : r.mu;
-      Ur[c] = mr * r.v[c];
-      Nr[c] = mr * r.dn[c];
-    } else {
-      Ur[c] = T(0);
-      Nr[c] = T(0);
-    }
-  }
-  T ie, im;
-  if (GHOST) {
-    ie = T(1) / l.eps;
-    im = T(1) / l.mu;
-  } else {
-    ie = T(2) / (l.eps + r.eps);
-    im = T(2) / (l.mu + r.mu);
-  }
-  // r-side raw values (zero on a ghost face)
-  T rv[6], rdn[6], rdt[6], rdw[6];
-#pragma unroll
-  for (int c = 0; c < 6; ++c) {
-    rv[c] = GHOST ? T(0) : r.v[c];
-    rdn[c] = GHOST ? T(0) : r.dn[c];
-    rdt[c] = GHOST ? T(0) : r.dt[c];
-    rdw[c] = GHOST ? T(0) : r.dw[c];
-  }
-  const T rmE = GHOST ? T(0) : r.eps, rmH = GHOST ? T(0) : r.mu;
-  // interface moment W0 (components Et, Ew, Ht, Hw) -> V0
-  const T W_Et = h * (Ul[ET] + Ur[ET]) + (l.v[HW] - rv[HW]) * K.inv2c;
-  const T W_Ew = h * (Ul[EW] + Ur[EW]) + (rv[HT] - l.v[HT]) * K.inv2c;
-  const T W_Ht = h * (Ul[HT] + Ur[HT]) + (rv[EW] - l.v[EW]) * K.inv2c;
-  const T W_Hw = h * (Ul[HW] + Ur[HW]) + (l.v[ET] - rv[ET]) * K.inv2c;
-  // d_n W0 (all six)
-  T Dn[6];
-  Dn[EN] = h * (Nl[EN] + Nr[EN]);
-  Dn[ET] = h * (Nl[ET] + Nr[ET]) + (l.dn[HW] - rdn[HW]) * K.inv2c;
-  Dn[EW] = h * (Nl[EW] + Nr[EW]) + (rdn[HT] - l.dn[HT]) * K.inv2c;
-  Dn[HN] = h * (Nl[HN] + Nr[HN]);
-  Dn[HT] = h * (Nl[HT] + Nr[HT]) + (rdn[EW] - l.dn[EW]) * K.inv2c;
-  Dn[HW] = h * (Nl[HW] + Nr[HW]) + (l.dn[ET] - rdn[ET]) * K.inv2c;
-  // d_t W0 (En, Et, Hn, Ht) and d_w W0 (En, Ew, Hn, Hw)
-  const T Dt_En = h * (l.eps * l.dt[EN] + rmE * rdt[EN]);
-  const T Dt_Et = h * (l.eps * l.dt[ET] + rmE * rdt[ET]) + (l.dt[HW] - rdt[HW]) * K.inv2c;
-  const T Dt_Hn = h * (l.mu * l.dt[HN] + rmH * rdt[HN]);
-  const T Dt_Ht = h * (l.mu * l.dt[HT] + rmH * rdt[HT]) + (rdt[EW] - l.dt[EW]) * K.inv2c;
-  const T Dw_En = h * (l.eps * l.dw[EN] + rmE * rdw[EN]);
-  const T Dw_Ew = h * (l.eps * l.dw[EW] + rmE * rdw[EW]) + (rdw[HT] - l.dw[HT]) * K.inv2c;
-  const T Dw_Hn = h * (l.mu * l.dw[HN] + rmH * rdw[HN]);
-  const T Dw_Hw = h * (l.mu * l.dw[HW] + rmH * rdw[HW]) + (l.dw[ET] - rdw[ET]) * K.inv2c;
-  // derivatives of V0 = W0 / M_s
-  const T aEn = Dt_En * ie, aEt = Dt_Et * ie, aHn = Dt_Hn * im, aHt = Dt_Ht * im;
-  const T bEn = Dw_En * ie, bEw = Dw_Ew * ie, bHn = Dw_Hn * im, bHw = Dw_Hw * im;
-  const T dEt = Dn[ET] * ie, dEw = Dn[EW] * ie, dHt = Dn[HT] * im, dHw = Dn[HW] * im;
-  // term 1: F_1(V0)
-  T t1[6] = {T(0), W_Hw * im, -W_Ht * im, T(0), -W_Ew * ie, W_Et * ie};
-  // term 2: c^2 d_n W0 + c (F_3(a) + F_2(b))
-  T X0[6] = {aHt - bHw, -aHn, bHn, bEw - aEt, aEn, -bEn};
-  // term 3: F_1(V0_t), V0_t = -(F_1(d) + F_2(a) + F_3(b)) / M_s (components Et, Ew, Ht, Hw)
-  const T Vt_Et = -(dHw - bHn) * ie;
-  const T Vt_Ew = -(aHn - dHt) * ie;
-  const T Vt_Ht = -(bEn - dEw) * im;
-  const T Vt_Hw = -(dEt - aEn) * im;
-  T t3[6] = {T(0), Vt_Hw, -Vt_Ht, T(0), -Vt_Ew, Vt_Et};
-  // term 4: (F_1^l + F_1^r)/2 - (c/2)(U^r - U^l)
-  T t4[6];
-  t4[EN] = -K.halfc * (Ur[EN] - Ul[EN]);
-  t4[ET] = h * (l.v[HW] + rv[HW]) - K.halfc * (Ur[ET] - Ul[ET]);
-  t4[EW] = -h * (l.v[HT] + rv[HT]) - K.halfc * (Ur[EW] - Ul[EW]);
-  t4[HN] = -K.halfc * (Ur[HN] - Ul[HN]);
-  t4[HT] = -h * (l.v[EW] + rv[EW]) - K.halfc * (Ur[HT] - Ul[HT]);
-  t4[HW] = h * (l.v[ET] + rv[ET]) - K.halfc * (Ur[HW] - Ul[HW]);
-  // term 5: free-transport gradient
-  T p[6], q[6];
-#pragma unroll
-  for (int c = 0; c < 6; ++c) {
-    p[c] = l.dt[c] + l.dw[c];
-    q[c] = rdt[c] - rdw[c];
-  }
-  const T SX_l[6] = {p[HT] - p[HW], -p[HN], p[HN], p[EW] - p[ET], p[EN], -p[EN]};
-  const T SX_r[6] = {-q[HW] - q[HT], q[HN], q[HN], q[EW] + q[ET], -q[EN], -q[EN]};
-  const T F1l[6] = {T(0), l.dn[HW], -l.dn[HT], T(0), -l.dn[EW], l.dn[ET]};
-  const T F1r[6] = {T(0), rdn[HW], -rdn[HT], T(0), -rdn[EW], rdn[ET]};
-#pragma unroll
-  for (int c = 0; c < 6; ++c) {
-    const T t2 = K.c2 * Dn[c] + K.c * X0[c];
-    const T t5 = K.c2half * (Nl[c] + Nr[c]) + K.halfc * ((F1l[c] + SX_l[c]) - (F1r[c] + SX_r[c]));
-    out[c] = K.k1 * t1[c] + K.k2 * t2 + K.k3 * t3[c] + K.k4 * t4[c] - K.k5 * t5;
-  }
-}
 
 // Signed-axis face frame: local axis k is sign S_k times global axis A_k.
 template <int AN, int SN, int AT, int ST, int AW, int SW>
@@ -531,16 +400,6 @@ __global__ void __launch_bounds__(NTH, sizeof(T) == 4 ? 2 : 1)
     (void)sm;
   }
   if (__any_sync(0xffffffffu, bad) && (tid & 31) == 0) atomicOr(p.flag, 1);
-}
-
-template <typename T>
-K3<T> make_k3(const double C[5], double h, double c) {
-  K3<T> k;
-  k.k1 = T(C[0] / h); k.k2 = T(C[1] / h); k.k3 = T(C[2] / h);
-  k.k4 = T(C[3] / h); k.k5 = T(C[4] / h);
-  k.c = T(c); k.c2 = T(c * c); k.inv2c = T(0.5 / c); k.halfc = T(0.5 * c);
-  k.c2half = T(0.5 * c * c);
-  return k;
 }
 
 template <typename T>

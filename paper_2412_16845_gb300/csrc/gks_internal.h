@@ -42,6 +42,51 @@ struct CartStepArgs {
   int *flag;            // non-finite flag (device)
 };
 
+// Tetrahedral mesh geometry on the host (FP64; cells in internal Morton order).
+struct TetHost {
+  int64_t nt = 0, nf = 0;
+  std::vector<int64_t> perm;    // internal cell k -> user cell perm[k]
+  std::vector<int64_t> iperm;   // user cell -> internal
+  std::vector<double> vol;      // [nt] internal
+  std::vector<int32_t> cnb;     // [nt][4] neighbour (internal) or -1
+  std::vector<int32_t> cface;   // [nt][4] face id
+  std::vector<double> csign;    // [nt][4] +1 if the cell is the face's L side, -1 if R
+  std::vector<double> cw;       // [nt][4][3] outward n |l| / |Omega|
+  std::vector<int32_t> fL, fR;  // [nf] internal cells (R = -1 on the boundary)
+  std::vector<double> fT;       // [nf][9] face frame rows (n, t, w)
+  std::vector<double> farea;    // [nf]
+  std::vector<double> fdL, fdR; // [nf][3] face centroid minus cell centroid
+  double min_h = 0.0;           // min_i 6 |Omega_i| / sum_s |l_s|
+};
+
+gks_status build_tet_geometry(const double *vert, int64_t nv, const int64_t *tet, int64_t nt,
+                              TetHost &g, std::string &err);
+void face_frame(const double n[3], double T[9]);
+
+// Device copies of the tet geometry plus the per-step scratch (gradients, face fluxes).
+struct TetDev {
+  int64_t nt = 0, nf = 0;
+  int64_t *perm = nullptr;
+  double *vol = nullptr;
+  int32_t *cnb = nullptr, *cface = nullptr;
+  double *csign = nullptr, *cw = nullptr;
+  int32_t *fL = nullptr, *fR = nullptr;
+  double *fT = nullptr, *farea = nullptr, *fdL = nullptr, *fdR = nullptr;
+  void *Gscratch = nullptr;     // [18][nt] gradients
+  void *Fscratch = nullptr;     // [6][nf] face fluxes (times dt and |l|)
+};
+
+cudaError_t launch_tet_step(const TetDev &g, const void *V, void *Vout, const void *eps,
+                            const void *mu, const void *src, double src_amp, const double C[5],
+                            double c, int *flag, bool fp64, cudaStream_t st);
+cudaError_t launch_user_to_tet(const TetDev &g, int ncomp, const double *user, void *dst,
+                               bool fp64, cudaStream_t st);
+cudaError_t launch_tet_to_user(const TetDev &g, int ncomp, const void *src, double *user,
+                               bool fp64, cudaStream_t st);
+cudaError_t launch_tet_energy(const TetDev &g, const void *V, const void *eps, const void *mu,
+                              bool fp64, double *partials, int npart, double *out,
+                              cudaStream_t st);
+
 // Launchers (return cudaGetLastError() of the launch).
 cudaError_t launch_cart2d_step(const CartGeom &g, const CartStepArgs &a, bool fp64,
                                cudaStream_t st);
@@ -67,6 +112,7 @@ struct gks_ctx {
   int64_t ncell = 0;
   size_t esize = 4;
   gks::CartGeom g;
+  gks::TetDev tet;              // kind == GKS_TET
   // device buffers
   void *V[2] = {nullptr, nullptr};
   int cur = 0;

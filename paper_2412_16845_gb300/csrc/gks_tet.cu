@@ -1,0 +1,305 @@
+// GKS step on a tetrahedral mesh (Sec. 3.1): three deterministic passes per step.
+//   1. tet_gradient_kernel: Green-Gauss cell gradients, face value = mean of the two cells
+//      (a non-reflecting face uses the cell itself), written to a gradient scratch [18][nt].
+//   2. tet_face_kernel: every face once -- reconstruct both sides at the face centroid, rotate
+//      fields and gradients into the face frame T'(n), evaluate the GKS flux (shared closed
+//      form, gks_flux3.cuh), rotate back, times the face area -> flux scratch [6][nf].
+//   3. tet_update_kernel: every cell gathers the fluxes of its four faces (no atomics, fixed
+//      order) and applies the FV update with the source.
+// Geometry (frames, areas, offsets, volumes, face weights) stays FP64 on the device; FP32
+// kernels convert it as they read it.
+#include <cuda_runtime.h>
+
+#include "gks_flux3.cuh"
+#include "gks_internal.h"
+
+namespace gks {
+namespace {
+
+constexpr int TB = 256;
+
+int blocks_for(int64_t n) {
+  int64_t b = (n + TB - 1) / TB;
+  return (int)(b < 1 ? 1 : b);
+}
+
+template <typename T>
+__global__ void tet_gradient_kernel(const T *__restrict__ V, const int32_t *__restrict__ cnb,
+                                    const double *__restrict__ cw, int64_t nt,
+                                    T *__restrict__ G) {
+  const int64_t i = blockIdx.x * (int64_t)TB + threadIdx.x;
+  if (i >= nt) return;
+  T vi[6];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) vi[c] = V[c * nt + i];
+  T g[3][6];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int c = 0; c < 6; ++c) g[a][c] = T(0);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int32_t nb = cnb[4 * i + k];
+    T vf[6];
+    if (nb >= 0) {
+#pragma unroll
+      for (int c = 0; c < 6; ++c) vf[c] = T(0.5) * (vi[c] + V[c * nt + nb]);
+    } else {
+#pragma unroll
+      for (int c = 0; c < 6; ++c) vf[c] = vi[c];
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const T w = T(cw[12 * i + 3 * k + a]);
+#pragma unroll
+      for (int c = 0; c < 6; ++c) g[a][c] += vf[c] * w;
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int c = 0; c < 6; ++c) G[(6 * a + c) * nt + i] = g[a][c];
+}
+
+// Side of a face in the frame with rows T (n, t, w): reconstruct V + G.d, then rotate the
+// field index of both blocks and the derivative index.
+template <typename T>
+__device__ __forceinline__ Side3<T> tet_side(const T *__restrict__ V, const T *__restrict__ G,
+                                             const T *__restrict__ eps, const T *__restrict__ mu,
+                                             int64_t nt, int64_t cell, const T Tm[9],
+                                             const T d[3]) {
+  T v[6], g[3][6];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int c = 0; c < 6; ++c) g[a][c] = G[(6 * a + c) * nt + cell];
+#pragma unroll
+  for (int c = 0; c < 6; ++c)
+    v[c] = V[c * nt + cell] + d[0] * g[0][c] + d[1] * g[1][c] + d[2] * g[2][c];
+  Side3<T> s;
+#pragma unroll
+  for (int b = 0; b < 2; ++b)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const T *r = Tm + 3 * k;                         // row k of T'
+      s.v[3 * b + k] = r[0] * v[3 * b] + r[1] * v[3 * b + 1] + r[2] * v[3 * b + 2];
+      // component k of the derivative along global axis a
+      T ga[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+        ga[a] = r[0] * g[a][3 * b] + r[1] * g[a][3 * b + 1] + r[2] * g[a][3 * b + 2];
+      s.dn[3 * b + k] = Tm[0] * ga[0] + Tm[1] * ga[1] + Tm[2] * ga[2];
+      s.dt[3 * b + k] = Tm[3] * ga[0] + Tm[4] * ga[1] + Tm[5] * ga[2];
+      s.dw[3 * b + k] = Tm[6] * ga[0] + Tm[7] * ga[1] + Tm[8] * ga[2];
+    }
+  s.eps = eps[cell];
+  s.mu = mu ? mu[cell] : T(1);
+  return s;
+}
+
+template <typename T>
+__global__ void tet_face_kernel(const T *__restrict__ V, const T *__restrict__ G,
+                                const T *__restrict__ eps, const T *__restrict__ mu,
+                                const int32_t *__restrict__ fL, const int32_t *__restrict__ fR,
+                                const double *__restrict__ fT, const double *__restrict__ farea,
+                                const double *__restrict__ fdL, const double *__restrict__ fdR,
+                                int64_t nt, int64_t nf, const K3<T> K, T *__restrict__ F) {
+  const int64_t f = blockIdx.x * (int64_t)TB + threadIdx.x;
+  if (f >= nf) return;
+  T Tm[9], dl[3], dr[3];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) Tm[k] = T(fT[9 * f + k]);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    dl[a] = T(fdL[3 * f + a]);
+    dr[a] = T(fdR[3 * f + a]);
+  }
+  const int32_t L = fL[f], R = fR[f];
+  const Side3<T> l = tet_side<T>(V, G, eps, mu, nt, L, Tm, dl);
+  T loc[6];
+  if (R >= 0) {
+    const Side3<T> r = tet_side<T>(V, G, eps, mu, nt, R, Tm, dr);
+    flux3<T, false>(l, r, K, loc);
+  } else {
+    flux3<T, true>(l, l, K, loc);
+  }
+  const T area = T(farea[f]);
+  // back to global components: Phi = T'^T Phi_local, times |l_s|
+#pragma unroll
+  for (int b = 0; b < 2; ++b)
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      F[(3 * b + a) * nf + f] =
+          area * (Tm[a] * loc[3 * b] + Tm[3 + a] * loc[3 * b + 1] + Tm[6 + a] * loc[3 * b + 2]);
+}
+
+template <typename T>
+__global__ void tet_update_kernel(const T *__restrict__ V, T *__restrict__ Vout,
+                                  const T *__restrict__ eps, const T *__restrict__ mu,
+                                  const T *__restrict__ src, T src_amp,
+                                  const int32_t *__restrict__ cface,
+                                  const double *__restrict__ csign, const double *__restrict__ vol,
+                                  const T *__restrict__ F, int64_t nt, int64_t nf,
+                                  int *__restrict__ flag) {
+  const int64_t i = blockIdx.x * (int64_t)TB + threadIdx.x;
+  bool bad = false;
+  if (i < nt) {
+    T d[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int32_t f = cface[4 * i + k];
+      const T sg = T(csign[4 * i + k]);
+#pragma unroll
+      for (int c = 0; c < 6; ++c) d[c] -= sg * F[c * nf + f];
+    }
+    const T iv = T(1.0 / vol[i]);
+    if (src) d[2] -= src_amp * src[i] * T(vol[i]);
+    const T ie = T(1) / eps[i];
+    const T im = mu ? T(1) / mu[i] : T(1);
+    T sum = T(0);
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      const T nv = V[c * nt + i] + d[c] * iv * (c < 3 ? ie : im);
+      Vout[c * nt + i] = nv;
+      sum += nv;
+    }
+    bad = !isfinite(sum);
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1);
+}
+
+template <typename T>
+__global__ void user_to_tet_kernel(const double *__restrict__ user, T *__restrict__ dst,
+                                   const int64_t *__restrict__ perm, int64_t nt, int ncomp) {
+  const int64_t total = nt * ncomp;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = i / nt, k = i - c * nt;
+    dst[i] = T(user[c * nt + perm[k]]);
+  }
+}
+
+template <typename T>
+__global__ void tet_to_user_kernel(const T *__restrict__ src, double *__restrict__ user,
+                                   const int64_t *__restrict__ perm, int64_t nt, int ncomp) {
+  const int64_t total = nt * ncomp;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = i / nt, k = i - c * nt;
+    user[c * nt + perm[k]] = double(src[i]);
+  }
+}
+
+template <typename T>
+__global__ void tet_energy_partial_kernel(const T *__restrict__ V, const T *__restrict__ eps,
+                                          const T *__restrict__ mu,
+                                          const double *__restrict__ vol, int64_t nt,
+                                          double *__restrict__ partials) {
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nt;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double se = 0.0, sh = 0.0;
+    for (int c = 0; c < 3; ++c) {
+      const double e = double(V[c * nt + i]), h = double(V[(3 + c) * nt + i]);
+      se += e * e;
+      sh += h * h;
+    }
+    acc += vol[i] * (double(eps[i]) * se + (mu ? double(mu[i]) : 1.0) * sh);
+  }
+  __shared__ double red[256];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partials[blockIdx.x] = red[0];
+}
+
+__global__ void tet_sum_partials_kernel(const double *__restrict__ partials, int n,
+                                        double *__restrict__ out) {
+  __shared__ double red[256];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) acc += partials[i];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = 0.5 * red[0];
+}
+
+template <typename T>
+cudaError_t step_t(const TetDev &g, const void *Vin, void *Vout, const void *eps, const void *mu,
+                   const void *src, double src_amp, const double C[5], double c, int *flag,
+                   cudaStream_t st) {
+  const T *V = static_cast<const T *>(Vin);
+  T *G = static_cast<T *>(g.Gscratch);
+  T *F = static_cast<T *>(g.Fscratch);
+  tet_gradient_kernel<T><<<blocks_for(g.nt), TB, 0, st>>>(V, g.cnb, g.cw, g.nt, G);
+  const K3<T> K = make_k3<T>(C, 1.0, c);     // fluxes carry dt (C_i), areas applied per face
+  tet_face_kernel<T><<<blocks_for(g.nf), TB, 0, st>>>(
+      V, G, static_cast<const T *>(eps), static_cast<const T *>(mu), g.fL, g.fR, g.fT, g.farea,
+      g.fdL, g.fdR, g.nt, g.nf, K, F);
+  tet_update_kernel<T><<<blocks_for(g.nt), TB, 0, st>>>(
+      V, static_cast<T *>(Vout), static_cast<const T *>(eps), static_cast<const T *>(mu),
+      static_cast<const T *>(src), T(src_amp), g.cface, g.csign, g.vol, F, g.nt, g.nf, flag);
+  return cudaGetLastError();
+}
+
+int grid_capped(int64_t n) {
+  int64_t b = (n + 255) / 256;
+  if (b > 152 * 16) b = 152 * 16;
+  return (int)(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+cudaError_t launch_tet_step(const TetDev &g, const void *V, void *Vout, const void *eps,
+                            const void *mu, const void *src, double src_amp, const double C[5],
+                            double c, int *flag, bool fp64, cudaStream_t st) {
+  return fp64 ? step_t<double>(g, V, Vout, eps, mu, src, src_amp, C, c, flag, st)
+              : step_t<float>(g, V, Vout, eps, mu, src, src_amp, C, c, flag, st);
+}
+
+cudaError_t launch_user_to_tet(const TetDev &g, int ncomp, const double *user, void *dst,
+                               bool fp64, cudaStream_t st) {
+  if (fp64)
+    user_to_tet_kernel<double><<<grid_capped(g.nt * ncomp), 256, 0, st>>>(
+        user, static_cast<double *>(dst), g.perm, g.nt, ncomp);
+  else
+    user_to_tet_kernel<float><<<grid_capped(g.nt * ncomp), 256, 0, st>>>(
+        user, static_cast<float *>(dst), g.perm, g.nt, ncomp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tet_to_user(const TetDev &g, int ncomp, const void *src, double *user,
+                               bool fp64, cudaStream_t st) {
+  if (fp64)
+    tet_to_user_kernel<double><<<grid_capped(g.nt * ncomp), 256, 0, st>>>(
+        static_cast<const double *>(src), user, g.perm, g.nt, ncomp);
+  else
+    tet_to_user_kernel<float><<<grid_capped(g.nt * ncomp), 256, 0, st>>>(
+        static_cast<const float *>(src), user, g.perm, g.nt, ncomp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tet_energy(const TetDev &g, const void *V, const void *eps, const void *mu,
+                              bool fp64, double *partials, int npart, double *out,
+                              cudaStream_t st) {
+  int blocks = grid_capped(g.nt);
+  if (blocks > npart) blocks = npart;
+  if (fp64)
+    tet_energy_partial_kernel<double><<<blocks, 256, 0, st>>>(
+        static_cast<const double *>(V), static_cast<const double *>(eps),
+        static_cast<const double *>(mu), g.vol, g.nt, partials);
+  else
+    tet_energy_partial_kernel<float><<<blocks, 256, 0, st>>>(
+        static_cast<const float *>(V), static_cast<const float *>(eps),
+        static_cast<const float *>(mu), g.vol, g.nt, partials);
+  tet_sum_partials_kernel<<<1, 256, 0, st>>>(partials, blocks, out);
+  return cudaGetLastError();
+}
+
+}  // namespace gks

@@ -232,6 +232,39 @@ class GKSSolver:
         self.ctx = gks_create_mesh(d)
 
     @classmethod
+    def from_tets(cls, vert, tet, cfl, precision="fp32", kappa=0.0, c_lattice=1.0, stream=0):
+        """A context on a conforming tetrahedral mesh (vert [nv][3], tet [nt][4]) with the
+        kinetic non-reflecting boundary on every boundary face."""
+        vert = np.ascontiguousarray(vert, dtype=np.float64)
+        tet = np.ascontiguousarray(tet, dtype=np.int64)
+        d = gks_mesh_desc()
+        d.dim = 3
+        d.kind = GKS_TET
+        d.precision = GKS_FP64 if precision == "fp64" else GKS_FP32
+        d.n_vert = vert.shape[0]
+        d.vert_xyz = vert.ctypes.data_as(_D)
+        d.n_tet = tet.shape[0]
+        d.tet_vert = tet.ctypes.data_as(_I64)
+        d.tet_bc = GKS_BC_NONREFLECTING
+        d.cfl = cfl
+        d.tau_over_dt = kappa
+        d.c_lattice = c_lattice
+        d.cuda_stream = ctypes.c_void_p(int(stream)) if stream else None
+        self = cls.__new__(cls)
+        self.spec = None
+        self.ncomp = 6
+        self.ncell = int(tet.shape[0])
+        self.ctx = gks_create_mesh(d)
+        return self
+
+    @classmethod
+    def from_tet_workload(cls, w, precision="fp32", kappa=0.0, stream=0):
+        s = cls.from_tets(w.vert, w.tet, w.cfl, precision=precision, kappa=kappa, stream=stream)
+        s.set_materials(w.eps, w.mu)
+        s.write_fields(w.fields0)
+        return s
+
+    @classmethod
     def from_workload(cls, w, precision="fp32", kappa=0.0, stream=0):
         s = cls(SolverSpec(dim=w.dim, n=w.n, lo=w.lo, hi=w.hi, bc=w.bc, cfl=w.cfl,
                            precision=precision, kappa=kappa,
