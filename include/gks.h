@@ -129,6 +129,45 @@ gks_status gks_read_fields(gks_ctx *ctx, double *out);
  * FP64 on the device; synchronises.  (Not in the paper: a diagnostic.) */
 gks_status gks_energy(gks_ctx *ctx, double *out);
 
+/* Probe objective and design region for the adjoint (2-D TM Cartesian grids; not in the
+ * paper).  After every gks_step the device accumulates, in FP64 with Kahan compensation,
+ *     J = sum_{n >= 1} dt sum_{i in probe} |Omega_i| Ez_i^n^2
+ * (reset by gks_write_fields).  probe: [np] user cell ids; design: [nd] user cell ids, the
+ * cells whose eps the gradient is taken with respect to (slot k = design[k]).  Host arrays,
+ * copied.  GKS_E_UNSUPPORTED on tets or 3-D grids, GKS_E_ARG on ids out of range or repeated. */
+gks_status gks_set_objective(gks_ctx *ctx, const int64_t *probe, int64_t np,
+                             const int64_t *design, int64_t nd);
+
+/* Wait for the stream and return the accumulated objective J.  GKS_E_STATE before
+ * gks_set_objective. */
+gks_status gks_objective(gks_ctx *ctx, double *J);
+
+/* Size of one state buffer in the context's internal layout (ncomp * padded cells) in elements
+ * of the context precision and in bytes.  Checkpoints and adjoint buffers use this layout. */
+gks_status gks_state_layout(const gks_ctx *ctx, int64_t *elements, int64_t *bytes);
+
+/* Device-to-device copy of the current state into dst (caller-owned, gks_state_layout bytes);
+ * asynchronous on the context stream. */
+gks_status gks_copy_state(gks_ctx *ctx, void *dst);
+
+/* Replace the current state by src (device, internal layout) and set the step counter, so that
+ * the time is t0 + step * dt (checkpoint restart); asynchronous. */
+gks_status gks_load_state(gks_ctx *ctx, const void *src, int64_t step);
+
+/* adj = dq/dV(state) for q(V) = dt sum_probe |Omega| Ez^2: the adjoint of the final step of J.
+ * state, adj: device, internal layout. */
+gks_status gks_adjoint_seed(gks_ctx *ctx, const void *state, void *adj);
+
+/* One step of the discrete adjoint of gks_step (hand-transposed fused stencil; not in the
+ * paper): adj_out = L^T adj_in (+ dq/dV(state_n) if add_probe), and
+ * grad_eps[k] += dV^{n+1}/d eps_{design[k]} . adj_in, with V^{n+1} = L(eps) V^n + s^n.
+ * state_n = V^n, state_np1 = V^{n+1} (device, internal layout; needed on the design cells and
+ * the probe), adj_in = lambda^{n+1}, adj_out = lambda^n (distinct device buffers),
+ * grad_eps: device [nd] doubles.  2-D TM, mu = 1.  Asynchronous. */
+gks_status gks_adjoint_step(gks_ctx *ctx, const void *state_n, const void *state_np1,
+                            const void *adj_in, void *adj_out, double *grad_eps,
+                            int32_t add_probe);
+
 /* Energy 1/2 |Omega| sum_i (eps_i |E_i|^2 + mu_i |H_i|^2) of caller-owned device arrays, for
  * callers that cannot allocate device memory (a framework that reserved the device memory for
  * its own pool, a hot loop that cannot pay for an allocation, or code without a gks context).

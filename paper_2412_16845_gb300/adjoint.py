@@ -1,0 +1,140 @@
+"""Gradient of the probe objective with respect to per-cell eps, by the hand-written adjoint of
+the GKS step (C ABI: gks_set_objective, gks_adjoint_seed, gks_adjoint_step), with sqrt(N)-step
+checkpointing and recomputation, and a ``torch.autograd.Function`` on top.
+
+J(eps) = sum_{n=1}^{N} dt sum_{i in probe} |Omega_i| Ez_i^n(eps)^2 for a 2-D TM workload with a
+design region.  The forward pass stores the state every K steps (device tensors in the
+library's layout); the backward pass walks the segments in reverse: restore the checkpoint,
+recompute the segment's states, then run the adjoint steps over them.  PyTorch provides the
+device buffers and the stream; every step of the method runs in the library's kernels.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from .gks import (GKSSolver, gks_adjoint_seed, gks_adjoint_step, gks_copy_state,
+                  gks_load_state, gks_objective, gks_set_objective, gks_state_layout)
+
+
+class DesignProblem:
+    def __init__(self, w, precision="fp32", nsteps=None, checkpoint_every=None, stream=None):
+        import torch
+        if w.dim != 2 or w.design is None or w.probe is None:
+            raise ValueError("a 2-D workload with a probe and a design region is required")
+        self.torch = torch
+        self.w = w
+        self.N = int(nsteps if nsteps is not None else w.steps)
+        self.K = int(checkpoint_every or max(1, int(round(math.sqrt(self.N)))))
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.solver = GKSSolver.from_workload(w, precision=precision,
+                                              stream=self.stream.cuda_stream)
+        self.ctx = self.solver.ctx
+        gks_set_objective(self.ctx, w.probe, w.design)
+        self.elems, _ = gks_state_layout(self.ctx)
+        self.dtype = torch.float64 if precision == "fp64" else torch.float32
+        self.base_eps = np.array(w.eps, dtype=np.float64)
+        self.design = np.asarray(w.design, dtype=np.int64)
+        self.checkpoints = None
+        self.final = None
+        self.eps_design = None
+
+    def _buf(self):
+        return self.torch.empty(self.elems, dtype=self.dtype, device="cuda")
+
+    def set_design(self, eps_design):
+        eps = self.base_eps.copy()
+        eps[self.design] = np.asarray(eps_design, dtype=np.float64)
+        self.solver.set_materials(eps, self.w.mu)
+        self.eps_design = np.array(eps_design, dtype=np.float64)
+
+    def forward(self, eps_design, keep_checkpoints=True):
+        """J(eps_design); keeps the checkpoints for a following backward()."""
+        self.set_design(eps_design)
+        self.solver.write_fields(self.w.fields0)
+        ck = []
+        n = 0
+        while n < self.N:
+            if keep_checkpoints:
+                b = self._buf()
+                gks_copy_state(self.ctx, b.data_ptr())
+                ck.append((n, b))
+            k = min(self.K, self.N - n)
+            self.solver.step(k)
+            n += k
+        J = gks_objective(self.ctx)
+        if keep_checkpoints:
+            self.final = self._buf()
+            gks_copy_state(self.ctx, self.final.data_ptr())
+            self.checkpoints = ck
+        return J
+
+    def backward(self):
+        """dJ/d eps over the design cells (device float64 tensor), after forward()."""
+        torch = self.torch
+        if self.checkpoints is None:
+            raise RuntimeError("forward() with keep_checkpoints=True must come first")
+        lam = self._buf()
+        lam2 = self._buf()
+        grad = torch.zeros(self.design.size, dtype=torch.float64, device="cuda")
+        gks_adjoint_seed(self.ctx, self.final.data_ptr(), lam.data_ptr())
+        for (s, ckb), e in zip(reversed(self.checkpoints),
+                               reversed([c[0] for c in self.checkpoints[1:]] + [self.N])):
+            # recompute V^s .. V^e of this segment
+            gks_load_state(self.ctx, ckb.data_ptr(), s)
+            states = [ckb]
+            for _ in range(e - s):
+                self.solver.step(1)
+                b = self._buf()
+                gks_copy_state(self.ctx, b.data_ptr())
+                states.append(b)
+            for n in range(e - 1, s - 1, -1):
+                gks_adjoint_step(self.ctx, states[n - s].data_ptr(), states[n - s + 1].data_ptr(),
+                                 lam.data_ptr(), lam2.data_ptr(), grad.data_ptr(), n >= 1)
+                lam, lam2 = lam2, lam
+            del states
+        return grad
+
+    def value_and_grad(self, eps_design):
+        J = self.forward(eps_design)
+        g = self.backward()
+        return J, g.cpu().numpy()
+
+    def close(self):
+        self.solver.close()
+
+
+def _autograd_class():
+    import torch
+
+    class GKSEnergyObjective(torch.autograd.Function):
+        """J = GKSEnergyObjective.apply(eps_design, problem): the probe objective of a
+        DesignProblem as a differentiable function of the design eps (float64 scalar)."""
+
+        @staticmethod
+        def forward(ctx, eps_design, problem):
+            J = problem.forward(eps_design.detach().to("cpu", torch.float64).numpy())
+            ctx.problem = problem
+            ctx.dev = eps_design.device
+            ctx.dt = eps_design.dtype
+            return torch.tensor(J, dtype=torch.float64, device=eps_design.device)
+
+        @staticmethod
+        def backward(ctx, gJ):
+            g = ctx.problem.backward()
+            return (gJ * g).to(ctx.dev, ctx.dt), None
+
+    return GKSEnergyObjective
+
+
+_CLASS = None
+
+
+def __getattr__(name):
+    global _CLASS
+    if name == "GKSEnergyObjective":
+        if _CLASS is None:
+            _CLASS = _autograd_class()
+        return _CLASS
+    raise AttributeError(name)

@@ -6,6 +6,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "gks_internal.h"
 
@@ -285,6 +286,7 @@ gks_status gks_write_fields(gks_ctx *ctx, const double *fields, double t0) {
   gks_status s = upload_cells(ctx, fields, ctx->ncomp, ctx->V[ctx->cur]);
   if (s != GKS_OK) return s;
   GKS_CUDA(cudaMemsetAsync(ctx->flag, 0, sizeof(int), ctx->st));
+  if (ctx->obj) GKS_CUDA(cudaMemsetAsync(ctx->obj, 0, 2 * sizeof(double), ctx->st));
   ctx->t0 = t0;
   ctx->step = 0;
   ctx->fields_written = true;
@@ -375,6 +377,12 @@ gks_status gks_step(gks_ctx *ctx, int64_t n_steps) {
     if (e != cudaSuccess) return cuda_fail(ctx, e, "step launch");
     ctx->cur ^= 1;
     ctx->step += 1;
+    if (ctx->np > 0) {
+      e = gks::launch_objective(ctx->V[ctx->cur], ctx->probe_off, ctx->probe_w, ctx->np, ctx->dt,
+                                ctx->obj, ctx->fp64, ctx->st);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "objective launch");
+      ctx->launches += 1;
+    }
   }
   return GKS_OK;
 }
@@ -415,6 +423,135 @@ gks_status gks_sync(gks_ctx *ctx) {
   return check_flag(ctx);
 }
 
+
+gks_status gks_set_objective(gks_ctx *ctx, const int64_t *probe, int64_t np, const int64_t *design,
+                             int64_t nd) {
+  if (!ctx) return GKS_E_ARG;
+  if (ctx->kind != GKS_CARTESIAN || ctx->dim != 2)
+    return fail(ctx, GKS_E_UNSUPPORTED, "the objective and its adjoint need a 2-D Cartesian grid");
+  if (np < 0 || nd < 0 || (np > 0 && !probe) || (nd > 0 && !design))
+    return fail(ctx, GKS_E_ARG, "probe / design lists");
+  const gks::CartGeom &g = ctx->g;
+  std::vector<int64_t> off(np);
+  std::vector<double> w(np, g.h[0] * g.h[1]);
+  for (int64_t i = 0; i < np; ++i) {
+    const int64_t c = probe[i];
+    if (c < 0 || c >= ctx->ncell) return fail(ctx, GKS_E_ARG, "probe cell out of range");
+    off[i] = (c / g.nx) * g.pitch + c % g.nx;          // Ez component of the state layout
+  }
+  std::vector<int32_t> slot((size_t)g.cstride, -1);
+  int box[4] = {g.nx, -1, g.ny, -1};
+  for (int64_t i = 0; i < nd; ++i) {
+    const int64_t c = design[i];
+    if (c < 0 || c >= ctx->ncell) return fail(ctx, GKS_E_ARG, "design cell out of range");
+    const int x = (int)(c % g.nx), y = (int)(c / g.nx);
+    const int64_t o = (int64_t)y * g.pitch + x;
+    if (slot[o] >= 0) return fail(ctx, GKS_E_ARG, "design cell listed twice");
+    slot[o] = (int32_t)i;
+    box[0] = std::min(box[0], x); box[1] = std::max(box[1], x);
+    box[2] = std::min(box[2], y); box[3] = std::max(box[3], y);
+  }
+  void *bufs[] = {ctx->probe_off, ctx->probe_w, ctx->dslot};
+  for (void *b : bufs)
+    if (b) GKS_CUDA(cudaFreeAsync(b, ctx->st));
+  ctx->probe_off = nullptr; ctx->probe_w = nullptr; ctx->dslot = nullptr;
+  gks_status s;
+  if ((s = upload_vec(ctx, off, &ctx->probe_off)) != GKS_OK ||
+      (s = upload_vec(ctx, w, &ctx->probe_w)) != GKS_OK || (s = upload_vec(ctx, slot, &ctx->dslot)) != GKS_OK)
+    return s;
+  if (!ctx->obj && (s = alloc_dev(ctx, (void **)&ctx->obj, 2 * sizeof(double))) != GKS_OK) return s;
+  GKS_CUDA(cudaMemsetAsync(ctx->obj, 0, 2 * sizeof(double), ctx->st));
+  GKS_CUDA(cudaStreamSynchronize(ctx->st));   // the host vectors go out of scope
+  ctx->np = np;
+  ctx->nd = nd;
+  if (nd > 0) {
+    ctx->dbox[0] = box[0]; ctx->dbox[1] = box[1] + 1; ctx->dbox[2] = box[2]; ctx->dbox[3] = box[3] + 1;
+  } else {
+    ctx->dbox[0] = ctx->dbox[1] = ctx->dbox[2] = ctx->dbox[3] = 0;
+  }
+  return GKS_OK;
+}
+
+gks_status gks_objective(gks_ctx *ctx, double *J) {
+  if (!ctx) return GKS_E_ARG;
+  if (!J) return fail(ctx, GKS_E_ARG, "J is NULL");
+  if (!ctx->obj) return fail(ctx, GKS_E_STATE, "gks_set_objective must come first");
+  double h[2];
+  GKS_CUDA(cudaMemcpyAsync(h, ctx->obj, sizeof(h), cudaMemcpyDeviceToHost, ctx->st));
+  gks_status s = check_flag(ctx);
+  if (s != GKS_OK) return s;
+  *J = h[0];
+  return GKS_OK;
+}
+
+gks_status gks_state_layout(const gks_ctx *ctx, int64_t *elements, int64_t *bytes) {
+  if (!ctx) return GKS_E_ARG;
+  const int64_t n = (int64_t)ctx->ncomp * ctx->g.cstride;
+  if (elements) *elements = n;
+  if (bytes) *bytes = n * (int64_t)ctx->esize;
+  return GKS_OK;
+}
+
+gks_status gks_copy_state(gks_ctx *ctx, void *dst) {
+  if (!ctx) return GKS_E_ARG;
+  if (!dst) return fail(ctx, GKS_E_ARG, "dst is NULL");
+  GKS_CUDA(cudaMemcpyAsync(dst, ctx->V[ctx->cur], ctx->esize * ctx->ncomp * (size_t)ctx->g.cstride,
+                           cudaMemcpyDeviceToDevice, ctx->st));
+  return GKS_OK;
+}
+
+gks_status gks_load_state(gks_ctx *ctx, const void *src, int64_t step) {
+  if (!ctx) return GKS_E_ARG;
+  if (!src || step < 0) return fail(ctx, GKS_E_ARG, "src is NULL or step < 0");
+  GKS_CUDA(cudaMemcpyAsync(ctx->V[ctx->cur], src, ctx->esize * ctx->ncomp * (size_t)ctx->g.cstride,
+                           cudaMemcpyDeviceToDevice, ctx->st));
+  ctx->step = step;
+  ctx->fields_written = true;
+  return GKS_OK;
+}
+
+gks_status gks_adjoint_seed(gks_ctx *ctx, const void *state, void *adj) {
+  if (!ctx) return GKS_E_ARG;
+  if (!state || !adj) return fail(ctx, GKS_E_ARG, "state / adj is NULL");
+  if (!ctx->obj) return fail(ctx, GKS_E_STATE, "gks_set_objective must come first");
+  GKS_CUDA(cudaMemsetAsync(adj, 0, ctx->esize * ctx->ncomp * (size_t)ctx->g.cstride, ctx->st));
+  GKS_CUDA(gks::launch_probe_grad(state, adj, ctx->probe_off, ctx->probe_w, ctx->np, ctx->dt, true,
+                                  ctx->fp64, ctx->st));
+  return GKS_OK;
+}
+
+gks_status gks_adjoint_step(gks_ctx *ctx, const void *state_n, const void *state_np1,
+                            const void *adj_in, void *adj_out, double *grad_eps,
+                            int32_t add_probe) {
+  if (!ctx) return GKS_E_ARG;
+  if (ctx->kind != GKS_CARTESIAN || ctx->dim != 2)
+    return fail(ctx, GKS_E_UNSUPPORTED, "the adjoint needs a 2-D Cartesian grid");
+  if (ctx->mu) return fail(ctx, GKS_E_UNSUPPORTED, "the adjoint supports mu = 1 only");
+  if (!adj_in || !adj_out || adj_in == adj_out) return fail(ctx, GKS_E_ARG, "adj_in / adj_out");
+  if (ctx->nd > 0 && (!grad_eps || !state_n || !state_np1))
+    return fail(ctx, GKS_E_ARG, "the eps-gradient needs both states and grad_eps");
+  if (add_probe && ctx->np > 0 && !state_n) return fail(ctx, GKS_E_ARG, "state_n is NULL");
+  gks::AdjointArgs a;
+  a.lam_in = adj_in;
+  a.lam_out = adj_out;
+  a.eps = ctx->eps;
+  a.Vn = state_n;
+  a.Vn1 = state_np1;
+  a.dslot = ctx->dslot;
+  a.grad = ctx->nd > 0 ? grad_eps : nullptr;
+  std::memcpy(a.dbox, ctx->dbox, sizeof(a.dbox));
+  std::memcpy(a.C, ctx->C, sizeof(a.C));
+  a.c = ctx->c;
+  GKS_CUDA(gks::launch_adjoint_step(ctx->g, a, ctx->fp64, ctx->st));
+  ctx->launches += 1;
+  if (add_probe && ctx->np > 0) {
+    GKS_CUDA(gks::launch_probe_grad(state_n, adj_out, ctx->probe_off, ctx->probe_w, ctx->np,
+                                    ctx->dt, false, ctx->fp64, ctx->st));
+    ctx->launches += 1;
+  }
+  return GKS_OK;
+}
+
 gks_status gks_get_info(const gks_ctx *ctx, double *dt, double *t, int64_t *step,
                         int64_t *n_cells, double *c_lattice) {
   if (!ctx) return GKS_E_ARG;
@@ -442,7 +579,8 @@ void gks_destroy(gks_ctx *ctx) {
   const gks::TetDev &t = ctx->tet;
   void *bufs[] = {ctx->V[0], ctx->V[1], ctx->eps, ctx->mu, ctx->src, ctx->flag, ctx->red,
                   ctx->staging, t.perm, t.vol, t.cnb, t.cface, t.csign, t.cw, t.fL, t.fR, t.fT,
-                  t.farea, t.fdL, t.fdR, t.Gscratch, t.Fscratch};
+                  t.farea, t.fdL, t.fdR, t.Gscratch, t.Fscratch, ctx->probe_off, ctx->probe_w,
+                  ctx->dslot, ctx->obj};
   for (void *p : bufs)
     if (p) cudaFreeAsync(p, ctx->st);
   cudaStreamSynchronize(ctx->st);

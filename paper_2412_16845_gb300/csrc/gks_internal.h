@@ -87,6 +87,26 @@ cudaError_t launch_tet_energy(const TetDev &g, const void *V, const void *eps, c
                               bool fp64, double *partials, int npart, double *out,
                               cudaStream_t st);
 
+// Adjoint of the 2-D TM step (see gks_adjoint.cu).
+struct AdjointArgs {
+  const void *lam_in;       // lambda^{n+1}, state layout
+  void *lam_out;            // lambda^n
+  const void *eps;
+  const void *Vn;           // state at t^n
+  const void *Vn1;          // state at t^{n+1}
+  const int32_t *dslot;     // design slot per cell (-1 elsewhere), state layout
+  double *grad;             // [nd], accumulated
+  int dbox[4];              // design box x0, x1, y0, y1 (half open)
+  double C[5];
+  double c;
+};
+cudaError_t launch_adjoint_step(const CartGeom &g, const AdjointArgs &a, bool fp64,
+                                cudaStream_t st);
+cudaError_t launch_probe_grad(const void *V, void *lam, const int64_t *off, const double *w,
+                              int64_t np, double dt, bool assign, bool fp64, cudaStream_t st);
+cudaError_t launch_objective(const void *V, const int64_t *off, const double *w, int64_t np,
+                             double dt, double *acc, bool fp64, cudaStream_t st);
+
 // Launchers (return cudaGetLastError() of the launch).
 cudaError_t launch_cart2d_step(const CartGeom &g, const CartStepArgs &a, bool fp64,
                                cudaStream_t st);
@@ -133,5 +153,13 @@ struct gks_ctx {
   double min_h = 1.0;
   bool fields_written = false;
   int64_t launches = 0;
+  // objective / adjoint (2-D Cartesian)
+  int64_t *probe_off = nullptr;   // [np] state offsets of the probe cells
+  double *probe_w = nullptr;      // [np] |Omega_i|
+  int64_t np = 0;
+  int32_t *dslot = nullptr;       // state layout, design slot or -1
+  int64_t nd = 0;
+  int dbox[4] = {0, 0, 0, 0};
+  double *obj = nullptr;          // (sum, Kahan compensation)
   std::string err;
 };

@@ -65,6 +65,14 @@ SIGNATURES = {
     "gks_read_fields": (ctypes.c_int, [_CTX, _D]),
     "gks_energy": (ctypes.c_int, [_CTX, _D]),
     "gks_sync": (ctypes.c_int, [_CTX]),
+    "gks_set_objective": (ctypes.c_int, [_CTX, _I64, ctypes.c_int64, _I64, ctypes.c_int64]),
+    "gks_objective": (ctypes.c_int, [_CTX, _D]),
+    "gks_state_layout": (ctypes.c_int, [_CTX, _I64, _I64]),
+    "gks_copy_state": (ctypes.c_int, [_CTX, ctypes.c_void_p]),
+    "gks_load_state": (ctypes.c_int, [_CTX, ctypes.c_void_p, ctypes.c_int64]),
+    "gks_adjoint_seed": (ctypes.c_int, [_CTX, ctypes.c_void_p, ctypes.c_void_p]),
+    "gks_adjoint_step": (ctypes.c_int, [_CTX, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32]),
     "gks_energy_noalloc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
                                           ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
@@ -159,6 +167,42 @@ def gks_energy_noalloc(precision, dim, n_cells, cell_volume, fields_ptr, eps_ptr
                                            out_ptr, stream or None)
     if st != GKS_OK:
         raise GksError(st, "gks_energy_noalloc rejected the call")
+
+
+def gks_set_objective(ctx, probe, design):
+    probe = np.ascontiguousarray(probe if probe is not None else [], dtype=np.int64)
+    design = np.ascontiguousarray(design if design is not None else [], dtype=np.int64)
+    _check(ctx, load_library().gks_set_objective(ctx, probe.ctypes.data_as(_I64), probe.size,
+                                                 design.ctypes.data_as(_I64), design.size))
+
+
+def gks_objective(ctx):
+    v = ctypes.c_double()
+    _check(ctx, load_library().gks_objective(ctx, ctypes.byref(v)))
+    return v.value
+
+
+def gks_state_layout(ctx):
+    n, b = ctypes.c_int64(), ctypes.c_int64()
+    _check(ctx, load_library().gks_state_layout(ctx, ctypes.byref(n), ctypes.byref(b)))
+    return n.value, b.value
+
+
+def gks_copy_state(ctx, dst_ptr):
+    _check(ctx, load_library().gks_copy_state(ctx, dst_ptr))
+
+
+def gks_load_state(ctx, src_ptr, step):
+    _check(ctx, load_library().gks_load_state(ctx, src_ptr, int(step)))
+
+
+def gks_adjoint_seed(ctx, state_ptr, adj_ptr):
+    _check(ctx, load_library().gks_adjoint_seed(ctx, state_ptr, adj_ptr))
+
+
+def gks_adjoint_step(ctx, state_n, state_np1, adj_in, adj_out, grad_eps, add_probe):
+    _check(ctx, load_library().gks_adjoint_step(ctx, state_n, state_np1, adj_in, adj_out,
+                                                grad_eps, 1 if add_probe else 0))
 
 
 def gks_sync(ctx):

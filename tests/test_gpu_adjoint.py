@@ -1,0 +1,140 @@
+"""The hand-written adjoint of the 2-D TM step and the eps-gradient of the probe objective.
+
+Checks: the transpose identity <L x, y> = <x, L^T y> (FP64, 1e-13); the gradient against the
+oracle's complex-step derivative (exact to round-off) and against central finite differences of
+the GPU's FP64 forward; FP32 against FP64; the torch.autograd wrapper."""
+import numpy as np
+import pytest
+
+from oracle import gks_oracle as go
+from paper_2412_16845_gb300 import workloads as wl
+from paper_2412_16845_gb300.gks import (GKSSolver, gks_adjoint_step, gks_copy_state,
+                                        gks_load_state, gks_state_layout, gks_set_objective)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2412_16845_gb300 import build
+    build.build()
+
+
+def _grid(nx, ny, bc, seed):
+    rng = np.random.default_rng(seed)
+    x, y = wl.cell_centres_2d(nx, ny, hi=(1.0, ny / nx))
+    f = rng.standard_normal((3, nx * ny))
+    eps = rng.uniform(1.0, 3.0, nx * ny)
+    return wl.CartWorkload(name="adj", dim=2, n=(nx, ny), lo=(0.0, 0.0), hi=(1.0, ny / nx),
+                           bc=bc, cfl=0.5, steps=0, eps=eps, mu=None, fields0=f)
+
+
+@pytest.mark.parametrize("bc", [("nrbc",) * 4, ("periodic",) * 4,
+                                ("periodic", "periodic", "nrbc", "nrbc")])
+@pytest.mark.parametrize("kappa", [0.0, 0.05, 1.0])
+@pytest.mark.parametrize("n", [(37, 23), (5, 3)])
+def test_transpose_identity(bc, kappa, n):
+    import torch
+    w = _grid(n[0], n[1], bc, 3 + n[0])
+    s = GKSSolver.from_workload(w, precision="fp64", kappa=kappa)
+    gks_set_objective(s.ctx, None, None)
+    elems, _ = gks_state_layout(s.ctx)
+    # random x, y in the padded layout (padding entries stay zero)
+    rng = np.random.default_rng(9)
+    pad = torch.zeros(elems, dtype=torch.float64, device="cuda")
+    gks_copy_state(s.ctx, pad.data_ptr())            # the layout of the written fields
+    mask = torch.zeros(elems, dtype=torch.float64, device="cuda")
+    s.write_fields(np.ones((3, w.ncell)))
+    gks_copy_state(s.ctx, mask.data_ptr())
+    x = torch.as_tensor(rng.standard_normal(elems), device="cuda") * mask
+    y = torch.as_tensor(rng.standard_normal(elems), device="cuda") * mask
+    gks_load_state(s.ctx, x.data_ptr(), 0)
+    s.step(1)
+    Lx = torch.empty_like(x)
+    gks_copy_state(s.ctx, Lx.data_ptr())
+    LTy = torch.zeros_like(y)
+    gks_adjoint_step(s.ctx, None, None, y.data_ptr(), LTy.data_ptr(), None, False)
+    torch.cuda.synchronize()
+    a = float((Lx * y).sum())
+    b = float((x * LTy * mask).sum())
+    s.close()
+    assert abs(a - b) <= 1e-13 * max(abs(a), float((x * x).sum()) ** 0.5 * float((y * y).sum()) ** 0.5), (a, b)
+
+
+def _design_workload(nx=24, ny=20, steps=30, seed=5):
+    rng = np.random.default_rng(seed)
+    x, y = wl.cell_centres_2d(nx, ny, hi=(1.0, ny / nx))
+    h = 1.0 / nx
+    f = np.zeros((3, nx * ny))
+    f[0] = np.exp(-((x - 0.3) ** 2 + (y - 0.4) ** 2) / (2 * 0.08 ** 2))
+    eps = np.ones(nx * ny)
+    ii, jj = np.arange(8, 16), np.arange(6, 14)
+    design = (jj[:, None] * nx + ii[None, :]).ravel()
+    eps[design] = rng.uniform(1.0, 3.0, design.size)
+    probe = np.nonzero((x - 0.6) ** 2 + (y - 0.45) ** 2 <= 0.1 ** 2)[0]
+    mask = np.zeros(nx * ny)
+    mask[(np.arange(nx * ny) % nx) == 3] = 1.0 / h
+    return wl.CartWorkload(name="design", dim=2, n=(nx, ny), lo=(0.0, 0.0), hi=(1.0, ny / nx),
+                           bc=("nrbc",) * 4, cfl=0.5, steps=steps, eps=eps, mu=None, fields0=f,
+                           jz_mask=mask, src=(1.0, 4.0, 0.1, 0.1), probe=probe,
+                           design=design.astype(np.int64))
+
+
+def _oracle_J(w, eps):
+    mesh = go.cartesian_mesh(w.n, w.lo, w.hi, w.bc)
+    _, info = go.run(mesh, w.fields0, eps, None, w.cfl, w.steps, c=1.0, jz_mask=w.jz_mask,
+                     src=w.src, probe=w.probe)
+    return info["J"]
+
+
+def test_gradient_matches_oracle_complex_step():
+    """FP64 adjoint gradient = the oracle's complex-step derivative (Im J(eps + i h e_d)/h)."""
+    from paper_2412_16845_gb300.adjoint import DesignProblem
+    w = _design_workload()
+    prob = DesignProblem(w, precision="fp64", checkpoint_every=7)
+    J, g = prob.value_and_grad(w.eps[w.design])
+    prob.close()
+    Jo = _oracle_J(w, w.eps)
+    assert abs(J - Jo) <= 1e-12 * abs(Jo)
+    picks = [0, 5, 17, 33, 50, 63]
+    for k in picks:
+        e = w.eps.astype(complex)
+        e[w.design[k]] += 1e-30j
+        ref = _oracle_J(w, e).imag / 1e-30
+        assert abs(g[k] - ref) <= 1e-9 * max(abs(ref), 1e-12 * abs(J)), (k, g[k], ref)
+
+
+def test_gradient_fd_fp64_and_fp32_agree():
+    """Central differences of the GPU FP64 forward, and the FP32 adjoint within 1e-3."""
+    from paper_2412_16845_gb300.adjoint import DesignProblem
+    w = _design_workload(nx=40, ny=32, steps=60, seed=6)
+    w.design = w.design  # same design box definition scaled to the grid
+    p64 = DesignProblem(w, precision="fp64")
+    J, g64 = p64.value_and_grad(w.eps[w.design])
+    base = w.eps[w.design].copy()
+    rng = np.random.default_rng(1)
+    for k in rng.choice(w.design.size, size=6, replace=False):
+        h = 1e-5
+        ep = base.copy(); ep[k] += h
+        em = base.copy(); em[k] -= h
+        fd = (p64.forward(ep, keep_checkpoints=False) - p64.forward(em, keep_checkpoints=False)) / (2 * h)
+        assert abs(fd - g64[k]) <= 1e-6 * np.abs(g64).max(), (k, fd, g64[k])
+    p64.close()
+    p32 = DesignProblem(w, precision="fp32")
+    J32, g32 = p32.value_and_grad(base)
+    p32.close()
+    assert abs(J32 - J) <= 1e-4 * abs(J)
+    assert np.linalg.norm(g32 - g64) <= 1e-3 * np.linalg.norm(g64)
+
+
+def test_autograd_function():
+    import torch
+    from paper_2412_16845_gb300.adjoint import DesignProblem, GKSEnergyObjective
+    w = _design_workload()
+    prob = DesignProblem(w, precision="fp64", checkpoint_every=5)
+    e = torch.tensor(w.eps[w.design], dtype=torch.float64, device="cuda", requires_grad=True)
+    J = GKSEnergyObjective.apply(e, prob)
+    J.backward()
+    _, g = prob.value_and_grad(w.eps[w.design])
+    prob.close()
+    assert np.allclose(e.grad.cpu().numpy(), g, rtol=1e-12, atol=0)
