@@ -199,6 +199,8 @@ def main():
     ap.add_argument("--n3", type=int, default=256)
     ap.add_argument("--steps3", type=int, default=100)
     ap.add_argument("--no-err3", dest="err3", action="store_false", default=True)
+    ap.add_argument("--no-adjoint", dest="with_adjoint", action="store_false", default=True)
+    ap.add_argument("--n5", type=int, default=2048)
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -349,6 +351,40 @@ def main():
                  "hbm_frac_fp32": 52 * n3 / (ms3 * 1e-3) / 1e9 / _peaks()[0],
                  "algorithmic_bytes_per_cell_step": 52}
 
+    # ---------------- adjoint: eps-gradient of the probe objective, 2048^2 design workload
+    adj = None
+    if args.with_adjoint:
+        from paper_2412_16845_gb300.adjoint import DesignProblem
+        w5 = wl.config5_design_tm(n=args.n5, steps=2000)
+        plain = GKSSolver.from_workload(w5, precision="fp32", stream=sptr)
+        plain.step(3)
+        plain.sync()
+        t0 = time.perf_counter()
+        plain.step(2000)
+        plain.sync()
+        t_plain = time.perf_counter() - t0
+        plain.close()
+        prob = DesignProblem(w5, precision="fp32", checkpoint_every=45, stream=stream)
+        e0 = w5.eps[w5.design]
+        prob.forward(e0)                       # warm-up of the whole path
+        prob.backward()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        J = prob.forward(e0)
+        torch.cuda.synchronize()
+        t_fwd = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        g = prob.backward()
+        torch.cuda.synchronize()
+        t_bwd = time.perf_counter() - t0
+        prob.close()
+        adj = {"workload": f"tm2d_design_{args.n5}", "steps": 2000, "checkpoint_every": 45,
+               "design_cells": int(w5.design.size), "probe_cells": int(w5.probe.size),
+               "forward_plain_s": t_plain, "forward_with_checkpoints_s": t_fwd,
+               "backward_s": t_bwd, "adjoint_over_forward": t_bwd / t_plain,
+               "gradient_over_forward": (t_fwd + t_bwd) / t_plain, "J": J,
+               "grad_norm": float(g.norm())}
+
     if rank == 0:
         hbm, how = _peaks()
         achieved = BYTES_PER_CELL_STEP["fp32"] * ncell / (ms_step * 1e-3) / 1e9
@@ -377,6 +413,7 @@ def main():
                     "definition": "write_fields(pinned FP64) + step(K) + read_fields, wall clock"},
             "gpu_launches": int(launches),
             "maxwell3d": three,
+            "adjoint": adj,
             "clocks": clocks,
         }
         if not args.no_cpu_baseline:

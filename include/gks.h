@@ -121,6 +121,15 @@ gks_status gks_set_dt(gks_ctx *ctx, double dt);
 /* Enqueue n_steps >= 0 GKS steps (Sec. 3.1) on the context stream; asynchronous. */
 gks_status gks_step(gks_ctx *ctx, int64_t n_steps);
 
+/* Enqueue n_steps steps that advance only the cells of the window [x0, x1) x [y0, y1) (2-D
+ * Cartesian grids).  Cells outside the window keep stale values, which act on the window's
+ * cells after one step through the stencil (radius two cells): after k windowed steps only the
+ * cells at least 2k cells inside the window are exact.  Used to recompute a region's domain of
+ * dependence from a checkpoint (adjoint).  Time and step counter advance as in gks_step; the
+ * probe objective is not accumulated. */
+gks_status gks_step_window(gks_ctx *ctx, int64_t n_steps, int64_t x0, int64_t x1, int64_t y0,
+                           int64_t y1);
+
 /* Wait for the stream, then copy the fields to out ([ncomp][n_cells] doubles, user order,
  * host).  GKS_E_NONFINITE if a step produced a non-finite value. */
 gks_status gks_read_fields(gks_ctx *ctx, double *out);
@@ -149,6 +158,10 @@ gks_status gks_state_layout(const gks_ctx *ctx, int64_t *elements, int64_t *byte
 /* Device-to-device copy of the current state into dst (caller-owned, gks_state_layout bytes);
  * asynchronous on the context stream. */
 gks_status gks_copy_state(gks_ctx *ctx, void *dst);
+
+/* Copy only the rows [y0, y1) (row index y + ny*z) of every component of the current state into
+ * dst at the same offsets of the internal layout (device, gks_state_layout bytes); asynchronous. */
+gks_status gks_copy_state_rows(gks_ctx *ctx, void *dst, int64_t y0, int64_t y1);
 
 /* Replace the current state by src (device, internal layout) and set the step counter, so that
  * the time is t0 + step * dt (checkpoint restart); asynchronous. */

@@ -15,7 +15,8 @@ import math
 import numpy as np
 
 from .gks import (GKSSolver, gks_adjoint_seed, gks_adjoint_step, gks_copy_state,
-                  gks_load_state, gks_objective, gks_set_objective, gks_state_layout)
+                  gks_copy_state_rows, gks_load_state, gks_objective, gks_set_objective,
+                  gks_state_layout, gks_step_window)
 
 
 class DesignProblem:
@@ -39,6 +40,17 @@ class DesignProblem:
         self.checkpoints = None
         self.final = None
         self.eps_design = None
+        # the adjoint reads states only on the design cells (two-cell stencil) and the probe:
+        # rows [ry0, ry1) are stored; a segment of K steps is recomputed on the design box
+        # widened by 2 + 2K cells (its domain of dependence), clipped to the grid
+        nx, ny = w.n
+        cells = np.concatenate([self.design, np.asarray(w.probe, dtype=np.int64)])
+        xs, ys = cells % nx, cells // nx
+        self.box = (int(xs.min()), int(xs.max()) + 1, int(ys.min()), int(ys.max()) + 1)
+        self.ry0, self.ry1 = max(0, self.box[2] - 2), min(ny, self.box[3] + 2)
+        m = 2 + 2 * self.K
+        self.win = (max(0, self.box[0] - m), min(nx, self.box[1] + m),
+                    max(0, self.box[2] - m), min(ny, self.box[3] + m))
 
     def _buf(self):
         return self.torch.empty(self.elems, dtype=self.dtype, device="cuda")
@@ -85,9 +97,9 @@ class DesignProblem:
             gks_load_state(self.ctx, ckb.data_ptr(), s)
             states = [ckb]
             for _ in range(e - s):
-                self.solver.step(1)
+                gks_step_window(self.ctx, 1, *self.win)
                 b = self._buf()
-                gks_copy_state(self.ctx, b.data_ptr())
+                gks_copy_state_rows(self.ctx, b.data_ptr(), self.ry0, self.ry1)
                 states.append(b)
             for n in range(e - 1, s - 1, -1):
                 gks_adjoint_step(self.ctx, states[n - s].data_ptr(), states[n - s + 1].data_ptr(),

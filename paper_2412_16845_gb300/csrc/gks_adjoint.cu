@@ -20,7 +20,11 @@
 namespace gks {
 namespace {
 
-constexpr int RX = 32, RY = 8;               // ring of threads: tile 30 x 6 plus one cell around
+// Division: FP32 uses the fast hardware reciprocal (about 1 ulp), FP64 divides.
+__device__ __forceinline__ float fdv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double fdv(double a, double b) { return a / b; }
+
+constexpr int RX = 32, RY = 16;              // ring of threads: tile 30 x 14 plus one cell around
 constexpr int TXI = RX - 2, TYI = RY - 2;    // inner (updated) cells
 constexpr int SX = RX + 2, SY = RY + 2;      // staged region: two cells around the tile
 constexpr int NXF = RX + 1, NYF = RY + 1;    // x-faces per ring row, y-faces per ring column
@@ -38,7 +42,7 @@ struct FOut {
 template <typename T, int GH>
 __device__ __forceinline__ void face_adj(T epsl, T epsr, const FaceK<T> &k, T fe, T fa, T fb,
                                          FOut<T> &oL, FOut<T> &oR) {
-  const T ie = GH == 0 ? T(2) / (epsl + epsr) : (GH == 1 ? T(1) / epsr : T(1) / epsl);
+  const T ie = GH == 0 ? fdv(T(2), epsl + epsr) : (GH == 1 ? fdv(T(1), epsr) : fdv(T(1), epsl));
   const T g = k.g0 - k.k3 * ie;
   const T w1 = g * fe;
   const T SUB = k.a1 * fe, De = k.a2 * fe;
@@ -96,7 +100,7 @@ __device__ __forceinline__ void face_deps(const FIn<T> &L, const FIn<T> &R, cons
   const T S_Uxe = epl * denl + epr * denr, D_xB = dhtr - dhtl;
   const T S_Ue = epl * el + epr * er, D_B = htr - htl;
   const T S_UxB = dhtl + dhtr, D_ex = denr - denl, S_UAt = datl + datr;
-  const T ie = GH == 0 ? T(2) / (L.eps + R.eps) : (GH == 1 ? T(1) / R.eps : T(1) / L.eps);
+  const T ie = GH == 0 ? fdv(T(2), L.eps + R.eps) : (GH == 1 ? fdv(T(1), R.eps) : fdv(T(1), L.eps));
   const T die = GH == 0 ? -T(0.5) * ie * ie : -ie * ie;
   const T g = k.g0 - k.k3 * ie, dg = -k.k3 * die;
   const T A = dg * (T(0.5) * S_Uxe + k.a3 * D_xB);
@@ -139,8 +143,8 @@ struct AdjSmem {
   T lam[3][SY][SX];
   T eps[SY][SX];
   T vn[3][SY][SX];
-  T xf[RY][NXF][2][8];    // x-face adjoints: [row][face][side][v(3) d(5)]
-  T yf[NYF][RX][2][8];    // y-face adjoints: [face][column][side][...]
+  T xf[2][8][RY][NXF];    // x-face adjoints: [side][v(3) d(5)][row][face]
+  T yf[2][8][NYF][RX];    // y-face adjoints: [side][...][face][column]
   T db[6][RY][RX];        // raw-difference adjoints of ring cells: dEx dEy dAx dAy dBx dBy
 };
 
@@ -213,63 +217,68 @@ __global__ void __launch_bounds__(RX * RY) adjoint_step_kernel(const AdjArgs<T> 
     const int ry = i / NXF, k = i - ry * NXF;
     const int sy = ry + 1, sxl = k, sxr = k + 1;
     const int gy = y0 - 1 + ry, glo = x0 - 2 + k;
-    T *ol = s.xf[ry][k][0], *orr = s.xf[ry][k][1];
     const int kind = (gy >= 0 && gy < p.ny) || p.pery ? face_kind(glo, p.nx, p.perx) : 3;
     FOut<T> oL = {}, oR = {};
     if (kind != 3) {
       const T el = s.eps[sy][sxl], er = s.eps[sy][sxr];
       // Fbar = -(lambda_L / M_L - lambda_R / M_R), components (Ez, Hx, Hy)
       T mu[3] = {T(0), T(0), T(0)};
-      if (kind != 1) { mu[0] += s.lam[0][sy][sxl] / el; mu[1] += s.lam[1][sy][sxl]; mu[2] += s.lam[2][sy][sxl]; }
-      if (kind != 2) { mu[0] -= s.lam[0][sy][sxr] / er; mu[1] -= s.lam[1][sy][sxr]; mu[2] -= s.lam[2][sy][sxr]; }
+      if (kind != 1) { mu[0] += fdv(s.lam[0][sy][sxl], el); mu[1] += s.lam[1][sy][sxl]; mu[2] += s.lam[2][sy][sxl]; }
+      if (kind != 2) { mu[0] -= fdv(s.lam[0][sy][sxr], er); mu[1] -= s.lam[1][sy][sxr]; mu[2] -= s.lam[2][sy][sxr]; }
       if (kind == 0) face_adj<T, 0>(el, er, p.fx, -mu[0], -mu[1], -mu[2], oL, oR);
       else if (kind == 1) face_adj<T, 1>(el, er, p.fx, -mu[0], -mu[1], -mu[2], oL, oR);
       else face_adj<T, 2>(el, er, p.fx, -mu[0], -mu[1], -mu[2], oL, oR);
     }
 #pragma unroll
-    for (int c = 0; c < 3; ++c) { ol[c] = oL.v[c]; orr[c] = oR.v[c]; }
+    for (int c = 0; c < 3; ++c) { s.xf[0][c][ry][k] = oL.v[c]; s.xf[1][c][ry][k] = oR.v[c]; }
 #pragma unroll
-    for (int c = 0; c < 5; ++c) { ol[3 + c] = oL.d[c]; orr[3 + c] = oR.d[c]; }
+    for (int c = 0; c < 5; ++c) { s.xf[0][3 + c][ry][k] = oL.d[c]; s.xf[1][3 + c][ry][k] = oR.d[c]; }
   }
   // y-face k of ring column rx lies between staged rows k and k+1; components (Ez, Hy, Hx)
   for (int i = tid; i < NYF * RX; i += RX * RY) {
     const int k = i / RX, rx = i - k * RX;
     const int sx = rx + 1, syl = k, syr = k + 1;
     const int gx = x0 - 1 + rx, glo = y0 - 2 + k;
-    T *ol = s.yf[k][rx][0], *orr = s.yf[k][rx][1];
     const int kind = (gx >= 0 && gx < p.nx) || p.perx ? face_kind(glo, p.ny, p.pery) : 3;
     FOut<T> oL = {}, oR = {};
     if (kind != 3) {
       const T el = s.eps[syl][sx], er = s.eps[syr][sx];
       T mu[3] = {T(0), T(0), T(0)};
-      if (kind != 1) { mu[0] += s.lam[0][syl][sx] / el; mu[1] += s.lam[2][syl][sx]; mu[2] += s.lam[1][syl][sx]; }
-      if (kind != 2) { mu[0] -= s.lam[0][syr][sx] / er; mu[1] -= s.lam[2][syr][sx]; mu[2] -= s.lam[1][syr][sx]; }
+      if (kind != 1) { mu[0] += fdv(s.lam[0][syl][sx], el); mu[1] += s.lam[2][syl][sx]; mu[2] += s.lam[1][syl][sx]; }
+      if (kind != 2) { mu[0] -= fdv(s.lam[0][syr][sx], er); mu[1] -= s.lam[2][syr][sx]; mu[2] -= s.lam[1][syr][sx]; }
       if (kind == 0) face_adj<T, 0>(el, er, p.fy, -mu[0], -mu[1], -mu[2], oL, oR);
       else if (kind == 1) face_adj<T, 1>(el, er, p.fy, -mu[0], -mu[1], -mu[2], oL, oR);
       else face_adj<T, 2>(el, er, p.fy, -mu[0], -mu[1], -mu[2], oL, oR);
     }
 #pragma unroll
-    for (int c = 0; c < 3; ++c) { ol[c] = oL.v[c]; orr[c] = oR.v[c]; }
+    for (int c = 0; c < 3; ++c) { s.yf[0][c][k][rx] = oL.v[c]; s.yf[1][c][k][rx] = oR.v[c]; }
 #pragma unroll
-    for (int c = 0; c < 5; ++c) { ol[3 + c] = oL.d[c]; orr[3 + c] = oR.d[c]; }
+    for (int c = 0; c < 5; ++c) { s.yf[0][3 + c][k][rx] = oL.d[c]; s.yf[1][3 + c][k][rx] = oR.d[c]; }
   }
   __syncthreads();
   // 3. gather per ring cell: value adjoints (registers) and difference adjoints (shared)
   const int rx = tid % RX, ry = tid / RX;
   T vb[3];        // (Ez, Hx, Hy)
   {
-    const T *xl = s.xf[ry][rx][1], *xr = s.xf[ry][rx + 1][0];     // cell is R of left face
-    const T *yb = s.yf[ry][rx][1], *yt = s.yf[ry + 1][rx][0];
-    vb[0] = xl[0] + xr[0] + yb[0] + yt[0];
-    vb[1] = xl[1] + xr[1] + yb[2] + yt[2];
-    vb[2] = xl[2] + xr[2] + yb[1] + yt[1];
+    // cell is the R side of its left / bottom face and the L side of its right / top face
+#define XL(c) s.xf[1][c][ry][rx]
+#define XR(c) s.xf[0][c][ry][rx + 1]
+#define YB(c) s.yf[1][c][ry][rx]
+#define YT(c) s.yf[0][c][ry + 1][rx]
+    vb[0] = XL(0) + XR(0) + YB(0) + YT(0);
+    vb[1] = XL(1) + XR(1) + YB(2) + YT(2);
+    vb[2] = XL(2) + XR(2) + YB(1) + YT(1);
     // x-face d order: (dEx, dAx, dBx, dAy, dEy); y-face: (dEy, dBy, dAy, dBx, dEx)
-    s.db[0][ry][rx] = xl[3] + xr[3] + yb[7] + yt[7];   // dEx
-    s.db[1][ry][rx] = xl[7] + xr[7] + yb[3] + yt[3];   // dEy
-    s.db[2][ry][rx] = xl[4] + xr[4];                   // dAx
-    s.db[3][ry][rx] = xl[6] + xr[6] + yb[5] + yt[5];   // dAy
-    s.db[4][ry][rx] = xl[5] + xr[5] + yb[6] + yt[6];   // dBx
-    s.db[5][ry][rx] = yb[4] + yt[4];                   // dBy
+    s.db[0][ry][rx] = XL(3) + XR(3) + YB(7) + YT(7);   // dEx
+    s.db[1][ry][rx] = XL(7) + XR(7) + YB(3) + YT(3);   // dEy
+    s.db[2][ry][rx] = XL(4) + XR(4);                   // dAx
+    s.db[3][ry][rx] = XL(6) + XR(6) + YB(5) + YT(5);   // dAy
+    s.db[4][ry][rx] = XL(5) + XR(5) + YB(6) + YT(6);   // dBx
+    s.db[5][ry][rx] = YB(4) + YT(4);                   // dBy
+#undef XL
+#undef XR
+#undef YB
+#undef YT
   }
   __syncthreads();
   // 4. inner cells: lambda^n = lambda^{n+1} + value adjoints + D^T(difference adjoints)
@@ -332,8 +341,8 @@ __global__ void __launch_bounds__(RX * RY) adjoint_step_kernel(const AdjArgs<T> 
             // mu_f = lambda_L/M_L - lambda_R/M_R in the face's (Ez, Hn, Ht) order
             const int hn = isx ? 1 : 2, ht = isx ? 2 : 1;
             T mu[3] = {T(0), T(0), T(0)};
-            if (kind != 1) { mu[0] += s.lam[0][lsy][lsx] / L.eps; mu[1] += s.lam[hn][lsy][lsx]; mu[2] += s.lam[ht][lsy][lsx]; }
-            if (kind != 2) { mu[0] -= s.lam[0][rsy][rsx] / R.eps; mu[1] -= s.lam[hn][rsy][rsx]; mu[2] -= s.lam[ht][rsy][rsx]; }
+            if (kind != 1) { mu[0] += fdv(s.lam[0][lsy][lsx], L.eps); mu[1] += s.lam[hn][lsy][lsx]; mu[2] += s.lam[ht][lsy][lsx]; }
+            if (kind != 2) { mu[0] -= fdv(s.lam[0][rsy][rsx], R.eps); mu[1] -= s.lam[hn][rsy][rsx]; mu[2] -= s.lam[ht][rsy][rsx]; }
             gsum -= double(mu[0] * dd[0] + mu[1] * dd[1] + mu[2] * dd[2]);
           }
           p.grad[slot] += gsum;
@@ -355,12 +364,13 @@ __global__ void probe_grad_kernel(const T *__restrict__ V, T *__restrict__ lam,
   lam[o] = assign ? v : lam[o] + v;
 }
 
-// One block: q(V) = dt sum_P |Omega| Ez^2 in a fixed order, Kahan-added to acc = (sum, comp).
+// q(V) = dt sum_P |Omega| Ez^2: one block, fixed order (deterministic); the running sum over
+// steps is Kahan-compensated in acc = (sum, comp).  1024 threads keep the single block short.
 template <typename T>
 __global__ void objective_kernel(const T *__restrict__ V, const int64_t *__restrict__ off,
                                  const double *__restrict__ w, int64_t np, double dt,
                                  double *__restrict__ acc) {
-  __shared__ double red[256];
+  __shared__ double red[1024];
   double a = 0.0;
   for (int64_t i = threadIdx.x; i < np; i += blockDim.x) {
     const double e = double(V[off[i]]);
@@ -430,9 +440,9 @@ cudaError_t launch_objective(const void *V, const int64_t *off, const double *w,
                              double dt, double *acc, bool fp64, cudaStream_t st) {
   if (np <= 0) return cudaSuccess;
   if (fp64)
-    objective_kernel<double><<<1, 256, 0, st>>>(static_cast<const double *>(V), off, w, np, dt, acc);
+    objective_kernel<double><<<1, 1024, 0, st>>>(static_cast<const double *>(V), off, w, np, dt, acc);
   else
-    objective_kernel<float><<<1, 256, 0, st>>>(static_cast<const float *>(V), off, w, np, dt, acc);
+    objective_kernel<float><<<1, 1024, 0, st>>>(static_cast<const float *>(V), off, w, np, dt, acc);
   return cudaGetLastError();
 }
 

@@ -342,16 +342,17 @@ gks_status gks_set_dt(gks_ctx *ctx, double dt) {
   return GKS_OK;
 }
 
-gks_status gks_step(gks_ctx *ctx, int64_t n_steps) {
-  if (!ctx) return GKS_E_ARG;
-  if (n_steps < 0) return fail(ctx, GKS_E_ARG, "n_steps must be >= 0");
-  if (!ctx->fields_written) return fail(ctx, GKS_E_STATE, "gks_write_fields must come first");
+namespace {
+
+// Advance n_steps over the window [x0, x1) x [y0, y1) (2-D) or the whole mesh.
+gks_status step_impl(gks_ctx *ctx, int64_t n_steps, const int win[4], bool objective) {
   gks::CartStepArgs a;
   a.eps = ctx->eps;
   a.mu = ctx->mu;
   a.src = ctx->src;
   std::memcpy(a.src_box, ctx->src_box, sizeof(a.src_box));
   std::memcpy(a.C, ctx->C, sizeof(a.C));
+  std::memcpy(a.window, win, sizeof(a.window));
   a.c = ctx->c;
   a.flag = ctx->flag;
   for (int64_t n = 0; n < n_steps; ++n) {
@@ -377,12 +378,48 @@ gks_status gks_step(gks_ctx *ctx, int64_t n_steps) {
     if (e != cudaSuccess) return cuda_fail(ctx, e, "step launch");
     ctx->cur ^= 1;
     ctx->step += 1;
-    if (ctx->np > 0) {
+    if (objective && ctx->np > 0) {
       e = gks::launch_objective(ctx->V[ctx->cur], ctx->probe_off, ctx->probe_w, ctx->np, ctx->dt,
                                 ctx->obj, ctx->fp64, ctx->st);
       if (e != cudaSuccess) return cuda_fail(ctx, e, "objective launch");
       ctx->launches += 1;
     }
+  }
+  return GKS_OK;
+}
+
+}  // namespace
+
+gks_status gks_step(gks_ctx *ctx, int64_t n_steps) {
+  if (!ctx) return GKS_E_ARG;
+  if (n_steps < 0) return fail(ctx, GKS_E_ARG, "n_steps must be >= 0");
+  if (!ctx->fields_written) return fail(ctx, GKS_E_STATE, "gks_write_fields must come first");
+  const int win[4] = {0, ctx->g.nx, 0, ctx->g.ny};
+  return step_impl(ctx, n_steps, win, true);
+}
+
+gks_status gks_step_window(gks_ctx *ctx, int64_t n_steps, int64_t x0, int64_t x1, int64_t y0,
+                           int64_t y1) {
+  if (!ctx) return GKS_E_ARG;
+  if (ctx->kind != GKS_CARTESIAN || ctx->dim != 2)
+    return fail(ctx, GKS_E_UNSUPPORTED, "windowed steps need a 2-D Cartesian grid");
+  if (n_steps < 0 || x0 < 0 || y0 < 0 || x1 > ctx->g.nx || y1 > ctx->g.ny || x0 >= x1 || y0 >= y1)
+    return fail(ctx, GKS_E_ARG, "window outside the grid or empty");
+  if (!ctx->fields_written) return fail(ctx, GKS_E_STATE, "gks_write_fields must come first");
+  const int win[4] = {(int)x0, (int)x1, (int)y0, (int)y1};
+  return step_impl(ctx, n_steps, win, false);
+}
+
+gks_status gks_copy_state_rows(gks_ctx *ctx, void *dst, int64_t y0, int64_t y1) {
+  if (!ctx) return GKS_E_ARG;
+  if (!dst || y0 < 0 || y1 > (int64_t)ctx->g.ny * ctx->g.nz || y0 >= y1)
+    return fail(ctx, GKS_E_ARG, "dst is NULL or the row range is empty / outside the grid");
+  const size_t row = ctx->esize * (size_t)ctx->g.pitch;
+  for (int c = 0; c < ctx->ncomp; ++c) {
+    const size_t off = ctx->esize * ((size_t)c * ctx->g.cstride + (size_t)y0 * ctx->g.pitch);
+    GKS_CUDA(cudaMemcpyAsync(static_cast<char *>(dst) + off,
+                             static_cast<const char *>(ctx->V[ctx->cur]) + off,
+                             row * (size_t)(y1 - y0), cudaMemcpyDeviceToDevice, ctx->st));
   }
   return GKS_OK;
 }

@@ -347,13 +347,14 @@ __device__ __forceinline__ void diffs2(const Row2<T> &c, const Row2<T> &dn, cons
 
 template <typename T, bool HAS_MU>
 __global__ void __launch_bounds__(WARPS * 32, GKS_CART2D_MINBLOCKS) cart2d_step_kernel(const Cart2DKernelArgs<T> p,
-                                                                 int nstrips, int rows) {
+                                                                 int nstrips, int rows,
+                                                                 int strip0, int ybeg, int yend) {
   const int lane = threadIdx.x & 31;
   const int wid = blockIdx.x * WARPS + (threadIdx.x >> 5);
-  const int strip = wid % nstrips, chunk = wid / nstrips;
-  const int y0 = chunk * rows;
-  if (y0 >= p.ny) return;                             // whole warp leaves together
-  const int y1 = min(y0 + rows, p.ny);
+  const int strip = strip0 + wid % nstrips, chunk = wid / nstrips;
+  const int y0 = ybeg + chunk * rows;
+  if (y0 >= yend) return;                             // whole warp leaves together
+  const int y1 = min(y0 + rows, yend);
   const int x0 = strip * WCOLS;
   const int X = x0 - 2 + 2 * lane;
   const int xend = min(x0 + WCOLS, p.nx);
@@ -532,22 +533,26 @@ cudaError_t launch_t(const CartGeom &g, const CartStepArgs &a, cudaStream_t st) 
   p.Kx = make_coef<T>(a.C, g.h[0], a.c);
   p.Ky = make_coef<T>(a.C, g.h[1], a.c);
   p.flag = a.flag;
-  // rows per warp: enough warps to fill the GPU (about 20 resident per SM), at most 256 rows
-  const int nstrips = (g.nx + WCOLS - 1) / WCOLS;
-  int rows = g.ny;
+  // window (the whole grid unless a sub-rectangle is asked for): strips covering its columns
+  const int wx0 = a.window[0], wx1 = a.window[1], wy0 = a.window[2], wy1 = a.window[3];
+  const int strip0 = wx0 / WCOLS;
+  const int nstrips = (wx1 - 1) / WCOLS - strip0 + 1;
+  const int wrows = wy1 - wy0;
+  // rows per warp: enough warps to fill the GPU (about 24 resident per SM), at most 256 rows
+  int rows = wrows;
   const int target = 152 * 24;
-  if ((int64_t)nstrips * 1 < target) {
+  if (nstrips < target) {
     const int chunks = (target + nstrips - 1) / nstrips;
-    rows = (g.ny + chunks - 1) / chunks;
+    rows = (wrows + chunks - 1) / chunks;
   }
   rows = rows < 16 ? 16 : (rows > 256 ? 256 : rows);
-  const int nchunks = (g.ny + rows - 1) / rows;
+  const int nchunks = (wrows + rows - 1) / rows;
   const int64_t nwarps = (int64_t)nstrips * nchunks;
   const int grid = (int)((nwarps + WARPS - 1) / WARPS);
   if (a.mu)
-    cart2d_step_kernel<T, true><<<grid, WARPS * 32, 0, st>>>(p, nstrips, rows);
+    cart2d_step_kernel<T, true><<<grid, WARPS * 32, 0, st>>>(p, nstrips, rows, strip0, wy0, wy1);
   else
-    cart2d_step_kernel<T, false><<<grid, WARPS * 32, 0, st>>>(p, nstrips, rows);
+    cart2d_step_kernel<T, false><<<grid, WARPS * 32, 0, st>>>(p, nstrips, rows, strip0, wy0, wy1);
   return cudaGetLastError();
 }
 

@@ -40,6 +40,7 @@ struct CartStepArgs {
   double C[5];          // C1..C5
   double c;             // lattice speed
   int *flag;            // non-finite flag (device)
+  int window[4];        // x0, x1, y0, y1 (half open) of the cells to advance (2-D)
 };
 
 // Tetrahedral mesh geometry on the host (FP64; cells in internal Morton order).
