@@ -159,9 +159,12 @@ gks_status gks_state_layout(const gks_ctx *ctx, int64_t *elements, int64_t *byte
  * asynchronous on the context stream. */
 gks_status gks_copy_state(gks_ctx *ctx, void *dst);
 
-/* Copy only the rows [y0, y1) (row index y + ny*z) of every component of the current state into
- * dst at the same offsets of the internal layout (device, gks_state_layout bytes); asynchronous. */
-gks_status gks_copy_state_rows(gks_ctx *ctx, void *dst, int64_t y0, int64_t y1);
+/* Copy only the box of columns [x0, x1) and rows [y0, y1) (row index y + ny*z) of every
+ * component of the current state into dst at the same offsets of the internal layout (device,
+ * gks_state_layout bytes; entries outside the box are left as they are); asynchronous.
+ * GKS_E_ARG for an empty box or one outside the grid. */
+gks_status gks_copy_state_box(gks_ctx *ctx, void *dst, int64_t x0, int64_t x1, int64_t y0,
+                              int64_t y1);
 
 /* Replace the current state by src (device, internal layout) and set the step counter, so that
  * the time is t0 + step * dt (checkpoint restart); asynchronous. */

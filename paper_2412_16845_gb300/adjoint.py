@@ -15,7 +15,7 @@ import math
 import numpy as np
 
 from .gks import (GKSSolver, gks_adjoint_seed, gks_adjoint_step, gks_copy_state,
-                  gks_copy_state_rows, gks_load_state, gks_objective, gks_set_objective,
+                  gks_copy_state_box, gks_load_state, gks_objective, gks_set_objective,
                   gks_state_layout, gks_step_window)
 
 
@@ -40,17 +40,27 @@ class DesignProblem:
         self.checkpoints = None
         self.final = None
         self.eps_design = None
-        # the adjoint reads states only on the design cells (two-cell stencil) and the probe:
-        # rows [ry0, ry1) are stored; a segment of K steps is recomputed on the design box
-        # widened by 2 + 2K cells (its domain of dependence), clipped to the grid
+        # the adjoint reads states only on the design cells and their two-cell stencil and on
+        # the probe: that box (cbox) is what is stored of a recomputed state.  Step m of a
+        # segment of k steps is recomputed on cbox widened by 2 (k - m) cells, its domain of
+        # dependence, so the window shrinks by the stencil radius every step.
         nx, ny = w.n
+        self.nx, self.ny = nx, ny
+        self.per = (w.bc[0] == "periodic", w.bc[2] == "periodic")
         cells = np.concatenate([self.design, np.asarray(w.probe, dtype=np.int64)])
         xs, ys = cells % nx, cells // nx
-        self.box = (int(xs.min()), int(xs.max()) + 1, int(ys.min()), int(ys.max()) + 1)
-        self.ry0, self.ry1 = max(0, self.box[2] - 2), min(ny, self.box[3] + 2)
-        m = 2 + 2 * self.K
-        self.win = (max(0, self.box[0] - m), min(nx, self.box[1] + m),
-                    max(0, self.box[2] - m), min(ny, self.box[3] + m))
+        self.cbox = (max(0, int(xs.min()) - 2), min(nx, int(xs.max()) + 3),
+                     max(0, int(ys.min()) - 2), min(ny, int(ys.max()) + 3))
+
+    def _window(self, r):
+        """cbox widened by r cells, clipped to the grid (a whole periodic axis once it wraps)."""
+        x0, x1, y0, y1 = self.cbox
+        x0, x1, y0, y1 = x0 - r, x1 + r, y0 - r, y1 + r
+        if x0 < 0 or x1 > self.nx:
+            x0, x1 = (0, self.nx) if self.per[0] else (max(0, x0), min(self.nx, x1))
+        if y0 < 0 or y1 > self.ny:
+            y0, y1 = (0, self.ny) if self.per[1] else (max(0, y0), min(self.ny, y1))
+        return x0, x1, y0, y1
 
     def _buf(self):
         return self.torch.empty(self.elems, dtype=self.dtype, device="cuda")
@@ -96,10 +106,10 @@ class DesignProblem:
             # recompute V^s .. V^e of this segment
             gks_load_state(self.ctx, ckb.data_ptr(), s)
             states = [ckb]
-            for _ in range(e - s):
-                gks_step_window(self.ctx, 1, *self.win)
+            for m in range(1, e - s + 1):
+                gks_step_window(self.ctx, 1, *self._window(2 * (e - s - m)))
                 b = self._buf()
-                gks_copy_state_rows(self.ctx, b.data_ptr(), self.ry0, self.ry1)
+                gks_copy_state_box(self.ctx, b.data_ptr(), *self.cbox)
                 states.append(b)
             for n in range(e - 1, s - 1, -1):
                 gks_adjoint_step(self.ctx, states[n - s].data_ptr(), states[n - s + 1].data_ptr(),

@@ -410,17 +410,16 @@ gks_status gks_step_window(gks_ctx *ctx, int64_t n_steps, int64_t x0, int64_t x1
   return step_impl(ctx, n_steps, win, false);
 }
 
-gks_status gks_copy_state_rows(gks_ctx *ctx, void *dst, int64_t y0, int64_t y1) {
+gks_status gks_copy_state_box(gks_ctx *ctx, void *dst, int64_t x0, int64_t x1, int64_t y0,
+                              int64_t y1) {
   if (!ctx) return GKS_E_ARG;
-  if (!dst || y0 < 0 || y1 > (int64_t)ctx->g.ny * ctx->g.nz || y0 >= y1)
-    return fail(ctx, GKS_E_ARG, "dst is NULL or the row range is empty / outside the grid");
-  const size_t row = ctx->esize * (size_t)ctx->g.pitch;
-  for (int c = 0; c < ctx->ncomp; ++c) {
-    const size_t off = ctx->esize * ((size_t)c * ctx->g.cstride + (size_t)y0 * ctx->g.pitch);
-    GKS_CUDA(cudaMemcpyAsync(static_cast<char *>(dst) + off,
-                             static_cast<const char *>(ctx->V[ctx->cur]) + off,
-                             row * (size_t)(y1 - y0), cudaMemcpyDeviceToDevice, ctx->st));
-  }
+  if (ctx->kind != GKS_CARTESIAN) return fail(ctx, GKS_E_UNSUPPORTED, "a Cartesian grid is required");
+  if (!dst || x0 < 0 || x1 > ctx->g.nx || x0 >= x1 || y0 < 0 ||
+      y1 > (int64_t)ctx->g.ny * ctx->g.nz || y0 >= y1)
+    return fail(ctx, GKS_E_ARG, "dst is NULL or the box is empty / outside the grid");
+  GKS_CUDA(gks::launch_copy_box(ctx->V[ctx->cur], dst, ctx->ncomp, ctx->g.cstride, ctx->g.pitch,
+                                 (int)x0, (int)x1, y0, y1, ctx->fp64, ctx->st));
+  ctx->launches += 1;
   return GKS_OK;
 }
 
@@ -471,10 +470,24 @@ gks_status gks_set_objective(gks_ctx *ctx, const int64_t *probe, int64_t np, con
   const gks::CartGeom &g = ctx->g;
   std::vector<int64_t> off(np);
   std::vector<double> w(np, g.h[0] * g.h[1]);
+  int pbox[4] = {g.nx, -1, g.ny, -1};
   for (int64_t i = 0; i < np; ++i) {
     const int64_t c = probe[i];
     if (c < 0 || c >= ctx->ncell) return fail(ctx, GKS_E_ARG, "probe cell out of range");
     off[i] = (c / g.nx) * g.pitch + c % g.nx;          // Ez component of the state layout
+    const int x = (int)(c % g.nx), y = (int)(c / g.nx);
+    pbox[0] = std::min(pbox[0], x); pbox[1] = std::max(pbox[1], x + 1);
+    pbox[2] = std::min(pbox[2], y); pbox[3] = std::max(pbox[3], y + 1);
+  }
+  // the same weights over the probe's bounding box (zero off the probe), for the adjoint
+  std::vector<double> wbox;
+  if (np > 0) {
+    const int bw = pbox[1] - pbox[0];
+    wbox.assign((size_t)bw * (pbox[3] - pbox[2]), 0.0);
+    for (int64_t i = 0; i < np; ++i) {
+      const int x = (int)(probe[i] % g.nx), y = (int)(probe[i] / g.nx);
+      wbox[(size_t)(y - pbox[2]) * bw + (x - pbox[0])] += w[i];
+    }
   }
   std::vector<int32_t> slot((size_t)g.cstride, -1);
   int box[4] = {g.nx, -1, g.ny, -1};
@@ -488,16 +501,20 @@ gks_status gks_set_objective(gks_ctx *ctx, const int64_t *probe, int64_t np, con
     box[0] = std::min(box[0], x); box[1] = std::max(box[1], x);
     box[2] = std::min(box[2], y); box[3] = std::max(box[3], y);
   }
-  void *bufs[] = {ctx->probe_off, ctx->probe_w, ctx->dslot};
+  void *bufs[] = {ctx->probe_off, ctx->probe_w, ctx->probe_box_w, ctx->dslot};
   for (void *b : bufs)
     if (b) GKS_CUDA(cudaFreeAsync(b, ctx->st));
-  ctx->probe_off = nullptr; ctx->probe_w = nullptr; ctx->dslot = nullptr;
+  ctx->probe_off = nullptr; ctx->probe_w = nullptr; ctx->probe_box_w = nullptr; ctx->dslot = nullptr;
   gks_status s;
   if ((s = upload_vec(ctx, off, &ctx->probe_off)) != GKS_OK ||
-      (s = upload_vec(ctx, w, &ctx->probe_w)) != GKS_OK || (s = upload_vec(ctx, slot, &ctx->dslot)) != GKS_OK)
+      (s = upload_vec(ctx, w, &ctx->probe_w)) != GKS_OK ||
+      (s = upload_vec(ctx, wbox, &ctx->probe_box_w)) != GKS_OK ||
+      (s = upload_vec(ctx, slot, &ctx->dslot)) != GKS_OK)
     return s;
-  if (!ctx->obj && (s = alloc_dev(ctx, (void **)&ctx->obj, 2 * sizeof(double))) != GKS_OK) return s;
-  GKS_CUDA(cudaMemsetAsync(ctx->obj, 0, 2 * sizeof(double), ctx->st));
+  std::memcpy(ctx->pbox, pbox, sizeof(pbox));
+  if (!ctx->obj && (s = alloc_dev(ctx, (void **)&ctx->obj, gks::kObjWords * sizeof(double))) != GKS_OK)
+    return s;
+  GKS_CUDA(cudaMemsetAsync(ctx->obj, 0, gks::kObjWords * sizeof(double), ctx->st));
   GKS_CUDA(cudaStreamSynchronize(ctx->st));   // the host vectors go out of scope
   ctx->np = np;
   ctx->nd = nd;
@@ -579,13 +596,11 @@ gks_status gks_adjoint_step(gks_ctx *ctx, const void *state_n, const void *state
   std::memcpy(a.dbox, ctx->dbox, sizeof(a.dbox));
   std::memcpy(a.C, ctx->C, sizeof(a.C));
   a.c = ctx->c;
+  a.probe_w = add_probe && ctx->np > 0 ? ctx->probe_box_w : nullptr;
+  std::memcpy(a.pbox, ctx->pbox, sizeof(a.pbox));
+  a.dt = ctx->dt;
   GKS_CUDA(gks::launch_adjoint_step(ctx->g, a, ctx->fp64, ctx->st));
-  ctx->launches += 1;
-  if (add_probe && ctx->np > 0) {
-    GKS_CUDA(gks::launch_probe_grad(state_n, adj_out, ctx->probe_off, ctx->probe_w, ctx->np,
-                                    ctx->dt, false, ctx->fp64, ctx->st));
-    ctx->launches += 1;
-  }
+  ctx->launches += a.grad && ctx->dbox[1] > ctx->dbox[0] ? 2 : 1;
   return GKS_OK;
 }
 
@@ -616,7 +631,7 @@ void gks_destroy(gks_ctx *ctx) {
   const gks::TetDev &t = ctx->tet;
   void *bufs[] = {ctx->V[0], ctx->V[1], ctx->eps, ctx->mu, ctx->src, ctx->flag, ctx->red,
                   ctx->staging, t.perm, t.vol, t.cnb, t.cface, t.csign, t.cw, t.fL, t.fR, t.fT,
-                  t.farea, t.fdL, t.fdR, t.Gscratch, t.Fscratch, ctx->probe_off, ctx->probe_w,
+                  t.farea, t.fdL, t.fdR, t.Gscratch, t.Fscratch, ctx->probe_off, ctx->probe_w, ctx->probe_box_w,
                   ctx->dslot, ctx->obj};
   for (void *p : bufs)
     if (p) cudaFreeAsync(p, ctx->st);

@@ -538,14 +538,15 @@ cudaError_t launch_t(const CartGeom &g, const CartStepArgs &a, cudaStream_t st) 
   const int strip0 = wx0 / WCOLS;
   const int nstrips = (wx1 - 1) / WCOLS - strip0 + 1;
   const int wrows = wy1 - wy0;
-  // rows per warp: enough warps to fill the GPU (about 24 resident per SM), at most 256 rows
+  // rows per warp: enough warps to fill the GPU (about 24 resident per SM), 4 to 256 rows (a
+  // warp spends about two rows of work on its prologue, so small windows take short chunks)
   int rows = wrows;
   const int target = 152 * 24;
   if (nstrips < target) {
     const int chunks = (target + nstrips - 1) / nstrips;
     rows = (wrows + chunks - 1) / chunks;
   }
-  rows = rows < 16 ? 16 : (rows > 256 ? 256 : rows);
+  rows = rows < 4 ? 4 : (rows > 256 ? 256 : rows);
   const int nchunks = (wrows + rows - 1) / rows;
   const int64_t nwarps = (int64_t)nstrips * nchunks;
   const int grid = (int)((nwarps + WARPS - 1) / WARPS);

@@ -98,6 +98,9 @@ struct AdjointArgs {
   const int32_t *dslot;     // design slot per cell (-1 elsewhere), state layout
   double *grad;             // [nd], accumulated
   int dbox[4];              // design box x0, x1, y0, y1 (half open)
+  const double *probe_w;    // probe weights |Omega_i| over the probe box (row-major), or null
+  int pbox[4];              // probe box x0, x1, y0, y1 (half open)
+  double dt;
   double C[5];
   double c;
 };
@@ -105,6 +108,9 @@ cudaError_t launch_adjoint_step(const CartGeom &g, const AdjointArgs &a, bool fp
                                 cudaStream_t st);
 cudaError_t launch_probe_grad(const void *V, void *lam, const int64_t *off, const double *w,
                               int64_t np, double dt, bool assign, bool fp64, cudaStream_t st);
+// The objective buffer: (sum, Kahan compensation), kObjParts per-block partials and a ticket.
+constexpr int kObjParts = 64;
+constexpr int kObjWords = 2 + kObjParts + 1;
 cudaError_t launch_objective(const void *V, const int64_t *off, const double *w, int64_t np,
                              double dt, double *acc, bool fp64, cudaStream_t st);
 
@@ -118,6 +124,9 @@ cudaError_t launch_user_to_cart(const CartGeom &g, int ncomp, const double *user
 cudaError_t launch_cart_to_user(const CartGeom &g, int ncomp, const void *src, double *user,
                                 bool fp64, cudaStream_t st);
 cudaError_t launch_fill(void *dst, int64_t n, double value, bool fp64, cudaStream_t st);
+// dst = src on the box of columns [x0, x1) x rows [y0, y1) of every component.
+cudaError_t launch_copy_box(const void *src, void *dst, int ncomp, int64_t cstride, int64_t pitch,
+                            int x0, int x1, int64_t y0, int64_t y1, bool fp64, cudaStream_t st);
 // Energy 1/2 sum |Omega| (eps |E|^2 + mu |H|^2) into *out (device double), FP64 accumulation.
 cudaError_t launch_cart_energy(const CartGeom &g, int ncomp, const void *V, const void *eps,
                                const void *mu, bool fp64, double *partials, int npart,
@@ -158,6 +167,8 @@ struct gks_ctx {
   int64_t *probe_off = nullptr;   // [np] state offsets of the probe cells
   double *probe_w = nullptr;      // [np] |Omega_i|
   int64_t np = 0;
+  double *probe_box_w = nullptr;  // probe weights over the probe box (row-major)
+  int pbox[4] = {0, 0, 0, 0};     // probe box x0, x1, y0, y1 (half open)
   int32_t *dslot = nullptr;       // state layout, design slot or -1
   int64_t nd = 0;
   int dbox[4] = {0, 0, 0, 0};

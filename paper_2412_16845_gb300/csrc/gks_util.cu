@@ -2,6 +2,8 @@
 // structure-of-arrays state, fills, and the FP64 energy reduction.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "gks_internal.h"
 
 namespace gks {
@@ -32,6 +34,21 @@ __global__ void cart_to_user_kernel(const T *__restrict__ src, double *__restric
     const int64_t x = cell % nx, yz = cell / nx;
     const int64_t y = yz % ny, z = yz / ny;
     user[i] = double(src[c * cstride + (z * ny + y) * pitch + x]);
+  }
+}
+
+// Copy of a box of columns [x0, x0+w) x rows [y0, y0+h) of every component (same offsets in
+// src and dst); consecutive threads take consecutive columns of a row.
+template <typename T>
+__global__ void copy_box_kernel(const T *__restrict__ src, T *__restrict__ dst, int64_t cstride,
+                                int64_t pitch, int x0, int w, int64_t y0, int64_t h, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / w;
+    const int x = (int)(i - r * w);
+    const int64_t c = r / h, y = r - c * h;
+    const int64_t o = c * cstride + (y0 + y) * pitch + x0 + x;
+    dst[o] = src[o];
   }
 }
 
@@ -116,6 +133,22 @@ cudaError_t launch_cart_to_user(const CartGeom &g, int ncomp, const void *src, d
   else
     cart_to_user_kernel<float><<<grid_for(total), 256, 0, st>>>(
         static_cast<const float *>(src), user, g.nx, g.ny, g.nz, g.pitch, g.cstride, ncomp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy_box(const void *src, void *dst, int ncomp, int64_t cstride, int64_t pitch,
+                            int x0, int x1, int64_t y0, int64_t y1, bool fp64, cudaStream_t st) {
+  const int64_t n = (int64_t)ncomp * (y1 - y0) * (x1 - x0);
+  if (n <= 0) return cudaSuccess;
+  const int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
+  if (fp64)
+    copy_box_kernel<double><<<blocks, 256, 0, st>>>(static_cast<const double *>(src),
+                                                    static_cast<double *>(dst), cstride, pitch, x0,
+                                                    x1 - x0, y0, y1 - y0, n);
+  else
+    copy_box_kernel<float><<<blocks, 256, 0, st>>>(static_cast<const float *>(src),
+                                                   static_cast<float *>(dst), cstride, pitch, x0,
+                                                   x1 - x0, y0, y1 - y0, n);
   return cudaGetLastError();
 }
 

@@ -69,7 +69,8 @@ SIGNATURES = {
     "gks_objective": (ctypes.c_int, [_CTX, _D]),
     "gks_state_layout": (ctypes.c_int, [_CTX, _I64, _I64]),
     "gks_copy_state": (ctypes.c_int, [_CTX, ctypes.c_void_p]),
-    "gks_copy_state_rows": (ctypes.c_int, [_CTX, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64]),
+    "gks_copy_state_box": (ctypes.c_int, [_CTX, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                          ctypes.c_int64, ctypes.c_int64]),
     "gks_step_window": (ctypes.c_int, [_CTX, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
                                        ctypes.c_int64, ctypes.c_int64]),
     "gks_load_state": (ctypes.c_int, [_CTX, ctypes.c_void_p, ctypes.c_int64]),
@@ -195,8 +196,8 @@ def gks_copy_state(ctx, dst_ptr):
     _check(ctx, load_library().gks_copy_state(ctx, dst_ptr))
 
 
-def gks_copy_state_rows(ctx, dst_ptr, y0, y1):
-    _check(ctx, load_library().gks_copy_state_rows(ctx, dst_ptr, int(y0), int(y1)))
+def gks_copy_state_box(ctx, dst_ptr, x0, x1, y0, y1):
+    _check(ctx, load_library().gks_copy_state_box(ctx, dst_ptr, int(x0), int(x1), int(y0), int(y1)))
 
 
 def gks_step_window(ctx, n_steps, x0, x1, y0, y1):

@@ -70,7 +70,7 @@ def smoothed_noise(rng: np.random.Generator, shape, sigma_cells) -> np.ndarray:
         sh = [1] * len(shape)
         sh[ax] = g.size
         filt = filt * g.reshape(sh)
-    p = np.fft.irfftn(W * filt, s=shape)
+    p = np.fft.irfftn(W * filt, s=shape, axes=tuple(range(len(shape))))
     p = (p - p.min()) / (p.max() - p.min())
     return p
 

@@ -32,7 +32,7 @@ def _grid(nx, ny, bc, seed):
 @pytest.mark.parametrize("bc", [("nrbc",) * 4, ("periodic",) * 4,
                                 ("periodic", "periodic", "nrbc", "nrbc")])
 @pytest.mark.parametrize("kappa", [0.0, 0.05, 1.0])
-@pytest.mark.parametrize("n", [(37, 23), (5, 3)])
+@pytest.mark.parametrize("n", [(37, 23), (5, 3), (131, 70)])
 def test_transpose_identity(bc, kappa, n):
     import torch
     w = _grid(n[0], n[1], bc, 3 + n[0])
