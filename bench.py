@@ -62,6 +62,22 @@ def _profiled_traffic():
     return float(m.group(1))
 
 
+def max_over_ranks(x, world, device="cuda"):
+    """The largest of the ranks' values of x (every rank gets it); x itself when world == 1."""
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(cells_per_rank, steps, ms_max, world):
+    """Whole-job cell-updates per second (in G): every rank advanced cells_per_rank cells by
+    `steps` steps, and the job took the slowest rank's time ms_max."""
+    return world * cells_per_rank * steps / (ms_max * 1e-3) / 1e9
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
 
@@ -199,6 +215,10 @@ def main():
     ap.add_argument("--n3", type=int, default=256)
     ap.add_argument("--steps3", type=int, default=100)
     ap.add_argument("--no-err3", dest="err3", action="store_false", default=True)
+    ap.add_argument("--no-tets", dest="with_tets", action="store_false", default=True)
+    ap.add_argument("--m4", type=int, default=64)
+    ap.add_argument("--steps4", type=int, default=100)
+    ap.add_argument("--no-err4", dest="err4", action="store_false", default=True)
     ap.add_argument("--no-adjoint", dest="with_adjoint", action="store_false", default=True)
     ap.add_argument("--n5", type=int, default=2048)
     args = ap.parse_args()
@@ -256,11 +276,8 @@ def main():
     clocks = sampler.stop() if rank == 0 else None
     ms = e0.elapsed_time(e1)
     launches = s32.launch_count() - L0
-    t_max = torch.tensor([ms], device="cuda", dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    ms = float(t_max.item())
-    value = world * ncell * args.steps / (ms * 1e-3) / 1e9
+    ms = max_over_ranks(ms, world)
+    value = job_throughput(ncell, args.steps, ms, world)
     ms_step = ms / args.steps
 
     # ---------------- FP64 path, FP32-vs-FP64 error after the configuration's step count
@@ -300,12 +317,8 @@ def main():
     s32.write_fields(hin)
     s32.step(args.steps)
     s32.read_fields(hout)
-    e2e_s = time.perf_counter() - t0
-    tt = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-    e2e_s = float(tt.item())
-    e2e = world * ncell * args.steps / e2e_s / 1e9
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
+    e2e = job_throughput(ncell, args.steps, e2e_s * 1e3, world)
     s32.close()
 
     # ---------------- 3-D sphere workload (256^3): FP32 and FP64, error after its 500 steps
@@ -350,6 +363,49 @@ def main():
                  "fp32_speedup": ms3_64 / ms3, "fp32_vs_fp64_rel_l2_after_500": err3,
                  "hbm_frac_fp32": 52 * n3 / (ms3 * 1e-3) / 1e9 / _peaks()[0],
                  "algorithmic_bytes_per_cell_step": 52}
+
+    # ---------------- tetrahedral sphere workload (64^3 x 6 Kuhn tets, jittered): FP32 and FP64
+    tets = None
+    if args.with_tets:
+        w4 = wl.config4_tets(m=args.m4, steps=500)
+        n4 = int(w4.tet.shape[0])
+        q32 = GKSSolver.from_tet_workload(w4, precision="fp32", stream=sptr)
+        q32.step(3)
+        q32.sync()
+        h0 = torch.cuda.Event(enable_timing=True)
+        h1 = torch.cuda.Event(enable_timing=True)
+        k4 = args.steps4
+        h0.record(stream)
+        q32.step(k4)
+        h1.record(stream)
+        torch.cuda.synchronize()
+        ms4 = h0.elapsed_time(h1) / k4
+        q64 = GKSSolver.from_tet_workload(w4, precision="fp64", stream=sptr)
+        q64.step(1)
+        q64.sync()
+        h0.record(stream)
+        q64.step(10)
+        h1.record(stream)
+        torch.cuda.synchronize()
+        ms4_64 = h0.elapsed_time(h1) / 10
+        q32.close()
+        q64.close()
+        err4 = None
+        if args.err4:
+            b32 = GKSSolver.from_tet_workload(w4, precision="fp32", stream=sptr)
+            b64 = GKSSolver.from_tet_workload(w4, precision="fp64", stream=sptr)
+            b32.step(500)
+            b64.step(500)
+            o32, o64 = b32.read_fields(), b64.read_fields()
+            err4 = float(np.sqrt(np.sum((o32 - o64) ** 2) / np.sum(o64 ** 2)))
+            b32.close()
+            b64.close()
+        tets = {"workload": f"tets_sphere_{args.m4}", "tets": n4, "steps_timed": k4,
+                "value_fp32": n4 / (ms4 * 1e-3) / 1e9, "ms_per_step_fp32": ms4,
+                "value_fp64": n4 / (ms4_64 * 1e-3) / 1e9, "ms_per_step_fp64": ms4_64,
+                "fp32_speedup": ms4_64 / ms4, "fp32_vs_fp64_rel_l2_after_500": err4,
+                "algorithmic_bytes_per_tet_step": 229,
+                "hbm_frac_fp32": 229 * n4 / (ms4 * 1e-3) / 1e9 / _peaks()[0]}
 
     # ---------------- adjoint: eps-gradient of the probe objective, 2048^2 design workload
     adj = None
@@ -413,6 +469,7 @@ def main():
                     "definition": "write_fields(pinned FP64) + step(K) + read_fields, wall clock"},
             "gpu_launches": int(launches),
             "maxwell3d": three,
+            "tets": tets,
             "adjoint": adj,
             "clocks": clocks,
         }

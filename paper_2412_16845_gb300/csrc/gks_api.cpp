@@ -125,6 +125,7 @@ gks_status setup_tets(gks_ctx *ctx, const gks_mesh_desc *d) {
   g.nt = h.nt;
   g.nf = h.nf;
   if ((s = upload_vec(ctx, h.perm, &g.perm)) != GKS_OK || (s = upload_vec(ctx, h.vol, &g.vol)) != GKS_OK ||
+      (s = upload_vec(ctx, h.ivol, &g.ivol)) != GKS_OK ||
       (s = upload_vec(ctx, h.cnb, &g.cnb)) != GKS_OK || (s = upload_vec(ctx, h.cface, &g.cface)) != GKS_OK ||
       (s = upload_vec(ctx, h.csign, &g.csign)) != GKS_OK || (s = upload_vec(ctx, h.cw, &g.cw)) != GKS_OK ||
       (s = upload_vec(ctx, h.fL, &g.fL)) != GKS_OK || (s = upload_vec(ctx, h.fR, &g.fR)) != GKS_OK ||
@@ -630,7 +631,7 @@ void gks_destroy(gks_ctx *ctx) {
   if (!ctx) return;
   const gks::TetDev &t = ctx->tet;
   void *bufs[] = {ctx->V[0], ctx->V[1], ctx->eps, ctx->mu, ctx->src, ctx->flag, ctx->red,
-                  ctx->staging, t.perm, t.vol, t.cnb, t.cface, t.csign, t.cw, t.fL, t.fR, t.fT,
+                  ctx->staging, t.perm, t.vol, t.ivol, t.cnb, t.cface, t.csign, t.cw, t.fL, t.fR, t.fT,
                   t.farea, t.fdL, t.fdR, t.Gscratch, t.Fscratch, ctx->probe_off, ctx->probe_w, ctx->probe_box_w,
                   ctx->dslot, ctx->obj};
   for (void *p : bufs)

@@ -83,12 +83,23 @@ __device__ __forceinline__ void to_global(const T loc[6], T glob[6]) {
     for (int k = 0; k < 3; ++k) glob[3 * b + ax[k]] = sg[k] * loc[3 * b + k];
 }
 
-// Interior face of frame F between cells L (low side) and R (high side), along +axis.
-template <typename T, typename F>
+// Reciprocals: FP32 uses the fast hardware reciprocal (about 1 ulp), FP64 divides.
+__device__ __forceinline__ float rcp3(float x) { return __fdividef(1.f, x); }
+__device__ __forceinline__ double rcp3(double x) { return 1.0 / x; }
+__device__ __forceinline__ float rcp3x2(float x) { return __fdividef(2.f, x); }
+__device__ __forceinline__ double rcp3x2(double x) { return 2.0 / x; }
+
+// Interior face of frame F between cells L (low side) and R (high side), along +axis.  Without
+// mu the sums-and-differences form flux3_mu1 is used.
+template <typename T, typename F, bool HAS_MU>
 __device__ __forceinline__ void interior_face(const Cell3<T> &L, const Cell3<T> &R, T halfh,
-                                              const K3<T> &K, T phi[6]) {
+                                              const K3<T> &K, const F3K<T> &FK, T phi[6]) {
   T loc[6];
-  flux3<T, false>(to_local<T, F>(L, halfh), to_local<T, F>(R, -halfh), K, loc);
+  if (HAS_MU)
+    flux3<T, false>(to_local<T, F>(L, halfh), to_local<T, F>(R, -halfh), K, loc);
+  else
+    flux3_mu1<T>(to_local<T, F>(L, halfh), to_local<T, F>(R, -halfh), FK, rcp3x2(L.eps + R.eps),
+                 loc);
   to_global<T, F>(loc, phi);
 }
 
@@ -129,6 +140,7 @@ struct Cart3DArgs {
   int per[3];
   T inv2h[3], halfh[3];
   K3<T> K[3];
+  F3K<T> FK[3];
   int zchunk;
   int *flag;
 };
@@ -268,7 +280,7 @@ __global__ void __launch_bounds__(NTH, sizeof(T) == 4 ? 2 : 1)
     if (z0 == 0 && znr)
       low_boundary_face<T, FrameZm>(c0, p.halfh[2], p.K[2], fzb);
     else
-      interior_face<T, FrameZp>(cm1, c0, p.halfh[2], p.K[2], fzb);
+      interior_face<T, FrameZp, HAS_MU>(cm1, c0, p.halfh[2], p.K[2], p.FK[2], fzb);
     const int gs = z0 & 1;
 #pragma unroll
     for (int a = 0; a < 3; ++a)
@@ -296,8 +308,8 @@ __global__ void __launch_bounds__(NTH, sizeof(T) == 4 ? 2 : 1)
       if (p.src && x >= p.sx0 && x < p.sx1 && y >= p.sy0 && y < p.sy1 && z - 1 >= p.sz0 &&
           z - 1 < p.sz1)
         d[2] -= p.src_amp * p.src[o];
-      const T ie = T(1) / s.V[sl][6][ty + 1][tx + 1];
-      const T im = HAS_MU ? T(1) / s.V[sl][7][ty + 1][tx + 1] : T(1);
+      const T ie = rcp3(s.V[sl][6][ty + 1][tx + 1]);
+      const T im = HAS_MU ? rcp3(s.V[sl][7][ty + 1][tx + 1]) : T(1);
       T sum = T(0);
 #pragma unroll
       for (int c = 0; c < 6; ++c) {
@@ -341,7 +353,7 @@ __global__ void __launch_bounds__(NTH, sizeof(T) == 4 ? 2 : 1)
         if (xlo)
           low_boundary_face<T, FrameXm>(cr, p.halfh[0], p.K[0], fx);
         else
-          interior_face<T, FrameXp>(c0, cr, p.halfh[0], p.K[0], fx);
+          interior_face<T, FrameXp, HAS_MU>(c0, cr, p.halfh[0], p.K[0], p.FK[0], fx);
       }
     }
     if (need_yface) {
@@ -355,7 +367,7 @@ __global__ void __launch_bounds__(NTH, sizeof(T) == 4 ? 2 : 1)
         if (ylo)
           low_boundary_face<T, FrameYm>(cu, p.halfh[1], p.K[1], fy);
         else
-          interior_face<T, FrameYp>(c0, cu, p.halfh[1], p.K[1], fy);
+          interior_face<T, FrameYp, HAS_MU>(c0, cu, p.halfh[1], p.K[1], p.FK[1], fy);
       }
     }
     if (inner) {
@@ -364,7 +376,7 @@ __global__ void __launch_bounds__(NTH, sizeof(T) == 4 ? 2 : 1)
       } else {
         Cell3<T> c1;
         cell_from<T>(s, s1, ty + 1, tx + 1, g1, c1);
-        interior_face<T, FrameZp>(c0, c1, p.halfh[2], p.K[2], fzt);
+        interior_face<T, FrameZp, HAS_MU>(c0, c1, p.halfh[2], p.K[2], p.FK[2], fzt);
       }
     } else {
 #pragma unroll
@@ -421,17 +433,41 @@ cudaError_t launch3_t(const CartGeom &g, const CartStepArgs &a, cudaStream_t st)
     p.inv2h[d] = T(0.5 / g.h[d]);
     p.halfh[d] = T(0.5 * g.h[d]);
     p.K[d] = make_k3<T>(a.C, g.h[d], a.c);
+    p.FK[d] = make_f3k<T>(a.C, g.h[d], a.c);
   }
   p.flag = a.flag;
   const int gx = (g.nx + BX - 3) / (BX - 2), gy = (g.ny + BY - 3) / (BY - 2);
-  // z chunks: enough CTAs for about two waves of two CTAs per SM
-  int zchunks = (2 * 2 * 152 + gx * gy - 1) / (gx * gy);
-  if (zchunks < 1) zchunks = 1;
-  if (zchunks > g.nz) zchunks = g.nz;
-  p.zchunk = (g.nz + zchunks - 1) / zchunks;
-  if (p.zchunk < 8 && g.nz >= 8) p.zchunk = 8;
-  zchunks = (g.nz + p.zchunk - 1) / p.zchunk;
   const int smem = (int)sizeof(Smem3<T>);
+  // z chunks: a CTA marches zchunk planes after a two-plane prologue.  Pick the chunk count
+  // that fills whole waves of resident CTAs best, counting the prologue as lost work.
+  static int resident[2][2] = {{0, 0}, {0, 0}};   // [fp64][has_mu]
+  int &res = resident[sizeof(T) == 8][a.mu ? 1 : 0];
+  if (!res) {
+    int dev = 0, sms = 0, bps = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (a.mu) {
+      cudaFuncSetAttribute(cart3d_step_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, cart3d_step_kernel<T, true>, NTH, smem);
+    } else {
+      cudaFuncSetAttribute(cart3d_step_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, cart3d_step_kernel<T, false>, NTH, smem);
+    }
+    res = sms * (bps > 0 ? bps : 1);
+  }
+  const int64_t tiles = (int64_t)gx * gy;
+  int zchunks = 1;
+  double best = -1.0;
+  for (int zc = 1; zc <= 64 && zc <= g.nz; ++zc) {
+    const int len = (g.nz + zc - 1) / zc;
+    const int nzc = (g.nz + len - 1) / len;
+    const int64_t ctas = tiles * nzc;
+    const double waves = (double)((ctas + res - 1) / res);
+    const double eff = (double)ctas / (waves * res) * (double)g.nz / (double)(nzc * (len + 2));
+    if (eff > best + 1e-9) { best = eff; zchunks = nzc; }
+  }
+  p.zchunk = (g.nz + zchunks - 1) / zchunks;
+  zchunks = (g.nz + p.zchunk - 1) / p.zchunk;
   dim3 grid(gx, gy, zchunks);
   if (a.mu) {
     cudaFuncSetAttribute(cart3d_step_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,

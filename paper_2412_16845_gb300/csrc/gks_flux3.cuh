@@ -139,6 +139,69 @@ __device__ __forceinline__ void flux3(const Side3<T> &l, const Side3<T> &r, cons
 }
 
 
+// Folded constants of flux3 for mu = 1 on both sides (see flux3_mu1); K_i = C_i / h_normal.
+template <typename T>
+struct F3K {
+  T A1, A2, A3, A4, A5, B1, B2, B3, B4, B5, C1, G1;
+};
+
+template <typename T>
+inline F3K<T> make_f3k(const double C[5], double h, double c) {
+  const double k1 = C[0] / h, k2 = C[1] / h, k3 = C[2] / h, k4 = C[3] / h, k5 = C[4] / h;
+  F3K<T> f;
+  f.A1 = T(0.5 * k2); f.A2 = T(0.5 * c * (k2 - k5)); f.A3 = T(0.5 * c * k5);
+  f.A4 = T(0.5 * c * k4); f.A5 = T(0.5 * c * c * (k2 - k5));
+  f.B1 = T(0.5 * (k1 + k4)); f.B2 = T(0.5 * k1 / c); f.B3 = T(0.5 * k3);
+  f.B4 = T(0.5 * k1); f.B5 = T(0.5 * k4); f.C1 = T(0.5 * c * k2); f.G1 = T(0.5 * k3 / c);
+  return f;
+}
+
+// flux3 of an interior face with mu = 1 on both sides, rewritten in sums S(x) = x_l + x_r and
+// differences D(x) = x_r - x_l of the side quantities (v reconstructed values, n/t/w the
+// derivatives along the face frame's axes; eps-weighted where marked e), with ie = 1/eps_s:
+//   En = A1 (D tEw + D wEt) + A2 (S tHt - S wHw) + A3 (D wHt - D tHw) - A4 D e.vEn + A5 S e.nEn
+//   Et = B1 S vHw - g D nHw - A2 S tHn - A3 D wHn - A4 D e.vEt - B2 D vEt + B3 ie S e.tEn + cg S e.nEt
+//   Ew = -B1 S vHt + g D nHt + A2 S wHn + A3 D tHn - A4 D e.vEw - B2 D vEw + B3 ie S e.wEn + cg S e.nEw
+//   Hn = -A4 D vHn + A5 S nHn + A3 (S tEt - S wEw + D tEw - D wEt)
+//        + ie (C1 (S e.wEw - S e.tEt) + A1 (D tHw + D wHt))
+//   Ht = -B4 ie S e.vEw - B5 S vEw + g D nEw - (A4 + B2 ie) D vHt + A3 (D wEn - S tEn)
+//        + B3 ie S tHn + cg S nHt + C1 ie S e.tEn
+//   Hw = B4 ie S e.vEt + B5 S vEt - g D nEt - (A4 + B2 ie) D vHw + A3 (S wEn - D tEn)
+//        + B3 ie S wHn + cg S nHw - C1 ie S e.wEn
+// with g = A2 - G1 ie and cg = A5 - B3 ie.  Equal to flux3<T, false> term by term.
+template <typename T>
+__device__ __forceinline__ void flux3_mu1(const Side3<T> &l, const Side3<T> &r, const F3K<T> &K,
+                                          T ie, T out[6]) {
+  const T el = l.eps, er = r.eps;
+  const T g = K.A2 - K.G1 * ie, cg = K.A5 - K.B3 * ie;
+  const T A4B2 = K.A4 + K.B2 * ie;
+#define GKS_S(f, c) (l.f[c] + r.f[c])
+#define GKS_D(f, c) (r.f[c] - l.f[c])
+#define GKS_SE(f, c) (el * l.f[c] + er * r.f[c])
+#define GKS_DE(f, c) (er * r.f[c] - el * l.f[c])
+  out[EN] = K.A1 * (GKS_D(dt, EW) + GKS_D(dw, ET)) + K.A2 * (GKS_S(dt, HT) - GKS_S(dw, HW)) +
+            K.A3 * (GKS_D(dw, HT) - GKS_D(dt, HW)) - K.A4 * GKS_DE(v, EN) + K.A5 * GKS_SE(dn, EN);
+  out[ET] = K.B1 * GKS_S(v, HW) - g * GKS_D(dn, HW) - K.A2 * GKS_S(dt, HN) - K.A3 * GKS_D(dw, HN) -
+            K.A4 * GKS_DE(v, ET) - K.B2 * GKS_D(v, ET) + K.B3 * ie * GKS_SE(dt, EN) +
+            cg * GKS_SE(dn, ET);
+  out[EW] = -K.B1 * GKS_S(v, HT) + g * GKS_D(dn, HT) + K.A2 * GKS_S(dw, HN) + K.A3 * GKS_D(dt, HN) -
+            K.A4 * GKS_DE(v, EW) - K.B2 * GKS_D(v, EW) + K.B3 * ie * GKS_SE(dw, EN) +
+            cg * GKS_SE(dn, EW);
+  out[HN] = -K.A4 * GKS_D(v, HN) + K.A5 * GKS_S(dn, HN) +
+            K.A3 * ((GKS_S(dt, ET) - GKS_S(dw, EW)) + (GKS_D(dt, EW) - GKS_D(dw, ET))) +
+            ie * (K.C1 * (GKS_SE(dw, EW) - GKS_SE(dt, ET)) + K.A1 * (GKS_D(dt, HW) + GKS_D(dw, HT)));
+  out[HT] = -K.B4 * ie * GKS_SE(v, EW) - K.B5 * GKS_S(v, EW) + g * GKS_D(dn, EW) -
+            A4B2 * GKS_D(v, HT) + K.A3 * (GKS_D(dw, EN) - GKS_S(dt, EN)) +
+            K.B3 * ie * GKS_S(dt, HN) + cg * GKS_S(dn, HT) + K.C1 * ie * GKS_SE(dt, EN);
+  out[HW] = K.B4 * ie * GKS_SE(v, ET) + K.B5 * GKS_S(v, ET) - g * GKS_D(dn, ET) -
+            A4B2 * GKS_D(v, HW) + K.A3 * (GKS_S(dw, EN) - GKS_D(dt, EN)) +
+            K.B3 * ie * GKS_S(dw, HN) + cg * GKS_S(dn, HW) - K.C1 * ie * GKS_SE(dw, EN);
+#undef GKS_S
+#undef GKS_D
+#undef GKS_SE
+#undef GKS_DE
+}
+
 template <typename T>
 K3<T> make_k3(const double C[5], double h, double c) {
   K3<T> k;

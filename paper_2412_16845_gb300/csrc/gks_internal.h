@@ -49,6 +49,7 @@ struct TetHost {
   std::vector<int64_t> perm;    // internal cell k -> user cell perm[k]
   std::vector<int64_t> iperm;   // user cell -> internal
   std::vector<double> vol;      // [nt] internal
+  std::vector<double> ivol;     // [nt] 1 / vol
   std::vector<int32_t> cnb;     // [nt][4] neighbour (internal) or -1
   std::vector<int32_t> cface;   // [nt][4] face id
   std::vector<double> csign;    // [nt][4] +1 if the cell is the face's L side, -1 if R
@@ -69,6 +70,7 @@ struct TetDev {
   int64_t nt = 0, nf = 0;
   int64_t *perm = nullptr;
   double *vol = nullptr;
+  double *ivol = nullptr;
   int32_t *cnb = nullptr, *cface = nullptr;
   double *csign = nullptr, *cw = nullptr;
   int32_t *fL = nullptr, *fR = nullptr;

@@ -18,6 +18,12 @@ namespace {
 
 constexpr int TB = 256;
 
+// Reciprocals: FP32 uses the fast hardware reciprocal (about 1 ulp), FP64 divides.
+__device__ __forceinline__ float trcp(float x) { return __fdividef(1.f, x); }
+__device__ __forceinline__ double trcp(double x) { return 1.0 / x; }
+__device__ __forceinline__ float trcp2(float x) { return __fdividef(2.f, x); }
+__device__ __forceinline__ double trcp2(double x) { return 2.0 / x; }
+
 int blocks_for(int64_t n) {
   int64_t b = (n + TB - 1) / TB;
   return (int)(b < 1 ? 1 : b);
@@ -97,13 +103,14 @@ __device__ __forceinline__ Side3<T> tet_side(const T *__restrict__ V, const T *_
   return s;
 }
 
-template <typename T>
+template <typename T, bool HAS_MU>
 __global__ void tet_face_kernel(const T *__restrict__ V, const T *__restrict__ G,
                                 const T *__restrict__ eps, const T *__restrict__ mu,
                                 const int32_t *__restrict__ fL, const int32_t *__restrict__ fR,
                                 const double *__restrict__ fT, const double *__restrict__ farea,
                                 const double *__restrict__ fdL, const double *__restrict__ fdR,
-                                int64_t nt, int64_t nf, const K3<T> K, T *__restrict__ F) {
+                                int64_t nt, int64_t nf, const K3<T> K, const F3K<T> FK,
+                                T *__restrict__ F) {
   const int64_t f = blockIdx.x * (int64_t)TB + threadIdx.x;
   if (f >= nf) return;
   T Tm[9], dl[3], dr[3];
@@ -119,7 +126,10 @@ __global__ void tet_face_kernel(const T *__restrict__ V, const T *__restrict__ G
   T loc[6];
   if (R >= 0) {
     const Side3<T> r = tet_side<T>(V, G, eps, mu, nt, R, Tm, dr);
-    flux3<T, false>(l, r, K, loc);
+    if (HAS_MU)
+      flux3<T, false>(l, r, K, loc);
+    else
+      flux3_mu1<T>(l, r, FK, trcp2(l.eps + r.eps), loc);
   } else {
     flux3<T, true>(l, l, K, loc);
   }
@@ -138,7 +148,7 @@ __global__ void tet_update_kernel(const T *__restrict__ V, T *__restrict__ Vout,
                                   const T *__restrict__ eps, const T *__restrict__ mu,
                                   const T *__restrict__ src, T src_amp,
                                   const int32_t *__restrict__ cface,
-                                  const double *__restrict__ csign, const double *__restrict__ vol,
+                                  const double *__restrict__ csign, const double *__restrict__ ivol,
                                   const T *__restrict__ F, int64_t nt, int64_t nf,
                                   int *__restrict__ flag) {
   const int64_t i = blockIdx.x * (int64_t)TB + threadIdx.x;
@@ -152,14 +162,16 @@ __global__ void tet_update_kernel(const T *__restrict__ V, T *__restrict__ Vout,
 #pragma unroll
       for (int c = 0; c < 6; ++c) d[c] -= sg * F[c * nf + f];
     }
-    const T iv = T(1.0 / vol[i]);
-    if (src) d[2] -= src_amp * src[i] * T(vol[i]);
-    const T ie = T(1) / eps[i];
-    const T im = mu ? T(1) / mu[i] : T(1);
+    const T iv = T(ivol[i]);
+#pragma unroll
+    for (int c = 0; c < 6; ++c) d[c] *= iv;
+    if (src) d[2] -= src_amp * src[i];
+    const T ie = trcp(eps[i]);
+    const T im = mu ? trcp(mu[i]) : T(1);
     T sum = T(0);
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
-      const T nv = V[c * nt + i] + d[c] * iv * (c < 3 ? ie : im);
+      const T nv = V[c * nt + i] + d[c] * (c < 3 ? ie : im);
       Vout[c * nt + i] = nv;
       sum += nv;
     }
@@ -239,12 +251,18 @@ cudaError_t step_t(const TetDev &g, const void *Vin, void *Vout, const void *eps
   T *F = static_cast<T *>(g.Fscratch);
   tet_gradient_kernel<T><<<blocks_for(g.nt), TB, 0, st>>>(V, g.cnb, g.cw, g.nt, G);
   const K3<T> K = make_k3<T>(C, 1.0, c);     // fluxes carry dt (C_i), areas applied per face
-  tet_face_kernel<T><<<blocks_for(g.nf), TB, 0, st>>>(
-      V, G, static_cast<const T *>(eps), static_cast<const T *>(mu), g.fL, g.fR, g.fT, g.farea,
-      g.fdL, g.fdR, g.nt, g.nf, K, F);
+  const F3K<T> FK = make_f3k<T>(C, 1.0, c);
+  if (mu)
+    tet_face_kernel<T, true><<<blocks_for(g.nf), TB, 0, st>>>(
+        V, G, static_cast<const T *>(eps), static_cast<const T *>(mu), g.fL, g.fR, g.fT, g.farea,
+        g.fdL, g.fdR, g.nt, g.nf, K, FK, F);
+  else
+    tet_face_kernel<T, false><<<blocks_for(g.nf), TB, 0, st>>>(
+        V, G, static_cast<const T *>(eps), nullptr, g.fL, g.fR, g.fT, g.farea, g.fdL, g.fdR,
+        g.nt, g.nf, K, FK, F);
   tet_update_kernel<T><<<blocks_for(g.nt), TB, 0, st>>>(
       V, static_cast<T *>(Vout), static_cast<const T *>(eps), static_cast<const T *>(mu),
-      static_cast<const T *>(src), T(src_amp), g.cface, g.csign, g.vol, F, g.nt, g.nf, flag);
+      static_cast<const T *>(src), T(src_amp), g.cface, g.csign, g.ivol, F, g.nt, g.nf, flag);
   return cudaGetLastError();
 }
 

@@ -197,9 +197,11 @@ gks_status build_tet_geometry(const double *vert, int64_t nv, const int64_t *tet
   for (int64_t k = 0; k < nt; ++k)
     if (fill[k] != 4) { err = "a tet does not have four faces"; return GKS_E_ARG; }
   g.vol.resize(nt);
+  g.ivol.resize(nt);
   g.min_h = 1e300;
   for (int64_t k = 0; k < nt; ++k) {
     g.vol[k] = vol_u[g.perm[k]];
+    g.ivol[k] = 1.0 / g.vol[k];
     g.min_h = std::min(g.min_h, 6.0 * g.vol[k] / perim[k]);
   }
   return GKS_OK;

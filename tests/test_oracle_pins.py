@@ -536,3 +536,45 @@ def test_tet_plane_wave_converges():
         e = out[2][inner] - np.sin(2 * np.pi * (x[inner] - T))
         errs.append(np.sqrt(np.mean(e ** 2)))
     assert errs[1] < errs[0] / 2.0, errs
+
+
+# ---------------------------------------------------------------------------- diagnostics
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_energy_of_sampled_waves_closed_form(dim):
+    """Energy 1/2 sum |Omega| (eps |E|^2 + mu |H|^2) of E = a cos(2 pi x), H = b sin(2 pi x)
+    sampled at the cell centres of a uniform periodic grid: the discrete sums of cos^2 and sin^2
+    over a period are exactly N/2, so the energy is (eps a^2 + mu b^2)/4 on the unit square/cube.
+    Distinct eps, mu, a, b catch a swapped material, component or a dropped factor 1/2."""
+    n = 12
+    mesh = go.cartesian_mesh((n,) * dim, (0.0,) * dim, (1.0,) * dim, ("periodic",) * (2 * dim))
+    x = mesh.centroid[:, 0]
+    a, b, e, m = 1.0, 2.0, 2.5, 1.5
+    V = np.zeros((mesh.ncell, 6))
+    V[:, 2 if dim == 2 else 1] = a * np.cos(2 * np.pi * x)       # Ez (2-D) or Ey (3-D)
+    V[:, 4 if dim == 2 else 5] = b * np.sin(2 * np.pi * x)       # Hy (2-D) or Hz (3-D)
+    md = go.material_diag(np.full(mesh.ncell, e), np.full(mesh.ncell, m))
+    assert abs(go.energy(mesh, V, md) - 0.25 * (e * a * a + m * b * b)) <= 1e-13
+
+
+def test_probe_objective_against_exact_wave():
+    """J = sum_{n=1}^{N} dt sum_{i in P} |Omega_i| Ez_i^n^2 for the grid-aligned TM plane wave
+    Ez = cos 2pi(x - t), Hy = -Ez (Sec. 4.1) on a periodic 64 x 4 grid, probe = the columns
+    x < 1/8, N = 32 steps at CFL 0.5 (t = 1/4): equal to the same sum over the exact solution
+    within the scheme's error.  The probe's term at t = 0 and at t = 1/4 differ by a factor of
+    about 4.5, so counting steps 0..N-1 instead of 1..N moves J by about 4%; a dropped dt or
+    |Omega| moves it by orders of magnitude."""
+    nx, ny, N = 64, 4, 32
+    h = 1.0 / nx
+    mesh = go.cartesian_mesh((nx, ny), (0.0, 0.0), (1.0, ny * h), ("periodic",) * 4)
+    x, y = mesh.centroid[:, 0], mesh.centroid[:, 1]
+    f0 = wl.plane_wave_tm(x, y, 0.0, kvec=(1.0, 0.0))
+    probe = np.nonzero(x < 0.125)[0]
+    _, info = go.run(mesh, f0, np.ones(mesh.ncell), None, 0.5, N, c=1.0, probe=probe)
+    dt = info["dt"]
+    assert abs(dt - 0.5 * h) < 1e-15
+    xs = x[probe]
+    exact = sum(dt * h * h * np.sum(np.cos(2 * np.pi * (xs - k * dt)) ** 2) for k in range(1, N + 1))
+    shifted = sum(dt * h * h * np.sum(np.cos(2 * np.pi * (xs - k * dt)) ** 2) for k in range(0, N))
+    assert abs(exact - shifted) > 0.02 * exact            # the pin can tell the two apart
+    assert abs(info["J"] - exact) <= 1e-3 * exact, (info["J"], exact)
