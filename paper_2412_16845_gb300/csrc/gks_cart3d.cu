@@ -21,10 +21,15 @@ namespace gks {
 namespace {
 
 constexpr int BX = 32;
-constexpr int BY = 8;
-constexpr int NTH = BX * BY;
 constexpr int PX = BX + 2;            // staged plane: one extra ring around the thread grid
-constexpr int PY = BY + 2;
+// Tile height: FP32 takes 32 x 16 threads (inner 30 x 14 cells, about 200 KB of shared memory,
+// one CTA per SM); FP64 32 x 8 (its planes are twice as large).
+template <typename T>
+struct Geo3 {
+  static constexpr int BY = sizeof(T) == 4 ? 16 : 8;
+  static constexpr int NTH = BX * BY;
+  static constexpr int PY = BY + 2;
+};
 constexpr int NV = 8;                 // staged quantities: Ex Ey Ez Hx Hy Hz eps mu
 constexpr int NSLOT = 4;              // staged planes z-1 .. z+2
 
@@ -155,9 +160,9 @@ __device__ __forceinline__ int wrap_clamp(int i, int n, int periodic) {
 
 template <typename T>
 struct Smem3 {
-  T V[NSLOT][NV][PY][PX];       // staged planes with one extra ring
-  T G[2][18][BY][BX];           // gradients (axis-major: x comps, y comps, z comps)
-  T F[2][12][BY][BX];           // x-face (0..5) and y-face (6..11) fluxes at the high side
+  T V[NSLOT][NV][Geo3<T>::PY][PX];   // staged planes with one extra ring
+  T G[2][18][Geo3<T>::BY][BX];       // gradients (axis-major: x comps, y comps, z comps)
+  T F[2][12][Geo3<T>::BY][BX];       // x-face (0..5) and y-face (6..11) fluxes at the high side
 };
 
 // Load one staged entry (x, y, z) of all quantities into registers.
@@ -214,10 +219,10 @@ __device__ __forceinline__ void load_grad(const Smem3<T> &s, int gs, int ty, int
     for (int k = 0; k < 6; ++k) g[a][k] = s.G[gs][6 * a + k][ty][tx];
 }
 
-// FP32: two CTAs per SM (registers capped at 128); FP64 keeps one (its planes fill the SM).
+// One CTA per SM: FP32 512 threads (registers capped at 128), FP64 256.
 template <typename T, bool HAS_MU>
-__global__ void __launch_bounds__(NTH, sizeof(T) == 4 ? 2 : 1)
-    cart3d_step_kernel(const Cart3DArgs<T> p) {
+__global__ void __launch_bounds__(Geo3<T>::NTH, 1) cart3d_step_kernel(const Cart3DArgs<T> p) {
+  constexpr int BY = Geo3<T>::BY, PY = Geo3<T>::PY;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem3<T> &s = *reinterpret_cast<Smem3<T> *>(smem_raw);
   const int tid = threadIdx.x;
@@ -436,6 +441,7 @@ cudaError_t launch3_t(const CartGeom &g, const CartStepArgs &a, cudaStream_t st)
     p.FK[d] = make_f3k<T>(a.C, g.h[d], a.c);
   }
   p.flag = a.flag;
+  constexpr int BY = Geo3<T>::BY, NTH = Geo3<T>::NTH;
   const int gx = (g.nx + BX - 3) / (BX - 2), gy = (g.ny + BY - 3) / (BY - 2);
   const int smem = (int)sizeof(Smem3<T>);
   // z chunks: a CTA marches zchunk planes after a two-plane prologue.  Pick the chunk count
