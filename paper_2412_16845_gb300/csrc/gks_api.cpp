@@ -124,14 +124,40 @@ gks_status setup_tets(gks_ctx *ctx, const gks_mesh_desc *d) {
   gks::TetDev &g = ctx->tet;
   g.nt = h.nt;
   g.nf = h.nf;
+  // packed step geometry (FP64 values, rounded once to FP32 for FP32 contexts)
+  std::vector<double> fgeo((size_t)h.nf * gks::kTetFaceGeo), cgeo((size_t)h.nt * gks::kTetCellGeo, 0.0);
+  for (int64_t f = 0; f < h.nf; ++f) {
+    double *q = &fgeo[(size_t)f * gks::kTetFaceGeo];
+    for (int k = 0; k < 9; ++k) q[k] = h.fT[9 * f + k];
+    for (int a = 0; a < 3; ++a) { q[9 + a] = h.fdL[3 * f + a]; q[12 + a] = h.fdR[3 * f + a]; }
+    q[15] = h.farea[f];
+  }
+  for (int64_t i = 0; i < h.nt; ++i) {
+    double *q = &cgeo[(size_t)i * gks::kTetCellGeo];
+    for (int k = 0; k < 12; ++k) q[k] = h.cw[12 * i + k];
+    for (int k = 0; k < 4; ++k) q[12 + k] = h.csign[4 * i + k];
+    q[16] = h.ivol[i];
+  }
   if ((s = upload_vec(ctx, h.perm, &g.perm)) != GKS_OK || (s = upload_vec(ctx, h.vol, &g.vol)) != GKS_OK ||
-      (s = upload_vec(ctx, h.ivol, &g.ivol)) != GKS_OK ||
       (s = upload_vec(ctx, h.cnb, &g.cnb)) != GKS_OK || (s = upload_vec(ctx, h.cface, &g.cface)) != GKS_OK ||
-      (s = upload_vec(ctx, h.csign, &g.csign)) != GKS_OK || (s = upload_vec(ctx, h.cw, &g.cw)) != GKS_OK ||
-      (s = upload_vec(ctx, h.fL, &g.fL)) != GKS_OK || (s = upload_vec(ctx, h.fR, &g.fR)) != GKS_OK ||
-      (s = upload_vec(ctx, h.fT, &g.fT)) != GKS_OK || (s = upload_vec(ctx, h.farea, &g.farea)) != GKS_OK ||
-      (s = upload_vec(ctx, h.fdL, &g.fdL)) != GKS_OK || (s = upload_vec(ctx, h.fdR, &g.fdR)) != GKS_OK)
+      (s = upload_vec(ctx, h.fL, &g.fL)) != GKS_OK || (s = upload_vec(ctx, h.fR, &g.fR)) != GKS_OK)
     return s;
+  if (ctx->fp64) {
+    double *fd = nullptr, *cd = nullptr;
+    s = upload_vec(ctx, fgeo, &fd);
+    g.fgeo = fd;
+    if (s != GKS_OK || (s = upload_vec(ctx, cgeo, &cd)) != GKS_OK) return s;
+    g.cgeo = cd;
+  } else {
+    std::vector<float> f32(fgeo.begin(), fgeo.end()), c32(cgeo.begin(), cgeo.end());
+    float *fd = nullptr, *cd = nullptr;
+    s = upload_vec(ctx, f32, &fd);
+    g.fgeo = fd;
+    if (s != GKS_OK || (s = upload_vec(ctx, c32, &cd)) != GKS_OK) return s;
+    g.cgeo = cd;
+    // the pageable host vectors must outlive the copies
+    GKS_CUDA(cudaStreamSynchronize(ctx->st));
+  }
   if ((s = alloc_dev(ctx, &g.Gscratch, ctx->esize * 18 * (size_t)g.nt)) != GKS_OK ||
       (s = alloc_dev(ctx, &g.Fscratch, ctx->esize * 6 * (size_t)g.nf)) != GKS_OK)
     return s;
@@ -631,8 +657,8 @@ void gks_destroy(gks_ctx *ctx) {
   if (!ctx) return;
   const gks::TetDev &t = ctx->tet;
   void *bufs[] = {ctx->V[0], ctx->V[1], ctx->eps, ctx->mu, ctx->src, ctx->flag, ctx->red,
-                  ctx->staging, t.perm, t.vol, t.ivol, t.cnb, t.cface, t.csign, t.cw, t.fL, t.fR, t.fT,
-                  t.farea, t.fdL, t.fdR, t.Gscratch, t.Fscratch, ctx->probe_off, ctx->probe_w, ctx->probe_box_w,
+                  ctx->staging, t.perm, t.vol, t.cnb, t.cface, t.fL, t.fR, t.fgeo, t.cgeo,
+                  t.Gscratch, t.Fscratch, ctx->probe_off, ctx->probe_w, ctx->probe_box_w,
                   ctx->dslot, ctx->obj};
   for (void *p : bufs)
     if (p) cudaFreeAsync(p, ctx->st);

@@ -65,16 +65,19 @@ gks_status build_tet_geometry(const double *vert, int64_t nv, const int64_t *tet
                               TetHost &g, std::string &err);
 void face_frame(const double n[3], double T[9]);
 
-// Device copies of the tet geometry plus the per-step scratch (gradients, face fluxes).
+// Device copies of the tet geometry plus the per-step scratch (gradients, face fluxes).  The
+// geometry is computed in FP64 on the host; the step kernels read it in the context's precision
+// (rounded once on the host for FP32 contexts), packed per face and per cell.
+constexpr int kTetFaceGeo = 16;   // per face: frame rows (n, t, w) 9, x_s - x_L 3, x_s - x_R 3, |l|
+constexpr int kTetCellGeo = 20;   // per cell: n |l| / |Omega| of its 4 faces 12, signs 4, 1/|Omega|, pad 3
 struct TetDev {
   int64_t nt = 0, nf = 0;
   int64_t *perm = nullptr;
-  double *vol = nullptr;
-  double *ivol = nullptr;
+  double *vol = nullptr;        // FP64 |Omega| (energy)
   int32_t *cnb = nullptr, *cface = nullptr;
-  double *csign = nullptr, *cw = nullptr;
   int32_t *fL = nullptr, *fR = nullptr;
-  double *fT = nullptr, *farea = nullptr, *fdL = nullptr, *fdR = nullptr;
+  void *fgeo = nullptr;         // [nf][kTetFaceGeo], context precision
+  void *cgeo = nullptr;         // [nt][kTetCellGeo], context precision
   void *Gscratch = nullptr;     // [18][nt] gradients
   void *Fscratch = nullptr;     // [6][nf] face fluxes (times dt and |l|)
 };

@@ -31,8 +31,7 @@ int blocks_for(int64_t n) {
 
 template <typename T>
 __global__ void tet_gradient_kernel(const T *__restrict__ V, const int32_t *__restrict__ cnb,
-                                    const double *__restrict__ cw, int64_t nt,
-                                    T *__restrict__ G) {
+                                    const T *__restrict__ cgeo, int64_t nt, T *__restrict__ G) {
   const int64_t i = blockIdx.x * (int64_t)TB + threadIdx.x;
   if (i >= nt) return;
   T vi[6];
@@ -56,7 +55,7 @@ __global__ void tet_gradient_kernel(const T *__restrict__ V, const int32_t *__re
     }
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      const T w = T(cw[12 * i + 3 * k + a]);
+      const T w = cgeo[kTetCellGeo * i + 3 * k + a];
 #pragma unroll
       for (int c = 0; c < 6; ++c) g[a][c] += vf[c] * w;
     }
@@ -65,6 +64,22 @@ __global__ void tet_gradient_kernel(const T *__restrict__ V, const int32_t *__re
   for (int a = 0; a < 3; ++a)
 #pragma unroll
     for (int c = 0; c < 6; ++c) G[(6 * a + c) * nt + i] = g[a][c];
+}
+
+// The packed geometry of one face (16 values, 64 or 128 bytes, aligned): vector loads.
+__device__ __forceinline__ void load_face_geo(const float *p, float q[kTetFaceGeo]) {
+#pragma unroll
+  for (int k = 0; k < kTetFaceGeo / 4; ++k) {
+    const float4 v = __ldg(reinterpret_cast<const float4 *>(p) + k);
+    q[4 * k] = v.x; q[4 * k + 1] = v.y; q[4 * k + 2] = v.z; q[4 * k + 3] = v.w;
+  }
+}
+__device__ __forceinline__ void load_face_geo(const double *p, double q[kTetFaceGeo]) {
+#pragma unroll
+  for (int k = 0; k < kTetFaceGeo / 2; ++k) {
+    const double2 v = __ldg(reinterpret_cast<const double2 *>(p) + k);
+    q[2 * k] = v.x; q[2 * k + 1] = v.y;
+  }
 }
 
 // Side of a face in the frame with rows T (n, t, w): reconstruct V + G.d, then rotate the
@@ -107,20 +122,13 @@ template <typename T, bool HAS_MU>
 __global__ void tet_face_kernel(const T *__restrict__ V, const T *__restrict__ G,
                                 const T *__restrict__ eps, const T *__restrict__ mu,
                                 const int32_t *__restrict__ fL, const int32_t *__restrict__ fR,
-                                const double *__restrict__ fT, const double *__restrict__ farea,
-                                const double *__restrict__ fdL, const double *__restrict__ fdR,
-                                int64_t nt, int64_t nf, const K3<T> K, const F3K<T> FK,
-                                T *__restrict__ F) {
+                                const T *__restrict__ fgeo, int64_t nt, int64_t nf,
+                                const K3<T> K, const F3K<T> FK, T *__restrict__ F) {
   const int64_t f = blockIdx.x * (int64_t)TB + threadIdx.x;
   if (f >= nf) return;
-  T Tm[9], dl[3], dr[3];
-#pragma unroll
-  for (int k = 0; k < 9; ++k) Tm[k] = T(fT[9 * f + k]);
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    dl[a] = T(fdL[3 * f + a]);
-    dr[a] = T(fdR[3 * f + a]);
-  }
+  T q[kTetFaceGeo];
+  load_face_geo(fgeo + kTetFaceGeo * f, q);
+  const T *Tm = q, *dl = q + 9, *dr = q + 12;
   const int32_t L = fL[f], R = fR[f];
   const Side3<T> l = tet_side<T>(V, G, eps, mu, nt, L, Tm, dl);
   T loc[6];
@@ -133,7 +141,7 @@ __global__ void tet_face_kernel(const T *__restrict__ V, const T *__restrict__ G
   } else {
     flux3<T, true>(l, l, K, loc);
   }
-  const T area = T(farea[f]);
+  const T area = q[15];
   // back to global components: Phi = T'^T Phi_local, times |l_s|
 #pragma unroll
   for (int b = 0; b < 2; ++b)
@@ -148,8 +156,8 @@ __global__ void tet_update_kernel(const T *__restrict__ V, T *__restrict__ Vout,
                                   const T *__restrict__ eps, const T *__restrict__ mu,
                                   const T *__restrict__ src, T src_amp,
                                   const int32_t *__restrict__ cface,
-                                  const double *__restrict__ csign, const double *__restrict__ ivol,
-                                  const T *__restrict__ F, int64_t nt, int64_t nf,
+                                  const T *__restrict__ cgeo, const T *__restrict__ F, int64_t nt,
+                                  int64_t nf,
                                   int *__restrict__ flag) {
   const int64_t i = blockIdx.x * (int64_t)TB + threadIdx.x;
   bool bad = false;
@@ -158,11 +166,11 @@ __global__ void tet_update_kernel(const T *__restrict__ V, T *__restrict__ Vout,
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       const int32_t f = cface[4 * i + k];
-      const T sg = T(csign[4 * i + k]);
+      const T sg = cgeo[kTetCellGeo * i + 12 + k];
 #pragma unroll
       for (int c = 0; c < 6; ++c) d[c] -= sg * F[c * nf + f];
     }
-    const T iv = T(ivol[i]);
+    const T iv = cgeo[kTetCellGeo * i + 16];
 #pragma unroll
     for (int c = 0; c < 6; ++c) d[c] *= iv;
     if (src) d[2] -= src_amp * src[i];
@@ -249,20 +257,20 @@ cudaError_t step_t(const TetDev &g, const void *Vin, void *Vout, const void *eps
   const T *V = static_cast<const T *>(Vin);
   T *G = static_cast<T *>(g.Gscratch);
   T *F = static_cast<T *>(g.Fscratch);
-  tet_gradient_kernel<T><<<blocks_for(g.nt), TB, 0, st>>>(V, g.cnb, g.cw, g.nt, G);
+  const T *fgeo = static_cast<const T *>(g.fgeo), *cgeo = static_cast<const T *>(g.cgeo);
+  tet_gradient_kernel<T><<<blocks_for(g.nt), TB, 0, st>>>(V, g.cnb, cgeo, g.nt, G);
   const K3<T> K = make_k3<T>(C, 1.0, c);     // fluxes carry dt (C_i), areas applied per face
   const F3K<T> FK = make_f3k<T>(C, 1.0, c);
   if (mu)
     tet_face_kernel<T, true><<<blocks_for(g.nf), TB, 0, st>>>(
-        V, G, static_cast<const T *>(eps), static_cast<const T *>(mu), g.fL, g.fR, g.fT, g.farea,
-        g.fdL, g.fdR, g.nt, g.nf, K, FK, F);
+        V, G, static_cast<const T *>(eps), static_cast<const T *>(mu), g.fL, g.fR, fgeo, g.nt,
+        g.nf, K, FK, F);
   else
     tet_face_kernel<T, false><<<blocks_for(g.nf), TB, 0, st>>>(
-        V, G, static_cast<const T *>(eps), nullptr, g.fL, g.fR, g.fT, g.farea, g.fdL, g.fdR,
-        g.nt, g.nf, K, FK, F);
+        V, G, static_cast<const T *>(eps), nullptr, g.fL, g.fR, fgeo, g.nt, g.nf, K, FK, F);
   tet_update_kernel<T><<<blocks_for(g.nt), TB, 0, st>>>(
       V, static_cast<T *>(Vout), static_cast<const T *>(eps), static_cast<const T *>(mu),
-      static_cast<const T *>(src), T(src_amp), g.cface, g.csign, g.ivol, F, g.nt, g.nf, flag);
+      static_cast<const T *>(src), T(src_amp), g.cface, cgeo, F, g.nt, g.nf, flag);
   return cudaGetLastError();
 }
 
