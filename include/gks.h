@@ -12,7 +12,7 @@
  * Conventions shared by every entry point
  *  - Fields: 2-D TM carries (Ez, Hx, Hy); 3-D carries (Ex, Ey, Ez, Hx, Hy, Hz).  The library
  *    stores the primitive state V = (E, H); the conserved state is U = (eps E, mu H).
- *    Units: c = eps0 = mu0 = 1 (Sec. 4) unless a lattice speed is given.
+ *    Units: c = eps0 = mu0 = 1 (Sec. 5) unless a lattice speed is given.
  *  - User order: host arrays are [ncomp][n_cells] in user cell order.  Cartesian cells are
  *    numbered x fastest (i + nx*(j + ny*k)); tetrahedra in the order of tet_vert.  Internal
  *    layouts (padded rows, reordered cells) never show at the API.
@@ -66,7 +66,7 @@ enum { GKS_BC_PERIODIC = 0, GKS_BC_NONREFLECTING = 1 };
  *             (GKS_BC_NONREFLECTING).
  *  cfl        dt = cfl * h_min / c, h_i = 2 dim |Omega_i| / sum_s |l_s| (edge of a square/cube).
  *  tau_over_dt  kappa = tau/dt of the BGK relaxation time (Sec. 2.2, eq. of the vector BGK
- *             model); 0 selects the tau -> 0 limit coefficients of Sec. 3.3.
+ *             model); 0 selects the tau -> 0 limit coefficients of Sec. 4.1.
  *  c_lattice  lattice speed c of the D3Q4 velocities (Sec. 2.2); <= 0 selects
  *             max_i 1/sqrt(eps_i mu_i) at gks_set_materials (1 in vacuum).
  *  cuda_stream  cudaStream_t of all device work of this context.                          */
@@ -98,7 +98,7 @@ typedef struct gks_mesh_desc {
 gks_status gks_create_mesh(const gks_mesh_desc *d, gks_ctx **out);
 
 /* Per-cell material eps, mu ([n_cells] doubles, user order, all > 0 and finite; mu == NULL
- * means mu = 1).  The paper has no materials (Sec. 4 uses vacuum); the library uses
+ * means mu = 1).  The paper has no materials (Sec. 5 uses vacuum); the library uses
  * U = (eps E, mu H) and the interface equilibrium M_s = (M_L + M_R)/2, which reduces to the
  * paper's scheme for eps = mu = 1.  Recomputes the lattice speed (c_lattice <= 0), dt and
  * C1..C5. */

@@ -31,7 +31,7 @@ Readings of passages that are silent, garbled or ambiguous (all listed in DESIGN
 * Upwind sets: l for u_k.n > 0, r for u_k.n < 0 (u_k.n never vanishes in the local frame).
 * "U_k/4" in the equilibrium is U/4.
 * tau = kappa * dt with kappa a parameter; kappa = 0 means the tau -> 0 limit coefficients
-  (Sec. 3.3, non-viscous limit): C1 = dt, C3 = dt^2/2, C2 = C4 = C5 = 0.
+  (Sec. 4.1, non-viscous limit): C1 = dt, C3 = dt^2/2, C2 = C4 = C5 = 0.
 * Ghost values for Green-Gauss at a non-reflecting face: a copy of the interior cell.
 * Face orientation: Cartesian faces use n = +e_d with L the cell on the -e_d side (wrap faces
   included); tetrahedral interior faces point from the smaller to the larger user cell index;
@@ -40,7 +40,7 @@ Readings of passages that are silent, garbled or ambiguous (all listed in DESIGN
 * Time step: dt = CFL * h_min / c with h_i = 2 dim |Omega_i| / sum_s |l_s| (= the edge of a
   square or cube).
 
-Units: c = eps0 = mu0 = 1 (Sec. 4) unless a lattice speed c is passed.
+Units: c = eps0 = mu0 = 1 (Sec. 5) unless a lattice speed c is passed.
 """
 from __future__ import annotations
 
@@ -119,7 +119,7 @@ def time_coefficients(dt: float, tau: float):
     """C1..C5 = integrals over [0, dt] of c1..c5 (Sec. 3.1), with c4 = e^{-t/tau},
     c5 = t e^{-t/tau}.
 
-    tau = 0 gives the non-viscous limit (Sec. 3.3): (dt, 0, dt^2/2, 0, 0).  For x = dt/tau < 2
+    tau = 0 gives the non-viscous limit (Sec. 4.1): (dt, 0, dt^2/2, 0, 0).  For x = dt/tau < 2
     the closed forms lose digits to cancellation, so their Taylor series in x (derived from the
     same closed forms) are summed instead."""
     if tau == 0.0:
@@ -267,6 +267,10 @@ class FVMesh:
     dL: np.ndarray         # [nface, 3] x_s - x_L
     dR: np.ndarray         # [nface, 3] x_s - x_R (periodic faces use the image of R)
     boundary: np.ndarray   # [nface] bool: kinetic non-reflecting face
+    pec: np.ndarray = None  # [nface] bool: perfect-electric-conductor wall (mirror ghost)
+
+    def pec_faces(self) -> np.ndarray:
+        return np.zeros(self.nface, dtype=bool) if self.pec is None else self.pec
 
     @property
     def ncell(self) -> int:
@@ -280,8 +284,9 @@ class FVMesh:
 def cartesian_mesh(n, lo, hi, bc) -> FVMesh:
     """Uniform Cartesian grid (2-D or 3-D), cells numbered x fastest.
 
-    bc: per side (-x, +x, -y, +y[, -z, +z]) 'periodic' or 'nrbc'.  2-D cells have unit depth in
-    z: |Omega| = hx hy, |l| = edge length."""
+    bc: per side (-x, +x, -y, +y[, -z, +z]) 'periodic', 'nrbc' (kinetic non-reflecting) or
+    'pec' (perfect electric conductor).  2-D cells have unit depth in z: |Omega| = hx hy,
+    |l| = edge length."""
     dim = len(n)
     n = tuple(int(v) for v in n)
     h = [(hi[d] - lo[d]) / n[d] for d in range(dim)]
@@ -293,7 +298,7 @@ def cartesian_mesh(n, lo, hi, bc) -> FVMesh:
     for d in range(dim):
         centroid[:, d] = coords[d].ravel()
     vol = np.full(ncell, float(np.prod(h)))
-    Ls, Rs, ns, As, dLs, dRs, bs = [], [], [], [], [], [], []
+    Ls, Rs, ns, As, dLs, dRs, bs, ps = [], [], [], [], [], [], [], []
     for d in range(dim):
         ax = dim - 1 - d                             # numpy axis of direction d
         area = float(np.prod([h[e] for e in range(dim) if e != d]))
@@ -313,19 +318,22 @@ def cartesian_mesh(n, lo, hi, bc) -> FVMesh:
         Ls.append(lower); Rs.append(upper)
         ns.append(np.tile(e, (nf, 1))); As.append(np.full(nf, area))
         dLs.append(np.tile(0.5 * h[d] * e, (nf, 1))); dRs.append(np.tile(-0.5 * h[d] * e, (nf, 1)))
-        bs.append(np.zeros(nf, dtype=bool))
+        bs.append(np.zeros(nf, dtype=bool)); ps.append(np.zeros(nf, dtype=bool))
         if not periodic:
-            for cells, sgn in ((first, -1.0), (last, 1.0)):
+            for cells, sgn, side in ((first, -1.0, bc[2 * d]), (last, 1.0, bc[2 * d + 1])):
+                if side not in ("nrbc", "pec"):
+                    raise ValueError(f"unknown boundary {side!r}")
                 nb = cells.size
                 Ls.append(cells); Rs.append(np.full(nb, -1))
                 ns.append(np.tile(sgn * e, (nb, 1))); As.append(np.full(nb, area))
                 dLs.append(np.tile(sgn * 0.5 * h[d] * e, (nb, 1)))
-                dRs.append(np.zeros((nb, 3))); bs.append(np.ones(nb, dtype=bool))
+                dRs.append(np.zeros((nb, 3)))
+                bs.append(np.full(nb, side == "nrbc")); ps.append(np.full(nb, side == "pec"))
     return FVMesh(dim=dim, vol=vol, centroid=centroid,
                   L=np.concatenate(Ls).astype(np.int64), R=np.concatenate(Rs).astype(np.int64),
                   normal=np.concatenate(ns), area=np.concatenate(As),
                   dL=np.concatenate(dLs), dR=np.concatenate(dRs),
-                  boundary=np.concatenate(bs))
+                  boundary=np.concatenate(bs), pec=np.concatenate(ps))
 
 
 def tet_mesh(vert, tet) -> FVMesh:
@@ -404,12 +412,34 @@ def _scatter_add(n, idx, vals):
     return out
 
 
+def pec_mirror(n, X):
+    """The field of the mirror ghost across a perfect-electric-conductor wall with unit normal n
+    (Sec. 5.5 interface conditions): tangential E and normal B (H) change sign, normal E and
+    tangential H are kept (their normal derivatives vanish at the wall).  X [..., 6] global
+    components (E, H), n [..., 3]."""
+    E, H = X[..., :3], X[..., 3:]
+    En = np.sum(E * n, axis=-1, keepdims=True)
+    Hn = np.sum(H * n, axis=-1, keepdims=True)
+    return np.concatenate([-E + 2.0 * En * n, H - 2.0 * Hn * n], axis=-1)
+
+
+def pec_mirror_grad(n, G):
+    """Gradient of the mirror ghost at the wall: the field mirror on the component index and the
+    reflection I - 2 n n^T on the derivative index.  G [nf, 3, 6] (derivative, component)."""
+    PG = pec_mirror(n[:, None, :], G)
+    return PG - 2.0 * n[:, :, None] * np.einsum("fk,fkc->fc", n, PG)[:, None, :]
+
+
 def green_gauss(mesh: FVMesh, V):
     """Cell gradients grad V_i = (1/|Omega_i|) sum_s V_s n_s |l_s|, V_s = (V_i + V_nb)/2
-    (Sec. 3.1, Green-Gauss); a non-reflecting face uses a ghost equal to V_i, i.e. V_s = V_i.
-    Returns [ncell, 3, 6]."""
+    (Sec. 3.1, Green-Gauss); a non-reflecting face uses a ghost equal to V_i, i.e. V_s = V_i; a
+    PEC face uses the mirror ghost, V_s = (V_i + P V_i)/2.  Returns [ncell, 3, 6]."""
     inter = mesh.R >= 0
     Vs = np.where(inter[:, None], 0.5 * (V[mesh.L] + V[np.maximum(mesh.R, 0)]), V[mesh.L])
+    pec = mesh.pec_faces()
+    if pec.any():
+        VL = V[mesh.L[pec]]
+        Vs[pec] = 0.5 * (VL + pec_mirror(mesh.normal[pec], VL))
     contrib = Vs[:, None, :] * (mesh.normal * mesh.area[:, None])[:, :, None]   # [nf, 3, 6]
     G = _scatter_add(mesh.ncell, mesh.L, contrib)
     G -= _scatter_add(mesh.ncell, mesh.R[inter], contrib[inter])
@@ -432,9 +462,18 @@ def face_fluxes(mesh: FVMesh, V, m, C, dt, c=1.0, faces=None):
     # piecewise-linear reconstruction at the face centre
     Vl = V[L] + np.einsum("fj,fjc->fc", mesh.dL[sel], G[L])
     Vr = V[Rc] + np.einsum("fj,fjc->fc", mesh.dR[sel], G[Rc])
+    Gr, mr = G[Rc], m[Rc]
+    pec = mesh.pec_faces()[sel]
+    if pec.any():
+        # PEC wall: the high side is the mirror ghost of the low side, with its materials
+        n = mesh.normal[sel][pec]
+        Vr = Vr.copy(); Gr = Gr.copy(); mr = mr.copy()
+        Vr[pec] = pec_mirror(n, Vl[pec])
+        Gr[pec] = pec_mirror_grad(n, G[L[pec]])
+        mr[pec] = m[L[pec]]
     T = rotation(mesh.normal[sel])
     Fl = face_flux_local(_rot_vec6(T, Vl), _rot_grad(T, G[L]), m[L],
-                         _rot_vec6(T, Vr), _rot_grad(T, G[Rc]), m[Rc], ghost, C, dt, c, mesh.dim)
+                         _rot_vec6(T, Vr), _rot_grad(T, Gr), mr, ghost, C, dt, c, mesh.dim)
     return _rot_vec6_back(T, Fl)
 
 

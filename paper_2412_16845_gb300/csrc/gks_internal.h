@@ -12,7 +12,7 @@
 namespace gks {
 
 // Time-integration coefficients C1..C5 of the GKS flux (Sec. 3.1) for step dt and relaxation
-// time tau (tau = 0: the tau -> 0 limit of Sec. 3.3).
+// time tau (tau = 0: the tau -> 0 limit of Sec. 4.1).
 void time_coefficients(double dt, double tau, double C[5]);
 
 // Cartesian grid geometry and state layout.  Fields are stored structure-of-arrays,

@@ -11,7 +11,7 @@ fastest (``i + nx*(j + ny*k)``), tetrahedra in the order they are emitted by
 :func:`kuhn_tet_mesh`.  Fields are returned as ``[ncomp][ncell]`` arrays with the components
 (Ez, Hx, Hy) in 2-D TM and (Ex, Ey, Ez, Hx, Hy, Hz) in 3-D.
 
-Units follow the paper's numerical section: c = eps0 = mu0 = 1 (Sec. 4).
+Units follow the paper's numerical section: c = eps0 = mu0 = 1 (Sec. 5).
 """
 from __future__ import annotations
 
@@ -78,7 +78,7 @@ def smoothed_noise(rng: np.random.Generator, shape, sigma_cells) -> np.ndarray:
 def plane_wave_tm(x, y, t, kvec=(2.0, 1.0)):
     """Exact TM plane wave Ez = cos(k.x - |k| t), H = Ez (sin th, -cos th) with k = 2 pi kvec.
 
-    With th = 0 this is the paper's plane wave E_z = cos 2pi(x - ct), B_y = -E_z (Sec. 4.1).
+    With th = 0 this is the paper's plane wave E_z = cos 2pi(x - ct), B_y = -E_z (Sec. 5.1).
     kvec must be integer for the wave to be periodic on the unit square."""
     k = 2.0 * np.pi * np.asarray(kvec, dtype=np.float64)
     kn = float(np.hypot(k[0], k[1]))
@@ -121,7 +121,7 @@ class CartWorkload:
     src: tuple = (SRC_A, SRC_F0, SRC_T0, SRC_S)
     probe: np.ndarray | None = None      # int64 cell ids
     design: np.ndarray | None = None     # int64 cell ids
-    c_lattice: float = 1.0               # lattice speed c of the workload (c = 1 in Sec. 4)
+    c_lattice: float = 1.0               # lattice speed c of the workload (c = 1 in Sec. 5)
     extra: dict = field(default_factory=dict)
 
     @property
