@@ -51,19 +51,22 @@ typedef enum gks_status {
 
 enum { GKS_CARTESIAN = 0, GKS_TET = 1 };
 enum { GKS_FP32 = 0, GKS_FP64 = 1 };
-enum { GKS_BC_PERIODIC = 0, GKS_BC_NONREFLECTING = 1 };
+enum { GKS_BC_PERIODIC = 0, GKS_BC_NONREFLECTING = 1, GKS_BC_PEC = 2 };
 
 /* Problem description (Sec. 3.1: cells Omega_i, faces l_s with normals n_s).
  *  dim        2 => TM (Ez, Hx, Hy) on an (x, y) grid; 3 => full Maxwell.
  *  kind       GKS_CARTESIAN, or GKS_TET (requires dim == 3).
  *  precision  GKS_FP32 or GKS_FP64: storage of the state and the flux/update arithmetic.
  *  n, lo, hi  Cartesian cells per axis and box (n[2] ignored in 2-D).
- *  bc         per side -x,+x,-y,+y,-z,+z: GKS_BC_PERIODIC (sides paired) or
- *             GKS_BC_NONREFLECTING (kinetic boundary of Sec. 3.1).
+ *  bc         per side -x,+x,-y,+y,-z,+z: GKS_BC_PERIODIC (sides paired),
+ *             GKS_BC_NONREFLECTING (kinetic boundary of Sec. 3.1) or GKS_BC_PEC (perfect
+ *             electric conductor wall, Sec. 5.5: tangential E and normal B vanish, normal E and
+ *             tangential H have zero normal derivative; a mirror ghost cell).  A PEC axis needs
+ *             at least 2 cells.
  *  vert_xyz   tets: [n_vert][3] doubles (host, copied).
  *  tet_vert   tets: [n_tet][4] int64 vertex ids (host, copied), any orientation.
  *  tet_bc     tets: boundary kind of every face that belongs to one tet only
- *             (GKS_BC_NONREFLECTING).
+ *             (GKS_BC_NONREFLECTING or GKS_BC_PEC).
  *  cfl        dt = cfl * h_min / c, h_i = 2 dim |Omega_i| / sum_s |l_s| (edge of a square/cube).
  *  tau_over_dt  kappa = tau/dt of the BGK relaxation time (Sec. 2.2, eq. of the vector BGK
  *             model); 0 selects the tau -> 0 limit coefficients of Sec. 4.1.

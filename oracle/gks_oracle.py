@@ -336,12 +336,12 @@ def cartesian_mesh(n, lo, hi, bc) -> FVMesh:
                   boundary=np.concatenate(bs), pec=np.concatenate(ps))
 
 
-def tet_mesh(vert, tet) -> FVMesh:
+def tet_mesh(vert, tet, bc="nrbc") -> FVMesh:
     """Face-based mesh of a conforming tetrahedral mesh.
 
     Faces are matched on their sorted vertex triples; an interior face's normal points from the
-    smaller to the larger tet index; a face seen once is a non-reflecting boundary face with
-    outward normal."""
+    smaller to the larger tet index; a face seen once is a boundary face with outward normal,
+    kinetic non-reflecting (bc="nrbc") or a PEC wall (bc="pec")."""
     vert = np.asarray(vert, dtype=np.float64)
     tet = np.asarray(tet, dtype=np.int64)
     nt = tet.shape[0]
@@ -387,9 +387,11 @@ def tet_mesh(vert, tet) -> FVMesh:
     nrm[flip] *= -1.0
     dL = xs - centroid[L]
     dR = np.where((R >= 0)[:, None], xs - centroid[np.maximum(R, 0)], 0.0)
+    if bc not in ("nrbc", "pec"):
+        raise ValueError(f"unknown boundary {bc!r}")
     return FVMesh(dim=3, vol=vol, centroid=centroid, L=L.astype(np.int64),
                   R=R.astype(np.int64), normal=nrm, area=area, dL=dL, dR=dR,
-                  boundary=(R < 0))
+                  boundary=(R < 0) & (bc == "nrbc"), pec=(R < 0) & (bc == "pec"))
 
 
 def time_step(mesh: FVMesh, cfl: float, c: float = 1.0) -> float:

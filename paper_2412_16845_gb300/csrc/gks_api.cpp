@@ -124,6 +124,7 @@ gks_status setup_tets(gks_ctx *ctx, const gks_mesh_desc *d) {
   gks::TetDev &g = ctx->tet;
   g.nt = h.nt;
   g.nf = h.nf;
+  g.pec = d->tet_bc == GKS_BC_PEC;
   // packed step geometry (FP64 values, rounded once to FP32 for FP32 contexts)
   std::vector<double> fgeo((size_t)h.nf * gks::kTetFaceGeo), cgeo((size_t)h.nt * gks::kTetCellGeo, 0.0);
   for (int64_t f = 0; f < h.nf; ++f) {
@@ -191,16 +192,18 @@ gks_status gks_create_mesh(const gks_mesh_desc *d, gks_ctx **out) {
   if (d->kind == GKS_TET) {
     if (d->dim != 3 || !d->vert_xyz || !d->tet_vert || d->n_vert < 4 || d->n_tet < 1)
       return GKS_E_ARG;
-    if (d->tet_bc != GKS_BC_NONREFLECTING) return GKS_E_UNSUPPORTED;
+    if (d->tet_bc != GKS_BC_NONREFLECTING && d->tet_bc != GKS_BC_PEC) return GKS_E_ARG;
   }
   for (int a = 0; a < (d->kind == GKS_TET ? 0 : d->dim); ++a) {
     if (d->n[a] < 1 || d->n[a] > (1 << 24)) return GKS_E_ARG;
     if (!(d->hi[a] > d->lo[a]) || !std::isfinite(d->hi[a] - d->lo[a])) return GKS_E_ARG;
     const int b0 = d->bc[2 * a], b1 = d->bc[2 * a + 1];
-    if ((b0 != GKS_BC_PERIODIC && b0 != GKS_BC_NONREFLECTING) ||
-        (b1 != GKS_BC_PERIODIC && b1 != GKS_BC_NONREFLECTING))
-      return GKS_E_ARG;
+    auto known = [](int b) {
+      return b == GKS_BC_PERIODIC || b == GKS_BC_NONREFLECTING || b == GKS_BC_PEC;
+    };
+    if (!known(b0) || !known(b1)) return GKS_E_ARG;
     if ((b0 == GKS_BC_PERIODIC) != (b1 == GKS_BC_PERIODIC)) return GKS_E_ARG;
+    if ((b0 == GKS_BC_PEC || b1 == GKS_BC_PEC) && d->n[a] < 2) return GKS_E_ARG;
   }
 
   gks_ctx *ctx = new (std::nothrow) gks_ctx();
@@ -240,6 +243,8 @@ gks_status gks_create_mesh(const gks_mesh_desc *d, gks_ctx **out) {
     for (int a = 0; a < d->dim; ++a) {
       g.h[a] = (d->hi[a] - d->lo[a]) / (double)d->n[a];
       g.periodic[a] = d->bc[2 * a] == GKS_BC_PERIODIC;
+      g.pec[2 * a] = d->bc[2 * a] == GKS_BC_PEC;
+      g.pec[2 * a + 1] = d->bc[2 * a + 1] == GKS_BC_PEC;
     }
     // h_i = 2 dim |Omega| / sum_s |l_s| for a box cell is dim / sum_a (1/h_a); it equals the
     // edge for squares and cubes.
@@ -608,6 +613,9 @@ gks_status gks_adjoint_step(gks_ctx *ctx, const void *state_n, const void *state
   if (ctx->kind != GKS_CARTESIAN || ctx->dim != 2)
     return fail(ctx, GKS_E_UNSUPPORTED, "the adjoint needs a 2-D Cartesian grid");
   if (ctx->mu) return fail(ctx, GKS_E_UNSUPPORTED, "the adjoint supports mu = 1 only");
+  for (int k = 0; k < 4; ++k)
+    if (ctx->g.pec[k])
+      return fail(ctx, GKS_E_UNSUPPORTED, "the adjoint supports periodic and non-reflecting sides only");
   if (!adj_in || !adj_out || adj_in == adj_out) return fail(ctx, GKS_E_ARG, "adj_in / adj_out");
   if (ctx->nd > 0 && (!grad_eps || !state_n || !state_np1))
     return fail(ctx, GKS_E_ARG, "the eps-gradient needs both states and grad_eps");

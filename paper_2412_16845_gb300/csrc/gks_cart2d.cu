@@ -10,7 +10,10 @@
 //
 // Face frames (Sec. 3.1, T'(n)): an x-face uses n = e_x (T' = I); a y-face n = e_y with local
 // axes (x', y') = (y, -x); the low boundary faces use the outward normals -e_x (T' =
-// diag(-1,-1,1)) and -e_y (local (x', y') = (-y, x)).  In 2-D TM the third-moment term of the
+// diag(-1,-1,1)) and -e_y (local (x', y') = (-y, x)).  A PEC wall (Sec. 5.5) is an interior face
+// against mirror-image cells: the loads reflect the index across the wall and negate the
+// tangential E and the normal H, so the ghost's gradient and reconstruction are the mirror of
+// the inner cell's.  In 2-D TM the third-moment term of the
 // D3Q4 flux vanishes, so a TM face flux does not depend on the tangential orientation.
 #include <cuda_runtime.h>
 
@@ -160,18 +163,36 @@ struct Cart2DKernelArgs {
   int nx, ny;
   int64_t pitch, cstride;
   int perx, pery;
+  int pec[4];          // PEC wall on the -x, +x, -y, +y side
   T inv2hx, inv2hy;
   FaceK<T> fx, fy;     // interior x- and y-faces
   Coef<T> Kx, Ky;      // boundary faces (scalar path)
   int *flag;
 };
 
-__device__ __forceinline__ int wrap_or_clamp(int i, int n, int periodic) {
+// Cell of index i on an axis of n cells: periodic wrap, PEC mirror (m = true: the entry is the
+// mirror image -1-i or 2n-1-i; indices further out than the two-cell stencil are clamped) or
+// the non-reflecting clamp.
+__device__ __forceinline__ int axis_index(int i, int n, int periodic, int pec_lo, int pec_hi,
+                                          bool &m) {
+  m = false;
   if (periodic) {
     i %= n;
     return i < 0 ? i + n : i;
   }
-  return i < 0 ? 0 : (i >= n ? n - 1 : i);
+  if (i < 0) {
+    if (!pec_lo) return 0;
+    m = true;
+    i = -1 - i;
+    return i < n ? i : n - 1;
+  }
+  if (i >= n) {
+    if (!pec_hi) return n - 1;
+    m = true;
+    i = 2 * n - 1 - i;
+    return i >= 0 ? i : 0;
+  }
+  return i;
 }
 
 // One row of a thread's column: (Ez, Hx, Hy) and the material.
@@ -211,7 +232,9 @@ template <typename T, bool HAS_MU>
 __device__ __forceinline__ Row2<T> load_row2(const Cart2DKernelArgs<T> &p, int X, int row) {
   using P = typename Pair2<T>::type;
   Row2<T> v;
-  const int r = wrap_or_clamp(row, p.ny, p.pery);
+  // PEC mirror images: an x-wall negates Ez and Hx, a y-wall Ez and Hy
+  bool ym;
+  const int r = axis_index(row, p.ny, p.pery, p.pec[2], p.pec[3], ym);
   const int64_t ro = (int64_t)r * p.pitch;
   if (X >= 0 && X + 1 < p.nx) {
     const P a = __ldg(reinterpret_cast<const P *>(p.V + ro + X));
@@ -227,13 +250,19 @@ __device__ __forceinline__ Row2<T> load_row2(const Cart2DKernelArgs<T> &p, int X
   } else {
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
-      const int64_t o = ro + wrap_or_clamp(X + k, p.nx, p.perx);
+      bool xm;
+      const int64_t o = ro + axis_index(X + k, p.nx, p.perx, p.pec[0], p.pec[1], xm);
       v.ez[k] = __ldg(p.V + o);
       v.hx[k] = __ldg(p.V + p.cstride + o);
       v.hy[k] = __ldg(p.V + 2 * p.cstride + o);
+      if (xm) { v.ez[k] = -v.ez[k]; v.hx[k] = -v.hx[k]; }
       v.eps[k] = __ldg(p.eps + o);
       if (HAS_MU) v.mu[k] = __ldg(p.mu + o);
     }
+  }
+  if (ym) {
+#pragma unroll
+    for (int k = 0; k < 2; ++k) { v.ez[k] = -v.ez[k]; v.hy[k] = -v.hy[k]; }
   }
   if (!HAS_MU) { v.mu[0] = T(1); v.mu[1] = T(1); }
   return v;
@@ -358,7 +387,10 @@ __global__ void __launch_bounds__(WARPS * 32, GKS_CART2D_MINBLOCKS) cart2d_step_
   const int x0 = strip * WCOLS;
   const int X = x0 - 2 + 2 * lane;
   const int xend = min(x0 + WCOLS, p.nx);
-  const bool xnr = !p.perx, ynr = !p.pery;
+  // non-reflecting sides use the kinetic ghost faces; PEC walls are interior faces against the
+  // mirrored loads, periodic sides wrap
+  const bool xlo_nr = !p.perx && !p.pec[0], xhi_nr = !p.perx && !p.pec[1];
+  const bool ylo_nr = !p.pery && !p.pec[2], yhi_nr = !p.pery && !p.pec[3];
   const T q4 = T(0.25), mq4 = T(-0.25);
 
   // ---------------- prologue: rows y0-2 .. y0+3 loaded, differences of rows y0-1, y0
@@ -375,7 +407,7 @@ __global__ void __launch_bounds__(WARPS * 32, GKS_CART2D_MINBLOCKS) cart2d_step_
   T fbE[2], fbHx[2], fbHy[2];                         // flux along +y below row j
 #pragma unroll
   for (int k = 0; k < 2; ++k) {
-    if (y0 == 0 && ynr)
+    if (y0 == 0 && ylo_nr)
       low_y_boundary_flux<T>(col_of(v0, k), g0[k], p, fbE[k], fbHx[k], fbHy[k]);
     else
       face_flux<T, HAS_MU>(yface_side<T>(col_of(vm1, k), gm1[k], q4),
@@ -408,7 +440,7 @@ __global__ void __launch_bounds__(WARPS * 32, GKS_CART2D_MINBLOCKS) cart2d_step_
                            fxE[0], fxHx[0], fxHy[0]);
       face_flux<T, HAS_MU>(xface_side<T>(c1, g0[1], q4), xface_side<T>(nb, gn, mq4), p.fx,
                            fxE[1], fxHx[1], fxHy[1]);
-      if (xnr) {
+      if (xhi_nr) {
         if (X == p.nx - 1) {            // first face on the high-x boundary
           const Side<T> q = xside_scalar<T>(c0, g0[0], q4, p.inv2hx, p.inv2hy);
           tm_face_flux<T, true>(q, q, p.Kx, fxE[0], fxHx[0], fxHy[0]);
@@ -417,10 +449,10 @@ __global__ void __launch_bounds__(WARPS * 32, GKS_CART2D_MINBLOCKS) cart2d_step_
           const Side<T> q = xside_scalar<T>(c1, g0[1], q4, p.inv2hx, p.inv2hy);
           tm_face_flux<T, true>(q, q, p.Kx, fxE[1], fxHx[1], fxHy[1]);
         }
-        if (X == -2) {                  // second face is the low-x boundary face of column 0
-          low_boundary_flux<T>(xside_scalar<T>(nb, gn, mq4, p.inv2hx, p.inv2hy), p.Kx, fxE[1],
-                               fxHx[1], fxHy[1]);
-        }
+      }
+      if (xlo_nr && X == -2) {          // second face is the low-x boundary face of column 0
+        low_boundary_flux<T>(xside_scalar<T>(nb, gn, mq4, p.inv2hx, p.inv2hy), p.Kx, fxE[1],
+                             fxHx[1], fxHy[1]);
       }
     }
     // y-faces between rows j and j+1
@@ -428,7 +460,7 @@ __global__ void __launch_bounds__(WARPS * 32, GKS_CART2D_MINBLOCKS) cart2d_step_
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
       const RowV<T> c = col_of(v0, k);
-      if (j + 1 == p.ny && ynr) {
+      if (j + 1 == p.ny && yhi_nr) {
         const Side<T> q = yside_scalar<T>(c, g0[k], q4, p.inv2hx, p.inv2hy);
         T oe, oa, ob;
         tm_face_flux<T, true>(q, q, p.Ky, oe, oa, ob);
@@ -527,6 +559,7 @@ cudaError_t launch_t(const CartGeom &g, const CartStepArgs &a, cudaStream_t st) 
   p.nx = g.nx; p.ny = g.ny;
   p.pitch = g.pitch; p.cstride = g.cstride;
   p.perx = g.periodic[0]; p.pery = g.periodic[1];
+  for (int k = 0; k < 4; ++k) p.pec[k] = g.pec[k];
   p.inv2hx = T(0.5 / g.h[0]); p.inv2hy = T(0.5 / g.h[1]);
   p.fx = make_face_k<T>(a.C, g.h[0], g.h[1], a.c, 1.0, 1.0);
   p.fy = make_face_k<T>(a.C, g.h[1], g.h[0], a.c, -1.0, -1.0);

@@ -11,7 +11,9 @@
 // Face frames (Sec. 3.1, T'(n)): interior faces use n = +e_x (frame (x, y, z)), n = +e_y
 // (frame (y, -x, z)) and n = +e_z (frame (z, y, -x)); boundary faces on the low sides use the
 // outward normals -e_x (frame (-x, -y, z)), -e_y (frame (-y, x, z)) and -e_z (frame (-z, y, x)).
-// Every frame is a signed permutation of the axes, so rotations cost nothing.
+// Every frame is a signed permutation of the axes, so rotations cost nothing.  A PEC wall
+// (Sec. 5.5) is an interior face against mirror-image cells (index reflected across the wall,
+// tangential E and normal H negated).
 #include <cuda_runtime.h>
 
 #include "gks_flux3.cuh"
@@ -143,6 +145,7 @@ struct Cart3DArgs {
   int nx, ny, nz;
   int64_t pitch, plane, cstride;
   int per[3];
+  int pec[6];          // PEC wall on the -x, +x, -y, +y, -z, +z side
   T inv2h[3], halfh[3];
   K3<T> K[3];
   F3K<T> FK[3];
@@ -150,12 +153,28 @@ struct Cart3DArgs {
   int *flag;
 };
 
-__device__ __forceinline__ int wrap_clamp(int i, int n, int periodic) {
+// Cell of index i on an axis of n cells: periodic wrap, PEC mirror (m = true: the entry is the
+// mirror image -1-i or 2n-1-i, clamped beyond the stencil) or the non-reflecting clamp.
+__device__ __forceinline__ int axis_index3(int i, int n, int periodic, int pec_lo, int pec_hi,
+                                           bool &m) {
+  m = false;
   if (periodic) {
     i %= n;
     return i < 0 ? i + n : i;
   }
-  return i < 0 ? 0 : (i >= n ? n - 1 : i);
+  if (i < 0) {
+    if (!pec_lo) return 0;
+    m = true;
+    i = -1 - i;
+    return i < n ? i : n - 1;
+  }
+  if (i >= n) {
+    if (!pec_hi) return n - 1;
+    m = true;
+    i = 2 * n - 1 - i;
+    return i >= 0 ? i : 0;
+  }
+  return i;
 }
 
 template <typename T>
@@ -168,12 +187,25 @@ struct Smem3 {
 // Load one staged entry (x, y, z) of all quantities into registers.
 template <typename T, bool HAS_MU>
 __device__ __forceinline__ void load_entry(const Cart3DArgs<T> &p, int x, int y, int z, T out[NV]) {
-  const int xx = wrap_clamp(x, p.nx, p.per[0]);
-  const int yy = wrap_clamp(y, p.ny, p.per[1]);
-  const int zz = wrap_clamp(z, p.nz, p.per[2]);
+  bool m[3];
+  const int xx = axis_index3(x, p.nx, p.per[0], p.pec[0], p.pec[1], m[0]);
+  const int yy = axis_index3(y, p.ny, p.per[1], p.pec[2], p.pec[3], m[1]);
+  const int zz = axis_index3(z, p.nz, p.per[2], p.pec[4], p.pec[5], m[2]);
   const int64_t o = (int64_t)zz * p.plane + (int64_t)yy * p.pitch + xx;
 #pragma unroll
   for (int c = 0; c < 6; ++c) out[c] = __ldg(p.V + c * p.cstride + o);
+  // PEC mirror image across the walls of axes a with m[a]: E_c keeps its sign if c == a (normal
+  // E) and flips otherwise; H_c flips if c == a (normal H) and keeps it otherwise
+  if (m[0] | m[1] | m[2]) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      if (m[a])
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          if (c == a) out[3 + c] = -out[3 + c];
+          else out[c] = -out[c];
+        }
+  }
   out[6] = __ldg(p.eps + o);
   out[7] = HAS_MU ? __ldg(p.mu + o) : T(1);
 }
@@ -244,9 +276,11 @@ __global__ void __launch_bounds__(Geo3<T>::NTH, 1) cart3d_step_kernel(const Cart
     else { const int k = tid - 2 * PX; rpy = 1 + (k >> 1); rpx = (k & 1) ? PX - 1 : 0; }
   }
   const int rx = x0 - 2 + rpx, ry = y0 - 2 + rpy;
-  const bool xlo = !p.per[0] && x == -1, xhi = !p.per[0] && x == p.nx - 1;
-  const bool ylo = !p.per[1] && y == -1, yhi = !p.per[1] && y == p.ny - 1;
-  const bool znr = !p.per[2];
+  // kinetic ghost faces on non-reflecting sides only (PEC walls are interior faces against the
+  // mirrored loads)
+  const bool xlo = !p.per[0] && !p.pec[0] && x == -1, xhi = !p.per[0] && !p.pec[1] && x == p.nx - 1;
+  const bool ylo = !p.per[1] && !p.pec[2] && y == -1, yhi = !p.per[1] && !p.pec[3] && y == p.ny - 1;
+  const bool zlo_nr = !p.per[2] && !p.pec[4], zhi_nr = !p.per[2] && !p.pec[5];
 
   T own[NV], ring[NV];
   // ---------------- prologue: stage planes z0-1, z0, z0+1; gradients of z0-1 and z0
@@ -282,7 +316,7 @@ __global__ void __launch_bounds__(Geo3<T>::NTH, 1) cart3d_step_kernel(const Cart
     Cell3<T> cm1, c0;
     cell_from<T>(s, sm1, ty + 1, tx + 1, gm1, cm1);
     cell_from<T>(s, s0, ty + 1, tx + 1, g0, c0);
-    if (z0 == 0 && znr)
+    if (z0 == 0 && zlo_nr)
       low_boundary_face<T, FrameZm>(c0, p.halfh[2], p.K[2], fzb);
     else
       interior_face<T, FrameZp, HAS_MU>(cm1, c0, p.halfh[2], p.K[2], p.FK[2], fzb);
@@ -376,7 +410,7 @@ __global__ void __launch_bounds__(Geo3<T>::NTH, 1) cart3d_step_kernel(const Cart
       }
     }
     if (inner) {
-      if (z + 1 == p.nz && znr) {
+      if (z + 1 == p.nz && zhi_nr) {
         high_boundary_face<T, FrameZp>(c0, p.halfh[2], p.K[2], fzt);
       } else {
         Cell3<T> c1;
@@ -435,6 +469,8 @@ cudaError_t launch3_t(const CartGeom &g, const CartStepArgs &a, cudaStream_t st)
   p.pitch = g.pitch; p.plane = g.plane; p.cstride = g.cstride;
   for (int d = 0; d < 3; ++d) {
     p.per[d] = g.periodic[d];
+    p.pec[2 * d] = g.pec[2 * d];
+    p.pec[2 * d + 1] = g.pec[2 * d + 1];
     p.inv2h[d] = T(0.5 / g.h[d]);
     p.halfh[d] = T(0.5 * g.h[d]);
     p.K[d] = make_k3<T>(a.C, g.h[d], a.c);

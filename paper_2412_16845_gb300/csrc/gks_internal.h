@@ -26,6 +26,7 @@ struct CartGeom {
   int64_t cstride = 0;  // elements per component: plane * nz
   double h[3] = {1, 1, 1};
   int periodic[3] = {0, 0, 0};
+  int pec[6] = {0, 0, 0, 0, 0, 0};   // per side -x,+x,-y,+y,-z,+z: PEC wall (mirror ghost)
 };
 
 // Arguments of one Cartesian step launch (precision-independent; kernels cast).
@@ -80,6 +81,7 @@ struct TetDev {
   void *cgeo = nullptr;         // [nt][kTetCellGeo], context precision
   void *Gscratch = nullptr;     // [18][nt] gradients
   void *Fscratch = nullptr;     // [6][nf] face fluxes (times dt and |l|)
+  int pec = 0;                  // boundary faces are PEC walls (else non-reflecting)
 };
 
 cudaError_t launch_tet_step(const TetDev &g, const void *V, void *Vout, const void *eps,

@@ -31,7 +31,8 @@ int blocks_for(int64_t n) {
 
 template <typename T>
 __global__ void tet_gradient_kernel(const T *__restrict__ V, const int32_t *__restrict__ cnb,
-                                    const T *__restrict__ cgeo, int64_t nt, T *__restrict__ G) {
+                                    const T *__restrict__ cgeo, int64_t nt, int pec,
+                                    T *__restrict__ G) {
   const int64_t i = blockIdx.x * (int64_t)TB + threadIdx.x;
   if (i >= nt) return;
   T vi[6];
@@ -49,6 +50,19 @@ __global__ void tet_gradient_kernel(const T *__restrict__ V, const int32_t *__re
     if (nb >= 0) {
 #pragma unroll
       for (int c = 0; c < 6; ++c) vf[c] = T(0.5) * (vi[c] + V[c * nt + nb]);
+    } else if (pec) {
+      // PEC wall: face value (V + P V)/2 of the mirror ghost P V = (-E + 2 (E.n) n, H - 2 (H.n) n),
+      // i.e. the normal part of E and the tangential part of H
+      const T *w = cgeo + kTetCellGeo * i + 3 * k;
+      const T inv = T(1) / sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+      const T n[3] = {w[0] * inv, w[1] * inv, w[2] * inv};
+      const T en = vi[0] * n[0] + vi[1] * n[1] + vi[2] * n[2];
+      const T hn = vi[3] * n[0] + vi[4] * n[1] + vi[5] * n[2];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        vf[a] = en * n[a];
+        vf[3 + a] = vi[3 + a] - hn * n[a];
+      }
     } else {
 #pragma unroll
       for (int c = 0; c < 6; ++c) vf[c] = vi[c];
@@ -118,11 +132,29 @@ __device__ __forceinline__ Side3<T> tet_side(const T *__restrict__ V, const T *_
   return s;
 }
 
+// The mirror ghost of a side across a PEC wall, in the face frame (n, t, w): values
+// (En, -Et, -Ew, -Hn, Ht, Hw); the normal derivative flips once more.
+template <typename T>
+__device__ __forceinline__ Side3<T> pec_ghost(const Side3<T> &l) {
+  Side3<T> g;
+  const T p[6] = {T(1), T(-1), T(-1), T(-1), T(1), T(1)};
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    g.v[c] = p[c] * l.v[c];
+    g.dn[c] = -p[c] * l.dn[c];
+    g.dt[c] = p[c] * l.dt[c];
+    g.dw[c] = p[c] * l.dw[c];
+  }
+  g.eps = l.eps;
+  g.mu = l.mu;
+  return g;
+}
+
 template <typename T, bool HAS_MU>
 __global__ void tet_face_kernel(const T *__restrict__ V, const T *__restrict__ G,
                                 const T *__restrict__ eps, const T *__restrict__ mu,
                                 const int32_t *__restrict__ fL, const int32_t *__restrict__ fR,
-                                const T *__restrict__ fgeo, int64_t nt, int64_t nf,
+                                const T *__restrict__ fgeo, int64_t nt, int64_t nf, int pec,
                                 const K3<T> K, const F3K<T> FK, T *__restrict__ F) {
   const int64_t f = blockIdx.x * (int64_t)TB + threadIdx.x;
   if (f >= nf) return;
@@ -138,6 +170,12 @@ __global__ void tet_face_kernel(const T *__restrict__ V, const T *__restrict__ G
       flux3<T, false>(l, r, K, loc);
     else
       flux3_mu1<T>(l, r, FK, trcp2(l.eps + r.eps), loc);
+  } else if (pec) {
+    const Side3<T> r = pec_ghost(l);
+    if (HAS_MU)
+      flux3<T, false>(l, r, K, loc);
+    else
+      flux3_mu1<T>(l, r, FK, trcp(l.eps), loc);
   } else {
     flux3<T, true>(l, l, K, loc);
   }
@@ -258,16 +296,16 @@ cudaError_t step_t(const TetDev &g, const void *Vin, void *Vout, const void *eps
   T *G = static_cast<T *>(g.Gscratch);
   T *F = static_cast<T *>(g.Fscratch);
   const T *fgeo = static_cast<const T *>(g.fgeo), *cgeo = static_cast<const T *>(g.cgeo);
-  tet_gradient_kernel<T><<<blocks_for(g.nt), TB, 0, st>>>(V, g.cnb, cgeo, g.nt, G);
+  tet_gradient_kernel<T><<<blocks_for(g.nt), TB, 0, st>>>(V, g.cnb, cgeo, g.nt, g.pec, G);
   const K3<T> K = make_k3<T>(C, 1.0, c);     // fluxes carry dt (C_i), areas applied per face
   const F3K<T> FK = make_f3k<T>(C, 1.0, c);
   if (mu)
     tet_face_kernel<T, true><<<blocks_for(g.nf), TB, 0, st>>>(
         V, G, static_cast<const T *>(eps), static_cast<const T *>(mu), g.fL, g.fR, fgeo, g.nt,
-        g.nf, K, FK, F);
+        g.nf, g.pec, K, FK, F);
   else
     tet_face_kernel<T, false><<<blocks_for(g.nf), TB, 0, st>>>(
-        V, G, static_cast<const T *>(eps), nullptr, g.fL, g.fR, fgeo, g.nt, g.nf, K, FK, F);
+        V, G, static_cast<const T *>(eps), nullptr, g.fL, g.fR, fgeo, g.nt, g.nf, g.pec, K, FK, F);
   tet_update_kernel<T><<<blocks_for(g.nt), TB, 0, st>>>(
       V, static_cast<T *>(Vout), static_cast<const T *>(eps), static_cast<const T *>(mu),
       static_cast<const T *>(src), T(src_amp), g.cface, cgeo, F, g.nt, g.nf, flag);

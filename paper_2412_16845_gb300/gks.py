@@ -20,7 +20,7 @@ GKS_OK, GKS_E_ARG, GKS_E_NOMEM, GKS_E_CUDA, GKS_E_UNSUPPORTED, GKS_E_STATE, \
     GKS_E_NONFINITE, GKS_E_TIMEOUT = range(8)
 GKS_CARTESIAN, GKS_TET = 0, 1
 GKS_FP32, GKS_FP64 = 0, 1
-GKS_BC_PERIODIC, GKS_BC_NONREFLECTING = 0, 1
+GKS_BC_PERIODIC, GKS_BC_NONREFLECTING, GKS_BC_PEC = 0, 1, 2
 
 STATUS_NAMES = {0: "GKS_OK", 1: "GKS_E_ARG", 2: "GKS_E_NOMEM", 3: "GKS_E_CUDA",
                 4: "GKS_E_UNSUPPORTED", 5: "GKS_E_STATE", 6: "GKS_E_NONFINITE",
@@ -249,7 +249,7 @@ def gks_destroy(ctx):
 
 # ------------------------------------------------------------------------ convenience class
 
-_BC = {"periodic": GKS_BC_PERIODIC, "nrbc": GKS_BC_NONREFLECTING}
+_BC = {"periodic": GKS_BC_PERIODIC, "nrbc": GKS_BC_NONREFLECTING, "pec": GKS_BC_PEC}
 
 
 @dataclass
@@ -289,9 +289,10 @@ class GKSSolver:
         self.ctx = gks_create_mesh(d)
 
     @classmethod
-    def from_tets(cls, vert, tet, cfl, precision="fp32", kappa=0.0, c_lattice=1.0, stream=0):
-        """A context on a conforming tetrahedral mesh (vert [nv][3], tet [nt][4]) with the
-        kinetic non-reflecting boundary on every boundary face."""
+    def from_tets(cls, vert, tet, cfl, precision="fp32", kappa=0.0, c_lattice=1.0, stream=0,
+                  bc="nrbc"):
+        """A context on a conforming tetrahedral mesh (vert [nv][3], tet [nt][4]); every boundary
+        face is kinetic non-reflecting (bc="nrbc") or a PEC wall (bc="pec")."""
         vert = np.ascontiguousarray(vert, dtype=np.float64)
         tet = np.ascontiguousarray(tet, dtype=np.int64)
         d = gks_mesh_desc()
@@ -302,7 +303,7 @@ class GKSSolver:
         d.vert_xyz = vert.ctypes.data_as(_D)
         d.n_tet = tet.shape[0]
         d.tet_vert = tet.ctypes.data_as(_I64)
-        d.tet_bc = GKS_BC_NONREFLECTING
+        d.tet_bc = _BC[bc]
         d.cfl = cfl
         d.tau_over_dt = kappa
         d.c_lattice = c_lattice
