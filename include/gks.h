@@ -118,6 +118,13 @@ gks_status gks_write_fields(gks_ctx *ctx, const double *fields, double t0);
 gks_status gks_set_source(gks_ctx *ctx, const double *jz_mask, double A, double f0, double t0,
                           double s);
 
+/* Continuous-wave current source of the oscillating-dipole workloads (Sec. 5.4), S = (-J, 0):
+ *     J_z(x_i, t) = jz_mask[i] * A * cos(2 pi f0 (t - t0))  for t >= t0, 0 before,
+ * evaluated explicitly at t^n (the paper's J_z = J_0 cos(2 pi t / T) is A = J_0, f0 = 1/T,
+ * t0 = 0).  jz_mask: [n_cells] doubles, user order, or NULL to remove the source.  Replaces a
+ * source set by gks_set_source. */
+gks_status gks_set_source_cw(gks_ctx *ctx, const double *jz_mask, double A, double f0, double t0);
+
 /* Override dt (> 0) and recompute C1..C5; used to land exactly on a final time. */
 gks_status gks_set_dt(gks_ctx *ctx, double dt);
 

@@ -538,10 +538,19 @@ def source_signal(t, A, f0, t0, s):
     return A * math.exp(-(((t - t0) / s) ** 2)) * math.sin(2.0 * math.pi * f0 * (t - t0))
 
 
+def source_signal_cw(t, A, f0, t0):
+    """Time-harmonic current of the oscillating dipole (Sec. 5.4): A cos(2 pi f0 (t - t0)),
+    switched on at t0."""
+    return A * math.cos(2.0 * math.pi * f0 * (t - t0)) if t >= t0 else 0.0
+
+
 def run(mesh: FVMesh, fields, eps, mu, cfl, nsteps, kappa=0.0, c=1.0, jz_mask=None,
-        src=None, t0=0.0, dt=None, probe=None, callback=None):
+        src=None, t0=0.0, dt=None, probe=None, callback=None, waveform="gauss_sine"):
     """Advance ``nsteps`` steps from user fields [ncomp][ncell].  Returns (fields, info) with
-    info = {dt, t, J} (J only when ``probe`` is given: sum over n = 1..N of the probe term)."""
+    info = {dt, t, J} (J only when ``probe`` is given: sum over n = 1..N of the probe term).
+    The source is jz_mask times source_signal(t, *src) ("gauss_sine") or
+    source_signal_cw(t, *src) ("cw")."""
+    signal = source_signal_cw if waveform == "cw" else source_signal
     dim = mesh.dim
     V = fields_to_state(fields, dim)
     m = material_diag(np.asarray(eps), None if mu is None else np.asarray(mu))
@@ -553,7 +562,7 @@ def run(mesh: FVMesh, fields, eps, mu, cfl, nsteps, kappa=0.0, c=1.0, jz_mask=No
         t = t0 + n * dt
         jz = None
         if jz_mask is not None:
-            jz = jz_mask * source_signal(t, *src)
+            jz = jz_mask * signal(t, *src)
         V = step(mesh, V, m, dt, C, c, jz)
         if probe is not None:
             J = J + probe_term(mesh, V, probe, dt)

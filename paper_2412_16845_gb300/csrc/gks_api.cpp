@@ -325,16 +325,10 @@ gks_status gks_write_fields(gks_ctx *ctx, const double *fields, double t0) {
   return GKS_OK;
 }
 
-gks_status gks_set_source(gks_ctx *ctx, const double *jz_mask, double A, double f0, double t0,
-                          double s) {
-  if (!ctx) return GKS_E_ARG;
-  if (!jz_mask) {
-    if (ctx->src) GKS_CUDA(cudaFreeAsync(ctx->src, ctx->st));
-    ctx->src = nullptr;
-    return GKS_OK;
-  }
-  if (!std::isfinite(A) || !std::isfinite(f0) || !std::isfinite(t0) || !finite_positive(s))
-    return fail(ctx, GKS_E_ARG, "source parameters must be finite and s > 0");
+namespace {
+
+// Upload a source mask and its bounding box (shared by both waveforms).
+gks_status set_source_mask(gks_ctx *ctx, const double *jz_mask) {
   const gks::CartGeom &g = ctx->g;
   int box[6] = {g.nx, -1, g.ny, -1, g.nz, -1};
   for (int64_t i = 0; i < ctx->ncell; ++i) {
@@ -359,10 +353,47 @@ gks_status gks_set_source(gks_ctx *ctx, const double *jz_mask, double A, double 
   ctx->src_box[0] = box[0]; ctx->src_box[1] = box[1] + 1;
   ctx->src_box[2] = box[2]; ctx->src_box[3] = box[3] + 1;
   ctx->src_box[4] = box[4]; ctx->src_box[5] = box[5] + 1;
+  return GKS_OK;
+}
+
+}  // namespace
+
+gks_status gks_set_source(gks_ctx *ctx, const double *jz_mask, double A, double f0, double t0,
+                          double s) {
+  if (!ctx) return GKS_E_ARG;
+  if (!jz_mask) {
+    if (ctx->src) GKS_CUDA(cudaFreeAsync(ctx->src, ctx->st));
+    ctx->src = nullptr;
+    return GKS_OK;
+  }
+  if (!std::isfinite(A) || !std::isfinite(f0) || !std::isfinite(t0) || !finite_positive(s))
+    return fail(ctx, GKS_E_ARG, "source parameters must be finite and s > 0");
+  gks_status st = set_source_mask(ctx, jz_mask);
+  if (st != GKS_OK) return st;
+  ctx->srcKind = 0;
   ctx->srcA = A;
   ctx->srcF0 = f0;
   ctx->srcT0 = t0;
   ctx->srcS = s;
+  return GKS_OK;
+}
+
+gks_status gks_set_source_cw(gks_ctx *ctx, const double *jz_mask, double A, double f0, double t0) {
+  if (!ctx) return GKS_E_ARG;
+  if (!jz_mask) {
+    if (ctx->src) GKS_CUDA(cudaFreeAsync(ctx->src, ctx->st));
+    ctx->src = nullptr;
+    return GKS_OK;
+  }
+  if (!std::isfinite(A) || !std::isfinite(f0) || !std::isfinite(t0))
+    return fail(ctx, GKS_E_ARG, "source parameters must be finite");
+  gks_status st = set_source_mask(ctx, jz_mask);
+  if (st != GKS_OK) return st;
+  ctx->srcKind = 1;
+  ctx->srcA = A;
+  ctx->srcF0 = f0;
+  ctx->srcT0 = t0;
+  ctx->srcS = 1.0;
   return GKS_OK;
 }
 
@@ -392,8 +423,11 @@ gks_status step_impl(gks_ctx *ctx, int64_t n_steps, const int win[4], bool objec
     a.src_amp = 0.0;
     if (ctx->src) {
       const double tt = t - ctx->srcT0;
-      a.src_amp = ctx->dt * ctx->srcA * std::exp(-(tt / ctx->srcS) * (tt / ctx->srcS)) *
-                  std::sin(2.0 * M_PI * ctx->srcF0 * tt);
+      if (ctx->srcKind == 1)
+        a.src_amp = tt >= 0.0 ? ctx->dt * ctx->srcA * std::cos(2.0 * M_PI * ctx->srcF0 * tt) : 0.0;
+      else
+        a.src_amp = ctx->dt * ctx->srcA * std::exp(-(tt / ctx->srcS) * (tt / ctx->srcS)) *
+                    std::sin(2.0 * M_PI * ctx->srcF0 * tt);
     }
     a.V = ctx->V[ctx->cur];
     a.Vout = ctx->V[ctx->cur ^ 1];

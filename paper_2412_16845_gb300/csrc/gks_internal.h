@@ -158,6 +158,7 @@ struct gks_ctx {
   void *src = nullptr;          // J_z mask or null
   int src_box[6] = {0, 0, 0, 0, 0, 0};
   double srcA = 0, srcF0 = 0, srcT0 = 0, srcS = 1;
+  int srcKind = 0;              // 0: Gaussian-modulated sine, 1: continuous wave (cosine)
   int *flag = nullptr;
   double *red = nullptr;        // reduction scratch (partials + result)
   int red_n = 0;

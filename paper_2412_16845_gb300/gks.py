@@ -60,6 +60,8 @@ SIGNATURES = {
     "gks_write_fields": (ctypes.c_int, [_CTX, _D, ctypes.c_double]),
     "gks_set_source": (ctypes.c_int, [_CTX, _D, ctypes.c_double, ctypes.c_double,
                                       ctypes.c_double, ctypes.c_double]),
+    "gks_set_source_cw": (ctypes.c_int, [_CTX, _D, ctypes.c_double, ctypes.c_double,
+                                         ctypes.c_double]),
     "gks_set_dt": (ctypes.c_int, [_CTX, ctypes.c_double]),
     "gks_step": (ctypes.c_int, [_CTX, ctypes.c_int64]),
     "gks_read_fields": (ctypes.c_int, [_CTX, _D]),
@@ -141,6 +143,10 @@ def gks_write_fields(ctx, fields, t0=0.0):
 
 def gks_set_source(ctx, jz_mask, A, f0, t0, s):
     _check(ctx, load_library().gks_set_source(ctx, _dptr(jz_mask), A, f0, t0, s))
+
+
+def gks_set_source_cw(ctx, jz_mask, A, f0, t0):
+    _check(ctx, load_library().gks_set_source_cw(ctx, _dptr(jz_mask), A, f0, t0))
 
 
 def gks_set_dt(ctx, dt):
@@ -330,7 +336,10 @@ class GKSSolver:
         s.set_materials(w.eps, w.mu)
         s.write_fields(w.fields0)
         if w.jz_mask is not None:
-            s.set_source(w.jz_mask, *w.src)
+            if getattr(w, "waveform", "gauss_sine") == "cw":
+                s.set_source_cw(w.jz_mask, *w.src)
+            else:
+                s.set_source(w.jz_mask, *w.src)
         return s
 
     def set_materials(self, eps, mu=None):
@@ -344,6 +353,10 @@ class GKSSolver:
     def set_source(self, jz_mask, A, f0, t0, s):
         gks_set_source(self.ctx, None if jz_mask is None else _f64(jz_mask, self.ncell),
                        A, f0, t0, s)
+
+    def set_source_cw(self, jz_mask, A, f0, t0=0.0):
+        gks_set_source_cw(self.ctx, None if jz_mask is None else _f64(jz_mask, self.ncell),
+                          A, f0, t0)
 
     def set_dt(self, dt):
         gks_set_dt(self.ctx, dt)

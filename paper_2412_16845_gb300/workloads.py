@@ -111,14 +111,15 @@ class CartWorkload:
     n: tuple
     lo: tuple
     hi: tuple
-    bc: tuple                 # per side (-x,+x,-y,+y[,-z,+z]): "periodic" | "nrbc"
+    bc: tuple                 # per side (-x,+x,-y,+y[,-z,+z]): "periodic" | "nrbc" | "pec"
     cfl: float
     steps: int
     eps: np.ndarray           # [ncell]
     mu: np.ndarray | None     # [ncell] or None (= 1)
     fields0: np.ndarray       # [ncomp][ncell]
     jz_mask: np.ndarray | None = None   # [ncell] or None
-    src: tuple = (SRC_A, SRC_F0, SRC_T0, SRC_S)
+    src: tuple = (SRC_A, SRC_F0, SRC_T0, SRC_S)   # "cw": (A, f0, t0)
+    waveform: str = "gauss_sine"         # "gauss_sine" or "cw" (continuous cosine)
     probe: np.ndarray | None = None      # int64 cell ids
     design: np.ndarray | None = None     # int64 cell ids
     c_lattice: float = 1.0               # lattice speed c of the workload (c = 1 in Sec. 5)
@@ -183,6 +184,33 @@ def config2_cylinders_tm(n: int = 4096, steps: int = 2000) -> CartWorkload:
         name=f"tm2d_cylinders_{n}", dim=2, n=(n, n), lo=(0.0, 0.0), hi=(1.0, 1.0),
         bc=("nrbc",) * 4, cfl=0.5, steps=steps, eps=eps, mu=None,
         fields0=np.zeros((3, n * n)), jz_mask=mask, extra={"cylinders": cyl, "i_src": i_src})
+
+
+def dipole_tm(n: int = 100, two: bool = False, t_end: float | None = None,
+              J0: float = 1.0, T: float = 0.1) -> CartWorkload:
+    """The oscillating electric dipole of Sec. 5.4: a z-directed current J_z = J0 cos(2 pi t/T)
+    on the 2 x 2 cells around the dipole point (the points are cell corners), vacuum,
+    non-reflecting boundary on all sides, CFL 0.5, fields start at zero.  One dipole at the
+    centre of [0,1]^2 on n x n cells (run to t = 3), or two at (0.7, 0.5) and (1.3, 0.5) on
+    [0,2] x [0,1] with 2n x n cells (run to t = 2)."""
+    nx, ny = (2 * n, n) if two else (n, n)
+    Lx = 2.0 if two else 1.0
+    h = Lx / nx
+    pts = [(0.7, 0.5), (1.3, 0.5)] if two else [(0.5, 0.5)]
+    mask = np.zeros(nx * ny)
+    for px, py in pts:
+        i, j = int(round(px / h)), int(round(py / h))      # the dipole point is the corner i, j
+        for jj in (j - 1, j):
+            for ii in (i - 1, i):
+                mask[jj * nx + ii] = 1.0
+    t_end = t_end if t_end is not None else (2.0 if two else 3.0)
+    dt = 0.5 * h
+    steps = int(math.ceil(t_end / dt - 1e-9))
+    return CartWorkload(
+        name=f"tm2d_dipole{'2' if two else ''}_{n}", dim=2, n=(nx, ny), lo=(0.0, 0.0),
+        hi=(Lx, 1.0), bc=("nrbc",) * 4, cfl=0.5, steps=steps, eps=np.ones(nx * ny), mu=None,
+        fields0=np.zeros((3, nx * ny)), jz_mask=mask, src=(J0, 1.0 / T, 0.0), waveform="cw",
+        extra={"dipoles": pts, "t_end": t_end})
 
 
 def incident_pulse_3d(x):

@@ -161,3 +161,4 @@ def test_pec_adjoint_is_unsupported():
     with pytest.raises(GksError):
         gks_adjoint_step(s.ctx, None, None, a.data_ptr(), b.data_ptr(), None, False)
     s.close()
+
