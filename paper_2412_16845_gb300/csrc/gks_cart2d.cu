@@ -222,19 +222,35 @@ template <typename T> struct Pair2;
 template <> struct Pair2<float> { using type = float2; };
 template <> struct Pair2<double> { using type = double2; };
 
-// Two columns of one row: (Ez, Hx, Hy, eps, mu).
+// Two columns of one row: (Ez, Hx, Hy, eps, mu), and which entries are PEC mirror images
+// (xm: of an x-wall, per column; ym: of a y-wall).  The signs of a mirror image are applied by
+// apply_mirror when the row enters the working window, not at the load, so that a prefetched
+// row is not waited for early.
 template <typename T>
 struct Row2 {
   T ez[2], hx[2], hy[2], eps[2], mu[2];
+  bool xm[2], ym;
 };
 
-template <typename T, bool HAS_MU>
+// PEC mirror image: an x-wall negates Ez and Hx, a y-wall Ez and Hy.
+template <typename T>
+__device__ __forceinline__ void apply_mirror(Row2<T> &v) {
+  if (v.ym | v.xm[0] | v.xm[1]) {
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      if (v.xm[k] != v.ym) v.ez[k] = -v.ez[k];
+      if (v.xm[k]) v.hx[k] = -v.hx[k];
+      if (v.ym) v.hy[k] = -v.hy[k];
+    }
+  }
+}
+
+template <typename T, bool HAS_MU, bool HAS_PEC>
 __device__ __forceinline__ Row2<T> load_row2(const Cart2DKernelArgs<T> &p, int X, int row) {
   using P = typename Pair2<T>::type;
   Row2<T> v;
-  // PEC mirror images: an x-wall negates Ez and Hx, a y-wall Ez and Hy
-  bool ym;
-  const int r = axis_index(row, p.ny, p.pery, p.pec[2], p.pec[3], ym);
+  const int r = axis_index(row, p.ny, p.pery, HAS_PEC && p.pec[2], HAS_PEC && p.pec[3], v.ym);
+  v.xm[0] = v.xm[1] = false;
   const int64_t ro = (int64_t)r * p.pitch;
   if (X >= 0 && X + 1 < p.nx) {
     const P a = __ldg(reinterpret_cast<const P *>(p.V + ro + X));
@@ -250,19 +266,14 @@ __device__ __forceinline__ Row2<T> load_row2(const Cart2DKernelArgs<T> &p, int X
   } else {
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
-      bool xm;
-      const int64_t o = ro + axis_index(X + k, p.nx, p.perx, p.pec[0], p.pec[1], xm);
+      const int64_t o =
+          ro + axis_index(X + k, p.nx, p.perx, HAS_PEC && p.pec[0], HAS_PEC && p.pec[1], v.xm[k]);
       v.ez[k] = __ldg(p.V + o);
       v.hx[k] = __ldg(p.V + p.cstride + o);
       v.hy[k] = __ldg(p.V + 2 * p.cstride + o);
-      if (xm) { v.ez[k] = -v.ez[k]; v.hx[k] = -v.hx[k]; }
       v.eps[k] = __ldg(p.eps + o);
       if (HAS_MU) v.mu[k] = __ldg(p.mu + o);
     }
-  }
-  if (ym) {
-#pragma unroll
-    for (int k = 0; k < 2; ++k) { v.ez[k] = -v.ez[k]; v.hy[k] = -v.hy[k]; }
   }
   if (!HAS_MU) { v.mu[0] = T(1); v.mu[1] = T(1); }
   return v;
@@ -374,7 +385,7 @@ __device__ __forceinline__ void diffs2(const Row2<T> &c, const Row2<T> &dn, cons
   right[0] = rE; right[1] = rA; right[2] = rB;
 }
 
-template <typename T, bool HAS_MU>
+template <typename T, bool HAS_MU, bool HAS_PEC>
 __global__ void __launch_bounds__(WARPS * 32, GKS_CART2D_MINBLOCKS) cart2d_step_kernel(const Cart2DKernelArgs<T> p,
                                                                  int nstrips, int rows,
                                                                  int strip0, int ybeg, int yend) {
@@ -394,12 +405,19 @@ __global__ void __launch_bounds__(WARPS * 32, GKS_CART2D_MINBLOCKS) cart2d_step_
   const T q4 = T(0.25), mq4 = T(-0.25);
 
   // ---------------- prologue: rows y0-2 .. y0+3 loaded, differences of rows y0-1, y0
-  Row2<T> vm2 = load_row2<T, HAS_MU>(p, X, y0 - 2);
-  Row2<T> vm1 = load_row2<T, HAS_MU>(p, X, y0 - 1);
-  Row2<T> v0 = load_row2<T, HAS_MU>(p, X, y0);
-  Row2<T> v1 = load_row2<T, HAS_MU>(p, X, y0 + 1);
-  Row2<T> v2 = load_row2<T, HAS_MU>(p, X, y0 + 2);
-  Row2<T> pf = load_row2<T, HAS_MU>(p, X, y0 + 3);
+  Row2<T> vm2 = load_row2<T, HAS_MU, HAS_PEC>(p, X, y0 - 2);
+  Row2<T> vm1 = load_row2<T, HAS_MU, HAS_PEC>(p, X, y0 - 1);
+  Row2<T> v0 = load_row2<T, HAS_MU, HAS_PEC>(p, X, y0);
+  Row2<T> v1 = load_row2<T, HAS_MU, HAS_PEC>(p, X, y0 + 1);
+  Row2<T> v2 = load_row2<T, HAS_MU, HAS_PEC>(p, X, y0 + 2);
+  Row2<T> pf = load_row2<T, HAS_MU, HAS_PEC>(p, X, y0 + 3);
+  if (HAS_PEC) {
+    apply_mirror(vm2);
+    apply_mirror(vm1);
+    apply_mirror(v0);
+    apply_mirror(v1);
+    apply_mirror(v2);
+  }
   RowG<T> g0[2], gm1[2];
   T r0[3], rm1[3];
   diffs2<T>(vm1, vm2, v0, gm1, rm1);
@@ -417,7 +435,7 @@ __global__ void __launch_bounds__(WARPS * 32, GKS_CART2D_MINBLOCKS) cart2d_step_
   bool bad = false;
 #pragma unroll 1
   for (int j = y0; j < y1; ++j) {
-    const Row2<T> pf2 = load_row2<T, HAS_MU>(p, X, j + 4);   // two rows ahead of use
+    const Row2<T> pf2 = load_row2<T, HAS_MU, HAS_PEC>(p, X, j + 4);   // two rows ahead of use
     RowG<T> g1[2];
     T r1[3];
     diffs2<T>(v1, v0, v2, g1, r1);
@@ -525,6 +543,7 @@ __global__ void __launch_bounds__(WARPS * 32, GKS_CART2D_MINBLOCKS) cart2d_step_
     }
     // rotate the register window
     v0 = v1; v1 = v2; v2 = pf; pf = pf2;
+    if (HAS_PEC) apply_mirror(v2);            // the prefetched row takes its mirror signs now
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
       g0[k] = g1[k];
@@ -583,10 +602,19 @@ cudaError_t launch_t(const CartGeom &g, const CartStepArgs &a, cudaStream_t st) 
   const int nchunks = (wrows + rows - 1) / rows;
   const int64_t nwarps = (int64_t)nstrips * nchunks;
   const int grid = (int)((nwarps + WARPS - 1) / WARPS);
-  if (a.mu)
-    cart2d_step_kernel<T, true><<<grid, WARPS * 32, 0, st>>>(p, nstrips, rows, strip0, wy0, wy1);
-  else
-    cart2d_step_kernel<T, false><<<grid, WARPS * 32, 0, st>>>(p, nstrips, rows, strip0, wy0, wy1);
+  // PEC walls get their own instantiation: without them the mirror bookkeeping folds away
+  const bool pec = g.pec[0] || g.pec[1] || g.pec[2] || g.pec[3];
+  if (a.mu) {
+    if (pec)
+      cart2d_step_kernel<T, true, true><<<grid, WARPS * 32, 0, st>>>(p, nstrips, rows, strip0, wy0, wy1);
+    else
+      cart2d_step_kernel<T, true, false><<<grid, WARPS * 32, 0, st>>>(p, nstrips, rows, strip0, wy0, wy1);
+  } else {
+    if (pec)
+      cart2d_step_kernel<T, false, true><<<grid, WARPS * 32, 0, st>>>(p, nstrips, rows, strip0, wy0, wy1);
+    else
+      cart2d_step_kernel<T, false, false><<<grid, WARPS * 32, 0, st>>>(p, nstrips, rows, strip0, wy0, wy1);
+  }
   return cudaGetLastError();
 }
 

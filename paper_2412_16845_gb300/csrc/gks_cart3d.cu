@@ -185,18 +185,18 @@ struct Smem3 {
 };
 
 // Load one staged entry (x, y, z) of all quantities into registers.
-template <typename T, bool HAS_MU>
+template <typename T, bool HAS_MU, bool HAS_PEC>
 __device__ __forceinline__ void load_entry(const Cart3DArgs<T> &p, int x, int y, int z, T out[NV]) {
   bool m[3];
-  const int xx = axis_index3(x, p.nx, p.per[0], p.pec[0], p.pec[1], m[0]);
-  const int yy = axis_index3(y, p.ny, p.per[1], p.pec[2], p.pec[3], m[1]);
-  const int zz = axis_index3(z, p.nz, p.per[2], p.pec[4], p.pec[5], m[2]);
+  const int xx = axis_index3(x, p.nx, p.per[0], HAS_PEC && p.pec[0], HAS_PEC && p.pec[1], m[0]);
+  const int yy = axis_index3(y, p.ny, p.per[1], HAS_PEC && p.pec[2], HAS_PEC && p.pec[3], m[1]);
+  const int zz = axis_index3(z, p.nz, p.per[2], HAS_PEC && p.pec[4], HAS_PEC && p.pec[5], m[2]);
   const int64_t o = (int64_t)zz * p.plane + (int64_t)yy * p.pitch + xx;
 #pragma unroll
   for (int c = 0; c < 6; ++c) out[c] = __ldg(p.V + c * p.cstride + o);
   // PEC mirror image across the walls of axes a with m[a]: E_c keeps its sign if c == a (normal
   // E) and flips otherwise; H_c flips if c == a (normal H) and keeps it otherwise
-  if (m[0] | m[1] | m[2]) {
+  if (HAS_PEC && (m[0] | m[1] | m[2])) {
 #pragma unroll
     for (int a = 0; a < 3; ++a)
       if (m[a])
@@ -252,7 +252,7 @@ __device__ __forceinline__ void load_grad(const Smem3<T> &s, int gs, int ty, int
 }
 
 // One CTA per SM: FP32 512 threads (registers capped at 128), FP64 256.
-template <typename T, bool HAS_MU>
+template <typename T, bool HAS_MU, bool HAS_PEC>
 __global__ void __launch_bounds__(Geo3<T>::NTH, 1) cart3d_step_kernel(const Cart3DArgs<T> p) {
   constexpr int BY = Geo3<T>::BY, PY = Geo3<T>::PY;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -285,18 +285,18 @@ __global__ void __launch_bounds__(Geo3<T>::NTH, 1) cart3d_step_kernel(const Cart
   T own[NV], ring[NV];
   // ---------------- prologue: stage planes z0-1, z0, z0+1; gradients of z0-1 and z0
   T ownm2[NV];
-  load_entry<T, HAS_MU>(p, x, y, z0 - 2, ownm2);
+  load_entry<T, HAS_MU, HAS_PEC>(p, x, y, z0 - 2, ownm2);
   for (int dz = -1; dz <= 1; ++dz) {
-    load_entry<T, HAS_MU>(p, x, y, z0 + dz, own);
+    load_entry<T, HAS_MU, HAS_PEC>(p, x, y, z0 + dz, own);
     stage<T>(s, (z0 + dz + NSLOT) % NSLOT, ty + 1, tx + 1, own);
     if (ringer) {
-      load_entry<T, HAS_MU>(p, rx, ry, z0 + dz, ring);
+      load_entry<T, HAS_MU, HAS_PEC>(p, rx, ry, z0 + dz, ring);
       stage<T>(s, (z0 + dz + NSLOT) % NSLOT, rpy, rpx, ring);
     }
   }
   T pf[NV], pfr[NV];
-  load_entry<T, HAS_MU>(p, x, y, z0 + 2, pf);
-  if (ringer) load_entry<T, HAS_MU>(p, rx, ry, z0 + 2, pfr);
+  load_entry<T, HAS_MU, HAS_PEC>(p, x, y, z0 + 2, pf);
+  if (ringer) load_entry<T, HAS_MU, HAS_PEC>(p, rx, ry, z0 + 2, pfr);
   __syncthreads();
   T fzb[6];     // flux along +z through the face below the plane being processed
   {
@@ -436,8 +436,8 @@ __global__ void __launch_bounds__(Geo3<T>::NTH, 1) cart3d_step_kernel(const Cart
       stage<T>(s, s2, ty + 1, tx + 1, pf);
       if (ringer) stage<T>(s, s2, rpy, rpx, pfr);
       if (z + 3 <= z1 + 1) {
-        load_entry<T, HAS_MU>(p, x, y, z + 3, pf);
-        if (ringer) load_entry<T, HAS_MU>(p, rx, ry, z + 3, pfr);
+        load_entry<T, HAS_MU, HAS_PEC>(p, x, y, z + 3, pf);
+        if (ringer) load_entry<T, HAS_MU, HAS_PEC>(p, rx, ry, z + 3, pfr);
       }
     }
 #pragma unroll
@@ -482,19 +482,19 @@ cudaError_t launch3_t(const CartGeom &g, const CartStepArgs &a, cudaStream_t st)
   const int smem = (int)sizeof(Smem3<T>);
   // z chunks: a CTA marches zchunk planes after a two-plane prologue.  Pick the chunk count
   // that fills whole waves of resident CTAs best, counting the prologue as lost work.
-  static int resident[2][2] = {{0, 0}, {0, 0}};   // [fp64][has_mu]
-  int &res = resident[sizeof(T) == 8][a.mu ? 1 : 0];
+  // PEC walls get their own instantiation: without them the mirror bookkeeping folds away
+  const bool pec = g.pec[0] || g.pec[1] || g.pec[2] || g.pec[3] || g.pec[4] || g.pec[5];
+  void (*kern)(const Cart3DArgs<T>) =
+      a.mu ? (pec ? cart3d_step_kernel<T, true, true> : cart3d_step_kernel<T, true, false>)
+           : (pec ? cart3d_step_kernel<T, false, true> : cart3d_step_kernel<T, false, false>);
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  static int resident[2][2][2] = {};   // [fp64][has_mu][pec]
+  int &res = resident[sizeof(T) == 8][a.mu ? 1 : 0][pec ? 1 : 0];
   if (!res) {
     int dev = 0, sms = 0, bps = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (a.mu) {
-      cudaFuncSetAttribute(cart3d_step_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, cart3d_step_kernel<T, true>, NTH, smem);
-    } else {
-      cudaFuncSetAttribute(cart3d_step_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, cart3d_step_kernel<T, false>, NTH, smem);
-    }
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, NTH, smem);
     res = sms * (bps > 0 ? bps : 1);
   }
   const int64_t tiles = (int64_t)gx * gy;
@@ -511,15 +511,7 @@ cudaError_t launch3_t(const CartGeom &g, const CartStepArgs &a, cudaStream_t st)
   p.zchunk = (g.nz + zchunks - 1) / zchunks;
   zchunks = (g.nz + p.zchunk - 1) / p.zchunk;
   dim3 grid(gx, gy, zchunks);
-  if (a.mu) {
-    cudaFuncSetAttribute(cart3d_step_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         smem);
-    cart3d_step_kernel<T, true><<<grid, NTH, smem, st>>>(p);
-  } else {
-    cudaFuncSetAttribute(cart3d_step_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         smem);
-    cart3d_step_kernel<T, false><<<grid, NTH, smem, st>>>(p);
-  }
+  kern<<<grid, NTH, smem, st>>>(p);
   return cudaGetLastError();
 }
 
