@@ -61,15 +61,23 @@ M_BLOCKS = np.array([
 ], dtype=np.float64)
 
 
-def flux_dir(j: int, V):
+def flux_dir(j: int, V, phm=None):
     """F_j(V) for direction j in {0,1,2}: the E rows are M_j H, the B (here H) rows M_j^T E.
 
-    V has shape [..., 6] = (E, H).  In the paper's units H = c^2 B, so this is the printed
-    F_j(U) of Sec. 2.1 with chi = gamma = 0."""
+    V has shape [..., 6] = (E, H), or [..., 8] = (E, H, phi, psi) for the divergence-cleaning
+    (PHM) system with phm = (chi, gamma): then E_j gains chi phi, H_j gains gamma psi, and the
+    phi and psi rows are chi E_j and gamma H_j.  In the paper's units H = c^2 B (c = 1), so this
+    is the printed F_j(U) of Sec. 2.1."""
     Mj = M_BLOCKS[j]
-    out = np.empty(V.shape, dtype=V.dtype)
+    out = np.zeros(V.shape, dtype=V.dtype)
     out[..., 0:3] = V[..., 3:6] @ Mj.T      # M_j H
     out[..., 3:6] = V[..., 0:3] @ Mj        # M_j^T E
+    if V.shape[-1] == 8:
+        chi, gamma = phm if phm is not None else (0.0, 0.0)
+        out[..., j] = out[..., j] + chi * V[..., 6]
+        out[..., 3 + j] = out[..., 3 + j] + gamma * V[..., 7]
+        out[..., 6] = chi * V[..., j]
+        out[..., 7] = gamma * V[..., 3 + j]
     return out
 
 
@@ -88,19 +96,19 @@ def lattice(dim: int, c: float = 1.0) -> np.ndarray:
     return u
 
 
-def equilibrium(U, V, uk, c: float):
+def equilibrium(U, V, uk, c: float, phm=None):
     """g_k = U/4 + sum_j u_k^j F_j(V) / (4 c^2)  (Sec. 2.2; material reading U = M V)."""
     g = U / 4.0
     for j in range(3):
         if uk[j] != 0.0:
-            g = g + uk[j] * flux_dir(j, V) / (4.0 * c * c)
+            g = g + uk[j] * flux_dir(j, V, phm) / (4.0 * c * c)
     return g
 
 
-def equilibria(U, V, u, c: float):
+def equilibria(U, V, u, c: float, phm=None):
     """[g_0, g_1, g_2, g_3] for all four lattice velocities (the same formula as
     :func:`equilibrium`, with the three F_j(V) evaluated once)."""
-    F = [flux_dir(j, V) for j in range(3)]
+    F = [flux_dir(j, V, phm) for j in range(3)]
     out = []
     for k in range(u.shape[0]):
         g = U / 4.0
@@ -175,23 +183,29 @@ def rotation(n) -> np.ndarray:
 
 
 def _rot_vec6(T, V):
-    """Apply diag(T', T') to [nf, 6] vectors."""
-    V3 = V.reshape(V.shape[0], 2, 3)
-    return np.matmul(V3, np.swapaxes(T, 1, 2)).reshape(V.shape)      # (T' v)^T = v^T T'^T
+    """Apply diag(T', T') to [nf, 6] vectors (the scalars phi, psi of [nf, 8] stay)."""
+    out = V.copy()
+    V3 = V[:, :6].reshape(V.shape[0], 2, 3)
+    out[:, :6] = np.matmul(V3, np.swapaxes(T, 1, 2)).reshape(V.shape[0], 6)   # (T' v)^T = v^T T'^T
+    return out
 
 
 def _rot_vec6_back(T, V):
-    """Apply diag(T', T')^{-1} = diag(T'^T, T'^T)."""
-    V3 = V.reshape(V.shape[0], 2, 3)
-    return np.matmul(V3, T).reshape(V.shape)
+    """Apply diag(T', T')^{-1} = diag(T'^T, T'^T) (scalars unchanged)."""
+    out = V.copy()
+    V3 = V[:, :6].reshape(V.shape[0], 2, 3)
+    out[:, :6] = np.matmul(V3, T).reshape(V.shape[0], 6)
+    return out
 
 
 def _rot_grad(T, G):
-    """Rotate gradients G [nf, 3(direction), 6(field)]: field index by T, direction by T'."""
+    """Rotate gradients G [nf, 3(direction), ncomp(field)]: field index by T (the E and H
+    3-vectors), direction by T'."""
     nf = G.shape[0]
-    G3 = G.reshape(nf, 6, 3)                       # rows (direction, block), columns component
+    G2 = G.copy()
+    G3 = G[:, :, :6].reshape(nf, 6, 3)             # rows (direction, block), columns component
     G3 = np.matmul(G3, np.swapaxes(T, 1, 2))       # field components: T' applied to each 3-vector
-    G2 = G3.reshape(nf, 3, 6)
+    G2[:, :, :6] = G3.reshape(nf, 3, 6)
     return np.matmul(T, G2)                        # direction index: d'_a = sum_d T'[a, d] d_d
 
 
@@ -199,10 +213,11 @@ def _rot_grad(T, G):
 # Sec. 3.1 -- the GKS interface flux, literally per discrete velocity
 # --------------------------------------------------------------------------------------------
 
-def face_flux_local(Vl, Gl, ml, Vr, Gr, mr, ghost, C, dt, c, dim):
+def face_flux_local(Vl, Gl, ml, Vr, Gr, mr, ghost, C, dt, c, dim, phm=None):
     """Time-averaged numerical flux in the face frame (normal = local x).
 
-    Vl, Vr [nf, 6]: reconstructed primitive states (E, H) on the two sides.
+    Vl, Vr [nf, 6]: reconstructed primitive states (E, H) on the two sides ([nf, 8] with the
+    cleaning potentials phi, psi when phm = (chi, gamma) is given).
     Gl, Gr [nf, 3, 6]: their gradients, Gl[:, j] = d/dx_j V^l.
     ml, mr [nf, 6]: diagonals of M on each side.
     ghost [nf] bool: kinetic non-reflecting face -- the r side is a ghost cell whose
@@ -215,10 +230,10 @@ def face_flux_local(Vl, Gl, ml, Vr, Gr, mr, ghost, C, dt, c, dim):
     keep_r = (~ghost).astype(np.float64)[:, None]
     Ul, Ur = ml * Vl, mr * Vr
 
-    gl = equilibria(Ul, Vl, u, c)
-    gr = [keep_r * g for g in equilibria(Ur, Vr, u, c)]
-    dgl_j = [equilibria(ml * Gl[:, j], Gl[:, j], u, c) for j in range(3)]
-    dgr_j = [[keep_r * g for g in equilibria(mr * Gr[:, j], Gr[:, j], u, c)] for j in range(3)]
+    gl = equilibria(Ul, Vl, u, c, phm)
+    gr = [keep_r * g for g in equilibria(Ur, Vr, u, c, phm)]
+    dgl_j = [equilibria(ml * Gl[:, j], Gl[:, j], u, c, phm) for j in range(3)]
+    dgr_j = [[keep_r * g for g in equilibria(mr * Gr[:, j], Gr[:, j], u, c, phm)] for j in range(3)]
     dgl = [[dgl_j[j][k] for j in range(3)] for k in range(4)]      # dgl[k][j] = d_j g_k^l
     dgr = [[dgr_j[j][k] for j in range(3)] for k in range(4)]
     pos = [k for k in range(4) if u[k, 0] > 0.0]
@@ -231,13 +246,13 @@ def face_flux_local(Vl, Gl, ml, Vr, Gr, mr, ghost, C, dt, c, dim):
     ms = np.where(ghost[:, None], ml, 0.5 * (ml + mr))
     V0 = W0 / ms
     dV0 = [dW0[j] / ms for j in range(3)]
-    g0 = equilibria(W0, V0, u, c)
-    dg0_j = [equilibria(dW0[j], dV0[j], u, c) for j in range(3)]
+    g0 = equilibria(W0, V0, u, c, phm)
+    dg0_j = [equilibria(dW0[j], dV0[j], u, c, phm) for j in range(3)]
     dg0 = [[dg0_j[j][k] for j in range(3)] for k in range(4)]
 
     # compatibility: <g_t> = -<u . grad g0>; g_t is the equilibrium of that moment
     W0t = -sum(u[k, j] * dg0[k][j] for k in range(4) for j in range(3))
-    gt = equilibria(W0t, W0t / ms, u, c)
+    gt = equilibria(W0t, W0t / ms, u, c, phm)
 
     def u_dot_grad(dg, k):
         return sum(u[k, j] * dg[k][j] for j in range(3))
@@ -418,11 +433,16 @@ def pec_mirror(n, X):
     """The field of the mirror ghost across a perfect-electric-conductor wall with unit normal n
     (Sec. 5.5 interface conditions): tangential E and normal B (H) change sign, normal E and
     tangential H are kept (their normal derivatives vanish at the wall).  X [..., 6] global
-    components (E, H), n [..., 3]."""
-    E, H = X[..., :3], X[..., 3:]
+    components (E, H), n [..., 3].  With the cleaning potentials (X [..., 8]) the mirror keeps
+    the parities their equations impose: phi (driven by div E, normal E even) is odd, psi
+    (driven by div B, normal B odd) is even."""
+    E, H = X[..., :3], X[..., 3:6]
     En = np.sum(E * n, axis=-1, keepdims=True)
     Hn = np.sum(H * n, axis=-1, keepdims=True)
-    return np.concatenate([-E + 2.0 * En * n, H - 2.0 * Hn * n], axis=-1)
+    parts = [-E + 2.0 * En * n, H - 2.0 * Hn * n]
+    if X.shape[-1] == 8:
+        parts += [-X[..., 6:7], X[..., 7:8]]
+    return np.concatenate(parts, axis=-1)
 
 
 def pec_mirror_grad(n, G):
@@ -448,14 +468,16 @@ def green_gauss(mesh: FVMesh, V):
     return G / mesh.vol[:, None, None]
 
 
-def material_diag(eps, mu):
-    """Diagonal of M = diag(eps I, mu I) per cell, [ncell, 6]."""
+def material_diag(eps, mu, ncomp=6):
+    """Diagonal of M = diag(eps I, mu I) per cell, [ncell, 6]; with the cleaning potentials
+    (ncomp = 8) M = diag(eps I, mu I, 1, 1)."""
     mu = np.ones_like(eps) if mu is None else mu
-    return np.stack([eps, eps, eps, mu, mu, mu], axis=1)
+    cols = [eps, eps, eps, mu, mu, mu] + [np.ones_like(eps)] * (ncomp - 6)
+    return np.stack(cols, axis=1)
 
 
-def face_fluxes(mesh: FVMesh, V, m, C, dt, c=1.0, faces=None):
-    """Global-frame flux F_s . n_s on every face (or on the subset ``faces``), [nf, 6]."""
+def face_fluxes(mesh: FVMesh, V, m, C, dt, c=1.0, faces=None, phm=None):
+    """Global-frame flux F_s . n_s on every face (or on the subset ``faces``), [nf, ncomp]."""
     G = green_gauss(mesh, V)
     sel = np.arange(mesh.nface) if faces is None else np.asarray(faces)
     L, R = mesh.L[sel], mesh.R[sel]
@@ -475,16 +497,17 @@ def face_fluxes(mesh: FVMesh, V, m, C, dt, c=1.0, faces=None):
         mr[pec] = m[L[pec]]
     T = rotation(mesh.normal[sel])
     Fl = face_flux_local(_rot_vec6(T, Vl), _rot_grad(T, G[L]), m[L],
-                         _rot_vec6(T, Vr), _rot_grad(T, Gr), mr, ghost, C, dt, c, mesh.dim)
+                         _rot_vec6(T, Vr), _rot_grad(T, Gr), mr, ghost, C, dt, c, mesh.dim, phm)
     return _rot_vec6_back(T, Fl)
 
 
-def step(mesh: FVMesh, V, m, dt, C, c=1.0, jz=None):
+def step(mesh: FVMesh, V, m, dt, C, c=1.0, jz=None, phm=None):
     """One GKS step: U^{n+1} = U^n - dt/|Omega_i| sum_s +-|l_s| F_s + dt S_i, S = (-J, 0).
 
-    V [ncell, 6] primitive state at t^n; m [ncell, 6] material diagonal; jz [ncell] current
-    density J_z at t^n (or None).  Returns V^{n+1}."""
-    F = face_fluxes(mesh, V, m, C, dt, c)
+    V [ncell, 6] primitive state at t^n ([ncell, 8] with phi, psi for the cleaning system,
+    phm = (chi, gamma)); m the matching material diagonal; jz [ncell] current density J_z at
+    t^n (or None).  Returns V^{n+1}."""
+    F = face_fluxes(mesh, V, m, C, dt, c, phm=phm)
     flux = F * mesh.area[:, None]
     inter = mesh.R >= 0
     net = _scatter_add(mesh.ncell, mesh.L, flux)
@@ -501,7 +524,8 @@ def step(mesh: FVMesh, V, m, dt, C, c=1.0, jz=None):
 # --------------------------------------------------------------------------------------------
 
 def energy(mesh: FVMesh, V, m):
-    """Electromagnetic energy 1/2 sum_i |Omega_i| (eps |E|^2 + mu |H|^2)."""
+    """Electromagnetic energy 1/2 sum_i |Omega_i| (eps |E|^2 + mu |H|^2) (plus phi^2 + psi^2
+    for the cleaning system, the quadratic form its equations conserve)."""
     return 0.5 * float(np.sum(mesh.vol[:, None] * m * V * V))
 
 
@@ -515,22 +539,27 @@ def probe_term(mesh: FVMesh, V, probe, dt):
 # --------------------------------------------------------------------------------------------
 
 TM_COMPONENTS = (2, 3, 4)     # (Ez, Hx, Hy) inside (Ex, Ey, Ez, Hx, Hy, Hz)
+TM_PSI_COMPONENTS = (2, 3, 4, 7)   # (Ez, Hx, Hy, psi) inside (E, H, phi, psi)
 
 
 def fields_to_state(fields, dim):
-    """[ncomp][ncell] user fields -> [ncell, 6] oracle state (2-D: TM in the (E, H) slots)."""
+    """[ncomp][ncell] user fields -> oracle state.  2-D: (Ez, Hx, Hy) -> [ncell, 6] with TM in
+    the (E, H) slots, or (Ez, Hx, Hy, psi) -> [ncell, 8]; 3-D: 6 or 8 rows (E, H[, phi, psi])."""
     fields = np.asarray(fields)
     if dim == 3:
         return np.ascontiguousarray(fields.T)
-    V = np.zeros((fields.shape[1], 6), dtype=fields.dtype)
-    V[:, list(TM_COMPONENTS)] = fields.T
+    width = 8 if fields.shape[0] == 4 else 6
+    comps = TM_PSI_COMPONENTS if width == 8 else TM_COMPONENTS
+    V = np.zeros((fields.shape[1], width), dtype=fields.dtype)
+    V[:, list(comps)] = fields.T
     return V
 
 
 def state_to_fields(V, dim):
     if dim == 3:
         return np.ascontiguousarray(V.T)
-    return np.ascontiguousarray(V[:, list(TM_COMPONENTS)].T)
+    comps = TM_PSI_COMPONENTS if V.shape[1] == 8 else TM_COMPONENTS
+    return np.ascontiguousarray(V[:, list(comps)].T)
 
 
 def source_signal(t, A, f0, t0, s):
@@ -545,15 +574,16 @@ def source_signal_cw(t, A, f0, t0):
 
 
 def run(mesh: FVMesh, fields, eps, mu, cfl, nsteps, kappa=0.0, c=1.0, jz_mask=None,
-        src=None, t0=0.0, dt=None, probe=None, callback=None, waveform="gauss_sine"):
+        src=None, t0=0.0, dt=None, probe=None, callback=None, waveform="gauss_sine", phm=None):
     """Advance ``nsteps`` steps from user fields [ncomp][ncell].  Returns (fields, info) with
     info = {dt, t, J} (J only when ``probe`` is given: sum over n = 1..N of the probe term).
     The source is jz_mask times source_signal(t, *src) ("gauss_sine") or
-    source_signal_cw(t, *src) ("cw")."""
+    source_signal_cw(t, *src) ("cw").  phm = (chi, gamma) runs the divergence-cleaning system of
+    Sec. 2.1 (fields then carry psi in 2-D, phi and psi in 3-D)."""
     signal = source_signal_cw if waveform == "cw" else source_signal
     dim = mesh.dim
     V = fields_to_state(fields, dim)
-    m = material_diag(np.asarray(eps), None if mu is None else np.asarray(mu))
+    m = material_diag(np.asarray(eps), None if mu is None else np.asarray(mu), V.shape[1])
     if dt is None:
         dt = time_step(mesh, cfl, c)
     C = time_coefficients(dt, kappa * dt)
@@ -563,7 +593,7 @@ def run(mesh: FVMesh, fields, eps, mu, cfl, nsteps, kappa=0.0, c=1.0, jz_mask=No
         jz = None
         if jz_mask is not None:
             jz = jz_mask * signal(t, *src)
-        V = step(mesh, V, m, dt, C, c, jz)
+        V = step(mesh, V, m, dt, C, c, jz, phm)
         if probe is not None:
             J = J + probe_term(mesh, V, probe, dt)
         if callback is not None:

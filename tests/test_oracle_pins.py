@@ -760,3 +760,122 @@ def test_dipole_workload_mirror_symmetry():
     assert s > 0
     for other in (ez[:, ::-1], ez[::-1, :], ez.T):
         assert np.max(np.abs(ez - other)) <= 1e-12 * s
+
+
+# ---------------------------------------------------------------------------- divergence cleaning
+
+def test_phm_flux_functions_are_the_cleaning_equations():
+    """Sec. 2.1 (PHM system, c = 1, H = B): for a linear field V(x) = V0 + x.G the divergence
+    of the fluxes, sum_j F_j(d_j V), must equal -dU/dt of dE/dt = curl H - chi grad phi,
+    dH/dt = -curl E - gamma grad psi, dphi/dt = -chi div E, dpsi/dt = -gamma div H, written
+    here with curls, gradients and divergences of the derivative matrix."""
+    rng = np.random.default_rng(11)
+    chi, gamma = 0.7, 1.3
+    G = rng.standard_normal((3, 8))                 # G[j] = d_j V
+    div_F = sum(go.flux_dir(j, G[j], (chi, gamma)) for j in range(3))
+    dE, dH = G[:, 0:3], G[:, 3:6]                   # dE[j, i] = d_j E_i
+    curl = lambda d: np.array([d[1, 2] - d[2, 1], d[2, 0] - d[0, 2], d[0, 1] - d[1, 0]])
+    grad_phi, grad_psi = G[:, 6], G[:, 7]
+    dUdt = np.concatenate([curl(dH) - chi * grad_phi, -curl(dE) - gamma * grad_psi,
+                           [-chi * np.trace(dE), -gamma * np.trace(dH)]])
+    assert np.allclose(div_F, -dUdt, atol=1e-14)
+    # chi = gamma = 0 leaves the Maxwell part and zero cleaning rows
+    F0 = go.flux_dir(1, G[1], (0.0, 0.0))
+    assert np.allclose(F0[:6], go.flux_dir(1, G[1, :6])) and np.all(F0[6:] == 0.0)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_phm_equilibrium_compatibility(dim):
+    """Sec. 2.2 with the cleaning potentials: sum_k g_k = U, sum_k u_k^j g_k = F_j(V)."""
+    rng = np.random.default_rng(12)
+    V = rng.standard_normal((30, 8))
+    m = np.abs(rng.standard_normal((30, 8))) + 0.5
+    m[:, 6:] = 1.0
+    phm = (0.6, 1.4)
+    for c in (1.5, 2.0):
+        u = go.lattice(dim, c)
+        g = go.equilibria(m * V, V, u, c, phm)
+        assert np.allclose(sum(g), m * V, atol=1e-14, rtol=0)
+        for j in range(dim):
+            assert np.allclose(sum(u[k, j] * g[k] for k in range(4)), go.flux_dir(j, V, phm),
+                               atol=1e-13, rtol=0)
+
+
+def _cleaning_wave_error(n, dim, speed):
+    """Standing cleaning wave along x: 2-D (H_x, psi) with gamma, 3-D (E_x, phi) with chi.
+    Initial H_x (E_x) = sin(2 pi x); exact H_x = sin(2 pi x) cos(2 pi s t),
+    psi = -cos(2 pi x) sin(2 pi s t) (s the cleaning speed)."""
+    shape = (n, 4) if dim == 2 else (n, 2, 2)
+    h = 1.0 / n
+    hi = (1.0, 4 * h) if dim == 2 else (1.0, 2 * h, 2 * h)
+    mesh = go.cartesian_mesh(shape, (0.0,) * dim, hi, ("periodic",) * (2 * dim))
+    x = mesh.centroid[:, 0]
+    if dim == 2:
+        f = np.zeros((4, mesh.ncell))
+        f[1] = np.sin(2 * np.pi * x)                 # H_x
+        phm, a, b = (0.0, speed), 1, 3
+    else:
+        f = np.zeros((8, mesh.ncell))
+        f[0] = np.sin(2 * np.pi * x)                 # E_x
+        phm, a, b = (speed, 0.0), 0, 6
+    T = 0.4
+    cfl = 0.4 if dim == 2 else 0.3
+    dt0 = go.time_step(mesh, cfl, 1.0)
+    nst = int(math.ceil(T / dt0))
+    out, info = go.run(mesh, f, np.ones(mesh.ncell), None, cfl, nst, dt=T / nst, phm=phm)
+    w = 2 * np.pi * speed * T
+    ea = out[a] - np.sin(2 * np.pi * x) * math.cos(w)
+    eb = out[b] + np.cos(2 * np.pi * x) * math.sin(w)
+    others = np.delete(out, [a, b], axis=0)
+    return math.sqrt(np.mean(ea ** 2 + eb ** 2)), np.max(np.abs(others))
+
+
+@pytest.mark.parametrize("dim,speed", [(2, 0.5), (2, 1.0), (3, 0.7)])
+def test_cleaning_wave_second_order(dim, speed):
+    """Sec. 2.1: the cleaning potentials carry divergence errors as waves of speed gamma (psi,
+    with div B) or chi (phi, with div E).  The 1-D standing wave converges at second order and
+    leaves the other components at zero."""
+    e1, o1 = _cleaning_wave_error(32, dim, speed)
+    e2, o2 = _cleaning_wave_error(64, dim, speed)
+    assert math.log2(e1 / e2) >= 1.8, (e1, e2)
+    assert e2 <= 2e-3
+    assert max(o1, o2) <= 1e-13
+
+
+def _phm_rho(dim, n, cfl, phm):
+    mesh = go.cartesian_mesh((n,) * dim, (0.0,) * dim, (1.0,) * dim, ("periodic",) * (2 * dim))
+    m = np.ones((mesh.ncell, 8))
+    dt = go.time_step(mesh, cfl)
+    C = go.time_coefficients(dt, 0.0)
+    comps = [2, 3, 4, 7] if dim == 2 else list(range(8))
+    modes = np.array(np.meshgrid(*[np.arange(n)] * dim, indexing="ij")).reshape(dim, -1).T
+    rho = 0.0
+    for kk in modes:
+        k = np.zeros(3)
+        k[:dim] = 2 * np.pi * kk
+        phase = np.exp(1j * (mesh.centroid @ k))
+        Gk = np.zeros((len(comps), len(comps)), dtype=complex)
+        for a, ca in enumerate(comps):
+            V = np.zeros((mesh.ncell, 8), dtype=complex)
+            V[:, ca] = phase
+            out = go.step(mesh, V, m, dt, C, phm=phm)
+            Gk[:, a] = (out[:, comps] / phase[:, None]).mean(axis=0)
+        rho = max(rho, np.abs(np.linalg.eigvals(Gk)).max())
+    return rho
+
+
+@pytest.mark.parametrize("dim,cfl,phm,stable", [
+    (2, 0.4, (0.0, 0.5), True), (2, 0.4, (0.0, 1.0), True), (2, 0.5, (0.0, 1.0), False),
+    (3, 0.3, (1.0, 1.0), True), (3, 0.4, (1.0, 1.0), False),
+])
+def test_phm_amplification_spectrum(dim, cfl, phm, stable):
+    """Von Neumann stability of the periodic step with cleaning (tau = 0, lattice speed 1):
+    with chi, gamma up to 1 the eigenvalues stay in the closed unit disc at CFL 0.4 in 2-D and
+    0.3 in 3-D, but not at the Maxwell workloads' CFL (0.5 in 2-D: rho ~ 1.09 at gamma = 1;
+    0.4 in 3-D: rho ~ 1.40 at chi = gamma = 1).  Cleaning therefore needs the smaller CFL (or a
+    larger lattice speed)."""
+    rho = _phm_rho(dim, 8 if dim == 2 else 5, cfl, phm)
+    if stable:
+        assert rho <= 1.0 + 1e-12, rho
+    else:
+        assert rho >= 1.05, rho
