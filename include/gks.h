@@ -72,7 +72,14 @@ enum { GKS_BC_PERIODIC = 0, GKS_BC_NONREFLECTING = 1, GKS_BC_PEC = 2 };
  *             model); 0 selects the tau -> 0 limit coefficients of Sec. 4.1.
  *  c_lattice  lattice speed c of the D3Q4 velocities (Sec. 2.2); <= 0 selects
  *             max_i 1/sqrt(eps_i mu_i) at gks_set_materials (1 in vacuum).
- *  cuda_stream  cudaStream_t of all device work of this context.                          */
+ *  cuda_stream  cudaStream_t of all device work of this context.
+ *  chi, gamma   divergence cleaning (the PHM system of Sec. 2.1): correction potentials phi,
+ *             psi carry div E and div B errors away at speeds chi c and gamma c.  0 and 0 is
+ *             plain Maxwell.  Supported on 2-D Cartesian grids (TM mode: the state gains psi,
+ *             fields become (Ez, Hx, Hy, psi); chi has no effect there, E being divergence
+ *             free) with mu = 1 and no adjoint; GKS_E_UNSUPPORTED otherwise.  With cleaning the
+ *             step is stable only at smaller CFL numbers (about 0.4 for gamma <= 1 at lattice
+ *             speed 1).                                                                     */
 typedef struct gks_mesh_desc {
   int32_t dim;
   int32_t kind;
@@ -92,6 +99,8 @@ typedef struct gks_mesh_desc {
   double tau_over_dt;
   double c_lattice;
   void *cuda_stream;
+  double chi;
+  double gamma;
 } gks_mesh_desc;
 
 /* Build the geometry (Sec. 3.1: |Omega_i|, |l_s|, n_s, face and cell centroids; T'(n_s) on

@@ -189,6 +189,10 @@ gks_status gks_create_mesh(const gks_mesh_desc *d, gks_ctx **out) {
   if (!finite_positive(d->cfl) || !(d->tau_over_dt >= 0.0) || !std::isfinite(d->tau_over_dt))
     return GKS_E_ARG;
   if (d->kind != GKS_CARTESIAN && d->kind != GKS_TET) return GKS_E_ARG;
+  if (!(d->chi >= 0.0) || !(d->gamma >= 0.0) || !std::isfinite(d->chi) || !std::isfinite(d->gamma))
+    return GKS_E_ARG;
+  const bool phm = d->chi > 0.0 || d->gamma > 0.0;
+  if (phm && (d->kind != GKS_CARTESIAN || d->dim != 2)) return GKS_E_UNSUPPORTED;
   if (d->kind == GKS_TET) {
     if (d->dim != 3 || !d->vert_xyz || !d->tet_vert || d->n_vert < 4 || d->n_tet < 1)
       return GKS_E_ARG;
@@ -214,7 +218,10 @@ gks_status gks_create_mesh(const gks_mesh_desc *d, gks_ctx **out) {
   ctx->st = (cudaStream_t)d->cuda_stream;
   ctx->dim = d->dim;
   ctx->kind = d->kind;
-  ctx->ncomp = d->dim == 2 ? 3 : 6;
+  ctx->ncomp = d->dim == 2 ? (phm ? 4 : 3) : 6;
+  ctx->phm = phm;
+  ctx->chi = d->chi;
+  ctx->gamma = d->gamma;
   ctx->fp64 = d->precision == GKS_FP64;
   ctx->esize = ctx->fp64 ? 8 : 4;
   ctx->cfl = d->cfl;
@@ -252,7 +259,7 @@ gks_status gks_create_mesh(const gks_mesh_desc *d, gks_ctx **out) {
     for (int a = 0; a < d->dim; ++a) sum += 1.0 / g.h[a];
     ctx->min_h = d->dim / sum;
   }
-  ctx->c = ctx->c_user > 0 ? ctx->c_user : 1.0;
+  ctx->c = ctx->c_user > 0 ? ctx->c_user : std::fmax(1.0, ctx->phm ? ctx->gamma : 0.0);
 
   gks_status s = GKS_OK;
   const size_t fbytes = ctx->esize * (size_t)ctx->ncomp * (size_t)g.cstride;
@@ -287,7 +294,9 @@ gks_status gks_create_mesh(const gks_mesh_desc *d, gks_ctx **out) {
 gks_status gks_set_materials(gks_ctx *ctx, const double *eps, const double *mu) {
   if (!ctx) return GKS_E_ARG;
   if (!eps) return fail(ctx, GKS_E_ARG, "eps is NULL");
-  double cmax = 0.0;
+  if (mu && ctx->phm) return fail(ctx, GKS_E_UNSUPPORTED, "divergence cleaning needs mu = 1");
+  // lattice speed: the fastest wave, light 1/sqrt(eps mu) or the cleaning wave gamma (mu = 1)
+  double cmax = ctx->phm ? ctx->gamma : 0.0;
   for (int64_t i = 0; i < ctx->ncell; ++i) {
     const double e = eps[i], m = mu ? mu[i] : 1.0;
     if (!finite_positive(e) || !finite_positive(m))
@@ -437,7 +446,8 @@ gks_status step_impl(gks_ctx *ctx, int64_t n_steps, const int win[4], bool objec
                                a.flag, ctx->fp64, ctx->st);
       ctx->launches += 3;
     } else {
-      e = ctx->dim == 2 ? gks::launch_cart2d_step(ctx->g, a, ctx->fp64, ctx->st)
+      e = ctx->dim == 2 ? (ctx->phm ? gks::launch_cart2d_psi_step(ctx->g, a, ctx->gamma, ctx->fp64, ctx->st)
+                                    : gks::launch_cart2d_step(ctx->g, a, ctx->fp64, ctx->st))
                         : gks::launch_cart3d_step(ctx->g, a, ctx->fp64, ctx->st);
       ctx->launches += 1;
     }
@@ -469,6 +479,7 @@ gks_status gks_step_window(gks_ctx *ctx, int64_t n_steps, int64_t x0, int64_t x1
   if (!ctx) return GKS_E_ARG;
   if (ctx->kind != GKS_CARTESIAN || ctx->dim != 2)
     return fail(ctx, GKS_E_UNSUPPORTED, "windowed steps need a 2-D Cartesian grid");
+  if (ctx->phm) return fail(ctx, GKS_E_UNSUPPORTED, "windowed steps do not cover divergence cleaning");
   if (n_steps < 0 || x0 < 0 || y0 < 0 || x1 > ctx->g.nx || y1 > ctx->g.ny || x0 >= x1 || y0 >= y1)
     return fail(ctx, GKS_E_ARG, "window outside the grid or empty");
   if (!ctx->fields_written) return fail(ctx, GKS_E_STATE, "gks_write_fields must come first");
@@ -647,6 +658,7 @@ gks_status gks_adjoint_step(gks_ctx *ctx, const void *state_n, const void *state
   if (ctx->kind != GKS_CARTESIAN || ctx->dim != 2)
     return fail(ctx, GKS_E_UNSUPPORTED, "the adjoint needs a 2-D Cartesian grid");
   if (ctx->mu) return fail(ctx, GKS_E_UNSUPPORTED, "the adjoint supports mu = 1 only");
+  if (ctx->phm) return fail(ctx, GKS_E_UNSUPPORTED, "the adjoint does not cover divergence cleaning");
   for (int k = 0; k < 4; ++k)
     if (ctx->g.pec[k])
       return fail(ctx, GKS_E_UNSUPPORTED, "the adjoint supports periodic and non-reflecting sides only");

@@ -1,0 +1,454 @@
+// Fused 2-D TM step with divergence cleaning (Sec. 2.1, the PHM system with gamma > 0): the
+// state is (Ez, Hx, Hy, psi), psi carrying div B away at speed gamma (phi decouples in TM: E =
+// Ez(x, y) is divergence free).  mu = 1; eps per cell.
+//
+// The same warp-strip march as cart2d_step_kernel (a warp owns 64 columns, 2 per lane, walks up
+// its rows with the state in registers, x-neighbours by shuffles).  Every face -- interior, PEC
+// wall (mirror-image loads, psi even) and kinetic non-reflecting boundary (a ghost side of zero
+// distributions with eps_s of the inner cell) -- goes through face_flux_psi, the closed form of
+// the per-velocity flux of Sec. 3.1 for this system in sums and differences of the two sides.
+#include <cuda_runtime.h>
+
+#include "gks_flux2.cuh"
+#include "gks_internal.h"
+
+namespace gks {
+namespace {
+
+__device__ __forceinline__ float prcp1(float x) { return __fdividef(1.f, x); }
+__device__ __forceinline__ double prcp1(double x) { return 1.0 / x; }
+__device__ __forceinline__ float prcp2(float x) { return __fdividef(2.f, x); }
+__device__ __forceinline__ double prcp2(double x) { return 2.0 / x; }
+
+// Constants of the gamma terms of a face (K_i = C_i / h_normal, sn = 1/(2 h_normal),
+// stt = 1/(2 h_tangential), sb / st the face frame's signs of H_t and of the tangential
+// derivative; see face_flux_psi).
+template <typename T>
+struct FacePsiK {
+  T pe1, pe2;                       // E
+  T pa1, pa2, pa3, pa4, pa5, pa6;   // H_n (pa1, pa2, pa4, pa5 shared with psi)
+  T h0, h1;                         // sb st stt H = h0 - h1 ie (H_t and psi)
+  T pp5;                            // psi
+};
+
+template <typename T>
+inline FacePsiK<T> make_face_psi(const double C[5], double hn, double ht, double c, double sb,
+                                 double st, double g) {
+  const double K1 = C[0] / hn, K2 = C[1] / hn, K3 = C[2] / hn, K4 = C[3] / hn, K5 = C[4] / hn;
+  const double sn = 0.5 / hn, stt = 0.5 / ht;
+  const double G = g * (K2 * c * c - K3 * g * g - K5 * c * c) / (2.0 * c);
+  FacePsiK<T> k;
+  k.pe1 = T(st * stt * K3 * g / 2.0);
+  k.pe2 = T(-st * stt * K3 * g * g / (2.0 * c));
+  k.pa1 = T(g * (K1 + K4) / 2.0);
+  k.pa2 = T(-K3 * g * g / 2.0 * sn);
+  k.pa3 = T(-K3 * g * g / 2.0 * sb * st * stt);
+  k.pa4 = T(-K1 * g * g / (2.0 * c));
+  k.pa5 = T(-G * sn);
+  k.pa6 = T(-K3 * g * g / (2.0 * c) * st * stt);
+  k.h0 = T(sb * st * stt * g * c * K5 / 2.0);
+  k.h1 = T(sb * st * stt * g * K3 / (2.0 * c));
+  k.pp5 = T(-K3 * g / 2.0 * st * stt);
+  return k;
+}
+
+// One side of a face in global components: reconstructed e = Ez, hn, ht, p = psi; raw central
+// differences along the normal (den, dhn, dht, dnp), along the tangent (dat of Hn, det of Ez,
+// dtp of psi, dtt of Ht); eps.  A kinetic ghost side is all zero.
+template <typename T>
+struct PSide {
+  T e, hn, ht, p, den, dhn, dht, dnp, dat, det, dtp, dtt, eps;
+};
+
+// Flux (times dt/h) of a face: the Maxwell part of face_flux (mu = 1) with ie = 1/eps_s given
+// (2/(eps_l + eps_r) inside, 1/eps of the inner cell on a non-reflecting face) plus the gamma
+// terms, in local quantities (t_x = tangential, n_x = normal true derivatives, S = l + r,
+// D = r - l, G = gamma (c^2 (K2 - K5) - K3 gamma^2)/(2c), H = gamma (c^2 K5 - K3 ie)/(2c)):
+//   E   += K3 gamma/2 S t_psi - K3 gamma^2/(2c) D t_Hn
+//   Hn  += gamma (K1+K4)/2 S psi - K3 gamma^2/2 (S n_Hn + S t_Ht) - K1 gamma^2/(2c) D Hn
+//          - G D n_psi - K3 gamma^2/(2c) D t_E
+//   Ht  += H D t_psi
+//   psi  = gamma (K1+K4)/2 S Hn - K3 gamma^2/2 S n_psi - K1 gamma^2/(2c) D psi - G D n_Hn
+//          + H D t_Ht - K3 gamma ie/2 S (eps t_E)
+template <typename T>
+__device__ __forceinline__ void face_flux_psi(const PSide<T> &l, const PSide<T> &r,
+                                              const FaceK<T> &k, const FacePsiK<T> &q, T ie,
+                                              T &fE, T &fHn, T &fHt, T &fP) {
+  const T Ue_l = l.eps * l.e, Ue_r = r.eps * r.e;
+  const T Uxe_l = l.eps * l.den, Uxe_r = r.eps * r.den;
+  const T S_B = l.ht + r.ht, D_e = r.e - l.e;
+  const T S_Uxe = Uxe_l + Uxe_r, D_xB = r.dht - l.dht;
+  const T D_Ue = Ue_r - Ue_l, D_At = r.dat - l.dat;
+  const T S_Uxa = l.dhn + r.dhn, D_Ua = r.hn - l.hn, D_Et = r.det - l.det;
+  const T S_Ue = Ue_l + Ue_r, D_B = r.ht - l.ht, S_UxB = l.dht + r.dht;
+  const T D_ex = r.den - l.den, S_UAt = l.dat + r.dat, S_e = l.e + r.e;
+  const T g = k.g0 - k.k3 * ie;
+  T fe = k.a1 * S_B + k.a2 * D_e;
+  fe += g * (T(0.5) * S_Uxe + k.a3 * D_xB);
+  fe += k.a4 * S_B - k.q2 * D_Ue - k.q3 * S_Uxe + k.a5 * D_At + k.a6 * D_xB;
+  T fa = k.q5 * S_Uxa - k.q2 * D_Ua + k.b1 * D_Et;
+  T fb = ie * (k.c1 * S_Ue + k.c2 * D_B);
+  fb += g * (T(0.5) * S_UxB + k.c3 * D_ex);
+  fb += k.c4 * ie * S_UAt + k.c5 * S_e - k.q2 * D_B - k.q3 * S_UxB + k.c6 * D_ex;
+  // gamma terms
+  const T S_p = l.p + r.p, D_p = r.p - l.p, S_np = l.dnp + r.dnp, D_np = r.dnp - l.dnp;
+  const T S_tp = l.dtp + r.dtp, D_tp = r.dtp - l.dtp, S_tt = l.dtt + r.dtt, D_tt = r.dtt - l.dtt;
+  const T S_hn = l.hn + r.hn, D_hn_n = r.dhn - l.dhn;
+  const T H = q.h0 - q.h1 * ie;
+  fe += q.pe1 * S_tp + q.pe2 * D_At;
+  fa += q.pa1 * S_p + q.pa2 * S_Uxa + q.pa3 * S_tt + q.pa4 * D_Ua + q.pa5 * D_np + q.pa6 * D_Et;
+  fb += H * D_tp;
+  const T fp = q.pa1 * S_hn + q.pa2 * S_np + q.pa4 * D_p + q.pa5 * D_hn_n + H * D_tt +
+               q.pp5 * ie * (l.eps * l.det + r.eps * r.det);
+  fE = fe;
+  fHn = fa;
+  fHt = fb;
+  fP = fp;
+}
+
+template <typename T>
+struct PsiArgs {
+  const T *__restrict__ V;
+  T *__restrict__ Vout;
+  const T *__restrict__ eps;
+  const T *__restrict__ src;
+  int sx0, sx1, sy0, sy1;
+  T src_amp;
+  int nx, ny;
+  int64_t pitch, cstride;
+  int perx, pery;
+  int pec[4];
+  FaceK<T> fx, fy;
+  FacePsiK<T> qx, qy;
+  int *flag;
+};
+
+__device__ __forceinline__ int psi_axis(int i, int n, int periodic, int pec_lo, int pec_hi,
+                                        bool &m) {
+  m = false;
+  if (periodic) {
+    i %= n;
+    return i < 0 ? i + n : i;
+  }
+  if (i < 0) {
+    if (!pec_lo) return 0;
+    m = true;
+    i = -1 - i;
+    return i < n ? i : n - 1;
+  }
+  if (i >= n) {
+    if (!pec_hi) return n - 1;
+    m = true;
+    i = 2 * n - 1 - i;
+    return i >= 0 ? i : 0;
+  }
+  return i;
+}
+
+constexpr int PWARPS = 4;
+constexpr int PCOLS = 60;
+constexpr unsigned PFULL = 0xffffffffu;
+
+template <typename T> struct PPair;
+template <> struct PPair<float> { using type = float2; };
+template <> struct PPair<double> { using type = double2; };
+
+// Two columns of a row: (Ez, Hx, Hy, psi, eps) and their PEC mirror flags (signs applied when
+// the row enters the working window; psi keeps its sign across a PEC wall).
+template <typename T>
+struct PRow {
+  T ez[2], hx[2], hy[2], ps[2], eps[2];
+  bool xm[2], ym;
+};
+
+template <typename T>
+__device__ __forceinline__ void psi_mirror(PRow<T> &v) {
+  if (v.ym | v.xm[0] | v.xm[1]) {
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      if (v.xm[k] != v.ym) v.ez[k] = -v.ez[k];
+      if (v.xm[k]) v.hx[k] = -v.hx[k];
+      if (v.ym) v.hy[k] = -v.hy[k];
+    }
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ PRow<T> psi_load(const PsiArgs<T> &p, int X, int row) {
+  using P = typename PPair<T>::type;
+  PRow<T> v;
+  const int r = psi_axis(row, p.ny, p.pery, p.pec[2], p.pec[3], v.ym);
+  v.xm[0] = v.xm[1] = false;
+  const int64_t ro = (int64_t)r * p.pitch;
+  if (X >= 0 && X + 1 < p.nx) {
+    const P a = __ldg(reinterpret_cast<const P *>(p.V + ro + X));
+    const P b = __ldg(reinterpret_cast<const P *>(p.V + p.cstride + ro + X));
+    const P c = __ldg(reinterpret_cast<const P *>(p.V + 2 * p.cstride + ro + X));
+    const P d = __ldg(reinterpret_cast<const P *>(p.V + 3 * p.cstride + ro + X));
+    const P e = __ldg(reinterpret_cast<const P *>(p.eps + ro + X));
+    v.ez[0] = a.x; v.ez[1] = a.y; v.hx[0] = b.x; v.hx[1] = b.y; v.hy[0] = c.x; v.hy[1] = c.y;
+    v.ps[0] = d.x; v.ps[1] = d.y; v.eps[0] = e.x; v.eps[1] = e.y;
+  } else {
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int64_t o = ro + psi_axis(X + k, p.nx, p.perx, p.pec[0], p.pec[1], v.xm[k]);
+      v.ez[k] = __ldg(p.V + o);
+      v.hx[k] = __ldg(p.V + p.cstride + o);
+      v.hy[k] = __ldg(p.V + 2 * p.cstride + o);
+      v.ps[k] = __ldg(p.V + 3 * p.cstride + o);
+      v.eps[k] = __ldg(p.eps + o);
+    }
+  }
+  return v;
+}
+
+// Raw central differences of one column: x and y differences of (Ez, Hx, Hy, psi).
+template <typename T>
+struct PG {
+  T ex, ey, ax, ay, bx, by, px, py;
+};
+
+// Differences of the lane's two columns (x-neighbours by shuffle); right[] receives column X+2.
+template <typename T>
+__device__ __forceinline__ void psi_diffs(const PRow<T> &c, const PRow<T> &dn, const PRow<T> &up,
+                                          PG<T> g[2], T right[4]) {
+  const T lE = __shfl_up_sync(PFULL, c.ez[1], 1), rE = __shfl_down_sync(PFULL, c.ez[0], 1);
+  const T lA = __shfl_up_sync(PFULL, c.hx[1], 1), rA = __shfl_down_sync(PFULL, c.hx[0], 1);
+  const T lB = __shfl_up_sync(PFULL, c.hy[1], 1), rB = __shfl_down_sync(PFULL, c.hy[0], 1);
+  const T lP = __shfl_up_sync(PFULL, c.ps[1], 1), rP = __shfl_down_sync(PFULL, c.ps[0], 1);
+  g[0].ex = c.ez[1] - lE; g[1].ex = rE - c.ez[0];
+  g[0].ax = c.hx[1] - lA; g[1].ax = rA - c.hx[0];
+  g[0].bx = c.hy[1] - lB; g[1].bx = rB - c.hy[0];
+  g[0].px = c.ps[1] - lP; g[1].px = rP - c.ps[0];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    g[k].ey = up.ez[k] - dn.ez[k];
+    g[k].ay = up.hx[k] - dn.hx[k];
+    g[k].by = up.hy[k] - dn.hy[k];
+    g[k].py = up.ps[k] - dn.ps[k];
+  }
+  right[0] = rE; right[1] = rA; right[2] = rB; right[3] = rP;
+}
+
+// x-face side (normal x: hn = Hx, ht = Hy, tangent y), reconstructed by sgn4 * raw difference.
+template <typename T>
+__device__ __forceinline__ PSide<T> psi_xside(T ez, T hx, T hy, T ps, T eps, const PG<T> &g,
+                                              T sgn4) {
+  PSide<T> s;
+  s.e = ez + sgn4 * g.ex; s.hn = hx + sgn4 * g.ax; s.ht = hy + sgn4 * g.bx; s.p = ps + sgn4 * g.px;
+  s.den = g.ex; s.dhn = g.ax; s.dht = g.bx; s.dnp = g.px;
+  s.dat = g.ay; s.det = g.ey; s.dtp = g.py; s.dtt = g.by;
+  s.eps = eps;
+  return s;
+}
+
+// y-face side (normal y: hn = Hy, ht = Hx, tangent x).
+template <typename T>
+__device__ __forceinline__ PSide<T> psi_yside(T ez, T hx, T hy, T ps, T eps, const PG<T> &g,
+                                              T sgn4) {
+  PSide<T> s;
+  s.e = ez + sgn4 * g.ey; s.hn = hy + sgn4 * g.by; s.ht = hx + sgn4 * g.ay; s.p = ps + sgn4 * g.py;
+  s.den = g.ey; s.dhn = g.by; s.dht = g.ay; s.dnp = g.py;
+  s.dat = g.bx; s.det = g.ex; s.dtp = g.px; s.dtt = g.ax;
+  s.eps = eps;
+  return s;
+}
+
+template <typename T>
+__device__ __forceinline__ PSide<T> psi_zero() {
+  PSide<T> s;
+  s.e = s.hn = s.ht = s.p = s.den = s.dhn = s.dht = s.dnp = T(0);
+  s.dat = s.det = s.dtp = s.dtt = s.eps = T(0);
+  return s;
+}
+
+template <typename T, bool HAS_PEC>
+__global__ void __launch_bounds__(PWARPS * 32) cart2d_psi_step_kernel(const PsiArgs<T> p,
+                                                                      int nstrips, int rows) {
+  const int lane = threadIdx.x & 31;
+  const int wid = blockIdx.x * PWARPS + (threadIdx.x >> 5);
+  const int strip = wid % nstrips, chunk = wid / nstrips;
+  const int y0 = chunk * rows;
+  if (y0 >= p.ny) return;                             // whole warp leaves together
+  const int y1 = min(y0 + rows, p.ny);
+  const int x0 = strip * PCOLS;
+  const int X = x0 - 2 + 2 * lane;
+  const int xend = min(x0 + PCOLS, p.nx);
+  const bool xlo_nr = !p.perx && !p.pec[0], xhi_nr = !p.perx && !p.pec[1];
+  const bool ylo_nr = !p.pery && !p.pec[2], yhi_nr = !p.pery && !p.pec[3];
+  const T q4 = T(0.25), mq4 = T(-0.25);
+
+  PRow<T> vm2 = psi_load(p, X, y0 - 2), vm1 = psi_load(p, X, y0 - 1), v0 = psi_load(p, X, y0);
+  PRow<T> v1 = psi_load(p, X, y0 + 1), v2 = psi_load(p, X, y0 + 2), pf = psi_load(p, X, y0 + 3);
+  if (HAS_PEC) {
+    psi_mirror(vm2); psi_mirror(vm1); psi_mirror(v0); psi_mirror(v1); psi_mirror(v2);
+  }
+  PG<T> g0[2], gm1[2];
+  T r0[4], rm1[4];
+  psi_diffs<T>(vm1, vm2, v0, gm1, rm1);
+  psi_diffs<T>(v0, vm1, v1, g0, r0);
+  T fbE[2], fbHx[2], fbHy[2], fbP[2];                 // flux along +y below row j
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const PSide<T> up = psi_yside(v0.ez[k], v0.hx[k], v0.hy[k], v0.ps[k], v0.eps[k], g0[k], mq4);
+    if (y0 == 0 && ylo_nr)
+      face_flux_psi<T>(psi_zero<T>(), up, p.fy, p.qy, prcp1(v0.eps[k]), fbE[k], fbHy[k], fbHx[k], fbP[k]);
+    else
+      face_flux_psi<T>(psi_yside(vm1.ez[k], vm1.hx[k], vm1.hy[k], vm1.ps[k], vm1.eps[k], gm1[k], q4),
+                       up, p.fy, p.qy, prcp2(vm1.eps[k] + v0.eps[k]), fbE[k], fbHy[k], fbHx[k], fbP[k]);
+  }
+  bool bad = false;
+#pragma unroll 1
+  for (int j = y0; j < y1; ++j) {
+    const PRow<T> pf2 = psi_load(p, X, j + 4);
+    PG<T> g1[2];
+    T r1[4];
+    psi_diffs<T>(v1, v0, v2, g1, r1);
+    // x-faces X+1/2 and X+3/2 (column X+2 from the next lane)
+    T fxE[2], fxHx[2], fxHy[2], fxP[2];
+    {
+      const T ne = __shfl_down_sync(PFULL, v0.eps[0], 1);
+      PG<T> gn;
+      gn.ex = __shfl_down_sync(PFULL, g0[0].ex, 1);
+      gn.ax = __shfl_down_sync(PFULL, g0[0].ax, 1);
+      gn.bx = __shfl_down_sync(PFULL, g0[0].bx, 1);
+      gn.px = __shfl_down_sync(PFULL, g0[0].px, 1);
+      gn.ay = __shfl_down_sync(PFULL, g0[0].ay, 1);
+      gn.ey = __shfl_down_sync(PFULL, g0[0].ey, 1);
+      gn.by = __shfl_down_sync(PFULL, g0[0].by, 1);
+      gn.py = __shfl_down_sync(PFULL, g0[0].py, 1);
+      const PSide<T> l0 = psi_xside(v0.ez[0], v0.hx[0], v0.hy[0], v0.ps[0], v0.eps[0], g0[0], q4);
+      const PSide<T> r1s = psi_xside(v0.ez[1], v0.hx[1], v0.hy[1], v0.ps[1], v0.eps[1], g0[1], mq4);
+      const PSide<T> l1 = psi_xside(v0.ez[1], v0.hx[1], v0.hy[1], v0.ps[1], v0.eps[1], g0[1], q4);
+      const PSide<T> rn = psi_xside(r0[0], r0[1], r0[2], r0[3], ne, gn, mq4);
+      // first face: high boundary if X is the last column
+      if (xhi_nr && X == p.nx - 1)
+        face_flux_psi<T>(l0, psi_zero<T>(), p.fx, p.qx, prcp1(v0.eps[0]), fxE[0], fxHx[0], fxHy[0], fxP[0]);
+      else
+        face_flux_psi<T>(l0, r1s, p.fx, p.qx, prcp2(v0.eps[0] + v0.eps[1]), fxE[0], fxHx[0], fxHy[0], fxP[0]);
+      // second face: high boundary if X+1 is the last column, low boundary if X+1 = -1
+      if (xhi_nr && X + 1 == p.nx - 1)
+        face_flux_psi<T>(l1, psi_zero<T>(), p.fx, p.qx, prcp1(v0.eps[1]), fxE[1], fxHx[1], fxHy[1], fxP[1]);
+      else if (xlo_nr && X == -2)
+        face_flux_psi<T>(psi_zero<T>(), rn, p.fx, p.qx, prcp1(ne), fxE[1], fxHx[1], fxHy[1], fxP[1]);
+      else
+        face_flux_psi<T>(l1, rn, p.fx, p.qx, prcp2(v0.eps[1] + ne), fxE[1], fxHx[1], fxHy[1], fxP[1]);
+    }
+    // y-faces j+1/2
+    T ftE[2], ftHx[2], ftHy[2], ftP[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const PSide<T> lo = psi_yside(v0.ez[k], v0.hx[k], v0.hy[k], v0.ps[k], v0.eps[k], g0[k], q4);
+      if (j + 1 == p.ny && yhi_nr)
+        face_flux_psi<T>(lo, psi_zero<T>(), p.fy, p.qy, prcp1(v0.eps[k]), ftE[k], ftHy[k], ftHx[k], ftP[k]);
+      else
+        face_flux_psi<T>(lo, psi_yside(v1.ez[k], v1.hx[k], v1.hy[k], v1.ps[k], v1.eps[k], g1[k], mq4),
+                         p.fy, p.qy, prcp2(v0.eps[k] + v1.eps[k]), ftE[k], ftHy[k], ftHx[k], ftP[k]);
+    }
+    // update row j
+    {
+      const T lE = __shfl_up_sync(PFULL, fxE[1], 1), lHx = __shfl_up_sync(PFULL, fxHx[1], 1);
+      const T lHy = __shfl_up_sync(PFULL, fxHy[1], 1), lP = __shfl_up_sync(PFULL, fxP[1], 1);
+      T dE[2], dHx[2], dHy[2], dP[2];
+      dE[0] = (lE - fxE[0]) + (fbE[0] - ftE[0]);
+      dHx[0] = (lHx - fxHx[0]) + (fbHx[0] - ftHx[0]);
+      dHy[0] = (lHy - fxHy[0]) + (fbHy[0] - ftHy[0]);
+      dP[0] = (lP - fxP[0]) + (fbP[0] - ftP[0]);
+      dE[1] = (fxE[0] - fxE[1]) + (fbE[1] - ftE[1]);
+      dHx[1] = (fxHx[0] - fxHx[1]) + (fbHx[1] - ftHx[1]);
+      dHy[1] = (fxHy[0] - fxHy[1]) + (fbHy[1] - ftHy[1]);
+      dP[1] = (fxP[0] - fxP[1]) + (fbP[1] - ftP[1]);
+      const int64_t ro = (int64_t)j * p.pitch;
+      if (p.src && j >= p.sy0 && j < p.sy1) {
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+          if (X + k >= p.sx0 && X + k < p.sx1) dE[k] -= p.src_amp * p.src[ro + X + k];
+      }
+      T out[4][2];
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        out[0][k] = v0.ez[k] + dE[k] * prcp1(v0.eps[k]);
+        out[1][k] = v0.hx[k] + dHx[k];
+        out[2][k] = v0.hy[k] + dHy[k];
+        out[3][k] = v0.ps[k] + dP[k];
+      }
+      const bool ok0 = X >= x0 && X < xend, ok1 = X + 1 >= x0 && X + 1 < xend;
+      using P = typename PPair<T>::type;
+      if (ok0 && ok1) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          P v;
+          v.x = out[c][0]; v.y = out[c][1];
+          *reinterpret_cast<P *>(p.Vout + c * p.cstride + ro + X) = v;
+          bad |= !(isfinite(out[c][0]) && isfinite(out[c][1]));
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+          if (k == 0 ? ok0 : ok1)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              p.Vout[c * p.cstride + ro + X + k] = out[c][k];
+              bad |= !isfinite(out[c][k]);
+            }
+      }
+    }
+    v0 = v1; v1 = v2; v2 = pf; pf = pf2;
+    if (HAS_PEC) psi_mirror(v2);
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      g0[k] = g1[k];
+      fbE[k] = ftE[k]; fbHx[k] = ftHx[k]; fbHy[k] = ftHy[k]; fbP[k] = ftP[k];
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) r0[c] = r1[c];
+  }
+  if (__any_sync(PFULL, bad) && lane == 0) atomicOr(p.flag, 1);
+}
+
+template <typename T>
+cudaError_t launch_psi_t(const CartGeom &g, const CartStepArgs &a, double gamma,
+                         cudaStream_t st) {
+  PsiArgs<T> p;
+  p.V = static_cast<const T *>(a.V);
+  p.Vout = static_cast<T *>(a.Vout);
+  p.eps = static_cast<const T *>(a.eps);
+  p.src = static_cast<const T *>(a.src);
+  p.sx0 = a.src_box[0]; p.sx1 = a.src_box[1];
+  p.sy0 = a.src_box[2]; p.sy1 = a.src_box[3];
+  p.src_amp = T(a.src_amp);
+  p.nx = g.nx; p.ny = g.ny;
+  p.pitch = g.pitch; p.cstride = g.cstride;
+  p.perx = g.periodic[0]; p.pery = g.periodic[1];
+  for (int k = 0; k < 4; ++k) p.pec[k] = g.pec[k];
+  p.fx = make_face_k<T>(a.C, g.h[0], g.h[1], a.c, 1.0, 1.0);
+  p.fy = make_face_k<T>(a.C, g.h[1], g.h[0], a.c, -1.0, -1.0);
+  p.qx = make_face_psi<T>(a.C, g.h[0], g.h[1], a.c, 1.0, 1.0, gamma);
+  p.qy = make_face_psi<T>(a.C, g.h[1], g.h[0], a.c, -1.0, -1.0, gamma);
+  p.flag = a.flag;
+  const int nstrips = (g.nx + PCOLS - 1) / PCOLS;
+  int rows = g.ny;
+  const int target = 152 * 16;
+  if (nstrips < target) {
+    const int chunks = (target + nstrips - 1) / nstrips;
+    rows = (g.ny + chunks - 1) / chunks;
+  }
+  rows = rows < 4 ? 4 : (rows > 256 ? 256 : rows);
+  const int nchunks = (g.ny + rows - 1) / rows;
+  const int64_t nwarps = (int64_t)nstrips * nchunks;
+  const int grid = (int)((nwarps + PWARPS - 1) / PWARPS);
+  if (g.pec[0] || g.pec[1] || g.pec[2] || g.pec[3])
+    cart2d_psi_step_kernel<T, true><<<grid, PWARPS * 32, 0, st>>>(p, nstrips, rows);
+  else
+    cart2d_psi_step_kernel<T, false><<<grid, PWARPS * 32, 0, st>>>(p, nstrips, rows);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_cart2d_psi_step(const CartGeom &g, const CartStepArgs &a, double gamma,
+                                   bool fp64, cudaStream_t st) {
+  return fp64 ? launch_psi_t<double>(g, a, gamma, st) : launch_psi_t<float>(g, a, gamma, st);
+}
+
+}  // namespace gks

@@ -126,6 +126,9 @@ cudaError_t launch_cart2d_step(const CartGeom &g, const CartStepArgs &a, bool fp
                                cudaStream_t st);
 cudaError_t launch_cart3d_step(const CartGeom &g, const CartStepArgs &a, bool fp64,
                                cudaStream_t st);
+// 2-D TM step with divergence cleaning (state Ez, Hx, Hy, psi; mu = 1).
+cudaError_t launch_cart2d_psi_step(const CartGeom &g, const CartStepArgs &a, double gamma,
+                                   bool fp64, cudaStream_t st);
 cudaError_t launch_user_to_cart(const CartGeom &g, int ncomp, const double *user, void *dst,
                                 bool fp64, cudaStream_t st);
 cudaError_t launch_cart_to_user(const CartGeom &g, int ncomp, const void *src, double *user,
@@ -159,6 +162,8 @@ struct gks_ctx {
   int src_box[6] = {0, 0, 0, 0, 0, 0};
   double srcA = 0, srcF0 = 0, srcT0 = 0, srcS = 1;
   int srcKind = 0;              // 0: Gaussian-modulated sine, 1: continuous wave (cosine)
+  bool phm = false;             // divergence cleaning (2-D TM: psi is the 4th component)
+  double chi = 0.0, gamma = 0.0;
   int *flag = nullptr;
   double *red = nullptr;        // reduction scratch (partials + result)
   int red_n = 0;

@@ -44,6 +44,7 @@ class gks_mesh_desc(ctypes.Structure):
         ("tet_bc", ctypes.c_int32), ("reserved1", ctypes.c_int32),
         ("cfl", ctypes.c_double), ("tau_over_dt", ctypes.c_double),
         ("c_lattice", ctypes.c_double), ("cuda_stream", ctypes.c_void_p),
+        ("chi", ctypes.c_double), ("gamma", ctypes.c_double),
     ]
 
 
@@ -269,6 +270,7 @@ class SolverSpec:
     precision: str = "fp32"
     kappa: float = 0.0
     c_lattice: float = 0.0
+    phm: tuple | None = None          # (chi, gamma) divergence cleaning, 2-D TM only
 
 
 class GKSSolver:
@@ -289,8 +291,11 @@ class GKSSolver:
         d.tau_over_dt = spec.kappa
         d.c_lattice = spec.c_lattice
         d.cuda_stream = ctypes.c_void_p(int(stream)) if stream else None
+        cleaning = spec.phm is not None and (spec.phm[0] > 0 or spec.phm[1] > 0)
+        if spec.phm is not None:
+            d.chi, d.gamma = float(spec.phm[0]), float(spec.phm[1])
         self.spec = spec
-        self.ncomp = 3 if spec.dim == 2 else 6
+        self.ncomp = (4 if cleaning else 3) if spec.dim == 2 else 6
         self.ncell = int(np.prod(spec.n[: spec.dim]))
         self.ctx = gks_create_mesh(d)
 
@@ -332,7 +337,8 @@ class GKSSolver:
     def from_workload(cls, w, precision="fp32", kappa=0.0, stream=0):
         s = cls(SolverSpec(dim=w.dim, n=w.n, lo=w.lo, hi=w.hi, bc=w.bc, cfl=w.cfl,
                            precision=precision, kappa=kappa,
-                           c_lattice=getattr(w, "c_lattice", 0.0) or 0.0), stream=stream)
+                           c_lattice=getattr(w, "c_lattice", 0.0) or 0.0,
+                           phm=getattr(w, "phm", None)), stream=stream)
         s.set_materials(w.eps, w.mu)
         s.write_fields(w.fields0)
         if w.jz_mask is not None:

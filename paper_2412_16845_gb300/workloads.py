@@ -120,6 +120,7 @@ class CartWorkload:
     jz_mask: np.ndarray | None = None   # [ncell] or None
     src: tuple = (SRC_A, SRC_F0, SRC_T0, SRC_S)   # "cw": (A, f0, t0)
     waveform: str = "gauss_sine"         # "gauss_sine" or "cw" (continuous cosine)
+    phm: tuple | None = None             # (chi, gamma): divergence cleaning (2-D: fields gain psi)
     probe: np.ndarray | None = None      # int64 cell ids
     design: np.ndarray | None = None     # int64 cell ids
     c_lattice: float = 1.0               # lattice speed c of the workload (c = 1 in Sec. 5)
