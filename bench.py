@@ -219,6 +219,7 @@ def main():
     ap.add_argument("--m4", type=int, default=64)
     ap.add_argument("--steps4", type=int, default=100)
     ap.add_argument("--no-err4", dest="err4", action="store_false", default=True)
+    ap.add_argument("--no-cleaning", dest="with_cleaning", action="store_false", default=True)
     ap.add_argument("--no-adjoint", dest="with_adjoint", action="store_false", default=True)
     ap.add_argument("--n5", type=int, default=2048)
     args = ap.parse_args()
@@ -407,6 +408,28 @@ def main():
                 "algorithmic_bytes_per_tet_step": 229,
                 "hbm_frac_fp32": 229 * n4 / (ms4 * 1e-3) / 1e9 / _peaks()[0]}
 
+    # ---------------- divergence cleaning (TM + psi, gamma = 1, CFL 0.4) on the cylinder grid
+    cleaning = None
+    if args.with_cleaning:
+        wc = wl.config2_cylinders_tm(n=n, steps=args.steps)
+        wc.cfl, wc.phm, wc.fields0 = 0.4, (0.0, 1.0), np.zeros((4, ncell))
+        c32 = GKSSolver.from_workload(wc, precision="fp32", stream=sptr)
+        c32.step(3)
+        c32.sync()
+        kc = min(args.steps, 500)
+        k0 = torch.cuda.Event(enable_timing=True)
+        k1 = torch.cuda.Event(enable_timing=True)
+        k0.record(stream)
+        c32.step(kc)
+        k1.record(stream)
+        torch.cuda.synchronize()
+        msc = k0.elapsed_time(k1) / kc
+        c32.close()
+        cleaning = {"workload": f"tm2d_cylinders_{n}_cleaning", "gamma": 1.0, "cfl": 0.4,
+                    "steps_timed": kc, "value_fp32": ncell / (msc * 1e-3) / 1e9,
+                    "ms_per_step_fp32": msc, "algorithmic_bytes_per_cell_step": 36,
+                    "hbm_frac_fp32": 36 * ncell / (msc * 1e-3) / 1e9 / _peaks()[0]}
+
     # ---------------- adjoint: eps-gradient of the probe objective, 2048^2 design workload
     adj = None
     if args.with_adjoint:
@@ -470,6 +493,7 @@ def main():
             "gpu_launches": int(launches),
             "maxwell3d": three,
             "tets": tets,
+            "cleaning": cleaning,
             "adjoint": adj,
             "clocks": clocks,
         }

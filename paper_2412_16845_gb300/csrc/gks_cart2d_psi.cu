@@ -29,6 +29,7 @@ struct FacePsiK {
   T pa1, pa2, pa3, pa4, pa5, pa6;   // H_n (pa1, pa2, pa4, pa5 shared with psi)
   T h0, h1;                         // sb st stt H = h0 - h1 ie (H_t and psi)
   T pp5;                            // psi
+  T pz1, pz2;                       // psi's own kinetic terms (nonzero for tau > 0)
 };
 
 template <typename T>
@@ -49,6 +50,8 @@ inline FacePsiK<T> make_face_psi(const double C[5], double hn, double ht, double
   k.h0 = T(sb * st * stt * g * c * K5 / 2.0);
   k.h1 = T(sb * st * stt * g * K3 / (2.0 * c));
   k.pp5 = T(-K3 * g / 2.0 * st * stt);
+  k.pz1 = T(-K4 * c / 2.0);
+  k.pz2 = T(c * c * (K2 - K5) / 2.0 * sn);
   return k;
 }
 
@@ -69,7 +72,8 @@ struct PSide {
 //          - G D n_psi - K3 gamma^2/(2c) D t_E
 //   Ht  += H D t_psi
 //   psi  = gamma (K1+K4)/2 S Hn - K3 gamma^2/2 S n_psi - K1 gamma^2/(2c) D psi - G D n_Hn
-//          + H D t_Ht - K3 gamma ie/2 S (eps t_E)
+//          + H D t_Ht - K3 gamma ie/2 S (eps t_E) - K4 c/2 D psi + c^2 (K2 - K5)/2 S n_psi
+// (the last two, present for tau > 0 even at gamma = 0, are the free transport of psi itself).
 template <typename T>
 __device__ __forceinline__ void face_flux_psi(const PSide<T> &l, const PSide<T> &r,
                                               const FaceK<T> &k, const FacePsiK<T> &q, T ie,
@@ -99,7 +103,7 @@ __device__ __forceinline__ void face_flux_psi(const PSide<T> &l, const PSide<T> 
   fa += q.pa1 * S_p + q.pa2 * S_Uxa + q.pa3 * S_tt + q.pa4 * D_Ua + q.pa5 * D_np + q.pa6 * D_Et;
   fb += H * D_tp;
   const T fp = q.pa1 * S_hn + q.pa2 * S_np + q.pa4 * D_p + q.pa5 * D_hn_n + H * D_tt +
-               q.pp5 * ie * (l.eps * l.det + r.eps * r.det);
+               q.pp5 * ie * (l.eps * l.det + r.eps * r.det) + q.pz1 * D_p + q.pz2 * S_np;
   fE = fe;
   fHn = fa;
   fHt = fb;
