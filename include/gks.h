@@ -116,6 +116,14 @@ gks_status gks_create_mesh(const gks_mesh_desc *d, gks_ctx **out);
  * C1..C5. */
 gks_status gks_set_materials(gks_ctx *ctx, const double *eps, const double *mu);
 
+/* Replace eps on the box of columns [x0, x1) x rows [y0, y1) of a 2-D Cartesian grid by eps_box
+ * (row-major, (y1 - y0) x (x1 - x0) doubles, host, copied; finite and > 0); the rest of eps and
+ * mu stay.  For design loops that change only a region (the update of Sec. 3.1 divides by
+ * eps per cell).  Needs a fixed lattice speed (c_lattice > 0 at creation), because dt and C1..C5
+ * are kept: GKS_E_STATE otherwise.  GKS_E_UNSUPPORTED on other meshes. */
+gks_status gks_set_materials_box(gks_ctx *ctx, int64_t x0, int64_t x1, int64_t y0, int64_t y1,
+                                 const double *eps_box);
+
 /* Upload the primitive fields V = (E, H) ([ncomp][n_cells] doubles, user order, host) and set
  * the time to t0 and the step counter to 0.  Converted to the context precision. */
 gks_status gks_write_fields(gks_ctx *ctx, const double *fields, double t0);
@@ -165,6 +173,10 @@ gks_status gks_energy(gks_ctx *ctx, double *out);
  * copied.  GKS_E_UNSUPPORTED on tets or 3-D grids, GKS_E_ARG on ids out of range or repeated. */
 gks_status gks_set_objective(gks_ctx *ctx, const int64_t *probe, int64_t np,
                              const int64_t *design, int64_t nd);
+
+/* Set the accumulated objective J (and its compensation) back to zero, for a run restarted with
+ * gks_load_state; asynchronous.  GKS_E_STATE before gks_set_objective. */
+gks_status gks_reset_objective(gks_ctx *ctx);
 
 /* Wait for the stream and return the accumulated objective J.  GKS_E_STATE before
  * gks_set_objective. */

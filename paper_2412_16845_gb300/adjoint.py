@@ -15,8 +15,19 @@ import math
 import numpy as np
 
 from .gks import (GKSSolver, gks_adjoint_seed, gks_adjoint_step, gks_copy_state,
-                  gks_copy_state_box, gks_load_state, gks_objective, gks_set_objective,
-                  gks_state_layout, gks_step_window)
+                  gks_copy_state_box, gks_load_state, gks_objective, gks_reset_objective,
+                  gks_set_materials_box, gks_set_objective, gks_state_layout, gks_step_window)
+
+
+def design_box(design, nx):
+    """Bounding box (x0, x1, y0, y1) of the design cells on an nx-wide grid, the position of each
+    design cell in the box's row-major order, and the grid index of every box cell."""
+    design = np.asarray(design, dtype=np.int64)
+    dx, dy = design % nx, design // nx
+    box = (int(dx.min()), int(dx.max()) + 1, int(dy.min()), int(dy.max()) + 1)
+    index = (dy - box[2]) * (box[1] - box[0]) + (dx - box[0])
+    ys, xs = np.mgrid[box[2]:box[3], box[0]:box[1]]
+    return box, index, (ys * nx + xs).ravel()
 
 
 class DesignProblem:
@@ -29,14 +40,25 @@ class DesignProblem:
         self.N = int(nsteps if nsteps is not None else w.steps)
         self.K = int(checkpoint_every or max(1, int(round(math.sqrt(self.N)))))
         self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.base_eps = np.array(w.eps, dtype=np.float64)
+        self.design = np.asarray(w.design, dtype=np.int64)
+        mu = np.ones_like(self.base_eps) if w.mu is None else np.asarray(w.mu, dtype=np.float64)
+        # J is differentiated at a fixed lattice speed c (the adjoint holds dt and C1..C5
+        # constant): c is the workload's, else the fastest light speed of its eps and mu.
+        self.c = float(getattr(w, "c_lattice", 0.0) or np.max(1.0 / np.sqrt(self.base_eps * mu)))
+        self.mu_design = mu[self.design]
         self.solver = GKSSolver.from_workload(w, precision=precision,
-                                              stream=self.stream.cuda_stream)
+                                              stream=self.stream.cuda_stream, c_lattice=self.c)
         self.ctx = self.solver.ctx
         gks_set_objective(self.ctx, w.probe, w.design)
         self.elems, _ = gks_state_layout(self.ctx)
         self.dtype = torch.float64 if precision == "fp64" else torch.float32
-        self.base_eps = np.array(w.eps, dtype=np.float64)
-        self.design = np.asarray(w.design, dtype=np.int64)
+        # V^0 stays on the device; each forward() restarts from it
+        self.init = self._buf()
+        gks_copy_state(self.ctx, self.init.data_ptr())
+        # a design update rewrites eps only on the design's bounding box
+        self.dbox, self.dbox_index, cells = design_box(self.design, w.n[0])
+        self.dbox_eps = self.base_eps[cells]
         self.checkpoints = None
         self.final = None
         self.eps_design = None
@@ -66,15 +88,23 @@ class DesignProblem:
         return self.torch.empty(self.elems, dtype=self.dtype, device="cuda")
 
     def set_design(self, eps_design):
-        eps = self.base_eps.copy()
-        eps[self.design] = np.asarray(eps_design, dtype=np.float64)
-        self.solver.set_materials(eps, self.w.mu)
-        self.eps_design = np.array(eps_design, dtype=np.float64)
+        e = np.array(eps_design, dtype=np.float64).reshape(-1)
+        if e.size != self.design.size:
+            raise ValueError("eps_design needs one value per design cell")
+        if not np.all(np.isfinite(e) & (e > 0)):
+            raise ValueError("eps_design must be finite and > 0")
+        if np.any(1.0 / np.sqrt(e * self.mu_design) > self.c * (1 + 1e-12)):
+            raise ValueError(f"eps_design puts a light speed above the lattice speed c = {self.c}")
+        box = self.dbox_eps.copy()
+        box[self.dbox_index] = e
+        gks_set_materials_box(self.ctx, *self.dbox, box)
+        self.eps_design = e
 
     def forward(self, eps_design, keep_checkpoints=True):
         """J(eps_design); keeps the checkpoints for a following backward()."""
         self.set_design(eps_design)
-        self.solver.write_fields(self.w.fields0)
+        gks_load_state(self.ctx, self.init.data_ptr(), 0)
+        gks_reset_objective(self.ctx)
         ck = []
         n = 0
         while n < self.N:

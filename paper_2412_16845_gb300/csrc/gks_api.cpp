@@ -320,6 +320,33 @@ gks_status gks_set_materials(gks_ctx *ctx, const double *eps, const double *mu) 
   return GKS_OK;
 }
 
+gks_status gks_set_materials_box(gks_ctx *ctx, int64_t x0, int64_t x1, int64_t y0, int64_t y1,
+                                 const double *eps_box) {
+  if (!ctx) return GKS_E_ARG;
+  if (ctx->kind != GKS_CARTESIAN || ctx->dim != 2)
+    return fail(ctx, GKS_E_UNSUPPORTED, "a box update of eps needs a 2-D Cartesian grid");
+  if (!eps_box || x0 < 0 || y0 < 0 || x1 > ctx->g.nx || y1 > ctx->g.ny || x0 >= x1 || y0 >= y1)
+    return fail(ctx, GKS_E_ARG, "eps_box is NULL or the box is empty / outside the grid");
+  if (!(ctx->c_user > 0))
+    return fail(ctx, GKS_E_STATE, "a box update of eps needs a fixed lattice speed (c_lattice > 0)");
+  const int64_t n = (x1 - x0) * (y1 - y0);
+  for (int64_t i = 0; i < n; ++i)
+    if (!finite_positive(eps_box[i]))
+      return fail(ctx, GKS_E_ARG, "eps must be finite and > 0 (box entry " + std::to_string(i) + ")");
+  GKS_CUDA(cudaMemcpyAsync(ctx->staging, eps_box, sizeof(double) * (size_t)n,
+                           cudaMemcpyHostToDevice, ctx->st));
+  GKS_CUDA(gks::launch_box_to_cart(ctx->staging, ctx->eps, (int)x0, (int)(x1 - x0), (int)y0,
+                                   (int)(y1 - y0), ctx->g.pitch, ctx->fp64, ctx->st));
+  return GKS_OK;
+}
+
+gks_status gks_reset_objective(gks_ctx *ctx) {
+  if (!ctx) return GKS_E_ARG;
+  if (!ctx->obj) return fail(ctx, GKS_E_STATE, "gks_set_objective must come first");
+  GKS_CUDA(cudaMemsetAsync(ctx->obj, 0, 2 * sizeof(double), ctx->st));
+  return GKS_OK;
+}
+
 gks_status gks_write_fields(gks_ctx *ctx, const double *fields, double t0) {
   if (!ctx) return GKS_E_ARG;
   if (!fields) return fail(ctx, GKS_E_ARG, "fields is NULL");

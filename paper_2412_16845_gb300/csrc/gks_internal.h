@@ -134,6 +134,9 @@ cudaError_t launch_user_to_cart(const CartGeom &g, int ncomp, const double *user
 cudaError_t launch_cart_to_user(const CartGeom &g, int ncomp, const void *src, double *user,
                                 bool fp64, cudaStream_t st);
 cudaError_t launch_fill(void *dst, int64_t n, double value, bool fp64, cudaStream_t st);
+// One 2-D component (pitched layout) = a row-major FP64 box of w x h cells at (x0, y0).
+cudaError_t launch_box_to_cart(const double *box, void *dst, int x0, int w, int y0, int h,
+                               int64_t pitch, bool fp64, cudaStream_t st);
 // dst = src on the box of columns [x0, x1) x rows [y0, y1) of every component.
 cudaError_t launch_copy_box(const void *src, void *dst, int ncomp, int64_t cstride, int64_t pitch,
                             int x0, int x1, int64_t y0, int64_t y1, bool fp64, cudaStream_t st);

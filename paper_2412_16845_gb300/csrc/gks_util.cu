@@ -52,6 +52,19 @@ __global__ void copy_box_kernel(const T *__restrict__ src, T *__restrict__ dst, 
   }
 }
 
+// dst (one component in the Cartesian layout) = box on columns [x0, x0+w) x rows [y0, y0+h);
+// box row-major FP64.
+template <typename T>
+__global__ void box_to_cart_kernel(const double *__restrict__ box, T *__restrict__ dst, int x0,
+                                   int w, int y0, int h, int64_t pitch) {
+  const int64_t n = (int64_t)w * h;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t y = i / w, x = i - y * w;
+    dst[(y0 + y) * pitch + x0 + x] = T(box[i]);
+  }
+}
+
 template <typename T>
 __global__ void fill_kernel(T *dst, int64_t n, T v) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -149,6 +162,20 @@ cudaError_t launch_copy_box(const void *src, void *dst, int ncomp, int64_t cstri
     copy_box_kernel<float><<<blocks, 256, 0, st>>>(static_cast<const float *>(src),
                                                    static_cast<float *>(dst), cstride, pitch, x0,
                                                    x1 - x0, y0, y1 - y0, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_box_to_cart(const double *box, void *dst, int x0, int w, int y0, int h,
+                               int64_t pitch, bool fp64, cudaStream_t st) {
+  const int64_t n = (int64_t)w * h;
+  if (n <= 0) return cudaSuccess;
+  const int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
+  if (fp64)
+    box_to_cart_kernel<double><<<blocks, 256, 0, st>>>(box, static_cast<double *>(dst), x0, w, y0,
+                                                       h, pitch);
+  else
+    box_to_cart_kernel<float><<<blocks, 256, 0, st>>>(box, static_cast<float *>(dst), x0, w, y0,
+                                                      h, pitch);
   return cudaGetLastError();
 }
 

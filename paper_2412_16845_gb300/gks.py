@@ -63,6 +63,9 @@ SIGNATURES = {
                                       ctypes.c_double, ctypes.c_double]),
     "gks_set_source_cw": (ctypes.c_int, [_CTX, _D, ctypes.c_double, ctypes.c_double,
                                          ctypes.c_double]),
+    "gks_set_materials_box": (ctypes.c_int, [_CTX, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                             ctypes.c_int64, _D]),
+    "gks_reset_objective": (ctypes.c_int, [_CTX]),
     "gks_set_dt": (ctypes.c_int, [_CTX, ctypes.c_double]),
     "gks_step": (ctypes.c_int, [_CTX, ctypes.c_int64]),
     "gks_read_fields": (ctypes.c_int, [_CTX, _D]),
@@ -148,6 +151,18 @@ def gks_set_source(ctx, jz_mask, A, f0, t0, s):
 
 def gks_set_source_cw(ctx, jz_mask, A, f0, t0):
     _check(ctx, load_library().gks_set_source_cw(ctx, _dptr(jz_mask), A, f0, t0))
+
+
+def gks_set_materials_box(ctx, x0, x1, y0, y1, eps_box):
+    eps_box = np.ascontiguousarray(eps_box, dtype=np.float64)
+    if eps_box.size != (x1 - x0) * (y1 - y0):
+        raise ValueError("eps_box must hold (y1 - y0) * (x1 - x0) values")
+    _check(ctx, load_library().gks_set_materials_box(ctx, int(x0), int(x1), int(y0), int(y1),
+                                                     eps_box.ctypes.data_as(_D)))
+
+
+def gks_reset_objective(ctx):
+    _check(ctx, load_library().gks_reset_objective(ctx))
 
 
 def gks_set_dt(ctx, dt):
@@ -334,10 +349,12 @@ class GKSSolver:
         return s
 
     @classmethod
-    def from_workload(cls, w, precision="fp32", kappa=0.0, stream=0):
+    def from_workload(cls, w, precision="fp32", kappa=0.0, stream=0, c_lattice=None):
+        """c_lattice: the lattice speed c; None takes the workload's (0 = fastest wave)."""
+        if c_lattice is None:
+            c_lattice = getattr(w, "c_lattice", 0.0) or 0.0
         s = cls(SolverSpec(dim=w.dim, n=w.n, lo=w.lo, hi=w.hi, bc=w.bc, cfl=w.cfl,
-                           precision=precision, kappa=kappa,
-                           c_lattice=getattr(w, "c_lattice", 0.0) or 0.0,
+                           precision=precision, kappa=kappa, c_lattice=c_lattice,
                            phm=getattr(w, "phm", None)), stream=stream)
         s.set_materials(w.eps, w.mu)
         s.write_fields(w.fields0)

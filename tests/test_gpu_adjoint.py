@@ -170,3 +170,48 @@ def test_full_size_design_gradient_fd_16_cells():
     ad = g32[ks]
     assert J32 > 0 and np.abs(fd).max() > 0
     assert np.linalg.norm(ad - fd) <= 1e-3 * np.linalg.norm(fd), (ad, fd)
+
+
+def test_materials_box_equals_full_update():
+    """gks_set_materials_box on a sub-rectangle gives bit-identical steps to gks_set_materials
+    with the same eps; its argument and state errors."""
+    from paper_2412_16845_gb300.gks import GksError, gks_set_materials_box
+    w = _design_workload(nx=40, ny=32, steps=20, seed=8)
+    rng = np.random.default_rng(9)
+    x0, x1, y0, y1 = 5, 29, 7, 19
+    new = w.eps.copy().reshape(32, 40)
+    new[y0:y1, x0:x1] = rng.uniform(1.0, 4.0, (y1 - y0, x1 - x0))
+    out = []
+    for use_box in (False, True):
+        for prec in ("fp64", "fp32"):
+            s = GKSSolver.from_workload(w, precision=prec, c_lattice=1.0)
+            if use_box:
+                gks_set_materials_box(s.ctx, x0, x1, y0, y1, new[y0:y1, x0:x1].copy())
+            else:
+                s.set_materials(new.ravel())
+            s.write_fields(w.fields0)
+            s.step(20)
+            out.append(s.read_fields())
+            s.close()
+    assert np.array_equal(out[0], out[2]) and np.array_equal(out[1], out[3])
+    s = GKSSolver.from_workload(w, precision="fp32")          # automatic lattice speed
+    with pytest.raises(GksError):
+        gks_set_materials_box(s.ctx, 0, 2, 0, 2, np.ones(4))
+    s.close()
+    s = GKSSolver.from_workload(w, precision="fp32", c_lattice=1.0)
+    with pytest.raises(GksError):
+        gks_set_materials_box(s.ctx, 30, 41, 0, 2, np.ones(22))
+    with pytest.raises(GksError):
+        gks_set_materials_box(s.ctx, 0, 2, 0, 2, np.array([1.0, 0.0, 1.0, 1.0]))
+    s.close()
+
+
+def test_design_below_lattice_speed_rejected():
+    from paper_2412_16845_gb300.adjoint import DesignProblem
+    w = _design_workload()
+    prob = DesignProblem(w, precision="fp32")
+    e = w.eps[w.design].copy()
+    e[3] = 0.5
+    with pytest.raises(ValueError):
+        prob.forward(e)
+    prob.close()
