@@ -194,7 +194,7 @@ def test_materials_box_equals_full_update():
             out.append(s.read_fields())
             s.close()
     assert np.array_equal(out[0], out[2]) and np.array_equal(out[1], out[3])
-    s = GKSSolver.from_workload(w, precision="fp32")          # automatic lattice speed
+    s = GKSSolver.from_workload(w, precision="fp32", c_lattice=0.0)   # automatic lattice speed
     with pytest.raises(GksError):
         gks_set_materials_box(s.ctx, 0, 2, 0, 2, np.ones(4))
     s.close()
