@@ -75,11 +75,12 @@ enum { GKS_BC_PERIODIC = 0, GKS_BC_NONREFLECTING = 1, GKS_BC_PEC = 2 };
  *  cuda_stream  cudaStream_t of all device work of this context.
  *  chi, gamma   divergence cleaning (the PHM system of Sec. 2.1): correction potentials phi,
  *             psi carry div E and div B errors away at speeds chi c and gamma c.  0 and 0 is
- *             plain Maxwell.  Supported on 2-D Cartesian grids (TM mode: the state gains psi,
- *             fields become (Ez, Hx, Hy, psi); chi has no effect there, E being divergence
- *             free) with mu = 1 and no adjoint; GKS_E_UNSUPPORTED otherwise.  With cleaning the
- *             step is stable only at smaller CFL numbers (about 0.4 for gamma <= 1 at lattice
- *             speed 1).                                                                     */
+ *             plain Maxwell.  Supported on Cartesian grids with mu = 1 and no adjoint
+ *             (GKS_E_UNSUPPORTED otherwise).  2-D TM: the fields become (Ez, Hx, Hy, psi);
+ *             chi has no effect there, E being divergence free.  3-D: the fields become
+ *             (Ex, Ey, Ez, Hx, Hy, Hz, phi, psi).  With cleaning the step is stable only at
+ *             smaller CFL numbers (about 0.4 in 2-D and 0.3 in 3-D for chi, gamma <= 1 at
+ *             lattice speed 1).                                                             */
 typedef struct gks_mesh_desc {
   int32_t dim;
   int32_t kind;
@@ -162,7 +163,9 @@ gks_status gks_step_window(gks_ctx *ctx, int64_t n_steps, int64_t x0, int64_t x1
 gks_status gks_read_fields(gks_ctx *ctx, double *out);
 
 /* Electromagnetic energy 1/2 sum_i |Omega_i| (eps_i |E_i|^2 + mu_i |H_i|^2), accumulated in
- * FP64 on the device; synchronises.  (Not in the paper: a diagnostic.) */
+ * FP64 on the device; synchronises.  With divergence cleaning the potentials' 1/2 |Omega_i|
+ * (phi_i^2 + psi_i^2) is added (the quantity the cleaning system conserves between walls).
+ * (Not in the paper: a diagnostic.) */
 gks_status gks_energy(gks_ctx *ctx, double *out);
 
 /* Probe objective and design region for the adjoint (2-D TM Cartesian grids; not in the

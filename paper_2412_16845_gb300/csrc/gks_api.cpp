@@ -82,6 +82,13 @@ gks_status cuda_fail(gks_ctx *ctx, cudaError_t e, const char *where) {
 
 bool finite_positive(double v) { return std::isfinite(v) && v > 0.0; }
 
+// Fastest cleaning wave: gamma (psi, div B) and, in 3-D, chi (phi, div E); the 2-D TM system
+// carries no phi.  0 without cleaning.
+double cleaning_speed(const gks_ctx *ctx) {
+  if (!ctx->phm) return 0.0;
+  return ctx->dim == 3 ? std::fmax(ctx->chi, ctx->gamma) : ctx->gamma;
+}
+
 // dt = CFL h_min / c and C1..C5 with tau = kappa dt.
 void refresh_time_step(gks_ctx *ctx) {
   ctx->dt = ctx->cfl * ctx->min_h / ctx->c;
@@ -192,7 +199,7 @@ gks_status gks_create_mesh(const gks_mesh_desc *d, gks_ctx **out) {
   if (!(d->chi >= 0.0) || !(d->gamma >= 0.0) || !std::isfinite(d->chi) || !std::isfinite(d->gamma))
     return GKS_E_ARG;
   const bool phm = d->chi > 0.0 || d->gamma > 0.0;
-  if (phm && (d->kind != GKS_CARTESIAN || d->dim != 2)) return GKS_E_UNSUPPORTED;
+  if (phm && d->kind != GKS_CARTESIAN) return GKS_E_UNSUPPORTED;
   if (d->kind == GKS_TET) {
     if (d->dim != 3 || !d->vert_xyz || !d->tet_vert || d->n_vert < 4 || d->n_tet < 1)
       return GKS_E_ARG;
@@ -218,7 +225,7 @@ gks_status gks_create_mesh(const gks_mesh_desc *d, gks_ctx **out) {
   ctx->st = (cudaStream_t)d->cuda_stream;
   ctx->dim = d->dim;
   ctx->kind = d->kind;
-  ctx->ncomp = d->dim == 2 ? (phm ? 4 : 3) : 6;
+  ctx->ncomp = d->dim == 2 ? (phm ? 4 : 3) : (phm ? 8 : 6);
   ctx->phm = phm;
   ctx->chi = d->chi;
   ctx->gamma = d->gamma;
@@ -259,7 +266,7 @@ gks_status gks_create_mesh(const gks_mesh_desc *d, gks_ctx **out) {
     for (int a = 0; a < d->dim; ++a) sum += 1.0 / g.h[a];
     ctx->min_h = d->dim / sum;
   }
-  ctx->c = ctx->c_user > 0 ? ctx->c_user : std::fmax(1.0, ctx->phm ? ctx->gamma : 0.0);
+  ctx->c = ctx->c_user > 0 ? ctx->c_user : std::fmax(1.0, cleaning_speed(ctx));
 
   gks_status s = GKS_OK;
   const size_t fbytes = ctx->esize * (size_t)ctx->ncomp * (size_t)g.cstride;
@@ -295,8 +302,8 @@ gks_status gks_set_materials(gks_ctx *ctx, const double *eps, const double *mu) 
   if (!ctx) return GKS_E_ARG;
   if (!eps) return fail(ctx, GKS_E_ARG, "eps is NULL");
   if (mu && ctx->phm) return fail(ctx, GKS_E_UNSUPPORTED, "divergence cleaning needs mu = 1");
-  // lattice speed: the fastest wave, light 1/sqrt(eps mu) or the cleaning wave gamma (mu = 1)
-  double cmax = ctx->phm ? ctx->gamma : 0.0;
+  // lattice speed: the fastest wave, light 1/sqrt(eps mu) or a cleaning wave (mu = 1)
+  double cmax = cleaning_speed(ctx);
   for (int64_t i = 0; i < ctx->ncell; ++i) {
     const double e = eps[i], m = mu ? mu[i] : 1.0;
     if (!finite_positive(e) || !finite_positive(m))
@@ -473,9 +480,13 @@ gks_status step_impl(gks_ctx *ctx, int64_t n_steps, const int win[4], bool objec
                                a.flag, ctx->fp64, ctx->st);
       ctx->launches += 3;
     } else {
-      e = ctx->dim == 2 ? (ctx->phm ? gks::launch_cart2d_psi_step(ctx->g, a, ctx->gamma, ctx->fp64, ctx->st)
-                                    : gks::launch_cart2d_step(ctx->g, a, ctx->fp64, ctx->st))
-                        : gks::launch_cart3d_step(ctx->g, a, ctx->fp64, ctx->st);
+      if (ctx->dim == 2)
+        e = ctx->phm ? gks::launch_cart2d_psi_step(ctx->g, a, ctx->gamma, ctx->fp64, ctx->st)
+                     : gks::launch_cart2d_step(ctx->g, a, ctx->fp64, ctx->st);
+      else
+        e = ctx->phm ? gks::launch_cart3d_phm_step(ctx->g, a, ctx->chi, ctx->gamma, ctx->fp64,
+                                                   ctx->st)
+                     : gks::launch_cart3d_step(ctx->g, a, ctx->fp64, ctx->st);
       ctx->launches += 1;
     }
     if (e != cudaSuccess) return cuda_fail(ctx, e, "step launch");

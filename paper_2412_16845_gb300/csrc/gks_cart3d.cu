@@ -14,7 +14,12 @@
 // Every frame is a signed permutation of the axes, so rotations cost nothing.  A PEC wall
 // (Sec. 5.5) is an interior face against mirror-image cells (index reflected across the wall,
 // tangential E and normal H negated).
+//
+// NC = 6 carries (E, H); NC = 8 the divergence-cleaning system (E, H, phi, psi) of Sec. 2.1,
+// whose potentials are scalars in every frame (phi odd and psi even across a PEC wall).
 #include <cuda_runtime.h>
+
+#include <type_traits>
 
 #include "gks_flux3.cuh"
 #include "gks_internal.h"
@@ -25,14 +30,15 @@ namespace {
 constexpr int BX = 32;
 constexpr int PX = BX + 2;            // staged plane: one extra ring around the thread grid
 // Tile height: FP32 takes 32 x 16 threads (inner 30 x 14 cells, about 200 KB of shared memory,
-// one CTA per SM); FP64 32 x 8 (its planes are twice as large).
-template <typename T>
+// one CTA per SM); FP64 32 x 8 (its planes are twice as large).  The eight-component cleaning
+// system stages a third more per cell: 32 x 8 (FP32) and 32 x 6 (FP64).
+template <typename T, int NC>
 struct Geo3 {
-  static constexpr int BY = sizeof(T) == 4 ? 16 : 8;
+  static constexpr int BY = NC == 6 ? (sizeof(T) == 4 ? 16 : 8) : (sizeof(T) == 4 ? 8 : 6);
   static constexpr int NTH = BX * BY;
   static constexpr int PY = BY + 2;
+  static constexpr int NV = NC + 2;   // staged quantities: the NC fields, eps, mu
 };
-constexpr int NV = 8;                 // staged quantities: Ex Ey Ez Hx Hy Hz eps mu
 constexpr int NSLOT = 4;              // staged planes z-1 .. z+2
 
 // Signed-axis face frame: local axis k is sign S_k times global axis A_k.
@@ -47,19 +53,23 @@ using FrameXm = Frame<0, -1, 1, -1, 2, 1>;
 using FrameYm = Frame<1, -1, 0, 1, 2, 1>;
 using FrameZm = Frame<2, -1, 1, 1, 0, 1>;
 
-// Global data of one cell: V (Ex..Hz), gradients G[axis][comp] (true derivatives), materials.
-template <typename T>
+// Global data of one cell: V (Ex..Hz [, phi, psi]), gradients G[axis][comp] (true
+// derivatives), materials.
+template <typename T, int NC>
 struct Cell3 {
-  T v[6];
-  T g[3][6];
+  T v[NC];
+  T g[3][NC];
   T eps, mu;
 };
 
+template <typename T, int NC>
+using SideT = typename std::conditional<NC == 6, Side3<T>, Side8<T>>::type;
+
 // Local side of a cell, reconstructed by `shift` along the face's global normal axis
 // (V + shift * d/d(axis) V; shift = +-h/2).
-template <typename T, typename F>
-__device__ __forceinline__ Side3<T> to_local(const Cell3<T> &c, T shift) {
-  Side3<T> s;
+template <typename T, typename F, int NC>
+__device__ __forceinline__ SideT<T, NC> to_local(const Cell3<T, NC> &c, T shift) {
+  SideT<T, NC> s;
   const int ax[3] = {F::an, F::at, F::aw};
   const T sg[3] = {T(F::sn), T(F::st), T(F::sw)};
 #pragma unroll
@@ -74,20 +84,29 @@ __device__ __forceinline__ Side3<T> to_local(const Cell3<T> &c, T shift) {
       s.dw[3 * b + k] = sgc * T(F::sw) * c.g[F::aw][gc];
     }
   }
+#pragma unroll
+  for (int k = 6; k < NC; ++k) {          // potentials: scalars
+    s.v[k] = c.v[k] + shift * c.g[F::an][k];
+    s.dn[k] = T(F::sn) * c.g[F::an][k];
+    s.dt[k] = T(F::st) * c.g[F::at][k];
+    s.dw[k] = T(F::sw) * c.g[F::aw][k];
+  }
   s.eps = c.eps;
   s.mu = c.mu;
   return s;
 }
 
 // Back to global components: Phi_global = T'^T Phi_local.
-template <typename T, typename F>
-__device__ __forceinline__ void to_global(const T loc[6], T glob[6]) {
+template <typename T, typename F, int NC>
+__device__ __forceinline__ void to_global(const T loc[NC], T glob[NC]) {
   const int ax[3] = {F::an, F::at, F::aw};
   const T sg[3] = {T(F::sn), T(F::st), T(F::sw)};
 #pragma unroll
   for (int b = 0; b < 2; ++b)
 #pragma unroll
     for (int k = 0; k < 3; ++k) glob[3 * b + ax[k]] = sg[k] * loc[3 * b + k];
+#pragma unroll
+  for (int k = 6; k < NC; ++k) glob[k] = loc[k];
 }
 
 // Reciprocals: FP32 uses the fast hardware reciprocal (about 1 ulp), FP64 divides.
@@ -96,41 +115,58 @@ __device__ __forceinline__ double rcp3(double x) { return 1.0 / x; }
 __device__ __forceinline__ float rcp3x2(float x) { return __fdividef(2.f, x); }
 __device__ __forceinline__ double rcp3x2(double x) { return 2.0 / x; }
 
-// Interior face of frame F between cells L (low side) and R (high side), along +axis.  Without
-// mu the sums-and-differences form flux3_mu1 is used.
-template <typename T, typename F, bool HAS_MU>
-__device__ __forceinline__ void interior_face(const Cell3<T> &L, const Cell3<T> &R, T halfh,
-                                              const K3<T> &K, const F3K<T> &FK, T phi[6]) {
-  T loc[6];
-  if (HAS_MU)
-    flux3<T, false>(to_local<T, F>(L, halfh), to_local<T, F>(R, -halfh), K, loc);
-  else
-    flux3_mu1<T>(to_local<T, F>(L, halfh), to_local<T, F>(R, -halfh), FK, rcp3x2(L.eps + R.eps),
-                 loc);
-  to_global<T, F>(loc, phi);
+// Face flux in the face frame: the Maxwell closed forms (NC = 6) or the cleaning system's.
+template <typename T, bool GHOST>
+__device__ __forceinline__ void face_flux(const Side3<T> &l, const Side3<T> &r, const K3<T> &K, T,
+                                          T, T out[6]) {
+  flux3<T, GHOST>(l, r, K, out);
+}
+template <typename T, bool GHOST>
+__device__ __forceinline__ void face_flux(const Side8<T> &l, const Side8<T> &r, const K3<T> &K,
+                                          T chi, T gam, T out[8]) {
+  flux3_phm<T, GHOST>(l, r, K, chi, gam, out);
+}
+
+// Interior face of frame F between cells L (low side) and R (high side), along +axis.  Maxwell
+// without mu uses the sums-and-differences form flux3_mu1.
+template <typename T, typename F, bool HAS_MU, int NC>
+__device__ __forceinline__ void interior_face(const Cell3<T, NC> &L, const Cell3<T, NC> &R,
+                                              T halfh, const K3<T> &K, const F3K<T> &FK, T chi,
+                                              T gam, T phi[NC]) {
+  T loc[NC];
+  if constexpr (NC == 6) {
+    if (HAS_MU)
+      flux3<T, false>(to_local<T, F>(L, halfh), to_local<T, F>(R, -halfh), K, loc);
+    else
+      flux3_mu1<T>(to_local<T, F>(L, halfh), to_local<T, F>(R, -halfh), FK,
+                   rcp3x2(L.eps + R.eps), loc);
+  } else {
+    flux3_phm<T, false>(to_local<T, F>(L, halfh), to_local<T, F>(R, -halfh), K, chi, gam, loc);
+  }
+  to_global<T, F, NC>(loc, phi);
 }
 
 // High-side boundary face (outward +axis, l = the cell): flux along +axis.
-template <typename T, typename F>
-__device__ __forceinline__ void high_boundary_face(const Cell3<T> &L, T halfh, const K3<T> &K,
-                                                   T phi[6]) {
-  T loc[6];
-  const Side3<T> s = to_local<T, F>(L, halfh);
-  flux3<T, true>(s, s, K, loc);
-  to_global<T, F>(loc, phi);
+template <typename T, typename F, int NC>
+__device__ __forceinline__ void high_boundary_face(const Cell3<T, NC> &L, T halfh, const K3<T> &K,
+                                                   T chi, T gam, T phi[NC]) {
+  T loc[NC];
+  const SideT<T, NC> s = to_local<T, F>(L, halfh);
+  face_flux<T, true>(s, s, K, chi, gam, loc);
+  to_global<T, F, NC>(loc, phi);
 }
 
 // Low-side boundary face (outward -axis, l = the cell): returns the flux along +axis, i.e.
 // minus F.n_out.
-template <typename T, typename F>
-__device__ __forceinline__ void low_boundary_face(const Cell3<T> &R, T halfh, const K3<T> &K,
-                                                  T phi[6]) {
-  T loc[6], g[6];
-  const Side3<T> s = to_local<T, F>(R, -halfh);
-  flux3<T, true>(s, s, K, loc);
-  to_global<T, F>(loc, g);
+template <typename T, typename F, int NC>
+__device__ __forceinline__ void low_boundary_face(const Cell3<T, NC> &R, T halfh, const K3<T> &K,
+                                                  T chi, T gam, T phi[NC]) {
+  T loc[NC], g[NC];
+  const SideT<T, NC> s = to_local<T, F>(R, -halfh);
+  face_flux<T, true>(s, s, K, chi, gam, loc);
+  to_global<T, F, NC>(loc, g);
 #pragma unroll
-  for (int c = 0; c < 6; ++c) phi[c] = -g[c];
+  for (int c = 0; c < NC; ++c) phi[c] = -g[c];
 }
 
 template <typename T>
@@ -149,6 +185,7 @@ struct Cart3DArgs {
   T inv2h[3], halfh[3];
   K3<T> K[3];
   F3K<T> FK[3];
+  T chi, gam;          // cleaning speeds (NC = 8)
   int zchunk;
   int *flag;
 };
@@ -177,23 +214,25 @@ __device__ __forceinline__ int axis_index3(int i, int n, int periodic, int pec_l
   return i;
 }
 
-template <typename T>
+template <typename T, int NC>
 struct Smem3 {
-  T V[NSLOT][NV][Geo3<T>::PY][PX];   // staged planes with one extra ring
-  T G[2][18][Geo3<T>::BY][BX];       // gradients (axis-major: x comps, y comps, z comps)
-  T F[2][12][Geo3<T>::BY][BX];       // x-face (0..5) and y-face (6..11) fluxes at the high side
+  using G_ = Geo3<T, NC>;
+  T V[NSLOT][G_::NV][G_::PY][PX];    // staged planes with one extra ring
+  T G[2][3 * NC][G_::BY][BX];        // gradients (axis-major: x comps, y comps, z comps)
+  T F[2][2 * NC][G_::BY][BX];        // x-face (0..NC-1) and y-face (NC..) fluxes at the high side
 };
 
 // Load one staged entry (x, y, z) of all quantities into registers.
-template <typename T, bool HAS_MU, bool HAS_PEC>
-__device__ __forceinline__ void load_entry(const Cart3DArgs<T> &p, int x, int y, int z, T out[NV]) {
+template <typename T, int NC, bool HAS_MU, bool HAS_PEC>
+__device__ __forceinline__ void load_entry(const Cart3DArgs<T> &p, int x, int y, int z,
+                                           T out[NC + 2]) {
   bool m[3];
   const int xx = axis_index3(x, p.nx, p.per[0], HAS_PEC && p.pec[0], HAS_PEC && p.pec[1], m[0]);
   const int yy = axis_index3(y, p.ny, p.per[1], HAS_PEC && p.pec[2], HAS_PEC && p.pec[3], m[1]);
   const int zz = axis_index3(z, p.nz, p.per[2], HAS_PEC && p.pec[4], HAS_PEC && p.pec[5], m[2]);
   const int64_t o = (int64_t)zz * p.plane + (int64_t)yy * p.pitch + xx;
 #pragma unroll
-  for (int c = 0; c < 6; ++c) out[c] = __ldg(p.V + c * p.cstride + o);
+  for (int c = 0; c < NC; ++c) out[c] = __ldg(p.V + c * p.cstride + o);
   // PEC mirror image across the walls of axes a with m[a]: E_c keeps its sign if c == a (normal
   // E) and flips otherwise; H_c flips if c == a (normal H) and keeps it otherwise
   if (HAS_PEC && (m[0] | m[1] | m[2])) {
@@ -205,58 +244,63 @@ __device__ __forceinline__ void load_entry(const Cart3DArgs<T> &p, int x, int y,
           if (c == a) out[3 + c] = -out[3 + c];
           else out[c] = -out[c];
         }
+    if (NC == 8 && (m[0] ^ m[1] ^ m[2])) out[6] = -out[6];   // phi odd per wall, psi even
   }
-  out[6] = __ldg(p.eps + o);
-  out[7] = HAS_MU ? __ldg(p.mu + o) : T(1);
+  out[NC] = __ldg(p.eps + o);
+  out[NC + 1] = HAS_MU ? __ldg(p.mu + o) : T(1);
 }
 
-template <typename T>
-__device__ __forceinline__ void stage(Smem3<T> &s, int slot, int py, int px, const T v[NV]) {
+template <typename T, int NC>
+__device__ __forceinline__ void stage(Smem3<T, NC> &s, int slot, int py, int px,
+                                      const T v[NC + 2]) {
 #pragma unroll
-  for (int c = 0; c < NV; ++c) s.V[slot][c][py][px] = v[c];
+  for (int c = 0; c < NC + 2; ++c) s.V[slot][c][py][px] = v[c];
 }
 
 // Gradient of the thread's cell in plane z: x/y neighbours from the staged plane, z neighbours
 // from the staged planes below/above.
-template <typename T>
-__device__ __forceinline__ void gradient(const Smem3<T> &s, int sl, int sdn, int sup, int ty,
-                                         int tx, const Cart3DArgs<T> &p, T g[3][6]) {
+template <typename T, int NC>
+__device__ __forceinline__ void gradient(const Smem3<T, NC> &s, int sl, int sdn, int sup, int ty,
+                                         int tx, const Cart3DArgs<T> &p, T g[3][NC]) {
   const int py = ty + 1, px = tx + 1;
 #pragma unroll
-  for (int c = 0; c < 6; ++c) {
+  for (int c = 0; c < NC; ++c) {
     g[0][c] = (s.V[sl][c][py][px + 1] - s.V[sl][c][py][px - 1]) * p.inv2h[0];
     g[1][c] = (s.V[sl][c][py + 1][px] - s.V[sl][c][py - 1][px]) * p.inv2h[1];
     g[2][c] = (s.V[sup][c][py][px] - s.V[sdn][c][py][px]) * p.inv2h[2];
   }
 }
 
-template <typename T>
-__device__ __forceinline__ void cell_from(const Smem3<T> &s, int sl, int py, int px,
-                                          const T g[3][6], Cell3<T> &c) {
+template <typename T, int NC>
+__device__ __forceinline__ void cell_from(const Smem3<T, NC> &s, int sl, int py, int px,
+                                          const T g[3][NC], Cell3<T, NC> &c) {
 #pragma unroll
-  for (int k = 0; k < 6; ++k) c.v[k] = s.V[sl][k][py][px];
-  c.eps = s.V[sl][6][py][px];
-  c.mu = s.V[sl][7][py][px];
-#pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int k = 0; k < 6; ++k) c.g[a][k] = g[a][k];
-}
-
-template <typename T>
-__device__ __forceinline__ void load_grad(const Smem3<T> &s, int gs, int ty, int tx, T g[3][6]) {
+  for (int k = 0; k < NC; ++k) c.v[k] = s.V[sl][k][py][px];
+  c.eps = s.V[sl][NC][py][px];
+  c.mu = s.V[sl][NC + 1][py][px];
 #pragma unroll
   for (int a = 0; a < 3; ++a)
 #pragma unroll
-    for (int k = 0; k < 6; ++k) g[a][k] = s.G[gs][6 * a + k][ty][tx];
+    for (int k = 0; k < NC; ++k) c.g[a][k] = g[a][k];
 }
 
-// One CTA per SM: FP32 512 threads (registers capped at 128), FP64 256.
-template <typename T, bool HAS_MU, bool HAS_PEC>
-__global__ void __launch_bounds__(Geo3<T>::NTH, 1) cart3d_step_kernel(const Cart3DArgs<T> p) {
-  constexpr int BY = Geo3<T>::BY, PY = Geo3<T>::PY;
+template <typename T, int NC>
+__device__ __forceinline__ void load_grad(const Smem3<T, NC> &s, int gs, int ty, int tx,
+                                          T g[3][NC]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int k = 0; k < NC; ++k) g[a][k] = s.G[gs][NC * a + k][ty][tx];
+}
+
+// One CTA per SM: FP32 512 threads (registers capped at 128), FP64 256; the cleaning system
+// 256 (FP32) and 192 (FP64).
+template <typename T, int NC, bool HAS_MU, bool HAS_PEC>
+__global__ void __launch_bounds__(Geo3<T, NC>::NTH, 1)
+    cart3d_step_kernel(const Cart3DArgs<T> p) {
+  constexpr int BY = Geo3<T, NC>::BY, PY = Geo3<T, NC>::PY, NV = Geo3<T, NC>::NV;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Smem3<T> &s = *reinterpret_cast<Smem3<T> *>(smem_raw);
+  Smem3<T, NC> &s = *reinterpret_cast<Smem3<T, NC> *>(smem_raw);
   const int tid = threadIdx.x;
   const int tx = tid % BX, ty = tid / BX;
   const int x0 = blockIdx.x * (BX - 2), y0 = blockIdx.y * (BY - 2);
@@ -285,51 +329,52 @@ __global__ void __launch_bounds__(Geo3<T>::NTH, 1) cart3d_step_kernel(const Cart
   T own[NV], ring[NV];
   // ---------------- prologue: stage planes z0-1, z0, z0+1; gradients of z0-1 and z0
   T ownm2[NV];
-  load_entry<T, HAS_MU, HAS_PEC>(p, x, y, z0 - 2, ownm2);
+  load_entry<T, NC, HAS_MU, HAS_PEC>(p, x, y, z0 - 2, ownm2);
   for (int dz = -1; dz <= 1; ++dz) {
-    load_entry<T, HAS_MU, HAS_PEC>(p, x, y, z0 + dz, own);
-    stage<T>(s, (z0 + dz + NSLOT) % NSLOT, ty + 1, tx + 1, own);
+    load_entry<T, NC, HAS_MU, HAS_PEC>(p, x, y, z0 + dz, own);
+    stage<T, NC>(s, (z0 + dz + NSLOT) % NSLOT, ty + 1, tx + 1, own);
     if (ringer) {
-      load_entry<T, HAS_MU, HAS_PEC>(p, rx, ry, z0 + dz, ring);
-      stage<T>(s, (z0 + dz + NSLOT) % NSLOT, rpy, rpx, ring);
+      load_entry<T, NC, HAS_MU, HAS_PEC>(p, rx, ry, z0 + dz, ring);
+      stage<T, NC>(s, (z0 + dz + NSLOT) % NSLOT, rpy, rpx, ring);
     }
   }
   T pf[NV], pfr[NV];
-  load_entry<T, HAS_MU, HAS_PEC>(p, x, y, z0 + 2, pf);
-  if (ringer) load_entry<T, HAS_MU, HAS_PEC>(p, rx, ry, z0 + 2, pfr);
+  load_entry<T, NC, HAS_MU, HAS_PEC>(p, x, y, z0 + 2, pf);
+  if (ringer) load_entry<T, NC, HAS_MU, HAS_PEC>(p, rx, ry, z0 + 2, pfr);
   __syncthreads();
-  T fzb[6];     // flux along +z through the face below the plane being processed
+  T fzb[NC];    // flux along +z through the face below the plane being processed
   {
     const int sm1 = (z0 - 1 + NSLOT) % NSLOT, s0 = z0 % NSLOT, s1 = (z0 + 1) % NSLOT;
-    T gm1[3][6], g0[3][6];
+    T gm1[3][NC], g0[3][NC];
     // gradient of z0-1: its lower z neighbour is not staged, use the register copy
     {
       const int py = ty + 1, px = tx + 1;
 #pragma unroll
-      for (int c = 0; c < 6; ++c) {
+      for (int c = 0; c < NC; ++c) {
         gm1[0][c] = (s.V[sm1][c][py][px + 1] - s.V[sm1][c][py][px - 1]) * p.inv2h[0];
         gm1[1][c] = (s.V[sm1][c][py + 1][px] - s.V[sm1][c][py - 1][px]) * p.inv2h[1];
         gm1[2][c] = (s.V[s0][c][py][px] - ownm2[c]) * p.inv2h[2];
       }
     }
-    gradient<T>(s, s0, sm1, s1, ty, tx, p, g0);
-    Cell3<T> cm1, c0;
-    cell_from<T>(s, sm1, ty + 1, tx + 1, gm1, cm1);
-    cell_from<T>(s, s0, ty + 1, tx + 1, g0, c0);
+    gradient<T, NC>(s, s0, sm1, s1, ty, tx, p, g0);
+    Cell3<T, NC> cm1, c0;
+    cell_from<T, NC>(s, sm1, ty + 1, tx + 1, gm1, cm1);
+    cell_from<T, NC>(s, s0, ty + 1, tx + 1, g0, c0);
     if (z0 == 0 && zlo_nr)
-      low_boundary_face<T, FrameZm>(c0, p.halfh[2], p.K[2], fzb);
+      low_boundary_face<T, FrameZm, NC>(c0, p.halfh[2], p.K[2], p.chi, p.gam, fzb);
     else
-      interior_face<T, FrameZp, HAS_MU>(cm1, c0, p.halfh[2], p.K[2], p.FK[2], fzb);
+      interior_face<T, FrameZp, HAS_MU, NC>(cm1, c0, p.halfh[2], p.K[2], p.FK[2], p.chi, p.gam,
+                                            fzb);
     const int gs = z0 & 1;
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
-      for (int k = 0; k < 6; ++k) s.G[gs][6 * a + k][ty][tx] = g0[a][k];
+      for (int k = 0; k < NC; ++k) s.G[gs][NC * a + k][ty][tx] = g0[a][k];
   }
   // fluxes of the plane whose update is pending
-  T px_[6], py_[6], pzb[6], pzt[6];
+  T px_[NC], py_[NC], pzb[NC], pzt[NC];
 #pragma unroll
-  for (int c = 0; c < 6; ++c) { px_[c] = py_[c] = pzb[c] = pzt[c] = T(0); }
+  for (int c = 0; c < NC; ++c) { px_[c] = py_[c] = pzb[c] = pzt[c] = T(0); }
   bool bad = false;
 #pragma unroll 1
   for (int z = z0; z <= z1; ++z) {
@@ -339,20 +384,20 @@ __global__ void __launch_bounds__(Geo3<T>::NTH, 1) cart3d_step_kernel(const Cart
       const int fs = (z - 1) & 1;
       const int sl = (z - 1 + NSLOT) % NSLOT;
       const int64_t o = (int64_t)(z - 1) * p.plane + (int64_t)y * p.pitch + x;
-      T d[6];
+      T d[NC];
 #pragma unroll
-      for (int c = 0; c < 6; ++c)
-        d[c] = (s.F[fs][c][ty][tx - 1] - px_[c]) + (s.F[fs][6 + c][ty - 1][tx] - py_[c]) +
+      for (int c = 0; c < NC; ++c)
+        d[c] = (s.F[fs][c][ty][tx - 1] - px_[c]) + (s.F[fs][NC + c][ty - 1][tx] - py_[c]) +
                (pzb[c] - pzt[c]);
       if (p.src && x >= p.sx0 && x < p.sx1 && y >= p.sy0 && y < p.sy1 && z - 1 >= p.sz0 &&
           z - 1 < p.sz1)
         d[2] -= p.src_amp * p.src[o];
-      const T ie = rcp3(s.V[sl][6][ty + 1][tx + 1]);
-      const T im = HAS_MU ? rcp3(s.V[sl][7][ty + 1][tx + 1]) : T(1);
+      const T ie = rcp3(s.V[sl][NC][ty + 1][tx + 1]);
+      const T im = HAS_MU ? rcp3(s.V[sl][NC + 1][ty + 1][tx + 1]) : T(1);
       T sum = T(0);
 #pragma unroll
-      for (int c = 0; c < 6; ++c) {
-        const T nv = s.V[sl][c][ty + 1][tx + 1] + d[c] * (c < 3 ? ie : im);
+      for (int c = 0; c < NC; ++c) {
+        const T nv = s.V[sl][c][ty + 1][tx + 1] + d[c] * (c < 3 ? ie : (c < 6 ? im : T(1)));
         p.Vout[c * p.cstride + o] = nv;
         sum += nv;
       }
@@ -363,63 +408,66 @@ __global__ void __launch_bounds__(Geo3<T>::NTH, 1) cart3d_step_kernel(const Cart
     const int s2 = (z + 2) % NSLOT;
     // gradient of plane z+1 (its upper neighbour, plane z+2, is still in registers: stage
     // it first into its slot, which no thread reads before the next barrier except here)
-    T g1[3][6];
+    T g1[3][NC];
     {
       const int py = ty + 1, px = tx + 1;
 #pragma unroll
-      for (int c = 0; c < 6; ++c) {
+      for (int c = 0; c < NC; ++c) {
         g1[0][c] = (s.V[s1][c][py][px + 1] - s.V[s1][c][py][px - 1]) * p.inv2h[0];
         g1[1][c] = (s.V[s1][c][py + 1][px] - s.V[s1][c][py - 1][px]) * p.inv2h[1];
         g1[2][c] = (pf[c] - s.V[s0][c][py][px]) * p.inv2h[2];
       }
     }
     // faces of plane z
-    T g0[3][6];
-    load_grad<T>(s, z & 1, ty, tx, g0);
-    Cell3<T> c0;
-    cell_from<T>(s, s0, ty + 1, tx + 1, g0, c0);
-    T fx[6], fy[6], fzt[6];
+    T g0[3][NC];
+    load_grad<T, NC>(s, z & 1, ty, tx, g0);
+    Cell3<T, NC> c0;
+    cell_from<T, NC>(s, s0, ty + 1, tx + 1, g0, c0);
+    T fx[NC], fy[NC], fzt[NC];
 #pragma unroll
-    for (int c = 0; c < 6; ++c) { fx[c] = fy[c] = T(0); }
+    for (int c = 0; c < NC; ++c) { fx[c] = fy[c] = T(0); }
     if (need_xface) {
       if (xhi) {
-        high_boundary_face<T, FrameXp>(c0, p.halfh[0], p.K[0], fx);
+        high_boundary_face<T, FrameXp, NC>(c0, p.halfh[0], p.K[0], p.chi, p.gam, fx);
       } else {
-        T gr[3][6];
-        load_grad<T>(s, z & 1, ty, tx + 1, gr);
-        Cell3<T> cr;
-        cell_from<T>(s, s0, ty + 1, tx + 2, gr, cr);
+        T gr[3][NC];
+        load_grad<T, NC>(s, z & 1, ty, tx + 1, gr);
+        Cell3<T, NC> cr;
+        cell_from<T, NC>(s, s0, ty + 1, tx + 2, gr, cr);
         if (xlo)
-          low_boundary_face<T, FrameXm>(cr, p.halfh[0], p.K[0], fx);
+          low_boundary_face<T, FrameXm, NC>(cr, p.halfh[0], p.K[0], p.chi, p.gam, fx);
         else
-          interior_face<T, FrameXp, HAS_MU>(c0, cr, p.halfh[0], p.K[0], p.FK[0], fx);
+          interior_face<T, FrameXp, HAS_MU, NC>(c0, cr, p.halfh[0], p.K[0], p.FK[0], p.chi,
+                                                p.gam, fx);
       }
     }
     if (need_yface) {
       if (yhi) {
-        high_boundary_face<T, FrameYp>(c0, p.halfh[1], p.K[1], fy);
+        high_boundary_face<T, FrameYp, NC>(c0, p.halfh[1], p.K[1], p.chi, p.gam, fy);
       } else {
-        T gu[3][6];
-        load_grad<T>(s, z & 1, ty + 1, tx, gu);
-        Cell3<T> cu;
-        cell_from<T>(s, s0, ty + 2, tx + 1, gu, cu);
+        T gu[3][NC];
+        load_grad<T, NC>(s, z & 1, ty + 1, tx, gu);
+        Cell3<T, NC> cu;
+        cell_from<T, NC>(s, s0, ty + 2, tx + 1, gu, cu);
         if (ylo)
-          low_boundary_face<T, FrameYm>(cu, p.halfh[1], p.K[1], fy);
+          low_boundary_face<T, FrameYm, NC>(cu, p.halfh[1], p.K[1], p.chi, p.gam, fy);
         else
-          interior_face<T, FrameYp, HAS_MU>(c0, cu, p.halfh[1], p.K[1], p.FK[1], fy);
+          interior_face<T, FrameYp, HAS_MU, NC>(c0, cu, p.halfh[1], p.K[1], p.FK[1], p.chi,
+                                                p.gam, fy);
       }
     }
     if (inner) {
       if (z + 1 == p.nz && zhi_nr) {
-        high_boundary_face<T, FrameZp>(c0, p.halfh[2], p.K[2], fzt);
+        high_boundary_face<T, FrameZp, NC>(c0, p.halfh[2], p.K[2], p.chi, p.gam, fzt);
       } else {
-        Cell3<T> c1;
-        cell_from<T>(s, s1, ty + 1, tx + 1, g1, c1);
-        interior_face<T, FrameZp, HAS_MU>(c0, c1, p.halfh[2], p.K[2], p.FK[2], fzt);
+        Cell3<T, NC> c1;
+        cell_from<T, NC>(s, s1, ty + 1, tx + 1, g1, c1);
+        interior_face<T, FrameZp, HAS_MU, NC>(c0, c1, p.halfh[2], p.K[2], p.FK[2], p.chi, p.gam,
+                                              fzt);
       }
     } else {
 #pragma unroll
-      for (int c = 0; c < 6; ++c) fzt[c] = T(0);
+      for (int c = 0; c < NC; ++c) fzt[c] = T(0);
     }
     // publish gradients of z+1, this thread's x/y faces; stage plane z+2; prefetch plane z+3
     {
@@ -427,21 +475,21 @@ __global__ void __launch_bounds__(Geo3<T>::NTH, 1) cart3d_step_kernel(const Cart
 #pragma unroll
       for (int a = 0; a < 3; ++a)
 #pragma unroll
-        for (int k = 0; k < 6; ++k) s.G[gs][6 * a + k][ty][tx] = g1[a][k];
+        for (int k = 0; k < NC; ++k) s.G[gs][NC * a + k][ty][tx] = g1[a][k];
 #pragma unroll
-      for (int c = 0; c < 6; ++c) {
+      for (int c = 0; c < NC; ++c) {
         s.F[fs][c][ty][tx] = fx[c];
-        s.F[fs][6 + c][ty][tx] = fy[c];
+        s.F[fs][NC + c][ty][tx] = fy[c];
       }
-      stage<T>(s, s2, ty + 1, tx + 1, pf);
-      if (ringer) stage<T>(s, s2, rpy, rpx, pfr);
+      stage<T, NC>(s, s2, ty + 1, tx + 1, pf);
+      if (ringer) stage<T, NC>(s, s2, rpy, rpx, pfr);
       if (z + 3 <= z1 + 1) {
-        load_entry<T, HAS_MU, HAS_PEC>(p, x, y, z + 3, pf);
-        if (ringer) load_entry<T, HAS_MU, HAS_PEC>(p, rx, ry, z + 3, pfr);
+        load_entry<T, NC, HAS_MU, HAS_PEC>(p, x, y, z + 3, pf);
+        if (ringer) load_entry<T, NC, HAS_MU, HAS_PEC>(p, rx, ry, z + 3, pfr);
       }
     }
 #pragma unroll
-    for (int c = 0; c < 6; ++c) {
+    for (int c = 0; c < NC; ++c) {
       px_[c] = fx[c];
       py_[c] = fy[c];
       pzb[c] = fzb[c];
@@ -453,8 +501,9 @@ __global__ void __launch_bounds__(Geo3<T>::NTH, 1) cart3d_step_kernel(const Cart
   if (__any_sync(0xffffffffu, bad) && (tid & 31) == 0) atomicOr(p.flag, 1);
 }
 
-template <typename T>
-cudaError_t launch3_t(const CartGeom &g, const CartStepArgs &a, cudaStream_t st) {
+template <typename T, int NC>
+cudaError_t launch3_t(const CartGeom &g, const CartStepArgs &a, double chi, double gamma,
+                      cudaStream_t st) {
   Cart3DArgs<T> p;
   p.V = static_cast<const T *>(a.V);
   p.Vout = static_cast<T *>(a.Vout);
@@ -476,20 +525,26 @@ cudaError_t launch3_t(const CartGeom &g, const CartStepArgs &a, cudaStream_t st)
     p.K[d] = make_k3<T>(a.C, g.h[d], a.c);
     p.FK[d] = make_f3k<T>(a.C, g.h[d], a.c);
   }
+  p.chi = T(chi);
+  p.gam = T(gamma);
   p.flag = a.flag;
-  constexpr int BY = Geo3<T>::BY, NTH = Geo3<T>::NTH;
+  constexpr int BY = Geo3<T, NC>::BY, NTH = Geo3<T, NC>::NTH;
   const int gx = (g.nx + BX - 3) / (BX - 2), gy = (g.ny + BY - 3) / (BY - 2);
-  const int smem = (int)sizeof(Smem3<T>);
+  const int smem = (int)sizeof(Smem3<T, NC>);
   // z chunks: a CTA marches zchunk planes after a two-plane prologue.  Pick the chunk count
   // that fills whole waves of resident CTAs best, counting the prologue as lost work.
   // PEC walls get their own instantiation: without them the mirror bookkeeping folds away
   const bool pec = g.pec[0] || g.pec[1] || g.pec[2] || g.pec[3] || g.pec[4] || g.pec[5];
+  // (the cleaning system runs with mu = 1 only)
+  constexpr bool MU_OK = NC == 6;
   void (*kern)(const Cart3DArgs<T>) =
-      a.mu ? (pec ? cart3d_step_kernel<T, true, true> : cart3d_step_kernel<T, true, false>)
-           : (pec ? cart3d_step_kernel<T, false, true> : cart3d_step_kernel<T, false, false>);
+      a.mu && MU_OK ? (pec ? cart3d_step_kernel<T, NC, MU_OK, true>
+                           : cart3d_step_kernel<T, NC, MU_OK, false>)
+                    : (pec ? cart3d_step_kernel<T, NC, false, true>
+                           : cart3d_step_kernel<T, NC, false, false>);
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  static int resident[2][2][2] = {};   // [fp64][has_mu][pec]
-  int &res = resident[sizeof(T) == 8][a.mu ? 1 : 0][pec ? 1 : 0];
+  static int resident[2][2] = {};   // [has_mu][pec], per instantiation of this launcher
+  int &res = resident[a.mu && MU_OK ? 1 : 0][pec ? 1 : 0];
   if (!res) {
     int dev = 0, sms = 0, bps = 0;
     cudaGetDevice(&dev);
@@ -519,7 +574,13 @@ cudaError_t launch3_t(const CartGeom &g, const CartStepArgs &a, cudaStream_t st)
 
 cudaError_t launch_cart3d_step(const CartGeom &g, const CartStepArgs &a, bool fp64,
                                cudaStream_t st) {
-  return fp64 ? launch3_t<double>(g, a, st) : launch3_t<float>(g, a, st);
+  return fp64 ? launch3_t<double, 6>(g, a, 0.0, 0.0, st) : launch3_t<float, 6>(g, a, 0.0, 0.0, st);
+}
+
+cudaError_t launch_cart3d_phm_step(const CartGeom &g, const CartStepArgs &a, double chi,
+                                   double gamma, bool fp64, cudaStream_t st) {
+  return fp64 ? launch3_t<double, 8>(g, a, chi, gamma, st)
+              : launch3_t<float, 8>(g, a, chi, gamma, st);
 }
 
 }  // namespace gks

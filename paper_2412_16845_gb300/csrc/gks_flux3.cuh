@@ -202,6 +202,141 @@ __device__ __forceinline__ void flux3_mu1(const Side3<T> &l, const Side3<T> &r, 
 #undef GKS_DE
 }
 
+// ---------------------------------------------------------------------------------------------
+// Divergence cleaning (PHM system, Sec. 2.1): V = (En, Et, Ew, Hn, Ht, Hw, phi, psi) in the
+// face frame.  F_j adds chi phi to E_j and gamma psi to H_j; the phi and psi rows are chi E_j
+// and gamma H_j.  M = diag(eps, eps, eps, mu, mu, mu, 1, 1).
+enum { PHI = 6, PSI = 7 };
+
+template <typename T>
+struct Side8 {
+  T v[8], dn[8], dt[8], dw[8];
+  T eps, mu;
+};
+
+template <typename T>
+__device__ __forceinline__ void phm_fn(const T v[8], T chi, T gam, T o[8]) {
+  o[EN] = chi * v[PHI]; o[ET] = v[HW]; o[EW] = -v[HT];
+  o[HN] = gam * v[PSI]; o[HT] = -v[EW]; o[HW] = v[ET];
+  o[PHI] = chi * v[EN]; o[PSI] = gam * v[HN];
+}
+template <typename T>
+__device__ __forceinline__ void phm_ft(const T v[8], T chi, T gam, T o[8]) {
+  o[EN] = -v[HW]; o[ET] = chi * v[PHI]; o[EW] = v[HN];
+  o[HN] = v[EW]; o[HT] = gam * v[PSI]; o[HW] = -v[EN];
+  o[PHI] = chi * v[ET]; o[PSI] = gam * v[HT];
+}
+template <typename T>
+__device__ __forceinline__ void phm_fw(const T v[8], T chi, T gam, T o[8]) {
+  o[EN] = v[HT]; o[ET] = -v[HN]; o[EW] = chi * v[PHI];
+  o[HN] = -v[ET]; o[HT] = v[EN]; o[HW] = gam * v[PSI];
+  o[PHI] = chi * v[EW]; o[PSI] = gam * v[HW];
+}
+
+// Time-integrated GKS flux of the cleaning system in the face frame, times dt/h.  The D3Q4
+// half-range sums have the same closed form for any linear flux function (right-moving
+// velocities c(1,1,1), c(1,-1,-1); sum over them of u_k^j u_k^m = 2c^2 (delta_jm + [jm = tw])):
+//   W0 = (U^l + U^r)/2 + (F_n^l - F_n^r)/(2c),  d_j W0 likewise,  V0 = W0 / M_s
+//   <u_n g0> = F_n(V0);  <u_n u.grad g0> = c^2 d_n W0 + c (F_t(d_w V0) + F_w(d_t V0))
+//   <u_n g_t> = F_n(V0_t),  V0_t = -(F_n(d_n V0) + F_t(d_t V0) + F_w(d_w V0)) / M_s
+//   free transport = (F_n^l + F_n^r)/2 - (c/2)(U^r - U^l)
+//   free-transport gradient = (c^2/2)(M_l d_n V^l + M_r d_n V^r)
+//       + (c/2)[F_n(d_n V^l) + (F_t + F_w)(d_t V^l + d_w V^l)]
+//       - (c/2)[F_n(d_n V^r) + (F_t - F_w)(d_t V^r - d_w V^r)]
+// GHOST: the r side is a non-reflecting ghost (no distributions; M_s = M_l).
+template <typename T, bool GHOST>
+__device__ __forceinline__ void flux3_phm(const Side8<T> &l, const Side8<T> &r, const K3<T> &K,
+                                          T chi, T gam, T out[8]) {
+  const T h = T(0.5);
+  T ml[8], mr[8], ims[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    ml[c] = c < 3 ? l.eps : (c < 6 ? l.mu : T(1));
+    mr[c] = GHOST ? T(0) : (c < 3 ? r.eps : (c < 6 ? r.mu : T(1)));
+  }
+  const T ie = GHOST ? T(1) / l.eps : T(2) / (l.eps + r.eps);
+  const T im = GHOST ? T(1) / l.mu : T(2) / (l.mu + r.mu);
+#pragma unroll
+  for (int c = 0; c < 8; ++c) ims[c] = c < 3 ? ie : (c < 6 ? im : T(1));
+  T rv[8], rn[8], rt[8], rw[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    rv[c] = GHOST ? T(0) : r.v[c];
+    rn[c] = GHOST ? T(0) : r.dn[c];
+    rt[c] = GHOST ? T(0) : r.dt[c];
+    rw[c] = GHOST ? T(0) : r.dw[c];
+  }
+  // interface moment and its derivatives: X0 = (M_l x^l + M_r x^r)/2 + F_n(x^l - x^r)/(2c)
+  T dv[8], dn[8], dt[8], dw[8], Fv[8], Fn_[8], Ft_[8], Fw_[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    dv[c] = l.v[c] - rv[c];
+    dn[c] = l.dn[c] - rn[c];
+    dt[c] = l.dt[c] - rt[c];
+    dw[c] = l.dw[c] - rw[c];
+  }
+  phm_fn(dv, chi, gam, Fv);
+  phm_fn(dn, chi, gam, Fn_);
+  phm_fn(dt, chi, gam, Ft_);
+  phm_fn(dw, chi, gam, Fw_);
+  T V0[8], Dn[8], V0n[8], V0t[8], V0w[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const T W = h * (ml[c] * l.v[c] + mr[c] * rv[c]) + Fv[c] * K.inv2c;
+    Dn[c] = h * (ml[c] * l.dn[c] + mr[c] * rn[c]) + Fn_[c] * K.inv2c;
+    const T Dt = h * (ml[c] * l.dt[c] + mr[c] * rt[c]) + Ft_[c] * K.inv2c;
+    const T Dw = h * (ml[c] * l.dw[c] + mr[c] * rw[c]) + Fw_[c] * K.inv2c;
+    V0[c] = W * ims[c];
+    V0n[c] = Dn[c] * ims[c];
+    V0t[c] = Dt * ims[c];
+    V0w[c] = Dw * ims[c];
+  }
+  T t1[8], a[8], b[8], q[8], t3[8], Vt[8];
+  phm_fn(V0, chi, gam, t1);
+  phm_ft(V0w, chi, gam, a);
+  phm_fw(V0t, chi, gam, b);
+  // V0_t
+  phm_fn(V0n, chi, gam, q);
+  {
+    T u[8], w[8];
+    phm_ft(V0t, chi, gam, u);
+    phm_fw(V0w, chi, gam, w);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) Vt[c] = -(q[c] + u[c] + w[c]) * ims[c];
+  }
+  phm_fn(Vt, chi, gam, t3);
+  // free transport and its gradient
+  T Fl[8], Fr[8], Gl[8], Gr[8], Sl[8], Sr[8];
+  phm_fn(l.v, chi, gam, Fl);
+  phm_fn(rv, chi, gam, Fr);
+  phm_fn(l.dn, chi, gam, Gl);
+  phm_fn(rn, chi, gam, Gr);
+  {
+    T pl[8], pr[8], x1[8], x2[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      pl[c] = l.dt[c] + l.dw[c];
+      pr[c] = rt[c] - rw[c];
+    }
+    phm_ft(pl, chi, gam, x1);
+    phm_fw(pl, chi, gam, x2);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) Sl[c] = x1[c] + x2[c];
+    phm_ft(pr, chi, gam, x1);
+    phm_fw(pr, chi, gam, x2);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) Sr[c] = x1[c] - x2[c];
+  }
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const T t2 = K.c2 * Dn[c] + K.c * (a[c] + b[c]);
+    const T t4 = h * (Fl[c] + Fr[c]) - K.halfc * (mr[c] * rv[c] - ml[c] * l.v[c]);
+    const T t5 = K.c2half * (ml[c] * l.dn[c] + mr[c] * rn[c]) +
+                 K.halfc * ((Gl[c] + Sl[c]) - (Gr[c] + Sr[c]));
+    out[c] = K.k1 * t1[c] + K.k2 * t2 + K.k3 * t3[c] + K.k4 * t4 - K.k5 * t5;
+  }
+}
+
 template <typename T>
 K3<T> make_k3(const double C[5], double h, double c) {
   K3<T> k;

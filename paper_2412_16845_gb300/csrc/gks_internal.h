@@ -127,6 +127,9 @@ cudaError_t launch_cart2d_step(const CartGeom &g, const CartStepArgs &a, bool fp
 cudaError_t launch_cart3d_step(const CartGeom &g, const CartStepArgs &a, bool fp64,
                                cudaStream_t st);
 // 2-D TM step with divergence cleaning (state Ez, Hx, Hy, psi; mu = 1).
+// Divergence-cleaning system on a 3-D grid: V = (E, H, phi, psi), 8 components.
+cudaError_t launch_cart3d_phm_step(const CartGeom &g, const CartStepArgs &a, double chi,
+                                   double gamma, bool fp64, cudaStream_t st);
 cudaError_t launch_cart2d_psi_step(const CartGeom &g, const CartStepArgs &a, double gamma,
                                    bool fp64, cudaStream_t st);
 cudaError_t launch_user_to_cart(const CartGeom &g, int ncomp, const double *user, void *dst,

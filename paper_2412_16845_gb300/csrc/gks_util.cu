@@ -72,12 +72,14 @@ __global__ void fill_kernel(T *dst, int64_t n, T v) {
     dst[i] = v;
 }
 
-// Per-block FP64 partial sums of (eps |E|^2 + mu |H|^2) over the cells, then one block sums
-// the partials in a fixed order (deterministic), times |Omega| / 2.
+// Per-block FP64 partial sums of (eps |E|^2 + mu |H|^2 + phi^2 + psi^2) over the cells (the
+// potentials only with divergence cleaning), then one block sums the partials in a fixed order
+// (deterministic), times |Omega| / 2.  Components [0, ne) are E, [ne, ne + nh) H, the rest the
+// potentials.
 template <typename T>
 __global__ void energy_partial_kernel(const T *__restrict__ V, const T *__restrict__ eps,
                                       const T *__restrict__ mu, int nx, int ny, int nz,
-                                      int64_t pitch, int64_t cstride, int ncomp, int ne,
+                                      int64_t pitch, int64_t cstride, int ncomp, int ne, int nh,
                                       double *__restrict__ partials) {
   const int64_t ncell = (int64_t)nx * ny * nz;
   double acc = 0.0;
@@ -86,12 +88,14 @@ __global__ void energy_partial_kernel(const T *__restrict__ V, const T *__restri
     const int64_t x = cell % nx, yz = cell / nx;
     const int64_t y = yz % ny, z = yz / ny;
     const int64_t o = (z * ny + y) * pitch + x;
-    double se = 0.0, sh = 0.0;
+    double se = 0.0, sh = 0.0, sp = 0.0;
     for (int c = 0; c < ncomp; ++c) {
       const double v = double(V[c * cstride + o]);
-      if (c < ne) se += v * v; else sh += v * v;
+      if (c < ne) se += v * v;
+      else if (c < ne + nh) sh += v * v;
+      else sp += v * v;
     }
-    acc += double(eps[o]) * se + (mu ? double(mu[o]) : 1.0) * sh;
+    acc += double(eps[o]) * se + (mu ? double(mu[o]) : 1.0) * sh + sp;
   }
   __shared__ double red[256];
   red[threadIdx.x] = acc;
@@ -193,18 +197,19 @@ cudaError_t launch_cart_energy(const CartGeom &g, int ncomp, const void *V, cons
   const int64_t ncell = (int64_t)g.nx * g.ny * g.nz;
   int blocks = grid_for(ncell);
   if (blocks > npart) blocks = npart;
-  const int ne = ncomp == 3 ? 1 : 3;  // number of E components
+  // E and H components: TM (Ez; Hx, Hy [; psi]) or 3-D (E; H [; phi, psi])
+  const int ne = ncomp <= 4 ? 1 : 3, nh = ncomp <= 4 ? 2 : 3;
   double vol = 1.0;
   for (int a = 0; a < g.dim; ++a) vol *= g.h[a];
   if (fp64)
     energy_partial_kernel<double><<<blocks, 256, 0, st>>>(
         static_cast<const double *>(V), static_cast<const double *>(eps),
-        static_cast<const double *>(mu), g.nx, g.ny, g.nz, g.pitch, g.cstride, ncomp, ne,
+        static_cast<const double *>(mu), g.nx, g.ny, g.nz, g.pitch, g.cstride, ncomp, ne, nh,
         partials);
   else
     energy_partial_kernel<float><<<blocks, 256, 0, st>>>(
         static_cast<const float *>(V), static_cast<const float *>(eps),
-        static_cast<const float *>(mu), g.nx, g.ny, g.nz, g.pitch, g.cstride, ncomp, ne,
+        static_cast<const float *>(mu), g.nx, g.ny, g.nz, g.pitch, g.cstride, ncomp, ne, nh,
         partials);
   sum_partials_kernel<<<1, 256, 0, st>>>(partials, blocks, 0.5 * vol, out);
   return cudaGetLastError();

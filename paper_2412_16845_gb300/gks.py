@@ -285,7 +285,7 @@ class SolverSpec:
     precision: str = "fp32"
     kappa: float = 0.0
     c_lattice: float = 0.0
-    phm: tuple | None = None          # (chi, gamma) divergence cleaning, 2-D TM only
+    phm: tuple | None = None          # (chi, gamma) divergence cleaning (Cartesian grids)
 
 
 class GKSSolver:
@@ -310,7 +310,7 @@ class GKSSolver:
         if spec.phm is not None:
             d.chi, d.gamma = float(spec.phm[0]), float(spec.phm[1])
         self.spec = spec
-        self.ncomp = (4 if cleaning else 3) if spec.dim == 2 else 6
+        self.ncomp = (4 if cleaning else 3) if spec.dim == 2 else (8 if cleaning else 6)
         self.ncell = int(np.prod(spec.n[: spec.dim]))
         self.ctx = gks_create_mesh(d)
 

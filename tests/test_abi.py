@@ -54,7 +54,7 @@ def _desc(**kw):
 
 @pytest.mark.parametrize("bad", [
     {"dim": 4}, {"precision": 7}, {"cfl": 0.0}, {"cfl": float("nan")}, {"tau_over_dt": -1.0},
-    {"kind": 9},
+    {"kind": 9}, {"chi": -1.0}, {"gamma": float("nan")},
 ])
 def test_create_rejects_bad_descriptions(lib, bad):
     d = _desc(**bad)
@@ -77,3 +77,10 @@ def test_create_rejects_unpaired_periodic_and_bad_box(lib):
     assert lib.gks_create_mesh(ctypes.byref(d), ctypes.byref(ctx)) == gks.GKS_E_ARG
     assert lib.gks_create_mesh(None, ctypes.byref(ctx)) == gks.GKS_E_ARG
     assert lib.gks_last_error(None) == b"null context"
+
+
+def test_cleaning_needs_a_cartesian_grid(lib):
+    d = _desc(kind=gks.GKS_TET, dim=3, chi=0.5, gamma=0.5)
+    ctx = ctypes.c_void_p()
+    assert lib.gks_create_mesh(ctypes.byref(d), ctypes.byref(ctx)) == gks.GKS_E_UNSUPPORTED
+    assert not ctx.value
