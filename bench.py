@@ -16,6 +16,7 @@ With N > 1 (torchrun) every rank runs its own replica of the workload (weak scal
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import hashlib
 import json
 import os
@@ -429,6 +430,26 @@ def main():
                     "steps_timed": kc, "value_fp32": ncell / (msc * 1e-3) / 1e9,
                     "ms_per_step_fp32": msc, "algorithmic_bytes_per_cell_step": 36,
                     "hbm_frac_fp32": 36 * ncell / (msc * 1e-3) / 1e9 / _peaks()[0]}
+        if args.with_3d:
+            # 3-D: (E, H, phi, psi) on the sphere grid, chi = gamma = 1, CFL 0.3
+            nq = n3
+            wq = dataclasses.replace(w3, cfl=0.3, phm=(1.0, 1.0),
+                                     fields0=np.concatenate([w3.fields0, np.zeros((2, nq))]))
+            q = GKSSolver.from_workload(wq, precision="fp32", stream=sptr)
+            q.step(3)
+            q.sync()
+            kq = args.steps3
+            k0.record(stream)
+            q.step(kq)
+            k1.record(stream)
+            torch.cuda.synchronize()
+            msq = k0.elapsed_time(k1) / kq
+            q.close()
+            cleaning["maxwell3d"] = {
+                "workload": f"maxwell3d_sphere_{args.n3}_cleaning", "chi": 1.0, "gamma": 1.0,
+                "cfl": 0.3, "steps_timed": kq, "value_fp32": nq / (msq * 1e-3) / 1e9,
+                "ms_per_step_fp32": msq, "algorithmic_bytes_per_cell_step": 68,
+                "hbm_frac_fp32": 68 * nq / (msq * 1e-3) / 1e9 / _peaks()[0]}
 
     # ---------------- adjoint: eps-gradient of the probe objective, 2048^2 design workload
     adj = None
