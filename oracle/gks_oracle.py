@@ -33,6 +33,8 @@ Readings of passages that are silent, garbled or ambiguous (all listed in DESIGN
 * tau = kappa * dt with kappa a parameter; kappa = 0 means the tau -> 0 limit coefficients
   (Sec. 4.1, non-viscous limit): C1 = dt, C3 = dt^2/2, C2 = C4 = C5 = 0.
 * Ghost values for Green-Gauss at a non-reflecting face: a copy of the interior cell.
+* Limiter (Sec. 5.3 names none): van Leer's, on the one-sided differences of each component of
+  V along each axis of a Cartesian grid (limited_gradient); off unless asked for.
 * Face orientation: Cartesian faces use n = +e_d with L the cell on the -e_d side (wrap faces
   included); tetrahedral interior faces point from the smaller to the larger user cell index;
   boundary faces point outward.
@@ -468,6 +470,52 @@ def green_gauss(mesh: FVMesh, V):
     return G / mesh.vol[:, None, None]
 
 
+def van_leer(a, b):
+    """van Leer's limiter of two one-sided slopes: their harmonic mean 2ab/(a + b) where they
+    have the same sign, 0 where they differ or one vanishes (an extremum)."""
+    ab = a * b
+    same = ab > 0.0
+    return np.where(same, 2.0 * ab / np.where(same, a + b, 1.0), 0.0)
+
+
+def limited_gradient(mesh: FVMesh, V):
+    """Limited cell gradients on a Cartesian grid, [ncell, 3, ncomp].
+
+    Reading (Sec. 5.3 uses a limiter that drops to first order at discontinuities and keeps
+    second order in smooth regions, without naming it): along each axis d the slope is
+    van_leer(D+, D-) of the one-sided differences D+ = (V_{i+e_d} - V_i)/h_d and
+    D- = (V_i - V_{i-e_d})/h_d, per component of V, with the ghosts of the Green-Gauss gradient
+    (a copy of the cell at a non-reflecting side, the mirror image at a PEC wall, the wrapped
+    cell on periodic sides).  (D+ + D-)/2 is the unlimited Green-Gauss gradient."""
+    axis = np.argmax(np.abs(mesh.normal), axis=1)
+    if not np.allclose(np.abs(mesh.normal[np.arange(mesh.nface), axis]), 1.0):
+        raise ValueError("the limiter is defined on Cartesian grids")
+    h = 2.0 * np.abs(mesh.dL[np.arange(mesh.nface), axis])
+    ncomp = V.shape[1]
+    fwd = np.zeros((mesh.ncell, 3, ncomp), dtype=V.dtype)
+    bwd = np.zeros_like(fwd)
+    inter = mesh.R >= 0
+    # interior face (normal +e_d, L below R): forward difference of L, backward difference of R
+    fi = np.nonzero(inter)[0]
+    D = (V[mesh.R[fi]] - V[mesh.L[fi]]) / h[fi, None]
+    fwd[mesh.L[fi], axis[fi]] = D
+    bwd[mesh.R[fi], axis[fi]] = D
+    # boundary face (outward normal +-e_d): the ghost beyond the cell
+    fb = np.nonzero(~inter)[0]
+    VL = V[mesh.L[fb]]
+    ghost = VL.copy()
+    pec = mesh.pec_faces()[fb]
+    if pec.any():
+        ghost[pec] = pec_mirror(mesh.normal[fb][pec], VL[pec])
+    up = mesh.normal[fb, axis[fb]] > 0
+    Db = (ghost - VL) / h[fb, None]
+    fwd[mesh.L[fb[up]], axis[fb[up]]] = Db[up]
+    bwd[mesh.L[fb[~up]], axis[fb[~up]]] = -Db[~up]
+    G = van_leer(fwd, bwd)
+    G[:, mesh.dim:, :] = 0.0
+    return G
+
+
 def material_diag(eps, mu, ncomp=6):
     """Diagonal of M = diag(eps I, mu I) per cell, [ncell, 6]; with the cleaning potentials
     (ncomp = 8) M = diag(eps I, mu I, 1, 1)."""
@@ -476,9 +524,15 @@ def material_diag(eps, mu, ncomp=6):
     return np.stack(cols, axis=1)
 
 
-def face_fluxes(mesh: FVMesh, V, m, C, dt, c=1.0, faces=None, phm=None):
-    """Global-frame flux F_s . n_s on every face (or on the subset ``faces``), [nf, ncomp]."""
-    G = green_gauss(mesh, V)
+def face_fluxes(mesh: FVMesh, V, m, C, dt, c=1.0, faces=None, phm=None, limiter=None):
+    """Global-frame flux F_s . n_s on every face (or on the subset ``faces``), [nf, ncomp].
+    limiter = "vanleer" takes the limited Cartesian gradient instead of Green-Gauss."""
+    if limiter is None:
+        G = green_gauss(mesh, V)
+    elif limiter == "vanleer":
+        G = limited_gradient(mesh, V)
+    else:
+        raise ValueError(f"unknown limiter {limiter!r}")
     sel = np.arange(mesh.nface) if faces is None else np.asarray(faces)
     L, R = mesh.L[sel], mesh.R[sel]
     ghost = mesh.boundary[sel]
@@ -501,13 +555,13 @@ def face_fluxes(mesh: FVMesh, V, m, C, dt, c=1.0, faces=None, phm=None):
     return _rot_vec6_back(T, Fl)
 
 
-def step(mesh: FVMesh, V, m, dt, C, c=1.0, jz=None, phm=None):
+def step(mesh: FVMesh, V, m, dt, C, c=1.0, jz=None, phm=None, limiter=None):
     """One GKS step: U^{n+1} = U^n - dt/|Omega_i| sum_s +-|l_s| F_s + dt S_i, S = (-J, 0).
 
     V [ncell, 6] primitive state at t^n ([ncell, 8] with phi, psi for the cleaning system,
     phm = (chi, gamma)); m the matching material diagonal; jz [ncell] current density J_z at
     t^n (or None).  Returns V^{n+1}."""
-    F = face_fluxes(mesh, V, m, C, dt, c, phm=phm)
+    F = face_fluxes(mesh, V, m, C, dt, c, phm=phm, limiter=limiter)
     flux = F * mesh.area[:, None]
     inter = mesh.R >= 0
     net = _scatter_add(mesh.ncell, mesh.L, flux)
@@ -574,12 +628,14 @@ def source_signal_cw(t, A, f0, t0):
 
 
 def run(mesh: FVMesh, fields, eps, mu, cfl, nsteps, kappa=0.0, c=1.0, jz_mask=None,
-        src=None, t0=0.0, dt=None, probe=None, callback=None, waveform="gauss_sine", phm=None):
+        src=None, t0=0.0, dt=None, probe=None, callback=None, waveform="gauss_sine", phm=None,
+        limiter=None):
     """Advance ``nsteps`` steps from user fields [ncomp][ncell].  Returns (fields, info) with
     info = {dt, t, J} (J only when ``probe`` is given: sum over n = 1..N of the probe term).
     The source is jz_mask times source_signal(t, *src) ("gauss_sine") or
     source_signal_cw(t, *src) ("cw").  phm = (chi, gamma) runs the divergence-cleaning system of
-    Sec. 2.1 (fields then carry psi in 2-D, phi and psi in 3-D)."""
+    Sec. 2.1 (fields then carry psi in 2-D, phi and psi in 3-D).  limiter = "vanleer" limits
+    the slopes (limited_gradient)."""
     signal = source_signal_cw if waveform == "cw" else source_signal
     dim = mesh.dim
     V = fields_to_state(fields, dim)
@@ -593,7 +649,7 @@ def run(mesh: FVMesh, fields, eps, mu, cfl, nsteps, kappa=0.0, c=1.0, jz_mask=No
         jz = None
         if jz_mask is not None:
             jz = jz_mask * signal(t, *src)
-        V = step(mesh, V, m, dt, C, c, jz, phm)
+        V = step(mesh, V, m, dt, C, c, jz, phm, limiter)
         if probe is not None:
             J = J + probe_term(mesh, V, probe, dt)
         if callback is not None:

@@ -124,6 +124,7 @@ class CartWorkload:
     probe: np.ndarray | None = None      # int64 cell ids
     design: np.ndarray | None = None     # int64 cell ids
     c_lattice: float = 1.0               # lattice speed c of the workload (c = 1 in Sec. 5)
+    limiter: str | None = None           # None or "vanleer" (limited slopes, 3-D)
     extra: dict = field(default_factory=dict)
 
     @property
@@ -339,3 +340,24 @@ def config4_tets(m: int = 64, steps: int = 500, jitter: float = 0.1) -> TetWorkl
     return TetWorkload(name=f"tets_sphere_{m}", vert=vert, tet=tet, cfl=0.4, steps=steps,
                        eps=eps, mu=None, fields0=incident_pulse_3d(cen[:, 0]),
                        extra={"m": m})
+
+
+def riemann_3d(n: int = 200, t_end: float = 0.25, limiter: str | None = "vanleer") -> CartWorkload:
+    """The electromagnetic Riemann problem of Sec. 5.3 on a 3-D grid: left state E_y = 1,
+    B_x = 1, B_y = -0.75 and right state E_y = -1, B_x = 1, B_y = 0.75 (all else 0), jump at
+    x = 0.5, t_end = 0.25, CFL 0.5, cell size 0.01 as in the paper (n = 200).  The x extent is
+    [-0.5, 1.5] with non-reflecting ends, so that the waves the kinetic boundary sends in from
+    the non-zero end states (speed 1) stay outside [0, 1] until t = 0.5; y and z are periodic and
+    two cells deep (the problem is 1-D).  H = B (c = 1)."""
+    h = 2.0 / n
+    idx = np.arange(n * 4)
+    x = -0.5 + (idx % n + 0.5) * h
+    left = x < 0.5
+    f = np.zeros((6, idx.size))
+    f[1] = np.where(left, 1.0, -1.0)
+    f[3] = 1.0
+    f[4] = np.where(left, -0.75, 0.75)
+    return CartWorkload(
+        name=f"riemann3d_{n}", dim=3, n=(n, 2, 2), lo=(-0.5, 0.0, 0.0), hi=(1.5, 2 * h, 2 * h),
+        bc=("nrbc", "nrbc") + ("periodic",) * 4, cfl=0.5, steps=0, eps=np.ones(idx.size),
+        mu=None, fields0=f, limiter=limiter, extra={"t_end": t_end, "x": x})

@@ -21,7 +21,8 @@ def oracle_cart_run(w, steps, kappa=0.0, dt=None, c=1.0):
     src = w.src if w.jz_mask is not None else None
     return go.run(mesh, w.fields0, w.eps, w.mu, w.cfl, steps, kappa=kappa, c=c,
                   jz_mask=w.jz_mask, src=src, dt=dt,
-                  waveform=getattr(w, "waveform", "gauss_sine"), phm=getattr(w, "phm", None))
+                  waveform=getattr(w, "waveform", "gauss_sine"), phm=getattr(w, "phm", None),
+                  limiter=getattr(w, "limiter", None))
 
 
 def oracle_block_step(w, fields, cells, dt, kappa, t, c=1.0):

@@ -879,3 +879,140 @@ def test_phm_amplification_spectrum(dim, cfl, phm, stable):
         assert rho <= 1.0 + 1e-12, rho
     else:
         assert rho >= 1.05, rho
+
+
+# ------------------------------------------------------------------------------------------
+# Sec. 5.3: slope limiter (van Leer's, a reading: the paper names no limiter)
+
+
+def test_van_leer_limiter_values():
+    """The harmonic mean of same-sign slopes, 0 at an extremum: equal slopes pass unchanged,
+    the result lies between the smaller slope and twice it, and it is odd and symmetric."""
+    a = np.array([1.0, 1.0, 1.0, 0.0, -2.0, 3.0, -1.0, 0.5])
+    b = np.array([1.0, 3.0, -1.0, 2.0, -2.0, 1.0, -3.0, 2.0])
+    assert np.array_equal(go.van_leer(a, b), [1.0, 1.5, 0.0, 0.0, -2.0, 1.5, -1.5, 0.8])
+    rng = np.random.default_rng(0)
+    x, y = rng.standard_normal(1000), rng.standard_normal(1000)
+    v = go.van_leer(x, y)
+    assert np.array_equal(v, go.van_leer(y, x))
+    assert np.array_equal(-v, go.van_leer(-x, -y))
+    same = x * y > 0
+    lo = np.minimum(np.abs(x), np.abs(y))
+    assert np.all(np.abs(v[same]) >= lo[same] * (1 - 1e-15))
+    assert np.all(np.abs(v[same]) <= 2 * lo[same] * (1 + 1e-15))
+    assert np.all(np.sign(v[same]) == np.sign(x[same]))
+    assert np.all(v[~same] == 0.0)
+
+
+def _vl(a, b):
+    return 2 * a * b / (a + b) if a * b > 0 else 0.0
+
+
+@pytest.mark.parametrize("n,bc", [
+    ((5, 4), ("nrbc", "pec", "periodic", "periodic")),
+    ((4, 3, 5), ("pec", "nrbc", "nrbc", "pec", "periodic", "periodic")),
+])
+def test_limited_gradient_brute_force(n, bc):
+    """limited_gradient against a per-cell loop over index neighbours: wrap on periodic axes, a
+    copy of the cell beyond a non-reflecting side, the PEC mirror image beyond a wall."""
+    dim = len(n)
+    rng = np.random.default_rng(7)
+    h = [0.1 * (d + 1) for d in range(dim)]
+    mesh = go.cartesian_mesh(n, (0.0,) * dim, tuple(n[d] * h[d] for d in range(dim)), bc)
+    V = rng.standard_normal((mesh.ncell, 6))
+    G = go.limited_gradient(mesh, V)
+    strides = [1, n[0], n[0] * n[1]][:dim]
+    for cell in range(mesh.ncell):
+        idx = [(cell // strides[d]) % n[d] for d in range(dim)]
+        for d in range(dim):
+            nb = []
+            for s in (-1, 1):
+                j = idx[d] + s
+                side = bc[2 * d + (s > 0)]
+                if 0 <= j < n[d] or side == "periodic":
+                    k = list(idx)
+                    k[d] = j % n[d]
+                    nb.append(V[sum(k[e] * strides[e] for e in range(dim))])
+                elif side == "nrbc":
+                    nb.append(V[cell])
+                else:
+                    e = np.zeros(3)
+                    e[d] = 1.0
+                    nb.append(go.pec_mirror(e, V[cell]))
+            for c in range(6):
+                want = _vl((nb[1][c] - V[cell, c]) / h[d], (V[cell, c] - nb[0][c]) / h[d])
+                assert abs(G[cell, d, c] - want) <= 1e-12 * max(1.0, abs(want)), (cell, d, c)
+        assert np.all(G[cell, dim:] == 0.0)
+
+
+def test_limited_gradient_exact_on_linear_fields():
+    """Away from the boundary a linear field has equal one-sided differences: the limited slope
+    is its exact gradient (no clipping in smooth monotone regions)."""
+    mesh = go.cartesian_mesh((7, 6, 5), (0.0,) * 3, (0.7, 0.6, 0.5), ("nrbc",) * 6)
+    A = np.random.default_rng(2).standard_normal((3, 6))
+    V = mesh.centroid @ A + 0.3
+    G = go.limited_gradient(mesh, V)
+    x = mesh.centroid
+    inner = np.all((x > 0.1 + 1e-9) & (x < np.array([0.6, 0.5, 0.4]) - 1e-9), axis=1)
+    assert inner.sum() == 5 * 4 * 3
+    assert np.allclose(G[inner], np.broadcast_to(A, (inner.sum(), 3, 6)), rtol=0, atol=1e-12)
+
+
+def _riemann_exact(x, t):
+    """Sec. 5.3 states: characteristic variables E_y +- B_z and E_z -+ B_y move at +-1."""
+    w1 = np.where(x - t < 0.5, 1.0, -1.0)
+    w2 = np.where(x + t < 0.5, 1.0, -1.0)
+    w3 = np.where(x - t < 0.5, 0.75, -0.75)
+    w4 = np.where(x + t < 0.5, -0.75, 0.75)
+    out = np.zeros((6, x.size))
+    out[1], out[5] = (w1 + w2) / 2, (w1 - w2) / 2
+    out[2], out[4] = (w3 + w4) / 2, (w4 - w3) / 2
+    out[3] = 1.0
+    return out
+
+
+def _riemann_run(limiter):
+    w = wl.riemann_3d(200, limiter=limiter)
+    mesh = go.cartesian_mesh(w.n, w.lo, w.hi, w.bc)
+    T = w.extra["t_end"]
+    nst = int(math.ceil(T / go.time_step(mesh, w.cfl, 1.0)))
+    out, _ = go.run(mesh, w.fields0, w.eps, None, w.cfl, nst, dt=T / nst, limiter=limiter)
+    x = w.extra["x"]
+    return out, x, _riemann_exact(x, T)
+
+
+def test_riemann_problem_limiter():
+    """Sec. 5.3: with the limiter the Riemann problem is captured without spurious oscillations
+    (the characteristic variables overshoot their end states by under 0.2 %); the unlimited
+    second-order step overshoots by 10 %.  The L1 error on [0, 1] against the exact two-wave
+    solution is 0.013 at the paper's cell size, E_x and B_x stay at their constant values."""
+    out, x, ex = _riemann_run("vanleer")
+    sel = (x > 0.0) & (x < 1.0)
+
+    def overshoot(o):
+        chars = [(o[1] + o[5], 1.0), (o[1] - o[5], 1.0), (o[2] - o[4], 0.75), (o[2] + o[4], 0.75)]
+        return max(np.abs(w[sel]).max() - bound for w, bound in chars)
+
+    assert overshoot(out) <= 2e-3, overshoot(out)
+    assert np.abs(out - ex)[:, sel].mean() <= 0.0135
+    assert np.max(np.abs(out[0])) <= 1e-14 and np.max(np.abs(out[3] - 1.0)) <= 1e-14
+    raw, _, _ = _riemann_run(None)
+    assert overshoot(raw) >= 0.05, overshoot(raw)
+
+
+def test_limiter_keeps_second_order_on_smooth_waves():
+    """Sec. 5.3: the limited step stays second order in smooth regions: a travelling TM wave
+    converges at order >= 1.9 in L1 (the clipping at extrema costs order only in max norm)."""
+    errs = []
+    for n in (64, 128):
+        h = 1.0 / n
+        mesh = go.cartesian_mesh((n, 2), (0.0, 0.0), (1.0, 2 * h), ("periodic",) * 4)
+        x = mesh.centroid[:, 0]
+        f = np.zeros((3, mesh.ncell))
+        f[0], f[2] = np.sin(2 * np.pi * x), -np.sin(2 * np.pi * x)    # E_z - H_y moves at +1
+        T = 0.5
+        nst = int(math.ceil(T / go.time_step(mesh, 0.5, 1.0)))
+        out, _ = go.run(mesh, f, np.ones(mesh.ncell), None, 0.5, nst, dt=T / nst,
+                        limiter="vanleer")
+        errs.append(np.abs(out[0] - np.sin(2 * np.pi * (x - T))).mean())
+    assert math.log2(errs[0] / errs[1]) >= 1.9, errs
