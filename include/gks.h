@@ -52,6 +52,7 @@ typedef enum gks_status {
 enum { GKS_CARTESIAN = 0, GKS_TET = 1 };
 enum { GKS_FP32 = 0, GKS_FP64 = 1 };
 enum { GKS_BC_PERIODIC = 0, GKS_BC_NONREFLECTING = 1, GKS_BC_PEC = 2 };
+enum { GKS_LIMITER_NONE = 0, GKS_LIMITER_VAN_LEER = 1 };
 
 /* Problem description (Sec. 3.1: cells Omega_i, faces l_s with normals n_s).
  *  dim        2 => TM (Ez, Hx, Hy) on an (x, y) grid; 3 => full Maxwell.
@@ -80,7 +81,14 @@ enum { GKS_BC_PERIODIC = 0, GKS_BC_NONREFLECTING = 1, GKS_BC_PEC = 2 };
  *             chi has no effect there, E being divergence free.  3-D: the fields become
  *             (Ex, Ey, Ez, Hx, Hy, Hz, phi, psi).  With cleaning the step is stable only at
  *             smaller CFL numbers (about 0.4 in 2-D and 0.3 in 3-D for chi, gamma <= 1 at
- *             lattice speed 1).                                                             */
+ *             lattice speed 1).
+ *  limiter    GKS_LIMITER_NONE (central-difference cell gradients, the scheme of Sec. 3.1) or
+ *             GKS_LIMITER_VAN_LEER: each component's slope along each axis is van Leer's
+ *             harmonic mean of its one-sided differences, 0 at extrema, so the step drops to
+ *             first order at discontinuities and stays second order in smooth regions (the
+ *             limited scheme of Sec. 5.3, whose limiter the paper does not name).  3-D
+ *             Cartesian grids; GKS_E_UNSUPPORTED elsewhere.  The limited step is not linear in
+ *             the state: the adjoint rejects it.  Other values: GKS_E_ARG.               */
 typedef struct gks_mesh_desc {
   int32_t dim;
   int32_t kind;
@@ -102,6 +110,8 @@ typedef struct gks_mesh_desc {
   void *cuda_stream;
   double chi;
   double gamma;
+  int32_t limiter;
+  int32_t reserved2;
 } gks_mesh_desc;
 
 /* Build the geometry (Sec. 3.1: |Omega_i|, |l_s|, n_s, face and cell centroids; T'(n_s) on

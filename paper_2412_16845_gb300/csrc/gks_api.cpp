@@ -199,6 +199,9 @@ gks_status gks_create_mesh(const gks_mesh_desc *d, gks_ctx **out) {
   if (!(d->chi >= 0.0) || !(d->gamma >= 0.0) || !std::isfinite(d->chi) || !std::isfinite(d->gamma))
     return GKS_E_ARG;
   const bool phm = d->chi > 0.0 || d->gamma > 0.0;
+  if (d->limiter != GKS_LIMITER_NONE && d->limiter != GKS_LIMITER_VAN_LEER) return GKS_E_ARG;
+  if (d->limiter != GKS_LIMITER_NONE && (d->kind != GKS_CARTESIAN || d->dim != 3))
+    return GKS_E_UNSUPPORTED;
   if (phm && d->kind != GKS_CARTESIAN) return GKS_E_UNSUPPORTED;
   if (d->kind == GKS_TET) {
     if (d->dim != 3 || !d->vert_xyz || !d->tet_vert || d->n_vert < 4 || d->n_tet < 1)
@@ -229,6 +232,7 @@ gks_status gks_create_mesh(const gks_mesh_desc *d, gks_ctx **out) {
   ctx->phm = phm;
   ctx->chi = d->chi;
   ctx->gamma = d->gamma;
+  ctx->limiter = d->limiter;
   ctx->fp64 = d->precision == GKS_FP64;
   ctx->esize = ctx->fp64 ? 8 : 4;
   ctx->cfl = d->cfl;
@@ -461,6 +465,7 @@ gks_status step_impl(gks_ctx *ctx, int64_t n_steps, const int win[4], bool objec
   std::memcpy(a.window, win, sizeof(a.window));
   a.c = ctx->c;
   a.flag = ctx->flag;
+  a.limiter = ctx->limiter;
   for (int64_t n = 0; n < n_steps; ++n) {
     const double t = ctx->t0 + (double)ctx->step * ctx->dt;
     a.src_amp = 0.0;
@@ -697,6 +702,8 @@ gks_status gks_adjoint_step(gks_ctx *ctx, const void *state_n, const void *state
     return fail(ctx, GKS_E_UNSUPPORTED, "the adjoint needs a 2-D Cartesian grid");
   if (ctx->mu) return fail(ctx, GKS_E_UNSUPPORTED, "the adjoint supports mu = 1 only");
   if (ctx->phm) return fail(ctx, GKS_E_UNSUPPORTED, "the adjoint does not cover divergence cleaning");
+  if (ctx->limiter)
+    return fail(ctx, GKS_E_UNSUPPORTED, "the limited step is not linear: no adjoint");
   for (int k = 0; k < 4; ++k)
     if (ctx->g.pec[k])
       return fail(ctx, GKS_E_UNSUPPORTED, "the adjoint supports periodic and non-reflecting sides only");

@@ -17,6 +17,8 @@
 //
 // NC = 6 carries (E, H); NC = 8 the divergence-cleaning system (E, H, phi, psi) of Sec. 2.1,
 // whose potentials are scalars in every frame (phi odd and psi even across a PEC wall).
+// LIMIT replaces the central differences of the cell gradients by van Leer-limited slopes (the
+// discontinuity capturing of Sec. 5.3).
 #include <cuda_runtime.h>
 
 #include <type_traits>
@@ -257,17 +259,28 @@ __device__ __forceinline__ void stage(Smem3<T, NC> &s, int slot, int py, int px,
   for (int c = 0; c < NC + 2; ++c) s.V[slot][c][py][px] = v[c];
 }
 
+// Slope of one component along an axis from the values below (vm), at (v0) and above (vp) the
+// cell: the central difference, or with the limiter van Leer's harmonic mean of the one-sided
+// differences, 0 where they differ in sign (an extremum).
+template <bool LIMIT, typename T>
+__device__ __forceinline__ T slope(T vm, T v0, T vp, T inv2h) {
+  if (!LIMIT) return (vp - vm) * inv2h;
+  const T a = vp - v0, b = v0 - vm, ab = a * b;
+  return ab > T(0) ? T(4) * ab / (a + b) * inv2h : T(0);
+}
+
 // Gradient of the thread's cell in plane z: x/y neighbours from the staged plane, z neighbours
 // from the staged planes below/above.
-template <typename T, int NC>
+template <typename T, int NC, bool LIMIT>
 __device__ __forceinline__ void gradient(const Smem3<T, NC> &s, int sl, int sdn, int sup, int ty,
                                          int tx, const Cart3DArgs<T> &p, T g[3][NC]) {
   const int py = ty + 1, px = tx + 1;
 #pragma unroll
   for (int c = 0; c < NC; ++c) {
-    g[0][c] = (s.V[sl][c][py][px + 1] - s.V[sl][c][py][px - 1]) * p.inv2h[0];
-    g[1][c] = (s.V[sl][c][py + 1][px] - s.V[sl][c][py - 1][px]) * p.inv2h[1];
-    g[2][c] = (s.V[sup][c][py][px] - s.V[sdn][c][py][px]) * p.inv2h[2];
+    const T v0 = s.V[sl][c][py][px];
+    g[0][c] = slope<LIMIT>(s.V[sl][c][py][px - 1], v0, s.V[sl][c][py][px + 1], p.inv2h[0]);
+    g[1][c] = slope<LIMIT>(s.V[sl][c][py - 1][px], v0, s.V[sl][c][py + 1][px], p.inv2h[1]);
+    g[2][c] = slope<LIMIT>(s.V[sdn][c][py][px], v0, s.V[sup][c][py][px], p.inv2h[2]);
   }
 }
 
@@ -295,7 +308,7 @@ __device__ __forceinline__ void load_grad(const Smem3<T, NC> &s, int gs, int ty,
 
 // One CTA per SM: FP32 512 threads (registers capped at 128), FP64 256; the cleaning system
 // 256 (FP32) and 192 (FP64).
-template <typename T, int NC, bool HAS_MU, bool HAS_PEC>
+template <typename T, int NC, bool HAS_MU, bool HAS_PEC, bool LIMIT>
 __global__ void __launch_bounds__(Geo3<T, NC>::NTH, 1)
     cart3d_step_kernel(const Cart3DArgs<T> p) {
   constexpr int BY = Geo3<T, NC>::BY, PY = Geo3<T, NC>::PY, NV = Geo3<T, NC>::NV;
@@ -351,12 +364,15 @@ __global__ void __launch_bounds__(Geo3<T, NC>::NTH, 1)
       const int py = ty + 1, px = tx + 1;
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
-        gm1[0][c] = (s.V[sm1][c][py][px + 1] - s.V[sm1][c][py][px - 1]) * p.inv2h[0];
-        gm1[1][c] = (s.V[sm1][c][py + 1][px] - s.V[sm1][c][py - 1][px]) * p.inv2h[1];
-        gm1[2][c] = (s.V[s0][c][py][px] - ownm2[c]) * p.inv2h[2];
+        const T v0 = s.V[sm1][c][py][px];
+        gm1[0][c] = slope<LIMIT>(s.V[sm1][c][py][px - 1], v0, s.V[sm1][c][py][px + 1],
+                                 p.inv2h[0]);
+        gm1[1][c] = slope<LIMIT>(s.V[sm1][c][py - 1][px], v0, s.V[sm1][c][py + 1][px],
+                                 p.inv2h[1]);
+        gm1[2][c] = slope<LIMIT>(ownm2[c], v0, s.V[s0][c][py][px], p.inv2h[2]);
       }
     }
-    gradient<T, NC>(s, s0, sm1, s1, ty, tx, p, g0);
+    gradient<T, NC, LIMIT>(s, s0, sm1, s1, ty, tx, p, g0);
     Cell3<T, NC> cm1, c0;
     cell_from<T, NC>(s, sm1, ty + 1, tx + 1, gm1, cm1);
     cell_from<T, NC>(s, s0, ty + 1, tx + 1, g0, c0);
@@ -413,9 +429,10 @@ __global__ void __launch_bounds__(Geo3<T, NC>::NTH, 1)
       const int py = ty + 1, px = tx + 1;
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
-        g1[0][c] = (s.V[s1][c][py][px + 1] - s.V[s1][c][py][px - 1]) * p.inv2h[0];
-        g1[1][c] = (s.V[s1][c][py + 1][px] - s.V[s1][c][py - 1][px]) * p.inv2h[1];
-        g1[2][c] = (pf[c] - s.V[s0][c][py][px]) * p.inv2h[2];
+        const T v0 = s.V[s1][c][py][px];
+        g1[0][c] = slope<LIMIT>(s.V[s1][c][py][px - 1], v0, s.V[s1][c][py][px + 1], p.inv2h[0]);
+        g1[1][c] = slope<LIMIT>(s.V[s1][c][py - 1][px], v0, s.V[s1][c][py + 1][px], p.inv2h[1]);
+        g1[2][c] = slope<LIMIT>(s.V[s0][c][py][px], v0, pf[c], p.inv2h[2]);
       }
     }
     // faces of plane z
@@ -537,14 +554,21 @@ cudaError_t launch3_t(const CartGeom &g, const CartStepArgs &a, double chi, doub
   const bool pec = g.pec[0] || g.pec[1] || g.pec[2] || g.pec[3] || g.pec[4] || g.pec[5];
   // (the cleaning system runs with mu = 1 only)
   constexpr bool MU_OK = NC == 6;
-  void (*kern)(const Cart3DArgs<T>) =
-      a.mu && MU_OK ? (pec ? cart3d_step_kernel<T, NC, MU_OK, true>
-                           : cart3d_step_kernel<T, NC, MU_OK, false>)
-                    : (pec ? cart3d_step_kernel<T, NC, false, true>
-                           : cart3d_step_kernel<T, NC, false, false>);
+  const bool mu = a.mu && MU_OK, lim = a.limiter != 0;
+  void (*kern)(const Cart3DArgs<T>);
+  if (lim)
+    kern = mu ? (pec ? cart3d_step_kernel<T, NC, MU_OK, true, true>
+                     : cart3d_step_kernel<T, NC, MU_OK, false, true>)
+              : (pec ? cart3d_step_kernel<T, NC, false, true, true>
+                     : cart3d_step_kernel<T, NC, false, false, true>);
+  else
+    kern = mu ? (pec ? cart3d_step_kernel<T, NC, MU_OK, true, false>
+                     : cart3d_step_kernel<T, NC, MU_OK, false, false>)
+              : (pec ? cart3d_step_kernel<T, NC, false, true, false>
+                     : cart3d_step_kernel<T, NC, false, false, false>);
   cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  static int resident[2][2] = {};   // [has_mu][pec], per instantiation of this launcher
-  int &res = resident[a.mu && MU_OK ? 1 : 0][pec ? 1 : 0];
+  static int resident[2][2][2] = {};   // [has_mu][pec][limiter], per instantiation of this launcher
+  int &res = resident[mu ? 1 : 0][pec ? 1 : 0][lim ? 1 : 0];
   if (!res) {
     int dev = 0, sms = 0, bps = 0;
     cudaGetDevice(&dev);

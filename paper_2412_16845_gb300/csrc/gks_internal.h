@@ -42,6 +42,7 @@ struct CartStepArgs {
   double c;             // lattice speed
   int *flag;            // non-finite flag (device)
   int window[4];        // x0, x1, y0, y1 (half open) of the cells to advance (2-D)
+  int limiter = 0;      // GKS_LIMITER_*: slopes of the cell gradients
 };
 
 // Tetrahedral mesh geometry on the host (FP64; cells in internal Morton order).
@@ -170,6 +171,7 @@ struct gks_ctx {
   int srcKind = 0;              // 0: Gaussian-modulated sine, 1: continuous wave (cosine)
   bool phm = false;             // divergence cleaning (2-D TM: psi is the 4th component)
   double chi = 0.0, gamma = 0.0;
+  int limiter = 0;
   int *flag = nullptr;
   double *red = nullptr;        // reduction scratch (partials + result)
   int red_n = 0;

@@ -21,6 +21,8 @@ GKS_OK, GKS_E_ARG, GKS_E_NOMEM, GKS_E_CUDA, GKS_E_UNSUPPORTED, GKS_E_STATE, \
 GKS_CARTESIAN, GKS_TET = 0, 1
 GKS_FP32, GKS_FP64 = 0, 1
 GKS_BC_PERIODIC, GKS_BC_NONREFLECTING, GKS_BC_PEC = 0, 1, 2
+GKS_LIMITER_NONE, GKS_LIMITER_VAN_LEER = 0, 1
+_LIMITER = {None: GKS_LIMITER_NONE, "none": GKS_LIMITER_NONE, "vanleer": GKS_LIMITER_VAN_LEER}
 
 STATUS_NAMES = {0: "GKS_OK", 1: "GKS_E_ARG", 2: "GKS_E_NOMEM", 3: "GKS_E_CUDA",
                 4: "GKS_E_UNSUPPORTED", 5: "GKS_E_STATE", 6: "GKS_E_NONFINITE",
@@ -45,6 +47,7 @@ class gks_mesh_desc(ctypes.Structure):
         ("cfl", ctypes.c_double), ("tau_over_dt", ctypes.c_double),
         ("c_lattice", ctypes.c_double), ("cuda_stream", ctypes.c_void_p),
         ("chi", ctypes.c_double), ("gamma", ctypes.c_double),
+        ("limiter", ctypes.c_int32), ("reserved2", ctypes.c_int32),
     ]
 
 
@@ -286,6 +289,7 @@ class SolverSpec:
     kappa: float = 0.0
     c_lattice: float = 0.0
     phm: tuple | None = None          # (chi, gamma) divergence cleaning (Cartesian grids)
+    limiter: str | None = None        # None or "vanleer" (3-D Cartesian grids)
 
 
 class GKSSolver:
@@ -309,6 +313,7 @@ class GKSSolver:
         cleaning = spec.phm is not None and (spec.phm[0] > 0 or spec.phm[1] > 0)
         if spec.phm is not None:
             d.chi, d.gamma = float(spec.phm[0]), float(spec.phm[1])
+        d.limiter = _LIMITER[spec.limiter]
         self.spec = spec
         self.ncomp = (4 if cleaning else 3) if spec.dim == 2 else (8 if cleaning else 6)
         self.ncell = int(np.prod(spec.n[: spec.dim]))
@@ -355,7 +360,8 @@ class GKSSolver:
             c_lattice = getattr(w, "c_lattice", 0.0) or 0.0
         s = cls(SolverSpec(dim=w.dim, n=w.n, lo=w.lo, hi=w.hi, bc=w.bc, cfl=w.cfl,
                            precision=precision, kappa=kappa, c_lattice=c_lattice,
-                           phm=getattr(w, "phm", None)), stream=stream)
+                           phm=getattr(w, "phm", None),
+                           limiter=getattr(w, "limiter", None)), stream=stream)
         s.set_materials(w.eps, w.mu)
         s.write_fields(w.fields0)
         if w.jz_mask is not None:

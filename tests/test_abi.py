@@ -54,7 +54,7 @@ def _desc(**kw):
 
 @pytest.mark.parametrize("bad", [
     {"dim": 4}, {"precision": 7}, {"cfl": 0.0}, {"cfl": float("nan")}, {"tau_over_dt": -1.0},
-    {"kind": 9}, {"chi": -1.0}, {"gamma": float("nan")},
+    {"kind": 9}, {"chi": -1.0}, {"gamma": float("nan")}, {"limiter": 2}, {"limiter": -1},
 ])
 def test_create_rejects_bad_descriptions(lib, bad):
     d = _desc(**bad)
@@ -84,3 +84,11 @@ def test_cleaning_needs_a_cartesian_grid(lib):
     ctx = ctypes.c_void_p()
     assert lib.gks_create_mesh(ctypes.byref(d), ctypes.byref(ctx)) == gks.GKS_E_UNSUPPORTED
     assert not ctx.value
+
+
+def test_limiter_needs_a_3d_cartesian_grid(lib):
+    ctx = ctypes.c_void_p()
+    for d in (_desc(limiter=gks.GKS_LIMITER_VAN_LEER),
+              _desc(kind=gks.GKS_TET, dim=3, limiter=gks.GKS_LIMITER_VAN_LEER)):
+        assert lib.gks_create_mesh(ctypes.byref(d), ctypes.byref(ctx)) == gks.GKS_E_UNSUPPORTED
+        assert not ctx.value
