@@ -86,8 +86,8 @@ enum { GKS_LIMITER_NONE = 0, GKS_LIMITER_VAN_LEER = 1 };
  *             GKS_LIMITER_VAN_LEER: each component's slope along each axis is van Leer's
  *             harmonic mean of its one-sided differences, 0 at extrema, so the step drops to
  *             first order at discontinuities and stays second order in smooth regions (the
- *             limited scheme of Sec. 5.3, whose limiter the paper does not name).  3-D
- *             Cartesian grids; GKS_E_UNSUPPORTED elsewhere.  The limited step is not linear in
+ *             limited scheme of Sec. 5.3, whose limiter the paper does not name).
+ *             Cartesian grids; GKS_E_UNSUPPORTED on tets.  The limited step is not linear in
  *             the state: the adjoint rejects it.  Other values: GKS_E_ARG.               */
 typedef struct gks_mesh_desc {
   int32_t dim;

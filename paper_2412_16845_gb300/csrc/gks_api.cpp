@@ -200,8 +200,7 @@ gks_status gks_create_mesh(const gks_mesh_desc *d, gks_ctx **out) {
     return GKS_E_ARG;
   const bool phm = d->chi > 0.0 || d->gamma > 0.0;
   if (d->limiter != GKS_LIMITER_NONE && d->limiter != GKS_LIMITER_VAN_LEER) return GKS_E_ARG;
-  if (d->limiter != GKS_LIMITER_NONE && (d->kind != GKS_CARTESIAN || d->dim != 3))
-    return GKS_E_UNSUPPORTED;
+  if (d->limiter != GKS_LIMITER_NONE && d->kind != GKS_CARTESIAN) return GKS_E_UNSUPPORTED;
   if (phm && d->kind != GKS_CARTESIAN) return GKS_E_UNSUPPORTED;
   if (d->kind == GKS_TET) {
     if (d->dim != 3 || !d->vert_xyz || !d->tet_vert || d->n_vert < 4 || d->n_tet < 1)

@@ -364,28 +364,31 @@ __device__ __forceinline__ void low_y_boundary_flux(const RowV<T> &v, const RowG
   fE = -oe; fHx = -ob; fHy = oa;
 }
 
-// Raw central differences of the lane's two columns in a row: x-neighbours by shuffle, the rows
-// below and above from registers.  right_* receive column X+2 of this row (reused by the
-// x-face of the row).
-template <typename T>
+// Raw central differences of the lane's two columns in a row (limited slopes with LIMIT):
+// x-neighbours by shuffle, the rows below and above from registers.  right_* receive column X+2
+// of this row (reused by the x-face of the row).
+template <typename T, bool LIMIT>
 __device__ __forceinline__ void diffs2(const Row2<T> &c, const Row2<T> &dn, const Row2<T> &up,
                                        RowG<T> g[2], T right[3]) {
   const T lE = __shfl_up_sync(FULL, c.ez[1], 1), rE = __shfl_down_sync(FULL, c.ez[0], 1);
   const T lA = __shfl_up_sync(FULL, c.hx[1], 1), rA = __shfl_down_sync(FULL, c.hx[0], 1);
   const T lB = __shfl_up_sync(FULL, c.hy[1], 1), rB = __shfl_down_sync(FULL, c.hy[0], 1);
-  g[0].ex = c.ez[1] - lE; g[1].ex = rE - c.ez[0];
-  g[0].ax = c.hx[1] - lA; g[1].ax = rA - c.hx[0];
-  g[0].bx = c.hy[1] - lB; g[1].bx = rB - c.hy[0];
+  g[0].ex = raw_slope<LIMIT>(lE, c.ez[0], c.ez[1]);
+  g[1].ex = raw_slope<LIMIT>(c.ez[0], c.ez[1], rE);
+  g[0].ax = raw_slope<LIMIT>(lA, c.hx[0], c.hx[1]);
+  g[1].ax = raw_slope<LIMIT>(c.hx[0], c.hx[1], rA);
+  g[0].bx = raw_slope<LIMIT>(lB, c.hy[0], c.hy[1]);
+  g[1].bx = raw_slope<LIMIT>(c.hy[0], c.hy[1], rB);
 #pragma unroll
   for (int k = 0; k < 2; ++k) {
-    g[k].ey = up.ez[k] - dn.ez[k];
-    g[k].ay = up.hx[k] - dn.hx[k];
-    g[k].by = up.hy[k] - dn.hy[k];
+    g[k].ey = raw_slope<LIMIT>(dn.ez[k], c.ez[k], up.ez[k]);
+    g[k].ay = raw_slope<LIMIT>(dn.hx[k], c.hx[k], up.hx[k]);
+    g[k].by = raw_slope<LIMIT>(dn.hy[k], c.hy[k], up.hy[k]);
   }
   right[0] = rE; right[1] = rA; right[2] = rB;
 }
 
-template <typename T, bool HAS_MU, bool HAS_PEC>
+template <typename T, bool HAS_MU, bool HAS_PEC, bool LIMIT>
 __global__ void __launch_bounds__(WARPS * 32, GKS_CART2D_MINBLOCKS) cart2d_step_kernel(const Cart2DKernelArgs<T> p,
                                                                  int nstrips, int rows,
                                                                  int strip0, int ybeg, int yend) {
@@ -420,8 +423,8 @@ __global__ void __launch_bounds__(WARPS * 32, GKS_CART2D_MINBLOCKS) cart2d_step_
   }
   RowG<T> g0[2], gm1[2];
   T r0[3], rm1[3];
-  diffs2<T>(vm1, vm2, v0, gm1, rm1);
-  diffs2<T>(v0, vm1, v1, g0, r0);
+  diffs2<T, LIMIT>(vm1, vm2, v0, gm1, rm1);
+  diffs2<T, LIMIT>(v0, vm1, v1, g0, r0);
   T fbE[2], fbHx[2], fbHy[2];                         // flux along +y below row j
 #pragma unroll
   for (int k = 0; k < 2; ++k) {
@@ -438,7 +441,7 @@ __global__ void __launch_bounds__(WARPS * 32, GKS_CART2D_MINBLOCKS) cart2d_step_
     const Row2<T> pf2 = load_row2<T, HAS_MU, HAS_PEC>(p, X, j + 4);   // two rows ahead of use
     RowG<T> g1[2];
     T r1[3];
-    diffs2<T>(v1, v0, v2, g1, r1);
+    diffs2<T, LIMIT>(v1, v0, v2, g1, r1);
     // x-faces of row j: X+1/2 (own columns) and X+3/2 (own X+1, column X+2 of the next lane)
     T fxE[2], fxHx[2], fxHy[2];
     {
@@ -602,19 +605,17 @@ cudaError_t launch_t(const CartGeom &g, const CartStepArgs &a, cudaStream_t st) 
   const int nchunks = (wrows + rows - 1) / rows;
   const int64_t nwarps = (int64_t)nstrips * nchunks;
   const int grid = (int)((nwarps + WARPS - 1) / WARPS);
-  // PEC walls get their own instantiation: without them the mirror bookkeeping folds away
+  // PEC walls and the limiter get their own instantiations: without them the mirror
+  // bookkeeping and the limiter fold away
   const bool pec = g.pec[0] || g.pec[1] || g.pec[2] || g.pec[3];
-  if (a.mu) {
-    if (pec)
-      cart2d_step_kernel<T, true, true><<<grid, WARPS * 32, 0, st>>>(p, nstrips, rows, strip0, wy0, wy1);
-    else
-      cart2d_step_kernel<T, true, false><<<grid, WARPS * 32, 0, st>>>(p, nstrips, rows, strip0, wy0, wy1);
-  } else {
-    if (pec)
-      cart2d_step_kernel<T, false, true><<<grid, WARPS * 32, 0, st>>>(p, nstrips, rows, strip0, wy0, wy1);
-    else
-      cart2d_step_kernel<T, false, false><<<grid, WARPS * 32, 0, st>>>(p, nstrips, rows, strip0, wy0, wy1);
-  }
+  using K = void (*)(const Cart2DKernelArgs<T>, int, int, int, int, int);
+  static const K kern[2][2][2] = {   // [mu][pec][limiter]
+      {{cart2d_step_kernel<T, false, false, false>, cart2d_step_kernel<T, false, false, true>},
+       {cart2d_step_kernel<T, false, true, false>, cart2d_step_kernel<T, false, true, true>}},
+      {{cart2d_step_kernel<T, true, false, false>, cart2d_step_kernel<T, true, false, true>},
+       {cart2d_step_kernel<T, true, true, false>, cart2d_step_kernel<T, true, true, true>}}};
+  kern[a.mu ? 1 : 0][pec ? 1 : 0][a.limiter ? 1 : 0]<<<grid, WARPS * 32, 0, st>>>(
+      p, nstrips, rows, strip0, wy0, wy1);
   return cudaGetLastError();
 }
 

@@ -212,24 +212,29 @@ struct PG {
   T ex, ey, ax, ay, bx, by, px, py;
 };
 
-// Differences of the lane's two columns (x-neighbours by shuffle); right[] receives column X+2.
-template <typename T>
+// Differences of the lane's two columns (x-neighbours by shuffle; limited slopes with LIMIT);
+// right[] receives column X+2.
+template <typename T, bool LIMIT>
 __device__ __forceinline__ void psi_diffs(const PRow<T> &c, const PRow<T> &dn, const PRow<T> &up,
                                           PG<T> g[2], T right[4]) {
   const T lE = __shfl_up_sync(PFULL, c.ez[1], 1), rE = __shfl_down_sync(PFULL, c.ez[0], 1);
   const T lA = __shfl_up_sync(PFULL, c.hx[1], 1), rA = __shfl_down_sync(PFULL, c.hx[0], 1);
   const T lB = __shfl_up_sync(PFULL, c.hy[1], 1), rB = __shfl_down_sync(PFULL, c.hy[0], 1);
   const T lP = __shfl_up_sync(PFULL, c.ps[1], 1), rP = __shfl_down_sync(PFULL, c.ps[0], 1);
-  g[0].ex = c.ez[1] - lE; g[1].ex = rE - c.ez[0];
-  g[0].ax = c.hx[1] - lA; g[1].ax = rA - c.hx[0];
-  g[0].bx = c.hy[1] - lB; g[1].bx = rB - c.hy[0];
-  g[0].px = c.ps[1] - lP; g[1].px = rP - c.ps[0];
+  g[0].ex = raw_slope<LIMIT>(lE, c.ez[0], c.ez[1]);
+  g[1].ex = raw_slope<LIMIT>(c.ez[0], c.ez[1], rE);
+  g[0].ax = raw_slope<LIMIT>(lA, c.hx[0], c.hx[1]);
+  g[1].ax = raw_slope<LIMIT>(c.hx[0], c.hx[1], rA);
+  g[0].bx = raw_slope<LIMIT>(lB, c.hy[0], c.hy[1]);
+  g[1].bx = raw_slope<LIMIT>(c.hy[0], c.hy[1], rB);
+  g[0].px = raw_slope<LIMIT>(lP, c.ps[0], c.ps[1]);
+  g[1].px = raw_slope<LIMIT>(c.ps[0], c.ps[1], rP);
 #pragma unroll
   for (int k = 0; k < 2; ++k) {
-    g[k].ey = up.ez[k] - dn.ez[k];
-    g[k].ay = up.hx[k] - dn.hx[k];
-    g[k].by = up.hy[k] - dn.hy[k];
-    g[k].py = up.ps[k] - dn.ps[k];
+    g[k].ey = raw_slope<LIMIT>(dn.ez[k], c.ez[k], up.ez[k]);
+    g[k].ay = raw_slope<LIMIT>(dn.hx[k], c.hx[k], up.hx[k]);
+    g[k].by = raw_slope<LIMIT>(dn.hy[k], c.hy[k], up.hy[k]);
+    g[k].py = raw_slope<LIMIT>(dn.ps[k], c.ps[k], up.ps[k]);
   }
   right[0] = rE; right[1] = rA; right[2] = rB; right[3] = rP;
 }
@@ -266,7 +271,7 @@ __device__ __forceinline__ PSide<T> psi_zero() {
   return s;
 }
 
-template <typename T, bool HAS_PEC>
+template <typename T, bool HAS_PEC, bool LIMIT>
 __global__ void __launch_bounds__(PWARPS * 32) cart2d_psi_step_kernel(const PsiArgs<T> p,
                                                                       int nstrips, int rows) {
   const int lane = threadIdx.x & 31;
@@ -289,8 +294,8 @@ __global__ void __launch_bounds__(PWARPS * 32) cart2d_psi_step_kernel(const PsiA
   }
   PG<T> g0[2], gm1[2];
   T r0[4], rm1[4];
-  psi_diffs<T>(vm1, vm2, v0, gm1, rm1);
-  psi_diffs<T>(v0, vm1, v1, g0, r0);
+  psi_diffs<T, LIMIT>(vm1, vm2, v0, gm1, rm1);
+  psi_diffs<T, LIMIT>(v0, vm1, v1, g0, r0);
   T fbE[2], fbHx[2], fbHy[2], fbP[2];                 // flux along +y below row j
 #pragma unroll
   for (int k = 0; k < 2; ++k) {
@@ -307,7 +312,7 @@ __global__ void __launch_bounds__(PWARPS * 32) cart2d_psi_step_kernel(const PsiA
     const PRow<T> pf2 = psi_load(p, X, j + 4);
     PG<T> g1[2];
     T r1[4];
-    psi_diffs<T>(v1, v0, v2, g1, r1);
+    psi_diffs<T, LIMIT>(v1, v0, v2, g1, r1);
     // x-faces X+1/2 and X+3/2 (column X+2 from the next lane)
     T fxE[2], fxHx[2], fxHy[2], fxP[2];
     {
@@ -441,10 +446,13 @@ cudaError_t launch_psi_t(const CartGeom &g, const CartStepArgs &a, double gamma,
   const int nchunks = (g.ny + rows - 1) / rows;
   const int64_t nwarps = (int64_t)nstrips * nchunks;
   const int grid = (int)((nwarps + PWARPS - 1) / PWARPS);
-  if (g.pec[0] || g.pec[1] || g.pec[2] || g.pec[3])
-    cart2d_psi_step_kernel<T, true><<<grid, PWARPS * 32, 0, st>>>(p, nstrips, rows);
-  else
-    cart2d_psi_step_kernel<T, false><<<grid, PWARPS * 32, 0, st>>>(p, nstrips, rows);
+  const bool pec = g.pec[0] || g.pec[1] || g.pec[2] || g.pec[3];
+  using K = void (*)(const PsiArgs<T>, int, int);
+  static const K kern[2][2] = {{cart2d_psi_step_kernel<T, false, false>,
+                                cart2d_psi_step_kernel<T, false, true>},
+                               {cart2d_psi_step_kernel<T, true, false>,
+                                cart2d_psi_step_kernel<T, true, true>}};   // [pec][limiter]
+  kern[pec ? 1 : 0][a.limiter ? 1 : 0]<<<grid, PWARPS * 32, 0, st>>>(p, nstrips, rows);
   return cudaGetLastError();
 }
 

@@ -36,4 +36,14 @@ inline FaceK<T> make_face_k(const double C[5], double hn, double ht, double c, d
   return k;
 }
 
+// Twice the slope times the cell size, from the values below (vm), at (v0) and above (vp) a
+// cell: the raw central difference vp - vm, or with the limiter twice van Leer's harmonic mean
+// of the one-sided differences, 4ab/(a + b) where they share a sign and 0 where they do not.
+template <bool LIMIT, typename T>
+__device__ __forceinline__ T raw_slope(T vm, T v0, T vp) {
+  if (!LIMIT) return vp - vm;
+  const T a = vp - v0, b = v0 - vm, ab = a * b;
+  return ab > T(0) ? T(4) * ab / (a + b) : T(0);
+}
+
 }  // namespace gks

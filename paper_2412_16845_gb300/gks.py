@@ -289,7 +289,7 @@ class SolverSpec:
     kappa: float = 0.0
     c_lattice: float = 0.0
     phm: tuple | None = None          # (chi, gamma) divergence cleaning (Cartesian grids)
-    limiter: str | None = None        # None or "vanleer" (3-D Cartesian grids)
+    limiter: str | None = None        # None or "vanleer" (Cartesian grids)
 
 
 class GKSSolver:

@@ -124,7 +124,7 @@ class CartWorkload:
     probe: np.ndarray | None = None      # int64 cell ids
     design: np.ndarray | None = None     # int64 cell ids
     c_lattice: float = 1.0               # lattice speed c of the workload (c = 1 in Sec. 5)
-    limiter: str | None = None           # None or "vanleer" (limited slopes, 3-D)
+    limiter: str | None = None           # None or "vanleer" (limited slopes)
     extra: dict = field(default_factory=dict)
 
     @property

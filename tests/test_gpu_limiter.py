@@ -87,3 +87,76 @@ def test_riemann_problem_on_the_gpu():
     assert max(np.abs(v[sel]).max() - b for v, b in chars) <= 2e-3
     from tests.test_oracle_pins import _riemann_exact
     assert np.abs(out - _riemann_exact(x, T))[:, sel].mean() <= 0.0135
+
+
+# ------------------------------------------------------------------------------------------
+# 2-D TM (and TM + psi)
+
+
+def _w2(nx, ny, bc, seed, mu=False, phm=None, with_src=False):
+    rng = np.random.default_rng(seed)
+    hi = (1.0, ny / nx)
+    x, y = wl.cell_centres_2d(nx, ny, hi=hi)
+    nc = 4 if phm else 3
+    f = np.stack([np.sin(2 * np.pi * (x + k * y) + 0.3 * k) for k in range(nc)])
+    f += 0.2 * rng.standard_normal(f.shape)
+    f[:, (x > 0.55) & (y > 0.3)] -= 1.0
+    mask = None
+    if with_src:
+        mask = np.zeros(nx * ny)
+        k = max(1, nx * ny // 20)
+        mask[rng.choice(nx * ny, size=k, replace=False)] = rng.uniform(-3, 3, k)
+    return wl.CartWorkload(name="lim2", dim=2, n=(nx, ny), lo=(0.0, 0.0), hi=hi, bc=bc,
+                           cfl=0.4, steps=0, eps=rng.uniform(1.0, 4.0, nx * ny),
+                           mu=rng.uniform(1.0, 2.0, nx * ny) if mu else None, fields0=f,
+                           jz_mask=mask, src=(1.0, 20.0, 0.02, 0.02), c_lattice=0.0, phm=phm,
+                           limiter="vanleer")
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("kappa", [0.0, 0.05])
+@pytest.mark.parametrize("case", [
+    (45, 37, ("nrbc",) * 4, False, None, True),
+    (131, 70, ("periodic",) * 4, False, None, False),          # several strips and row chunks
+    (70, 33, ("pec", "nrbc", "periodic", "periodic"), True, None, True),
+    (66, 41, ("nrbc", "pec", "pec", "nrbc"), False, (0.0, 0.8), True),   # TM + psi
+    (2, 3, ("pec",) * 4, False, (0.0, 1.2), False),
+])
+def test_limited_step_2d(precision, kappa, case):
+    nx, ny, bc, mu, phm, with_src = case
+    w = _w2(nx, ny, bc, seed=3 * nx + ny, mu=mu, phm=phm, with_src=with_src)
+    s = GKSSolver.from_workload(w, precision=precision, kappa=kappa)
+    s.step(15)
+    out, info = s.read_fields(), s.info()
+    s.close()
+    ref, _ = oracle_cart_run(w, 15, kappa=kappa, c=info["c"])
+    assert rel_l2(out, ref) <= TOL[precision], rel_l2(out, ref)
+
+
+def test_tm_riemann_problem_on_the_gpu():
+    """The TM part of the Sec. 5.3 states (E_z = 0, H_x = 1, H_y = -0.75 | 0.75) on a 2-D grid
+    over [-0.5, 1.5] x 4h, to t = 0.25: the limited FP32 GPU step matches the oracle, and the
+    characteristic variables E_z -+ H_y stay within 0.2 % of their end states."""
+    n = 200
+    h = 2.0 / n
+    x, y = wl.cell_centres_2d(n, 4, hi=(2.0, 4 * h))
+    x = x - 0.5
+    f = np.zeros((3, n * 4))
+    f[1] = 1.0
+    f[2] = np.where(x < 0.5, -0.75, 0.75)
+    w = wl.CartWorkload(name="rp2", dim=2, n=(n, 4), lo=(-0.5, 0.0), hi=(1.5, 4 * h),
+                        bc=("nrbc", "nrbc", "periodic", "periodic"), cfl=0.5, steps=0,
+                        eps=np.ones(n * 4), mu=None, fields0=f, limiter="vanleer")
+    s = GKSSolver.from_workload(w, precision="fp32")
+    T = 0.25
+    nst = int(math.ceil(T / s.info()["dt"]))
+    from paper_2412_16845_gb300.gks import gks_set_dt
+    gks_set_dt(s.ctx, T / nst)
+    s.step(nst)
+    out = s.read_fields()
+    s.close()
+    ref, _ = oracle_cart_run(w, nst, dt=T / nst, c=1.0)
+    assert rel_l2(out, ref) <= 2e-5, rel_l2(out, ref)
+    sel = (x > 0.0) & (x < 1.0)
+    for v in (out[0] - out[2], out[0] + out[2]):
+        assert np.abs(v[sel]).max() <= 0.75 * (1 + 2e-3) + 1e-6
