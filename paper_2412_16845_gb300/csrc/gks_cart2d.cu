@@ -557,6 +557,330 @@ __global__ void __launch_bounds__(WARPS * 32, GKS_CART2D_MINBLOCKS) cart2d_step_
   if (__any_sync(FULL, bad) && lane == 0) atomicOr(p.flag, 1);
 }
 
+// ------------------------------------------------------------------ paired FP32 path
+// FP32 with mu = 1.  A lane's two x-faces (X+1/2, X+3/2), its two y-faces (columns X, X+1) and
+// its two cell updates run the same arithmetic, so they go through Blackwell's paired FP32
+// instructions (__fadd2_rn, __fmul2_rn, __ffma2_rn): component x is the first face or column,
+// y the second.  Same march, same closed-form face flux as cart2d_step_kernel.
+using f2 = float2;
+__device__ __forceinline__ f2 pk(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ f2 padd(f2 a, f2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ f2 psub(f2 a, f2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ f2 pmul(f2 a, f2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ f2 pfma(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, c); }
+
+// face_flux constants for mu = 1, each as a pair (a14 = a1 + a4, n* negated).
+struct FaceKP {
+  f2 a14, a2, a3, a5, a6, nq2, nq3, q5, b1, c1, c2, c3, c4, c5, c6, g0, nk3, half;
+};
+
+inline FaceKP make_face_kp(const FaceK<float> &k) {
+  auto b = [](float v) { return make_float2(v, v); };
+  FaceKP q;
+  q.a14 = b(k.a1 + k.a4); q.a2 = b(k.a2); q.a3 = b(k.a3); q.a5 = b(k.a5); q.a6 = b(k.a6);
+  q.nq2 = b(-k.q2); q.nq3 = b(-k.q3); q.q5 = b(k.q5); q.b1 = b(k.b1);
+  q.c1 = b(k.c1); q.c2 = b(k.c2); q.c3 = b(k.c3); q.c4 = b(k.c4); q.c5 = b(k.c5); q.c6 = b(k.c6);
+  q.g0 = b(k.g0); q.nk3 = b(-k.k3); q.half = b(0.5f);
+  return q;
+}
+
+// Two face sides (see FSide) with mu = 1.
+struct FSideP {
+  f2 e, hn, ht, den, dhn, dht, dat, det, eps;
+};
+
+// face_flux<float, false> for two faces at once.
+__device__ __forceinline__ void face_flux_p(const FSideP &l, const FSideP &r, const FaceKP &k,
+                                            f2 &fE, f2 &fHn, f2 &fHt) {
+  const f2 Ue_l = pmul(l.eps, l.e), Ue_r = pmul(r.eps, r.e);
+  const f2 Uxe_l = pmul(l.eps, l.den), Uxe_r = pmul(r.eps, r.den);
+  const f2 S_B = padd(l.ht, r.ht), D_e = psub(r.e, l.e);
+  const f2 S_Uxe = padd(Uxe_l, Uxe_r), D_xB = psub(r.dht, l.dht);
+  const f2 D_Ue = psub(Ue_r, Ue_l), D_At = psub(r.dat, l.dat);
+  const f2 S_Uxa = padd(l.dhn, r.dhn), D_Ua = psub(r.hn, l.hn), D_Et = psub(r.det, l.det);
+  const f2 S_Ue = padd(Ue_l, Ue_r), D_B = psub(r.ht, l.ht), S_UxB = padd(l.dht, r.dht);
+  const f2 D_ex = psub(r.den, l.den), S_UAt = padd(l.dat, r.dat), S_e = padd(l.e, r.e);
+  const f2 se = padd(l.eps, r.eps);
+  const f2 ie = pk(rcp2(se.x), rcp2(se.y));
+  const f2 g = pfma(k.nk3, ie, k.g0);
+  f2 fe = pmul(k.a14, S_B);
+  fe = pfma(k.a2, D_e, fe);
+  fe = pfma(g, pfma(k.a3, D_xB, pmul(k.half, S_Uxe)), fe);
+  fe = pfma(k.nq2, D_Ue, fe);
+  fe = pfma(k.nq3, S_Uxe, fe);
+  fe = pfma(k.a5, D_At, fe);
+  fe = pfma(k.a6, D_xB, fe);
+  f2 fa = pmul(k.q5, S_Uxa);
+  fa = pfma(k.nq2, D_Ua, fa);
+  fa = pfma(k.b1, D_Et, fa);
+  f2 u = pmul(k.c1, S_Ue);
+  u = pfma(k.c2, D_B, u);
+  u = pfma(k.c4, S_UAt, u);
+  f2 fb = pmul(ie, u);
+  fb = pfma(g, pfma(k.c3, D_ex, pmul(k.half, S_UxB)), fb);
+  fb = pfma(k.c5, S_e, fb);
+  fb = pfma(k.nq2, D_B, fb);
+  fb = pfma(k.nq3, S_UxB, fb);
+  fb = pfma(k.c6, D_ex, fb);
+  fE = fe;
+  fHn = fa;
+  fHt = fb;
+}
+
+// Two columns of one row as pairs, plus the PEC mirror flags (as in Row2).
+struct RowP {
+  f2 ez, hx, hy, eps;
+  bool xm[2], ym;
+};
+// Raw differences of the two columns (component x: column X, y: column X+1).
+struct GP {
+  f2 ex, ey, ax, ay, bx, by;
+};
+
+__device__ __forceinline__ void apply_mirror_p(RowP &v) {
+  if (v.ym | v.xm[0] | v.xm[1]) {
+    if (v.xm[0] != v.ym) v.ez.x = -v.ez.x;
+    if (v.xm[1] != v.ym) v.ez.y = -v.ez.y;
+    if (v.xm[0]) v.hx.x = -v.hx.x;
+    if (v.xm[1]) v.hx.y = -v.hx.y;
+    if (v.ym) { v.hy.x = -v.hy.x; v.hy.y = -v.hy.y; }
+  }
+}
+
+template <bool HAS_PEC>
+__device__ __forceinline__ RowP load_row_p(const Cart2DKernelArgs<float> &p, int X, int row) {
+  RowP v;
+  const int r = axis_index(row, p.ny, p.pery, HAS_PEC && p.pec[2], HAS_PEC && p.pec[3], v.ym);
+  v.xm[0] = v.xm[1] = false;
+  const int64_t ro = (int64_t)r * p.pitch;
+  if (X >= 0 && X + 1 < p.nx) {
+    v.ez = __ldg(reinterpret_cast<const f2 *>(p.V + ro + X));
+    v.hx = __ldg(reinterpret_cast<const f2 *>(p.V + p.cstride + ro + X));
+    v.hy = __ldg(reinterpret_cast<const f2 *>(p.V + 2 * p.cstride + ro + X));
+    v.eps = __ldg(reinterpret_cast<const f2 *>(p.eps + ro + X));
+  } else {
+    int64_t o[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+      o[k] = ro + axis_index(X + k, p.nx, p.perx, HAS_PEC && p.pec[0], HAS_PEC && p.pec[1],
+                             v.xm[k]);
+    v.ez = pk(__ldg(p.V + o[0]), __ldg(p.V + o[1]));
+    v.hx = pk(__ldg(p.V + p.cstride + o[0]), __ldg(p.V + p.cstride + o[1]));
+    v.hy = pk(__ldg(p.V + 2 * p.cstride + o[0]), __ldg(p.V + 2 * p.cstride + o[1]));
+    v.eps = pk(__ldg(p.eps + o[0]), __ldg(p.eps + o[1]));
+  }
+  return v;
+}
+
+__device__ __forceinline__ RowV<float> col_of_p(const RowP &v, int k) {
+  RowV<float> c;
+  c.ez = k ? v.ez.y : v.ez.x; c.hx = k ? v.hx.y : v.hx.x; c.hy = k ? v.hy.y : v.hy.x;
+  c.eps = k ? v.eps.y : v.eps.x; c.mu = 1.f;
+  return c;
+}
+__device__ __forceinline__ RowG<float> grad_of_p(const GP &g, int k) {
+  RowG<float> r;
+  r.ex = k ? g.ex.y : g.ex.x; r.ey = k ? g.ey.y : g.ey.x; r.ax = k ? g.ax.y : g.ax.x;
+  r.ay = k ? g.ay.y : g.ay.x; r.bx = k ? g.bx.y : g.bx.x; r.by = k ? g.by.y : g.by.x;
+  return r;
+}
+
+// Raw differences of the lane's two columns (limited slopes with LIMIT); right[] receives
+// column X+2 of this row.
+template <bool LIMIT>
+__device__ __forceinline__ void diffs_p(const RowP &c, const RowP &dn, const RowP &up, GP &g,
+                                        float right[3]) {
+  const float lE = __shfl_up_sync(FULL, c.ez.y, 1), rE = __shfl_down_sync(FULL, c.ez.x, 1);
+  const float lA = __shfl_up_sync(FULL, c.hx.y, 1), rA = __shfl_down_sync(FULL, c.hx.x, 1);
+  const float lB = __shfl_up_sync(FULL, c.hy.y, 1), rB = __shfl_down_sync(FULL, c.hy.x, 1);
+  if (LIMIT) {
+    g.ex = pk(raw_slope<true>(lE, c.ez.x, c.ez.y), raw_slope<true>(c.ez.x, c.ez.y, rE));
+    g.ax = pk(raw_slope<true>(lA, c.hx.x, c.hx.y), raw_slope<true>(c.hx.x, c.hx.y, rA));
+    g.bx = pk(raw_slope<true>(lB, c.hy.x, c.hy.y), raw_slope<true>(c.hy.x, c.hy.y, rB));
+    g.ey = pk(raw_slope<true>(dn.ez.x, c.ez.x, up.ez.x), raw_slope<true>(dn.ez.y, c.ez.y, up.ez.y));
+    g.ay = pk(raw_slope<true>(dn.hx.x, c.hx.x, up.hx.x), raw_slope<true>(dn.hx.y, c.hx.y, up.hx.y));
+    g.by = pk(raw_slope<true>(dn.hy.x, c.hy.x, up.hy.x), raw_slope<true>(dn.hy.y, c.hy.y, up.hy.y));
+  } else {
+    g.ex = psub(pk(c.ez.y, rE), pk(lE, c.ez.x));
+    g.ax = psub(pk(c.hx.y, rA), pk(lA, c.hx.x));
+    g.bx = psub(pk(c.hy.y, rB), pk(lB, c.hy.x));
+    g.ey = psub(up.ez, dn.ez);
+    g.ay = psub(up.hx, dn.hx);
+    g.by = psub(up.hy, dn.hy);
+  }
+  right[0] = rE; right[1] = rA; right[2] = rB;
+}
+
+struct Cart2DPackArgs {
+  Cart2DKernelArgs<float> b;
+  FaceKP fx, fy;
+};
+
+template <bool HAS_PEC, bool LIMIT>
+__global__ void __launch_bounds__(WARPS * 32, GKS_CART2D_MINBLOCKS)
+    cart2d_step_kernel_p(const Cart2DPackArgs P, int nstrips, int rows, int strip0, int ybeg,
+                         int yend) {
+  const Cart2DKernelArgs<float> &p = P.b;
+  const int lane = threadIdx.x & 31;
+  const int wid = blockIdx.x * WARPS + (threadIdx.x >> 5);
+  const int strip = strip0 + wid % nstrips, chunk = wid / nstrips;
+  const int y0 = ybeg + chunk * rows;
+  if (y0 >= yend) return;                             // whole warp leaves together
+  const int y1 = min(y0 + rows, yend);
+  const int x0 = strip * WCOLS;
+  const int X = x0 - 2 + 2 * lane;
+  const int xend = min(x0 + WCOLS, p.nx);
+  const bool xlo_nr = !p.perx && !p.pec[0], xhi_nr = !p.perx && !p.pec[1];
+  const bool ylo_nr = !p.pery && !p.pec[2], yhi_nr = !p.pery && !p.pec[3];
+  const float q4 = 0.25f, mq4 = -0.25f;
+  const f2 Q4 = pk(q4, q4), MQ4 = pk(mq4, mq4);
+
+  RowP vm2 = load_row_p<HAS_PEC>(p, X, y0 - 2);
+  RowP vm1 = load_row_p<HAS_PEC>(p, X, y0 - 1);
+  RowP v0 = load_row_p<HAS_PEC>(p, X, y0);
+  RowP v1 = load_row_p<HAS_PEC>(p, X, y0 + 1);
+  RowP v2 = load_row_p<HAS_PEC>(p, X, y0 + 2);
+  RowP pf = load_row_p<HAS_PEC>(p, X, y0 + 3);
+  if (HAS_PEC) {
+    apply_mirror_p(vm2);
+    apply_mirror_p(vm1);
+    apply_mirror_p(v0);
+    apply_mirror_p(v1);
+    apply_mirror_p(v2);
+  }
+  GP g0, gm1;
+  float r0[3], rm1[3];
+  diffs_p<LIMIT>(vm1, vm2, v0, gm1, rm1);
+  diffs_p<LIMIT>(v0, vm1, v1, g0, r0);
+  // y-face sides of two columns: normal y (hn = Hy, ht = Hx, tangent x)
+  auto yside = [](const RowP &v, const GP &g, f2 sgn) {
+    FSideP s;
+    s.e = pfma(sgn, g.ey, v.ez); s.hn = pfma(sgn, g.by, v.hy); s.ht = pfma(sgn, g.ay, v.hx);
+    s.den = g.ey; s.dhn = g.by; s.dht = g.ay; s.dat = g.bx; s.det = g.ex;
+    s.eps = v.eps;
+    return s;
+  };
+  f2 fbE, fbHx, fbHy;                                 // flux along +y below row j
+  face_flux_p(yside(vm1, gm1, Q4), yside(v0, g0, MQ4), P.fy, fbE, fbHy, fbHx);
+  if (y0 == 0 && ylo_nr) {
+    float e[2], hx[2], hy[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+      low_y_boundary_flux<float>(col_of_p(v0, k), grad_of_p(g0, k), p, e[k], hx[k], hy[k]);
+    fbE = pk(e[0], e[1]); fbHx = pk(hx[0], hx[1]); fbHy = pk(hy[0], hy[1]);
+  }
+  bool bad = false;
+#pragma unroll 1
+  for (int j = y0; j < y1; ++j) {
+    const RowP pf2 = load_row_p<HAS_PEC>(p, X, j + 4);   // two rows ahead of use
+    GP g1;
+    float r1[3];
+    diffs_p<LIMIT>(v1, v0, v2, g1, r1);
+    // x-faces of row j: X+1/2 (component x) and X+3/2 (component y, column X+2 of the next
+    // lane on its right side)
+    f2 fxE, fxHx, fxHy;
+    {
+      const float nb_eps = __shfl_down_sync(FULL, v0.eps.x, 1);
+      const float gn_ex = __shfl_down_sync(FULL, g0.ex.x, 1);
+      const float gn_ax = __shfl_down_sync(FULL, g0.ax.x, 1);
+      const float gn_bx = __shfl_down_sync(FULL, g0.bx.x, 1);
+      const float gn_ay = __shfl_down_sync(FULL, g0.ay.x, 1);
+      const float gn_ey = __shfl_down_sync(FULL, g0.ey.x, 1);
+      FSideP l, r;
+      l.e = pfma(Q4, g0.ex, v0.ez); l.hn = pfma(Q4, g0.ax, v0.hx); l.ht = pfma(Q4, g0.bx, v0.hy);
+      l.den = g0.ex; l.dhn = g0.ax; l.dht = g0.bx; l.dat = g0.ay; l.det = g0.ey;
+      l.eps = v0.eps;
+      r.den = pk(g0.ex.y, gn_ex); r.dhn = pk(g0.ax.y, gn_ax); r.dht = pk(g0.bx.y, gn_bx);
+      r.dat = pk(g0.ay.y, gn_ay); r.det = pk(g0.ey.y, gn_ey);
+      r.e = pfma(MQ4, r.den, pk(v0.ez.y, r0[0]));
+      r.hn = pfma(MQ4, r.dhn, pk(v0.hx.y, r0[1]));
+      r.ht = pfma(MQ4, r.dht, pk(v0.hy.y, r0[2]));
+      r.eps = pk(v0.eps.y, nb_eps);
+      face_flux_p(l, r, P.fx, fxE, fxHx, fxHy);
+      if (xhi_nr) {
+        if (X == p.nx - 1) {            // first face on the high-x boundary
+          const Side<float> q = xside_scalar<float>(col_of_p(v0, 0), grad_of_p(g0, 0), q4,
+                                                    p.inv2hx, p.inv2hy);
+          tm_face_flux<float, true>(q, q, p.Kx, fxE.x, fxHx.x, fxHy.x);
+        }
+        if (X + 1 == p.nx - 1) {        // second face on the high-x boundary
+          const Side<float> q = xside_scalar<float>(col_of_p(v0, 1), grad_of_p(g0, 1), q4,
+                                                    p.inv2hx, p.inv2hy);
+          tm_face_flux<float, true>(q, q, p.Kx, fxE.y, fxHx.y, fxHy.y);
+        }
+      }
+      if (xlo_nr && X == -2) {          // second face is the low-x boundary face of column 0
+        RowV<float> nb;
+        nb.ez = r0[0]; nb.hx = r0[1]; nb.hy = r0[2]; nb.eps = nb_eps; nb.mu = 1.f;
+        RowG<float> gn;
+        gn.ex = gn_ex; gn.ax = gn_ax; gn.bx = gn_bx; gn.ay = gn_ay; gn.ey = gn_ey; gn.by = 0.f;
+        low_boundary_flux<float>(xside_scalar<float>(nb, gn, mq4, p.inv2hx, p.inv2hy), p.Kx,
+                                 fxE.y, fxHx.y, fxHy.y);
+      }
+    }
+    // y-faces between rows j and j+1
+    f2 ftE, ftHx, ftHy;
+    face_flux_p(yside(v0, g0, Q4), yside(v1, g1, MQ4), P.fy, ftE, ftHy, ftHx);
+    if (j + 1 == p.ny && yhi_nr) {
+      float e[2], hx[2], hy[2];
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const Side<float> q = yside_scalar<float>(col_of_p(v0, k), grad_of_p(g0, k), q4,
+                                                  p.inv2hx, p.inv2hy);
+        float oe, oa, ob;
+        tm_face_flux<float, true>(q, q, p.Ky, oe, oa, ob);
+        e[k] = oe; hx[k] = -ob; hy[k] = oa;
+      }
+      ftE = pk(e[0], e[1]); ftHx = pk(hx[0], hx[1]); ftHy = pk(hy[0], hy[1]);
+    }
+    // update row j: left face of column X is the previous lane's second face
+    {
+      const float lE = __shfl_up_sync(FULL, fxE.y, 1);
+      const float lHx = __shfl_up_sync(FULL, fxHx.y, 1);
+      const float lHy = __shfl_up_sync(FULL, fxHy.y, 1);
+      f2 dE = padd(psub(pk(lE, fxE.x), fxE), psub(fbE, ftE));
+      const f2 dHx = padd(psub(pk(lHx, fxHx.x), fxHx), psub(fbHx, ftHx));
+      const f2 dHy = padd(psub(pk(lHy, fxHy.x), fxHy), psub(fbHy, ftHy));
+      const int64_t ro = (int64_t)j * p.pitch;
+      if (p.src && j >= p.sy0 && j < p.sy1) {
+        if (X >= p.sx0 && X < p.sx1) dE.x -= p.src_amp * p.src[ro + X];
+        if (X + 1 >= p.sx0 && X + 1 < p.sx1) dE.y -= p.src_amp * p.src[ro + X + 1];
+      }
+      const f2 ne = pfma(dE, pk(rcp1(v0.eps.x), rcp1(v0.eps.y)), v0.ez);
+      const f2 nhx = padd(v0.hx, dHx);
+      const f2 nhy = padd(v0.hy, dHy);
+      const bool ok0 = X >= x0 && X < xend, ok1 = X + 1 >= x0 && X + 1 < xend;
+      if (ok0 && ok1) {
+        *reinterpret_cast<f2 *>(p.Vout + ro + X) = ne;
+        *reinterpret_cast<f2 *>(p.Vout + p.cstride + ro + X) = nhx;
+        *reinterpret_cast<f2 *>(p.Vout + 2 * p.cstride + ro + X) = nhy;
+        const f2 sum = padd(padd(ne, nhx), nhy);
+        bad |= !(isfinite(sum.x) && isfinite(sum.y));
+      } else {
+        if (ok0) {
+          p.Vout[ro + X] = ne.x;
+          p.Vout[p.cstride + ro + X] = nhx.x;
+          p.Vout[2 * p.cstride + ro + X] = nhy.x;
+          bad |= !(isfinite(ne.x) && isfinite(nhx.x) && isfinite(nhy.x));
+        }
+        if (ok1) {
+          p.Vout[ro + X + 1] = ne.y;
+          p.Vout[p.cstride + ro + X + 1] = nhx.y;
+          p.Vout[2 * p.cstride + ro + X + 1] = nhy.y;
+          bad |= !(isfinite(ne.y) && isfinite(nhx.y) && isfinite(nhy.y));
+        }
+      }
+    }
+    // rotate the register window
+    v0 = v1; v1 = v2; v2 = pf; pf = pf2;
+    if (HAS_PEC) apply_mirror_p(v2);          // the prefetched row takes its mirror signs now
+    g0 = g1;
+    fbE = ftE; fbHx = ftHx; fbHy = ftHy;
+    r0[0] = r1[0]; r0[1] = r1[1]; r0[2] = r1[2];
+  }
+  if (__any_sync(FULL, bad) && lane == 0) atomicOr(p.flag, 1);
+}
+
 template <typename T>
 Coef<T> make_coef(const double C[5], double h, double c) {
   Coef<T> k;
@@ -614,6 +938,22 @@ cudaError_t launch_t(const CartGeom &g, const CartStepArgs &a, cudaStream_t st) 
        {cart2d_step_kernel<T, false, true, false>, cart2d_step_kernel<T, false, true, true>}},
       {{cart2d_step_kernel<T, true, false, false>, cart2d_step_kernel<T, true, false, true>},
        {cart2d_step_kernel<T, true, true, false>, cart2d_step_kernel<T, true, true, true>}}};
+  if constexpr (sizeof(T) == 4) {
+    if (!a.mu) {                       // FP32 with mu = 1: the paired-instruction kernel
+      Cart2DPackArgs P;
+      P.b = p;
+      P.fx = make_face_kp(p.fx);
+      P.fy = make_face_kp(p.fy);
+      using KP = void (*)(const Cart2DPackArgs, int, int, int, int, int);
+      static const KP kp[2][2] = {{cart2d_step_kernel_p<false, false>,
+                                   cart2d_step_kernel_p<false, true>},
+                                  {cart2d_step_kernel_p<true, false>,
+                                   cart2d_step_kernel_p<true, true>}};   // [pec][limiter]
+      kp[pec ? 1 : 0][a.limiter ? 1 : 0]<<<grid, WARPS * 32, 0, st>>>(P, nstrips, rows, strip0,
+                                                                       wy0, wy1);
+      return cudaGetLastError();
+    }
+  }
   kern[a.mu ? 1 : 0][pec ? 1 : 0][a.limiter ? 1 : 0]<<<grid, WARPS * 32, 0, st>>>(
       p, nstrips, rows, strip0, wy0, wy1);
   return cudaGetLastError();
