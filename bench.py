@@ -502,7 +502,7 @@ def main():
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "peak_source": how,
                          "traffic": _profiled_traffic(),
-                         "kernel": "cart2d_step_kernel<float>",
+                         "kernel": "cart2d_step_kernel_p (FP32, mu = 1)",
                          "algorithmic_bytes_per_launch": BYTES_PER_CELL_STEP["fp32"] * ncell},
             "fp64": {"value": value64, "ms_per_step": ms64, "unit": UNIT,
                      "fp32_speedup": value / world / value64},
