@@ -779,14 +779,13 @@ __global__ void __launch_bounds__(WARPS * 32, GKS_CART2D_MINBLOCKS)
     // x-faces of row j: X+1/2 (component x) and X+3/2 (component y, column X+2 of the next
     // lane on its right side)
     f2 fxE, fxHx, fxHy;
-    // column X+2 (the next lane's first column): material and differences, taken by every lane
-    const float nb_eps = __shfl_down_sync(FULL, v0.eps.x, 1);
-    const float gn_ex = __shfl_down_sync(FULL, g0.ex.x, 1);
-    const float gn_ax = __shfl_down_sync(FULL, g0.ax.x, 1);
-    const float gn_bx = __shfl_down_sync(FULL, g0.bx.x, 1);
-    const float gn_ay = __shfl_down_sync(FULL, g0.ay.x, 1);
-    const float gn_ey = __shfl_down_sync(FULL, g0.ey.x, 1);
     {
+      const float nb_eps = __shfl_down_sync(FULL, v0.eps.x, 1);
+      const float gn_ex = __shfl_down_sync(FULL, g0.ex.x, 1);
+      const float gn_ax = __shfl_down_sync(FULL, g0.ax.x, 1);
+      const float gn_bx = __shfl_down_sync(FULL, g0.bx.x, 1);
+      const float gn_ay = __shfl_down_sync(FULL, g0.ay.x, 1);
+      const float gn_ey = __shfl_down_sync(FULL, g0.ey.x, 1);
       FSideP l, r;
       l.e = pfma(Q4, g0.ex, v0.ez); l.hn = pfma(Q4, g0.ax, v0.hx); l.ht = pfma(Q4, g0.bx, v0.hy);
       l.den = g0.ex; l.dhn = g0.ax; l.dht = g0.bx; l.dat = g0.ay; l.det = g0.ey;
@@ -798,13 +797,6 @@ __global__ void __launch_bounds__(WARPS * 32, GKS_CART2D_MINBLOCKS)
       r.ht = pfma(MQ4, r.dht, pk(v0.hy.y, r0[2]));
       r.eps = pk(v0.eps.y, nb_eps);
       face_flux_p(l, r, P.fx, fxE, fxHx, fxHy);
-    }
-    // y-faces between rows j and j+1 (in the same basic block as the x-faces, so that the two
-    // independent flux chains interleave)
-    f2 ftE, ftHx, ftHy;
-    face_flux_p(yside(v0, g0, Q4), yside(v1, g1, MQ4), P.fy, ftE, ftHy, ftHx);
-    // boundary faces replace the interior results (rare, divergent)
-    {
       if (xhi_nr) {
         if (X == p.nx - 1) {            // first face on the high-x boundary
           const Side<float> q = xside_scalar<float>(col_of_p(v0, 0), grad_of_p(g0, 0), q4,
@@ -826,6 +818,9 @@ __global__ void __launch_bounds__(WARPS * 32, GKS_CART2D_MINBLOCKS)
                                  fxE.y, fxHx.y, fxHy.y);
       }
     }
+    // y-faces between rows j and j+1
+    f2 ftE, ftHx, ftHy;
+    face_flux_p(yside(v0, g0, Q4), yside(v1, g1, MQ4), P.fy, ftE, ftHy, ftHx);
     if (j + 1 == p.ny && yhi_nr) {
       float e[2], hx[2], hy[2];
 #pragma unroll
