@@ -221,6 +221,7 @@ def main():
     ap.add_argument("--steps4", type=int, default=100)
     ap.add_argument("--no-err4", dest="err4", action="store_false", default=True)
     ap.add_argument("--no-cleaning", dest="with_cleaning", action="store_false", default=True)
+    ap.add_argument("--no-limiter", dest="with_limiter", action="store_false", default=True)
     ap.add_argument("--no-adjoint", dest="with_adjoint", action="store_false", default=True)
     ap.add_argument("--n5", type=int, default=2048)
     args = ap.parse_args()
@@ -409,6 +410,26 @@ def main():
                 "algorithmic_bytes_per_tet_step": 229,
                 "hbm_frac_fp32": 229 * n4 / (ms4 * 1e-3) / 1e9 / _peaks()[0]}
 
+    # ---------------- van Leer limiter: the cylinder workload with limited slopes (FP32)
+    limited = None
+    if args.with_limiter:
+        wlim = dataclasses.replace(wl.config2_cylinders_tm(n=n, steps=args.steps),
+                                   limiter="vanleer")
+        ls = GKSSolver.from_workload(wlim, precision="fp32", stream=sptr)
+        ls.step(3)
+        ls.sync()
+        kl = min(args.steps, 500)
+        l0 = torch.cuda.Event(enable_timing=True)
+        l1 = torch.cuda.Event(enable_timing=True)
+        l0.record(stream)
+        ls.step(kl)
+        l1.record(stream)
+        torch.cuda.synchronize()
+        msl = l0.elapsed_time(l1) / kl
+        ls.close()
+        limited = {"workload": f"tm2d_cylinders_{n}_vanleer", "steps_timed": kl,
+                   "value_fp32": ncell / (msl * 1e-3) / 1e9, "ms_per_step_fp32": msl}
+
     # ---------------- divergence cleaning (TM + psi, gamma = 1, CFL 0.4) on the cylinder grid
     cleaning = None
     if args.with_cleaning:
@@ -514,6 +535,7 @@ def main():
             "gpu_launches": int(launches),
             "maxwell3d": three,
             "tets": tets,
+            "limiter": limited,
             "cleaning": cleaning,
             "adjoint": adj,
             "clocks": clocks,
