@@ -126,7 +126,7 @@ __device__ __forceinline__ void face_flux(const Side3<T> &l, const Side3<T> &r, 
 template <typename T, bool GHOST>
 __device__ __forceinline__ void face_flux(const Side8<T> &l, const Side8<T> &r, const K3<T> &K,
                                           T chi, T gam, T out[8]) {
-  flux3_phm<T, GHOST>(l, r, K, chi, gam, out);
+  flux3_phm<T, GHOST, true>(l, r, K, chi, gam, out);   // the cleaning system runs with mu = 1
 }
 
 // Interior face of frame F between cells L (low side) and R (high side), along +axis.  Maxwell
@@ -143,7 +143,8 @@ __device__ __forceinline__ void interior_face(const Cell3<T, NC> &L, const Cell3
       flux3_mu1<T>(to_local<T, F>(L, halfh), to_local<T, F>(R, -halfh), FK,
                    rcp3x2(L.eps + R.eps), loc);
   } else {
-    flux3_phm<T, false>(to_local<T, F>(L, halfh), to_local<T, F>(R, -halfh), K, chi, gam, loc);
+    flux3_phm<T, false, true>(to_local<T, F>(L, halfh), to_local<T, F>(R, -halfh), K, chi, gam,
+                              loc);
   }
   to_global<T, F, NC>(loc, phi);
 }
