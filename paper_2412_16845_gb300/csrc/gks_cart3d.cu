@@ -33,10 +33,11 @@ constexpr int BX = 32;
 constexpr int PX = BX + 2;            // staged plane: one extra ring around the thread grid
 // Tile height: FP32 takes 32 x 16 threads (inner 30 x 14 cells, about 200 KB of shared memory,
 // one CTA per SM); FP64 32 x 8 (its planes are twice as large).  The eight-component cleaning
-// system stages a third more per cell: 32 x 8 (FP32) and 32 x 6 (FP64).
+// system stages a third more per cell: 32 x 12 (FP32: 199 KB, 168 registers, 12 warps per SM)
+// and 32 x 6 (FP64).
 template <typename T, int NC>
 struct Geo3 {
-  static constexpr int BY = NC == 6 ? (sizeof(T) == 4 ? 16 : 8) : (sizeof(T) == 4 ? 8 : 6);
+  static constexpr int BY = NC == 6 ? (sizeof(T) == 4 ? 16 : 8) : (sizeof(T) == 4 ? 12 : 6);
   static constexpr int NTH = BX * BY;
   static constexpr int PY = BY + 2;
   static constexpr int NV = NC + 2;   // staged quantities: the NC fields, eps, mu
@@ -308,7 +309,7 @@ __device__ __forceinline__ void load_grad(const Smem3<T, NC> &s, int gs, int ty,
 }
 
 // One CTA per SM: FP32 512 threads (registers capped at 128), FP64 256; the cleaning system
-// 256 (FP32) and 192 (FP64).
+// 384 (FP32) and 192 (FP64).
 template <typename T, int NC, bool HAS_MU, bool HAS_PEC, bool LIMIT>
 __global__ void __launch_bounds__(Geo3<T, NC>::NTH, 1)
     cart3d_step_kernel(const Cart3DArgs<T> p) {
