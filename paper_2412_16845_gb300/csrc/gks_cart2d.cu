@@ -716,134 +716,6 @@ struct Cart2DPackArgs {
   FaceKP fx, fy;
 };
 
-// Per-warp constants of the paired march.
-struct MarchP {
-  int X, x0, xend;
-  bool xlo_nr, xhi_nr, yhi_nr;
-};
-
-// y-face sides of two columns: normal y (hn = Hy, ht = Hx, tangent x).
-__device__ __forceinline__ FSideP yside_p(const RowP &v, const GP &g, f2 sgn) {
-  FSideP s;
-  s.e = pfma(sgn, g.ey, v.ez); s.hn = pfma(sgn, g.by, v.hy); s.ht = pfma(sgn, g.ay, v.hx);
-  s.den = g.ey; s.dhn = g.by; s.dht = g.ay; s.dat = g.bx; s.det = g.ex;
-  s.eps = v.eps;
-  return s;
-}
-
-// One row j of the paired march.  In: rows j (a), j+1 (b), j+2 (c, its PEC signs still to
-// apply), the differences g0 of row j, the flux fb through the face below row j, r0 = column
-// X+2 of row j.  Out: the differences g1 of row j+1, the flux ft above row j, r1; row j+4 is
-// loaded into a (row j is dead once updated).  The caller rotates the roles, so no register
-// copies are needed between rows.
-template <bool HAS_PEC, bool LIMIT>
-__device__ __forceinline__ void row_p(const Cart2DPackArgs &P, const MarchP &m, int j, RowP &a,
-                                      const RowP &b, RowP &c, const GP &g0, GP &g1,
-                                      const f2 fb[3], f2 ft[3], const float r0[3], float r1[3],
-                                      bool &bad) {
-  const Cart2DKernelArgs<float> &p = P.b;
-  const int X = m.X;
-  const float q4 = 0.25f, mq4 = -0.25f;
-  const f2 Q4 = pk(q4, q4), MQ4 = pk(mq4, mq4);
-  if (HAS_PEC) apply_mirror_p(c);             // row j+2 enters the working window
-  diffs_p<LIMIT>(b, a, c, g1, r1);
-  // x-faces of row j: X+1/2 (component x) and X+3/2 (component y, column X+2 of the next
-  // lane on its right side)
-  f2 fxE, fxHx, fxHy;
-  {
-    const float nb_eps = __shfl_down_sync(FULL, a.eps.x, 1);
-    const float gn_ex = __shfl_down_sync(FULL, g0.ex.x, 1);
-    const float gn_ax = __shfl_down_sync(FULL, g0.ax.x, 1);
-    const float gn_bx = __shfl_down_sync(FULL, g0.bx.x, 1);
-    const float gn_ay = __shfl_down_sync(FULL, g0.ay.x, 1);
-    const float gn_ey = __shfl_down_sync(FULL, g0.ey.x, 1);
-    FSideP l, r;
-    l.e = pfma(Q4, g0.ex, a.ez); l.hn = pfma(Q4, g0.ax, a.hx); l.ht = pfma(Q4, g0.bx, a.hy);
-    l.den = g0.ex; l.dhn = g0.ax; l.dht = g0.bx; l.dat = g0.ay; l.det = g0.ey;
-    l.eps = a.eps;
-    r.den = pk(g0.ex.y, gn_ex); r.dhn = pk(g0.ax.y, gn_ax); r.dht = pk(g0.bx.y, gn_bx);
-    r.dat = pk(g0.ay.y, gn_ay); r.det = pk(g0.ey.y, gn_ey);
-    r.e = pfma(MQ4, r.den, pk(a.ez.y, r0[0]));
-    r.hn = pfma(MQ4, r.dhn, pk(a.hx.y, r0[1]));
-    r.ht = pfma(MQ4, r.dht, pk(a.hy.y, r0[2]));
-    r.eps = pk(a.eps.y, nb_eps);
-    face_flux_p(l, r, P.fx, fxE, fxHx, fxHy);
-    if (m.xhi_nr) {
-      if (X == p.nx - 1) {            // first face on the high-x boundary
-        const Side<float> q = xside_scalar<float>(col_of_p(a, 0), grad_of_p(g0, 0), q4,
-                                                  p.inv2hx, p.inv2hy);
-        tm_face_flux<float, true>(q, q, p.Kx, fxE.x, fxHx.x, fxHy.x);
-      }
-      if (X + 1 == p.nx - 1) {        // second face on the high-x boundary
-        const Side<float> q = xside_scalar<float>(col_of_p(a, 1), grad_of_p(g0, 1), q4,
-                                                  p.inv2hx, p.inv2hy);
-        tm_face_flux<float, true>(q, q, p.Kx, fxE.y, fxHx.y, fxHy.y);
-      }
-    }
-    if (m.xlo_nr && X == -2) {        // second face is the low-x boundary face of column 0
-      RowV<float> nb;
-      nb.ez = r0[0]; nb.hx = r0[1]; nb.hy = r0[2]; nb.eps = nb_eps; nb.mu = 1.f;
-      RowG<float> gn;
-      gn.ex = gn_ex; gn.ax = gn_ax; gn.bx = gn_bx; gn.ay = gn_ay; gn.ey = gn_ey; gn.by = 0.f;
-      low_boundary_flux<float>(xside_scalar<float>(nb, gn, mq4, p.inv2hx, p.inv2hy), p.Kx,
-                               fxE.y, fxHx.y, fxHy.y);
-    }
-  }
-  // y-faces between rows j and j+1
-  face_flux_p(yside_p(a, g0, Q4), yside_p(b, g1, MQ4), P.fy, ft[0], ft[2], ft[1]);
-  if (j + 1 == p.ny && m.yhi_nr) {
-    float e[2], hx[2], hy[2];
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-      const Side<float> q = yside_scalar<float>(col_of_p(a, k), grad_of_p(g0, k), q4, p.inv2hx,
-                                                p.inv2hy);
-      float oe, oa, ob;
-      tm_face_flux<float, true>(q, q, p.Ky, oe, oa, ob);
-      e[k] = oe; hx[k] = -ob; hy[k] = oa;
-    }
-    ft[0] = pk(e[0], e[1]); ft[1] = pk(hx[0], hx[1]); ft[2] = pk(hy[0], hy[1]);
-  }
-  // update row j: left face of column X is the previous lane's second face
-  {
-    const float lE = __shfl_up_sync(FULL, fxE.y, 1);
-    const float lHx = __shfl_up_sync(FULL, fxHx.y, 1);
-    const float lHy = __shfl_up_sync(FULL, fxHy.y, 1);
-    f2 dE = padd(psub(pk(lE, fxE.x), fxE), psub(fb[0], ft[0]));
-    const f2 dHx = padd(psub(pk(lHx, fxHx.x), fxHx), psub(fb[1], ft[1]));
-    const f2 dHy = padd(psub(pk(lHy, fxHy.x), fxHy), psub(fb[2], ft[2]));
-    const int64_t ro = (int64_t)j * p.pitch;
-    if (p.src && j >= p.sy0 && j < p.sy1) {
-      if (X >= p.sx0 && X < p.sx1) dE.x -= p.src_amp * p.src[ro + X];
-      if (X + 1 >= p.sx0 && X + 1 < p.sx1) dE.y -= p.src_amp * p.src[ro + X + 1];
-    }
-    const f2 ne = pfma(dE, pk(rcp1(a.eps.x), rcp1(a.eps.y)), a.ez);
-    const f2 nhx = padd(a.hx, dHx);
-    const f2 nhy = padd(a.hy, dHy);
-    const bool ok0 = X >= m.x0 && X < m.xend, ok1 = X + 1 >= m.x0 && X + 1 < m.xend;
-    if (ok0 && ok1) {
-      *reinterpret_cast<f2 *>(p.Vout + ro + X) = ne;
-      *reinterpret_cast<f2 *>(p.Vout + p.cstride + ro + X) = nhx;
-      *reinterpret_cast<f2 *>(p.Vout + 2 * p.cstride + ro + X) = nhy;
-      const f2 sum = padd(padd(ne, nhx), nhy);
-      bad |= !(isfinite(sum.x) && isfinite(sum.y));
-    } else {
-      if (ok0) {
-        p.Vout[ro + X] = ne.x;
-        p.Vout[p.cstride + ro + X] = nhx.x;
-        p.Vout[2 * p.cstride + ro + X] = nhy.x;
-        bad |= !(isfinite(ne.x) && isfinite(nhx.x) && isfinite(nhy.x));
-      }
-      if (ok1) {
-        p.Vout[ro + X + 1] = ne.y;
-        p.Vout[p.cstride + ro + X + 1] = nhx.y;
-        p.Vout[2 * p.cstride + ro + X + 1] = nhy.y;
-        bad |= !(isfinite(ne.y) && isfinite(nhx.y) && isfinite(nhy.y));
-      }
-    }
-  }
-  a = load_row_p<HAS_PEC>(p, X, j + 4);      // two rows ahead of its first use
-}
-
 template <bool HAS_PEC, bool LIMIT>
 __global__ void __launch_bounds__(WARPS * 32, GKS_CART2D_MINBLOCKS)
     cart2d_step_kernel_p(const Cart2DPackArgs P, int nstrips, int rows, int strip0, int ybeg,
@@ -855,55 +727,156 @@ __global__ void __launch_bounds__(WARPS * 32, GKS_CART2D_MINBLOCKS)
   const int y0 = ybeg + chunk * rows;
   if (y0 >= yend) return;                             // whole warp leaves together
   const int y1 = min(y0 + rows, yend);
-  MarchP m;
-  m.x0 = strip * WCOLS;
-  m.X = m.x0 - 2 + 2 * lane;
-  m.xend = min(m.x0 + WCOLS, p.nx);
-  m.xlo_nr = !p.perx && !p.pec[0];
-  m.xhi_nr = !p.perx && !p.pec[1];
-  m.yhi_nr = !p.pery && !p.pec[3];
-  const bool ylo_nr = !p.pery && !p.pec[2];
-  const int X = m.X;
-  const f2 Q4 = pk(0.25f, 0.25f), MQ4 = pk(-0.25f, -0.25f);
+  const int x0 = strip * WCOLS;
+  const int X = x0 - 2 + 2 * lane;
+  const int xend = min(x0 + WCOLS, p.nx);
+  const bool xlo_nr = !p.perx && !p.pec[0], xhi_nr = !p.perx && !p.pec[1];
+  const bool ylo_nr = !p.pery && !p.pec[2], yhi_nr = !p.pery && !p.pec[3];
+  const float q4 = 0.25f, mq4 = -0.25f;
+  const f2 Q4 = pk(q4, q4), MQ4 = pk(mq4, mq4);
 
-  // ---------------- prologue: rows y0-2 .. y0+3; differences of rows y0-1, y0; the face
-  // below row y0.  Rows y0+2 and y0+3 take their PEC signs when they enter the window.
   RowP vm2 = load_row_p<HAS_PEC>(p, X, y0 - 2);
   RowP vm1 = load_row_p<HAS_PEC>(p, X, y0 - 1);
   RowP v0 = load_row_p<HAS_PEC>(p, X, y0);
   RowP v1 = load_row_p<HAS_PEC>(p, X, y0 + 1);
   RowP v2 = load_row_p<HAS_PEC>(p, X, y0 + 2);
-  RowP v3 = load_row_p<HAS_PEC>(p, X, y0 + 3);
+  RowP pf = load_row_p<HAS_PEC>(p, X, y0 + 3);
   if (HAS_PEC) {
     apply_mirror_p(vm2);
     apply_mirror_p(vm1);
     apply_mirror_p(v0);
     apply_mirror_p(v1);
+    apply_mirror_p(v2);
   }
-  GP gA, gB, gm1;
-  float rA[3], rB[3], rm1[3];
+  GP g0, gm1;
+  float r0[3], rm1[3];
   diffs_p<LIMIT>(vm1, vm2, v0, gm1, rm1);
-  diffs_p<LIMIT>(v0, vm1, v1, gA, rA);
-  f2 fA[3], fB[3];                                    // (E, Hx, Hy) flux along +y
-  face_flux_p(yside_p(vm1, gm1, Q4), yside_p(v0, gA, MQ4), P.fy, fA[0], fA[2], fA[1]);
+  diffs_p<LIMIT>(v0, vm1, v1, g0, r0);
+  // y-face sides of two columns: normal y (hn = Hy, ht = Hx, tangent x)
+  auto yside = [](const RowP &v, const GP &g, f2 sgn) {
+    FSideP s;
+    s.e = pfma(sgn, g.ey, v.ez); s.hn = pfma(sgn, g.by, v.hy); s.ht = pfma(sgn, g.ay, v.hx);
+    s.den = g.ey; s.dhn = g.by; s.dht = g.ay; s.dat = g.bx; s.det = g.ex;
+    s.eps = v.eps;
+    return s;
+  };
+  f2 fbE, fbHx, fbHy;                                 // flux along +y below row j
+  face_flux_p(yside(vm1, gm1, Q4), yside(v0, g0, MQ4), P.fy, fbE, fbHy, fbHx);
   if (y0 == 0 && ylo_nr) {
     float e[2], hx[2], hy[2];
 #pragma unroll
     for (int k = 0; k < 2; ++k)
-      low_y_boundary_flux<float>(col_of_p(v0, k), grad_of_p(gA, k), p, e[k], hx[k], hy[k]);
-    fA[0] = pk(e[0], e[1]); fA[1] = pk(hx[0], hx[1]); fA[2] = pk(hy[0], hy[1]);
+      low_y_boundary_flux<float>(col_of_p(v0, k), grad_of_p(g0, k), p, e[k], hx[k], hy[k]);
+    fbE = pk(e[0], e[1]); fbHx = pk(hx[0], hx[1]); fbHy = pk(hy[0], hy[1]);
   }
   bool bad = false;
-  // four rows per trip: the row, difference, flux and column-X+2 registers change roles
 #pragma unroll 1
-  for (int j = y0; j < y1; j += 4) {
-    row_p<HAS_PEC, LIMIT>(P, m, j, v0, v1, v2, gA, gB, fA, fB, rA, rB, bad);
-    if (j + 1 >= y1) break;
-    row_p<HAS_PEC, LIMIT>(P, m, j + 1, v1, v2, v3, gB, gA, fB, fA, rB, rA, bad);
-    if (j + 2 >= y1) break;
-    row_p<HAS_PEC, LIMIT>(P, m, j + 2, v2, v3, v0, gA, gB, fA, fB, rA, rB, bad);
-    if (j + 3 >= y1) break;
-    row_p<HAS_PEC, LIMIT>(P, m, j + 3, v3, v0, v1, gB, gA, fB, fA, rB, rA, bad);
+  for (int j = y0; j < y1; ++j) {
+    const RowP pf2 = load_row_p<HAS_PEC>(p, X, j + 4);   // two rows ahead of use
+    GP g1;
+    float r1[3];
+    diffs_p<LIMIT>(v1, v0, v2, g1, r1);
+    // x-faces of row j: X+1/2 (component x) and X+3/2 (component y, column X+2 of the next
+    // lane on its right side)
+    f2 fxE, fxHx, fxHy;
+    {
+      const float nb_eps = __shfl_down_sync(FULL, v0.eps.x, 1);
+      const float gn_ex = __shfl_down_sync(FULL, g0.ex.x, 1);
+      const float gn_ax = __shfl_down_sync(FULL, g0.ax.x, 1);
+      const float gn_bx = __shfl_down_sync(FULL, g0.bx.x, 1);
+      const float gn_ay = __shfl_down_sync(FULL, g0.ay.x, 1);
+      const float gn_ey = __shfl_down_sync(FULL, g0.ey.x, 1);
+      FSideP l, r;
+      l.e = pfma(Q4, g0.ex, v0.ez); l.hn = pfma(Q4, g0.ax, v0.hx); l.ht = pfma(Q4, g0.bx, v0.hy);
+      l.den = g0.ex; l.dhn = g0.ax; l.dht = g0.bx; l.dat = g0.ay; l.det = g0.ey;
+      l.eps = v0.eps;
+      r.den = pk(g0.ex.y, gn_ex); r.dhn = pk(g0.ax.y, gn_ax); r.dht = pk(g0.bx.y, gn_bx);
+      r.dat = pk(g0.ay.y, gn_ay); r.det = pk(g0.ey.y, gn_ey);
+      r.e = pfma(MQ4, r.den, pk(v0.ez.y, r0[0]));
+      r.hn = pfma(MQ4, r.dhn, pk(v0.hx.y, r0[1]));
+      r.ht = pfma(MQ4, r.dht, pk(v0.hy.y, r0[2]));
+      r.eps = pk(v0.eps.y, nb_eps);
+      face_flux_p(l, r, P.fx, fxE, fxHx, fxHy);
+      if (xhi_nr) {
+        if (X == p.nx - 1) {            // first face on the high-x boundary
+          const Side<float> q = xside_scalar<float>(col_of_p(v0, 0), grad_of_p(g0, 0), q4,
+                                                    p.inv2hx, p.inv2hy);
+          tm_face_flux<float, true>(q, q, p.Kx, fxE.x, fxHx.x, fxHy.x);
+        }
+        if (X + 1 == p.nx - 1) {        // second face on the high-x boundary
+          const Side<float> q = xside_scalar<float>(col_of_p(v0, 1), grad_of_p(g0, 1), q4,
+                                                    p.inv2hx, p.inv2hy);
+          tm_face_flux<float, true>(q, q, p.Kx, fxE.y, fxHx.y, fxHy.y);
+        }
+      }
+      if (xlo_nr && X == -2) {          // second face is the low-x boundary face of column 0
+        RowV<float> nb;
+        nb.ez = r0[0]; nb.hx = r0[1]; nb.hy = r0[2]; nb.eps = nb_eps; nb.mu = 1.f;
+        RowG<float> gn;
+        gn.ex = gn_ex; gn.ax = gn_ax; gn.bx = gn_bx; gn.ay = gn_ay; gn.ey = gn_ey; gn.by = 0.f;
+        low_boundary_flux<float>(xside_scalar<float>(nb, gn, mq4, p.inv2hx, p.inv2hy), p.Kx,
+                                 fxE.y, fxHx.y, fxHy.y);
+      }
+    }
+    // y-faces between rows j and j+1
+    f2 ftE, ftHx, ftHy;
+    face_flux_p(yside(v0, g0, Q4), yside(v1, g1, MQ4), P.fy, ftE, ftHy, ftHx);
+    if (j + 1 == p.ny && yhi_nr) {
+      float e[2], hx[2], hy[2];
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const Side<float> q = yside_scalar<float>(col_of_p(v0, k), grad_of_p(g0, k), q4,
+                                                  p.inv2hx, p.inv2hy);
+        float oe, oa, ob;
+        tm_face_flux<float, true>(q, q, p.Ky, oe, oa, ob);
+        e[k] = oe; hx[k] = -ob; hy[k] = oa;
+      }
+      ftE = pk(e[0], e[1]); ftHx = pk(hx[0], hx[1]); ftHy = pk(hy[0], hy[1]);
+    }
+    // update row j: left face of column X is the previous lane's second face
+    {
+      const float lE = __shfl_up_sync(FULL, fxE.y, 1);
+      const float lHx = __shfl_up_sync(FULL, fxHx.y, 1);
+      const float lHy = __shfl_up_sync(FULL, fxHy.y, 1);
+      f2 dE = padd(psub(pk(lE, fxE.x), fxE), psub(fbE, ftE));
+      const f2 dHx = padd(psub(pk(lHx, fxHx.x), fxHx), psub(fbHx, ftHx));
+      const f2 dHy = padd(psub(pk(lHy, fxHy.x), fxHy), psub(fbHy, ftHy));
+      const int64_t ro = (int64_t)j * p.pitch;
+      if (p.src && j >= p.sy0 && j < p.sy1) {
+        if (X >= p.sx0 && X < p.sx1) dE.x -= p.src_amp * p.src[ro + X];
+        if (X + 1 >= p.sx0 && X + 1 < p.sx1) dE.y -= p.src_amp * p.src[ro + X + 1];
+      }
+      const f2 ne = pfma(dE, pk(rcp1(v0.eps.x), rcp1(v0.eps.y)), v0.ez);
+      const f2 nhx = padd(v0.hx, dHx);
+      const f2 nhy = padd(v0.hy, dHy);
+      const bool ok0 = X >= x0 && X < xend, ok1 = X + 1 >= x0 && X + 1 < xend;
+      if (ok0 && ok1) {
+        *reinterpret_cast<f2 *>(p.Vout + ro + X) = ne;
+        *reinterpret_cast<f2 *>(p.Vout + p.cstride + ro + X) = nhx;
+        *reinterpret_cast<f2 *>(p.Vout + 2 * p.cstride + ro + X) = nhy;
+        const f2 sum = padd(padd(ne, nhx), nhy);
+        bad |= !(isfinite(sum.x) && isfinite(sum.y));
+      } else {
+        if (ok0) {
+          p.Vout[ro + X] = ne.x;
+          p.Vout[p.cstride + ro + X] = nhx.x;
+          p.Vout[2 * p.cstride + ro + X] = nhy.x;
+          bad |= !(isfinite(ne.x) && isfinite(nhx.x) && isfinite(nhy.x));
+        }
+        if (ok1) {
+          p.Vout[ro + X + 1] = ne.y;
+          p.Vout[p.cstride + ro + X + 1] = nhx.y;
+          p.Vout[2 * p.cstride + ro + X + 1] = nhy.y;
+          bad |= !(isfinite(ne.y) && isfinite(nhx.y) && isfinite(nhy.y));
+        }
+      }
+    }
+    // rotate the register window
+    v0 = v1; v1 = v2; v2 = pf; pf = pf2;
+    if (HAS_PEC) apply_mirror_p(v2);          // the prefetched row takes its mirror signs now
+    g0 = g1;
+    fbE = ftE; fbHx = ftHx; fbHy = ftHy;
+    r0[0] = r1[0]; r0[1] = r1[1]; r0[2] = r1[2];
   }
   if (__any_sync(FULL, bad) && lane == 0) atomicOr(p.flag, 1);
 }
