@@ -215,3 +215,29 @@ def test_design_below_lattice_speed_rejected():
     with pytest.raises(ValueError):
         prob.forward(e)
     prob.close()
+
+
+def test_reset_objective():
+    """gks_reset_objective needs an objective (GKS_E_STATE before gks_set_objective) and sets the
+    accumulated J back to zero; a run restarted from a stored state then repeats J exactly."""
+    import torch
+    from paper_2412_16845_gb300.gks import (GksError, gks_copy_state, gks_load_state,
+                                            gks_objective, gks_reset_objective,
+                                            gks_set_objective, gks_state_layout)
+    w = _design_workload()
+    s = GKSSolver.from_workload(w, precision="fp64")
+    with pytest.raises(GksError):
+        gks_reset_objective(s.ctx)
+    gks_set_objective(s.ctx, w.probe, w.design)
+    n, _ = gks_state_layout(s.ctx)
+    v0 = torch.empty(n, dtype=torch.float64, device="cuda")
+    gks_copy_state(s.ctx, v0.data_ptr())
+    s.step(10)
+    J1 = gks_objective(s.ctx)
+    assert J1 > 0
+    gks_reset_objective(s.ctx)
+    assert gks_objective(s.ctx) == 0.0
+    gks_load_state(s.ctx, v0.data_ptr(), 0)
+    s.step(10)
+    assert gks_objective(s.ctx) == J1
+    s.close()
