@@ -21,7 +21,7 @@ arXiv 2412.16845), in the paper's order and notation:
 Every step is written per discrete velocity, exactly as the paper states it; no closed form of
 the flux is used here (the tests derive the closed forms independently and compare).
 
-Readings of passages that are silent, garbled or ambiguous (all listed in the design doc):
+Readings of passages that are silent, garbled or ambiguous:
 
 * Materials (the paper has none): V = (E, H) is stored, U = M V with M = diag(eps I, mu I);
   F_j acts on V exactly like the paper's F_j acts on (E, c^2 B); the interface equilibrium uses

@@ -24,7 +24,7 @@ def lib():
     return gks.load_library()
 
 
-def test_header_declares_the_north_star_calls():
+def test_header_declares_the_step_calls():
     names = declared_functions()
     for must in ("gks_create_mesh", "gks_set_materials", "gks_step", "gks_read_fields"):
         assert must in names
