@@ -222,6 +222,7 @@ def main():
     ap.add_argument("--no-err4", dest="err4", action="store_false", default=True)
     ap.add_argument("--no-cleaning", dest="with_cleaning", action="store_false", default=True)
     ap.add_argument("--no-limiter", dest="with_limiter", action="store_false", default=True)
+    ap.add_argument("--no-variants", dest="with_variants", action="store_false", default=True)
     ap.add_argument("--no-adjoint", dest="with_adjoint", action="store_false", default=True)
     ap.add_argument("--n5", type=int, default=2048)
     args = ap.parse_args()
@@ -430,6 +431,33 @@ def main():
         limited = {"workload": f"tm2d_cylinders_{n}_vanleer", "steps_timed": kl,
                    "value_fp32": ncell / (msl * 1e-3) / 1e9, "ms_per_step_fp32": msl}
 
+    # ---------------- boundary and source variants of the 2-D step (FP32, 500 steps each):
+    # PEC walls on all four sides (the cylinder grid as a closed cavity, Sec. 5.5) and the two
+    # oscillating dipoles of Sec. 5.4 on a 2n x n grid
+    variants = None
+    if args.with_variants:
+        variants = {}
+        cases = [("pec_walls", dataclasses.replace(wl.config2_cylinders_tm(n=n, steps=args.steps),
+                                                   bc=("pec",) * 4)),
+                 ("dipole", wl.dipole_tm(n=n // 2, two=True))]
+        for key, wv in cases:
+            sv = GKSSolver.from_workload(wv, precision="fp32", stream=sptr)
+            sv.step(3)
+            sv.sync()
+            kv = min(args.steps, 500)
+            v0e = torch.cuda.Event(enable_timing=True)
+            v1e = torch.cuda.Event(enable_timing=True)
+            v0e.record(stream)
+            sv.step(kv)
+            v1e.record(stream)
+            torch.cuda.synchronize()
+            msv = v0e.elapsed_time(v1e) / kv
+            sv.close()
+            nv = int(np.prod(wv.n))
+            variants[key] = {"workload": wv.name + ("_pec" if key == "pec_walls" else ""),
+                             "grid": list(wv.n), "steps_timed": kv,
+                             "value_fp32": nv / (msv * 1e-3) / 1e9, "ms_per_step_fp32": msv}
+
     # ---------------- divergence cleaning (TM + psi, gamma = 1, CFL 0.4) on the cylinder grid
     cleaning = None
     if args.with_cleaning:
@@ -536,6 +564,7 @@ def main():
             "maxwell3d": three,
             "tets": tets,
             "limiter": limited,
+            "variants": variants,
             "cleaning": cleaning,
             "adjoint": adj,
             "clocks": clocks,
