@@ -264,12 +264,12 @@ __device__ __forceinline__ void stage(Smem3<T, NC> &s, int slot, int py, int px,
 // Slope of one component along an axis from the values below (vm), at (v0) and above (vp) the
 // cell: the central difference, or with the limiter van Leer's harmonic mean of the one-sided
 // differences, 0 where they differ in sign (an extremum).  FP32 divides with the fast hardware
-// division (phm_rcp).
+// division (fast_div).
 template <bool LIMIT, typename T>
 __device__ __forceinline__ T slope(T vm, T v0, T vp, T inv2h) {
   if (!LIMIT) return (vp - vm) * inv2h;
   const T a = vp - v0, b = v0 - vm, ab = a * b;
-  return ab > T(0) ? phm_rcp(T(4) * ab, a + b) * inv2h : T(0);
+  return ab > T(0) ? fast_div(T(4) * ab, a + b) * inv2h : T(0);
 }
 
 // Gradient of the thread's cell in plane z: x/y neighbours from the staged plane, z neighbours

@@ -246,8 +246,8 @@ __device__ __forceinline__ void phm_fw(const T v[8], T chi, T gam, T o[8]) {
 // GHOST: the r side is a non-reflecting ghost (no distributions; M_s = M_l).  MU1: mu = 1 on
 // both sides (the sides' mu fields are not read).  The reciprocals 1/eps_s are the fast ones in
 // FP32 (about 1 ulp), as in the Maxwell kernels.
-__device__ __forceinline__ float phm_rcp(float a, float x) { return __fdividef(a, x); }
-__device__ __forceinline__ double phm_rcp(double a, double x) { return a / x; }
+__device__ __forceinline__ float fast_div(float a, float x) { return __fdividef(a, x); }
+__device__ __forceinline__ double fast_div(double a, double x) { return a / x; }
 
 template <typename T, bool GHOST, bool MU1 = false>
 __device__ __forceinline__ void flux3_phm(const Side8<T> &l, const Side8<T> &r, const K3<T> &K,
@@ -260,7 +260,7 @@ __device__ __forceinline__ void flux3_phm(const Side8<T> &l, const Side8<T> &r, 
     ml[c] = c < 3 ? l.eps : (c < 6 ? lmu : T(1));
     mr[c] = GHOST ? T(0) : (c < 3 ? r.eps : (c < 6 ? rmu : T(1)));
   }
-  const T ie = GHOST ? phm_rcp(T(1), l.eps) : phm_rcp(T(2), l.eps + r.eps);
+  const T ie = GHOST ? fast_div(T(1), l.eps) : fast_div(T(2), l.eps + r.eps);
   const T im = MU1 ? T(1) : (GHOST ? T(1) / lmu : T(2) / (lmu + rmu));
 #pragma unroll
   for (int c = 0; c < 8; ++c) ims[c] = c < 3 ? ie : (c < 6 ? im : T(1));
