@@ -133,7 +133,8 @@ gks_status setup_tets(gks_ctx *ctx, const gks_mesh_desc *d) {
   g.nf = h.nf;
   g.pec = d->tet_bc == GKS_BC_PEC;
   // packed step geometry (FP64 values, rounded once to FP32 for FP32 contexts)
-  std::vector<double> fgeo((size_t)h.nf * gks::kTetFaceGeo), cgeo((size_t)h.nt * gks::kTetCellGeo, 0.0);
+  std::vector<double> fgeo((size_t)h.nf * gks::kTetFaceGeo);
+  std::vector<double> cw((size_t)h.nt * gks::kTetCellW), cu((size_t)h.nt * gks::kTetCellU);
   for (int64_t f = 0; f < h.nf; ++f) {
     double *q = &fgeo[(size_t)f * gks::kTetFaceGeo];
     for (int k = 0; k < 9; ++k) q[k] = h.fT[9 * f + k];
@@ -141,28 +142,31 @@ gks_status setup_tets(gks_ctx *ctx, const gks_mesh_desc *d) {
     q[15] = h.farea[f];
   }
   for (int64_t i = 0; i < h.nt; ++i) {
-    double *q = &cgeo[(size_t)i * gks::kTetCellGeo];
-    for (int k = 0; k < 12; ++k) q[k] = h.cw[12 * i + k];
-    for (int k = 0; k < 4; ++k) q[12 + k] = h.csign[4 * i + k];
-    q[16] = h.ivol[i];
+    for (int k = 0; k < 12; ++k) cw[(size_t)i * gks::kTetCellW + k] = h.cw[12 * i + k];
+    for (int k = 0; k < 4; ++k) cu[(size_t)i * gks::kTetCellU + k] = h.csign[4 * i + k] * h.ivol[i];
   }
   if ((s = upload_vec(ctx, h.perm, &g.perm)) != GKS_OK || (s = upload_vec(ctx, h.vol, &g.vol)) != GKS_OK ||
       (s = upload_vec(ctx, h.cnb, &g.cnb)) != GKS_OK || (s = upload_vec(ctx, h.cface, &g.cface)) != GKS_OK ||
       (s = upload_vec(ctx, h.fL, &g.fL)) != GKS_OK || (s = upload_vec(ctx, h.fR, &g.fR)) != GKS_OK)
     return s;
   if (ctx->fp64) {
-    double *fd = nullptr, *cd = nullptr;
+    double *fd = nullptr, *wd = nullptr, *ud = nullptr;
     s = upload_vec(ctx, fgeo, &fd);
     g.fgeo = fd;
-    if (s != GKS_OK || (s = upload_vec(ctx, cgeo, &cd)) != GKS_OK) return s;
-    g.cgeo = cd;
+    if (s != GKS_OK || (s = upload_vec(ctx, cw, &wd)) != GKS_OK) return s;
+    g.cw = wd;
+    if ((s = upload_vec(ctx, cu, &ud)) != GKS_OK) return s;
+    g.cu = ud;
   } else {
-    std::vector<float> f32(fgeo.begin(), fgeo.end()), c32(cgeo.begin(), cgeo.end());
-    float *fd = nullptr, *cd = nullptr;
+    std::vector<float> f32(fgeo.begin(), fgeo.end()), w32(cw.begin(), cw.end()),
+        u32(cu.begin(), cu.end());
+    float *fd = nullptr, *wd = nullptr, *ud = nullptr;
     s = upload_vec(ctx, f32, &fd);
     g.fgeo = fd;
-    if (s != GKS_OK || (s = upload_vec(ctx, c32, &cd)) != GKS_OK) return s;
-    g.cgeo = cd;
+    if (s != GKS_OK || (s = upload_vec(ctx, w32, &wd)) != GKS_OK) return s;
+    g.cw = wd;
+    if ((s = upload_vec(ctx, u32, &ud)) != GKS_OK) return s;
+    g.cu = ud;
     // the pageable host vectors must outlive the copies
     GKS_CUDA(cudaStreamSynchronize(ctx->st));
   }
@@ -755,7 +759,7 @@ void gks_destroy(gks_ctx *ctx) {
   if (!ctx) return;
   const gks::TetDev &t = ctx->tet;
   void *bufs[] = {ctx->V[0], ctx->V[1], ctx->eps, ctx->mu, ctx->src, ctx->flag, ctx->red,
-                  ctx->staging, t.perm, t.vol, t.cnb, t.cface, t.fL, t.fR, t.fgeo, t.cgeo,
+                  ctx->staging, t.perm, t.vol, t.cnb, t.cface, t.fL, t.fR, t.fgeo, t.cw, t.cu,
                   t.Gscratch, t.Fscratch, ctx->probe_off, ctx->probe_w, ctx->probe_box_w,
                   ctx->dslot, ctx->obj};
   for (void *p : bufs)

@@ -71,7 +71,8 @@ void face_frame(const double n[3], double T[9]);
 // geometry is computed in FP64 on the host; the step kernels read it in the context's precision
 // (rounded once on the host for FP32 contexts), packed per face and per cell.
 constexpr int kTetFaceGeo = 16;   // per face: frame rows (n, t, w) 9, x_s - x_L 3, x_s - x_R 3, |l|
-constexpr int kTetCellGeo = 20;   // per cell: n |l| / |Omega| of its 4 faces 12, signs 4, 1/|Omega|, pad 3
+constexpr int kTetCellW = 12;     // per cell, gradient pass: n |l| / |Omega| of its 4 faces
+constexpr int kTetCellU = 4;      // per cell, update pass: sign_k / |Omega| of its 4 faces
 struct TetDev {
   int64_t nt = 0, nf = 0;
   int64_t *perm = nullptr;
@@ -79,7 +80,8 @@ struct TetDev {
   int32_t *cnb = nullptr, *cface = nullptr;
   int32_t *fL = nullptr, *fR = nullptr;
   void *fgeo = nullptr;         // [nf][kTetFaceGeo], context precision
-  void *cgeo = nullptr;         // [nt][kTetCellGeo], context precision
+  void *cw = nullptr;           // [nt][kTetCellW], context precision
+  void *cu = nullptr;           // [nt][kTetCellU], context precision
   void *Gscratch = nullptr;     // [18][nt] gradients
   void *Fscratch = nullptr;     // [6][nf] face fluxes (times dt and |l|)
   int pec = 0;                  // boundary faces are PEC walls (else non-reflecting)

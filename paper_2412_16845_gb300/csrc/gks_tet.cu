@@ -31,7 +31,7 @@ int blocks_for(int64_t n) {
 
 template <typename T>
 __global__ void tet_gradient_kernel(const T *__restrict__ V, const int32_t *__restrict__ cnb,
-                                    const T *__restrict__ cgeo, int64_t nt, int pec,
+                                    const T *__restrict__ cw, int64_t nt, int pec,
                                     T *__restrict__ G) {
   const int64_t i = blockIdx.x * (int64_t)TB + threadIdx.x;
   if (i >= nt) return;
@@ -53,7 +53,7 @@ __global__ void tet_gradient_kernel(const T *__restrict__ V, const int32_t *__re
     } else if (pec) {
       // PEC wall: face value (V + P V)/2 of the mirror ghost P V = (-E + 2 (E.n) n, H - 2 (H.n) n),
       // i.e. the normal part of E and the tangential part of H
-      const T *w = cgeo + kTetCellGeo * i + 3 * k;
+      const T *w = cw + kTetCellW * i + 3 * k;
       const T inv = T(1) / sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
       const T n[3] = {w[0] * inv, w[1] * inv, w[2] * inv};
       const T en = vi[0] * n[0] + vi[1] * n[1] + vi[2] * n[2];
@@ -69,7 +69,7 @@ __global__ void tet_gradient_kernel(const T *__restrict__ V, const int32_t *__re
     }
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      const T w = cgeo[kTetCellGeo * i + 3 * k + a];
+      const T w = cw[kTetCellW * i + 3 * k + a];
 #pragma unroll
       for (int c = 0; c < 6; ++c) g[a][c] += vf[c] * w;
     }
@@ -189,28 +189,37 @@ __global__ void tet_face_kernel(const T *__restrict__ V, const T *__restrict__ G
           area * (Tm[a] * loc[3 * b] + Tm[3 + a] * loc[3 * b + 1] + Tm[6 + a] * loc[3 * b + 2]);
 }
 
+// The four update weights sign_k / |Omega| of a cell: one vector load (FP32) or two (FP64).
+__device__ __forceinline__ void load_cell_u(const float *p, float w[4]) {
+  const float4 v = __ldg(reinterpret_cast<const float4 *>(p));
+  w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
+}
+__device__ __forceinline__ void load_cell_u(const double *p, double w[4]) {
+  const double2 a = __ldg(reinterpret_cast<const double2 *>(p));
+  const double2 b = __ldg(reinterpret_cast<const double2 *>(p) + 1);
+  w[0] = a.x; w[1] = a.y; w[2] = b.x; w[3] = b.y;
+}
+
 template <typename T>
 __global__ void tet_update_kernel(const T *__restrict__ V, T *__restrict__ Vout,
                                   const T *__restrict__ eps, const T *__restrict__ mu,
                                   const T *__restrict__ src, T src_amp,
                                   const int32_t *__restrict__ cface,
-                                  const T *__restrict__ cgeo, const T *__restrict__ F, int64_t nt,
+                                  const T *__restrict__ cu, const T *__restrict__ F, int64_t nt,
                                   int64_t nf,
                                   int *__restrict__ flag) {
   const int64_t i = blockIdx.x * (int64_t)TB + threadIdx.x;
   bool bad = false;
   if (i < nt) {
+    T w[4];
+    load_cell_u(cu + kTetCellU * i, w);
+    const int4 fc = __ldg(reinterpret_cast<const int4 *>(cface) + i);
+    const int32_t fk[4] = {fc.x, fc.y, fc.z, fc.w};
     T d[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const int32_t f = cface[4 * i + k];
-      const T sg = cgeo[kTetCellGeo * i + 12 + k];
+    for (int k = 0; k < 4; ++k)
 #pragma unroll
-      for (int c = 0; c < 6; ++c) d[c] -= sg * F[c * nf + f];
-    }
-    const T iv = cgeo[kTetCellGeo * i + 16];
-#pragma unroll
-    for (int c = 0; c < 6; ++c) d[c] *= iv;
+      for (int c = 0; c < 6; ++c) d[c] -= w[k] * F[c * nf + fk[k]];
     if (src) d[2] -= src_amp * src[i];
     const T ie = trcp(eps[i]);
     const T im = mu ? trcp(mu[i]) : T(1);
@@ -295,8 +304,9 @@ cudaError_t step_t(const TetDev &g, const void *Vin, void *Vout, const void *eps
   const T *V = static_cast<const T *>(Vin);
   T *G = static_cast<T *>(g.Gscratch);
   T *F = static_cast<T *>(g.Fscratch);
-  const T *fgeo = static_cast<const T *>(g.fgeo), *cgeo = static_cast<const T *>(g.cgeo);
-  tet_gradient_kernel<T><<<blocks_for(g.nt), TB, 0, st>>>(V, g.cnb, cgeo, g.nt, g.pec, G);
+  const T *fgeo = static_cast<const T *>(g.fgeo);
+  const T *cw = static_cast<const T *>(g.cw), *cu = static_cast<const T *>(g.cu);
+  tet_gradient_kernel<T><<<blocks_for(g.nt), TB, 0, st>>>(V, g.cnb, cw, g.nt, g.pec, G);
   const K3<T> K = make_k3<T>(C, 1.0, c);     // fluxes carry dt (C_i), areas applied per face
   const F3K<T> FK = make_f3k<T>(C, 1.0, c);
   if (mu)
@@ -308,7 +318,7 @@ cudaError_t step_t(const TetDev &g, const void *Vin, void *Vout, const void *eps
         V, G, static_cast<const T *>(eps), nullptr, g.fL, g.fR, fgeo, g.nt, g.nf, g.pec, K, FK, F);
   tet_update_kernel<T><<<blocks_for(g.nt), TB, 0, st>>>(
       V, static_cast<T *>(Vout), static_cast<const T *>(eps), static_cast<const T *>(mu),
-      static_cast<const T *>(src), T(src_amp), g.cface, cgeo, F, g.nt, g.nf, flag);
+      static_cast<const T *>(src), T(src_amp), g.cface, cu, F, g.nt, g.nf, flag);
   return cudaGetLastError();
 }
 
