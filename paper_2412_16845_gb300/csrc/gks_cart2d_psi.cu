@@ -415,6 +415,358 @@ __global__ void __launch_bounds__(PWARPS * 32) cart2d_psi_step_kernel(const PsiA
   if (__any_sync(PFULL, bad) && lane == 0) atomicOr(p.flag, 1);
 }
 
+// ------------------------------------------------------------------ paired FP32 path
+// As cart2d_step_kernel_p for the Maxwell step: a lane's two x-faces, two y-faces and two cell
+// updates go through the paired FP32 instructions (component x: first face or column, y: the
+// second).  Boundary faces are evaluated by the scalar face_flux_psi and replace their
+// component afterwards.
+using q2 = float2;
+__device__ __forceinline__ q2 qk(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ q2 qadd(q2 a, q2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ q2 qsub(q2 a, q2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ q2 qmul(q2 a, q2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ q2 qfma(q2 a, q2 b, q2 c) { return __ffma2_rn(a, b, c); }
+
+// FaceK and FacePsiK constants as pairs (a14 = a1 + a4; n* negated).
+struct PsiKP {
+  q2 a14, a2, a3, a5, a6, nq2, nq3, q5, b1, c1, c2, c3, c4, c5, c6, g0, nk3, half;
+  q2 pe1, pe2, pa1, pa2, pa3, pa4, pa5, pa6, h0, nh1, pp5, pz1, pz2;
+};
+
+inline PsiKP make_psi_kp(const FaceK<float> &k, const FacePsiK<float> &q) {
+  auto b = [](float v) { return make_float2(v, v); };
+  PsiKP r;
+  r.a14 = b(k.a1 + k.a4); r.a2 = b(k.a2); r.a3 = b(k.a3); r.a5 = b(k.a5); r.a6 = b(k.a6);
+  r.nq2 = b(-k.q2); r.nq3 = b(-k.q3); r.q5 = b(k.q5); r.b1 = b(k.b1);
+  r.c1 = b(k.c1); r.c2 = b(k.c2); r.c3 = b(k.c3); r.c4 = b(k.c4); r.c5 = b(k.c5); r.c6 = b(k.c6);
+  r.g0 = b(k.g0); r.nk3 = b(-k.k3); r.half = b(0.5f);
+  r.pe1 = b(q.pe1); r.pe2 = b(q.pe2); r.pa1 = b(q.pa1); r.pa2 = b(q.pa2); r.pa3 = b(q.pa3);
+  r.pa4 = b(q.pa4); r.pa5 = b(q.pa5); r.pa6 = b(q.pa6); r.h0 = b(q.h0); r.nh1 = b(-q.h1);
+  r.pp5 = b(q.pp5); r.pz1 = b(q.pz1); r.pz2 = b(q.pz2);
+  return r;
+}
+
+// Two face sides (see PSide).
+struct PSideP {
+  q2 e, hn, ht, p, den, dhn, dht, dnp, dat, det, dtp, dtt, eps;
+};
+
+// face_flux_psi<float> of two interior faces at once (ie = 2/(eps_l + eps_r) per face).
+__device__ __forceinline__ void face_flux_psi_p(const PSideP &l, const PSideP &r, const PsiKP &k,
+                                                q2 &fE, q2 &fHn, q2 &fHt, q2 &fP) {
+  const q2 Ue_l = qmul(l.eps, l.e), Ue_r = qmul(r.eps, r.e);
+  const q2 Uxe_l = qmul(l.eps, l.den), Uxe_r = qmul(r.eps, r.den);
+  const q2 S_B = qadd(l.ht, r.ht), D_e = qsub(r.e, l.e);
+  const q2 S_Uxe = qadd(Uxe_l, Uxe_r), D_xB = qsub(r.dht, l.dht);
+  const q2 D_Ue = qsub(Ue_r, Ue_l), D_At = qsub(r.dat, l.dat);
+  const q2 S_Uxa = qadd(l.dhn, r.dhn), D_Ua = qsub(r.hn, l.hn), D_Et = qsub(r.det, l.det);
+  const q2 S_Ue = qadd(Ue_l, Ue_r), D_B = qsub(r.ht, l.ht), S_UxB = qadd(l.dht, r.dht);
+  const q2 D_ex = qsub(r.den, l.den), S_UAt = qadd(l.dat, r.dat), S_e = qadd(l.e, r.e);
+  const q2 se = qadd(l.eps, r.eps);
+  const q2 ie = qk(prcp2(se.x), prcp2(se.y));
+  const q2 g = qfma(k.nk3, ie, k.g0);
+  // Maxwell part (mu = 1)
+  q2 fe = qmul(k.a14, S_B);
+  fe = qfma(k.a2, D_e, fe);
+  fe = qfma(g, qfma(k.a3, D_xB, qmul(k.half, S_Uxe)), fe);
+  fe = qfma(k.nq2, D_Ue, fe);
+  fe = qfma(k.nq3, S_Uxe, fe);
+  fe = qfma(k.a5, D_At, fe);
+  fe = qfma(k.a6, D_xB, fe);
+  q2 fa = qmul(k.q5, S_Uxa);
+  fa = qfma(k.nq2, D_Ua, fa);
+  fa = qfma(k.b1, D_Et, fa);
+  q2 u = qmul(k.c1, S_Ue);
+  u = qfma(k.c2, D_B, u);
+  u = qfma(k.c4, S_UAt, u);
+  q2 fb = qmul(ie, u);
+  fb = qfma(g, qfma(k.c3, D_ex, qmul(k.half, S_UxB)), fb);
+  fb = qfma(k.c5, S_e, fb);
+  fb = qfma(k.nq2, D_B, fb);
+  fb = qfma(k.nq3, S_UxB, fb);
+  fb = qfma(k.c6, D_ex, fb);
+  // gamma terms and psi's own transport
+  const q2 S_p = qadd(l.p, r.p), D_p = qsub(r.p, l.p);
+  const q2 S_np = qadd(l.dnp, r.dnp), D_np = qsub(r.dnp, l.dnp);
+  const q2 S_tp = qadd(l.dtp, r.dtp), D_tp = qsub(r.dtp, l.dtp);
+  const q2 S_tt = qadd(l.dtt, r.dtt), D_tt = qsub(r.dtt, l.dtt);
+  const q2 S_hn = qadd(l.hn, r.hn), D_hn_n = qsub(r.dhn, l.dhn);
+  const q2 H = qfma(k.nh1, ie, k.h0);
+  fe = qfma(k.pe1, S_tp, fe);
+  fe = qfma(k.pe2, D_At, fe);
+  fa = qfma(k.pa1, S_p, fa);
+  fa = qfma(k.pa2, S_Uxa, fa);
+  fa = qfma(k.pa3, S_tt, fa);
+  fa = qfma(k.pa4, D_Ua, fa);
+  fa = qfma(k.pa5, D_np, fa);
+  fa = qfma(k.pa6, D_Et, fa);
+  fb = qfma(H, D_tp, fb);
+  const q2 Edet = qfma(l.eps, l.det, qmul(r.eps, r.det));
+  q2 fp = qmul(k.pa1, S_hn);
+  fp = qfma(k.pa2, S_np, fp);
+  fp = qfma(k.pa4, D_p, fp);
+  fp = qfma(k.pa5, D_hn_n, fp);
+  fp = qfma(H, D_tt, fp);
+  fp = qfma(qmul(k.pp5, ie), Edet, fp);
+  fp = qfma(k.pz1, D_p, fp);
+  fp = qfma(k.pz2, S_np, fp);
+  fE = fe;
+  fHn = fa;
+  fHt = fb;
+  fP = fp;
+}
+
+struct PRowP {
+  q2 ez, hx, hy, ps, eps;
+  bool xm[2], ym;
+};
+struct PGP {
+  q2 ex, ey, ax, ay, bx, by, px, py;
+};
+
+__device__ __forceinline__ void psi_mirror_p(PRowP &v) {
+  if (v.ym | v.xm[0] | v.xm[1]) {
+    if (v.xm[0] != v.ym) v.ez.x = -v.ez.x;
+    if (v.xm[1] != v.ym) v.ez.y = -v.ez.y;
+    if (v.xm[0]) v.hx.x = -v.hx.x;
+    if (v.xm[1]) v.hx.y = -v.hx.y;
+    if (v.ym) { v.hy.x = -v.hy.x; v.hy.y = -v.hy.y; }
+  }
+}
+
+__device__ __forceinline__ PRowP psi_load_p(const PsiArgs<float> &p, int X, int row) {
+  PRowP v;
+  const int r = psi_axis(row, p.ny, p.pery, p.pec[2], p.pec[3], v.ym);
+  v.xm[0] = v.xm[1] = false;
+  const int64_t ro = (int64_t)r * p.pitch;
+  if (X >= 0 && X + 1 < p.nx) {
+    v.ez = __ldg(reinterpret_cast<const q2 *>(p.V + ro + X));
+    v.hx = __ldg(reinterpret_cast<const q2 *>(p.V + p.cstride + ro + X));
+    v.hy = __ldg(reinterpret_cast<const q2 *>(p.V + 2 * p.cstride + ro + X));
+    v.ps = __ldg(reinterpret_cast<const q2 *>(p.V + 3 * p.cstride + ro + X));
+    v.eps = __ldg(reinterpret_cast<const q2 *>(p.eps + ro + X));
+  } else {
+    int64_t o[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) o[k] = ro + psi_axis(X + k, p.nx, p.perx, p.pec[0], p.pec[1], v.xm[k]);
+    v.ez = qk(__ldg(p.V + o[0]), __ldg(p.V + o[1]));
+    v.hx = qk(__ldg(p.V + p.cstride + o[0]), __ldg(p.V + p.cstride + o[1]));
+    v.hy = qk(__ldg(p.V + 2 * p.cstride + o[0]), __ldg(p.V + 2 * p.cstride + o[1]));
+    v.ps = qk(__ldg(p.V + 3 * p.cstride + o[0]), __ldg(p.V + 3 * p.cstride + o[1]));
+    v.eps = qk(__ldg(p.eps + o[0]), __ldg(p.eps + o[1]));
+  }
+  return v;
+}
+
+// Scalar views of one column (for the boundary faces).
+__device__ __forceinline__ PG<float> pg_of(const PGP &g, int k) {
+  PG<float> r;
+  r.ex = k ? g.ex.y : g.ex.x; r.ey = k ? g.ey.y : g.ey.x; r.ax = k ? g.ax.y : g.ax.x;
+  r.ay = k ? g.ay.y : g.ay.x; r.bx = k ? g.bx.y : g.bx.x; r.by = k ? g.by.y : g.by.x;
+  r.px = k ? g.px.y : g.px.x; r.py = k ? g.py.y : g.py.x;
+  return r;
+}
+#define GKS_COL(v, f, k) ((k) ? (v).f.y : (v).f.x)
+
+template <bool LIMIT>
+__device__ __forceinline__ void psi_diffs_p(const PRowP &c, const PRowP &dn, const PRowP &up,
+                                            PGP &g, float right[4]) {
+  const float lE = __shfl_up_sync(PFULL, c.ez.y, 1), rE = __shfl_down_sync(PFULL, c.ez.x, 1);
+  const float lA = __shfl_up_sync(PFULL, c.hx.y, 1), rA = __shfl_down_sync(PFULL, c.hx.x, 1);
+  const float lB = __shfl_up_sync(PFULL, c.hy.y, 1), rB = __shfl_down_sync(PFULL, c.hy.x, 1);
+  const float lP = __shfl_up_sync(PFULL, c.ps.y, 1), rP = __shfl_down_sync(PFULL, c.ps.x, 1);
+  if (LIMIT) {
+    g.ex = qk(raw_slope<true>(lE, c.ez.x, c.ez.y), raw_slope<true>(c.ez.x, c.ez.y, rE));
+    g.ax = qk(raw_slope<true>(lA, c.hx.x, c.hx.y), raw_slope<true>(c.hx.x, c.hx.y, rA));
+    g.bx = qk(raw_slope<true>(lB, c.hy.x, c.hy.y), raw_slope<true>(c.hy.x, c.hy.y, rB));
+    g.px = qk(raw_slope<true>(lP, c.ps.x, c.ps.y), raw_slope<true>(c.ps.x, c.ps.y, rP));
+    g.ey = qk(raw_slope<true>(dn.ez.x, c.ez.x, up.ez.x), raw_slope<true>(dn.ez.y, c.ez.y, up.ez.y));
+    g.ay = qk(raw_slope<true>(dn.hx.x, c.hx.x, up.hx.x), raw_slope<true>(dn.hx.y, c.hx.y, up.hx.y));
+    g.by = qk(raw_slope<true>(dn.hy.x, c.hy.x, up.hy.x), raw_slope<true>(dn.hy.y, c.hy.y, up.hy.y));
+    g.py = qk(raw_slope<true>(dn.ps.x, c.ps.x, up.ps.x), raw_slope<true>(dn.ps.y, c.ps.y, up.ps.y));
+  } else {
+    g.ex = qsub(qk(c.ez.y, rE), qk(lE, c.ez.x));
+    g.ax = qsub(qk(c.hx.y, rA), qk(lA, c.hx.x));
+    g.bx = qsub(qk(c.hy.y, rB), qk(lB, c.hy.x));
+    g.px = qsub(qk(c.ps.y, rP), qk(lP, c.ps.x));
+    g.ey = qsub(up.ez, dn.ez);
+    g.ay = qsub(up.hx, dn.hx);
+    g.by = qsub(up.hy, dn.hy);
+    g.py = qsub(up.ps, dn.ps);
+  }
+  right[0] = rE; right[1] = rA; right[2] = rB; right[3] = rP;
+}
+
+// y-face sides of the two columns (normal y: hn = Hy, ht = Hx, tangent x).
+__device__ __forceinline__ PSideP psi_yside_p(const PRowP &v, const PGP &g, q2 sgn) {
+  PSideP s;
+  s.e = qfma(sgn, g.ey, v.ez); s.hn = qfma(sgn, g.by, v.hy); s.ht = qfma(sgn, g.ay, v.hx);
+  s.p = qfma(sgn, g.py, v.ps);
+  s.den = g.ey; s.dhn = g.by; s.dht = g.ay; s.dnp = g.py;
+  s.dat = g.bx; s.det = g.ex; s.dtp = g.px; s.dtt = g.ax;
+  s.eps = v.eps;
+  return s;
+}
+
+struct PsiPackArgs {
+  PsiArgs<float> b;
+  PsiKP kx, ky;
+};
+
+template <bool HAS_PEC, bool LIMIT>
+__global__ void __launch_bounds__(PWARPS * 32) cart2d_psi_step_kernel_p(const PsiPackArgs P,
+                                                                        int nstrips, int rows) {
+  const PsiArgs<float> &p = P.b;
+  const int lane = threadIdx.x & 31;
+  const int wid = blockIdx.x * PWARPS + (threadIdx.x >> 5);
+  const int strip = wid % nstrips, chunk = wid / nstrips;
+  const int y0 = chunk * rows;
+  if (y0 >= p.ny) return;                             // whole warp leaves together
+  const int y1 = min(y0 + rows, p.ny);
+  const int x0 = strip * PCOLS;
+  const int X = x0 - 2 + 2 * lane;
+  const int xend = min(x0 + PCOLS, p.nx);
+  const bool xlo_nr = !p.perx && !p.pec[0], xhi_nr = !p.perx && !p.pec[1];
+  const bool ylo_nr = !p.pery && !p.pec[2], yhi_nr = !p.pery && !p.pec[3];
+  const float q4 = 0.25f, mq4 = -0.25f;
+  const q2 Q4 = qk(q4, q4), MQ4 = qk(mq4, mq4);
+
+  PRowP vm2 = psi_load_p(p, X, y0 - 2), vm1 = psi_load_p(p, X, y0 - 1), v0 = psi_load_p(p, X, y0);
+  PRowP v1 = psi_load_p(p, X, y0 + 1), v2 = psi_load_p(p, X, y0 + 2), pf = psi_load_p(p, X, y0 + 3);
+  if (HAS_PEC) {
+    psi_mirror_p(vm2); psi_mirror_p(vm1); psi_mirror_p(v0); psi_mirror_p(v1); psi_mirror_p(v2);
+  }
+  PGP g0, gm1;
+  float r0[4], rm1[4];
+  psi_diffs_p<LIMIT>(vm1, vm2, v0, gm1, rm1);
+  psi_diffs_p<LIMIT>(v0, vm1, v1, g0, r0);
+  q2 fbE, fbHx, fbHy, fbP;                            // flux along +y below row j
+  face_flux_psi_p(psi_yside_p(vm1, gm1, Q4), psi_yside_p(v0, g0, MQ4), P.ky, fbE, fbHy, fbHx, fbP);
+  if (y0 == 0 && ylo_nr) {
+    float e[2], hx[2], hy[2], ps[2];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const PSide<float> up = psi_yside<float>(GKS_COL(v0, ez, k), GKS_COL(v0, hx, k),
+                                               GKS_COL(v0, hy, k), GKS_COL(v0, ps, k),
+                                               GKS_COL(v0, eps, k), pg_of(g0, k), mq4);
+      face_flux_psi<float>(psi_zero<float>(), up, p.fy, p.qy, prcp1(GKS_COL(v0, eps, k)), e[k],
+                           hy[k], hx[k], ps[k]);
+    }
+    fbE = qk(e[0], e[1]); fbHx = qk(hx[0], hx[1]); fbHy = qk(hy[0], hy[1]); fbP = qk(ps[0], ps[1]);
+  }
+  bool bad = false;
+#pragma unroll 1
+  for (int j = y0; j < y1; ++j) {
+    const PRowP pf2 = psi_load_p(p, X, j + 4);
+    PGP g1;
+    float r1[4];
+    psi_diffs_p<LIMIT>(v1, v0, v2, g1, r1);
+    // x-faces X+1/2 (component x) and X+3/2 (component y; column X+2 from the next lane)
+    q2 fxE, fxHx, fxHy, fxP;
+    {
+      const float ne = __shfl_down_sync(PFULL, v0.eps.x, 1);
+      PG<float> gn;
+      gn.ex = __shfl_down_sync(PFULL, g0.ex.x, 1);
+      gn.ax = __shfl_down_sync(PFULL, g0.ax.x, 1);
+      gn.bx = __shfl_down_sync(PFULL, g0.bx.x, 1);
+      gn.px = __shfl_down_sync(PFULL, g0.px.x, 1);
+      gn.ay = __shfl_down_sync(PFULL, g0.ay.x, 1);
+      gn.ey = __shfl_down_sync(PFULL, g0.ey.x, 1);
+      gn.by = __shfl_down_sync(PFULL, g0.by.x, 1);
+      gn.py = __shfl_down_sync(PFULL, g0.py.x, 1);
+      PSideP l, r;
+      l.e = qfma(Q4, g0.ex, v0.ez); l.hn = qfma(Q4, g0.ax, v0.hx); l.ht = qfma(Q4, g0.bx, v0.hy);
+      l.p = qfma(Q4, g0.px, v0.ps);
+      l.den = g0.ex; l.dhn = g0.ax; l.dht = g0.bx; l.dnp = g0.px;
+      l.dat = g0.ay; l.det = g0.ey; l.dtp = g0.py; l.dtt = g0.by;
+      l.eps = v0.eps;
+      r.den = qk(g0.ex.y, gn.ex); r.dhn = qk(g0.ax.y, gn.ax); r.dht = qk(g0.bx.y, gn.bx);
+      r.dnp = qk(g0.px.y, gn.px); r.dat = qk(g0.ay.y, gn.ay); r.det = qk(g0.ey.y, gn.ey);
+      r.dtp = qk(g0.py.y, gn.py); r.dtt = qk(g0.by.y, gn.by);
+      r.e = qfma(MQ4, r.den, qk(v0.ez.y, r0[0]));
+      r.hn = qfma(MQ4, r.dhn, qk(v0.hx.y, r0[1]));
+      r.ht = qfma(MQ4, r.dht, qk(v0.hy.y, r0[2]));
+      r.p = qfma(MQ4, r.dnp, qk(v0.ps.y, r0[3]));
+      r.eps = qk(v0.eps.y, ne);
+      face_flux_psi_p(l, r, P.kx, fxE, fxHx, fxHy, fxP);
+      // boundary faces replace their component (rare, divergent)
+      if (xhi_nr && X == p.nx - 1) {
+        const PSide<float> l0 = psi_xside<float>(v0.ez.x, v0.hx.x, v0.hy.x, v0.ps.x, v0.eps.x,
+                                                 pg_of(g0, 0), q4);
+        face_flux_psi<float>(l0, psi_zero<float>(), p.fx, p.qx, prcp1(v0.eps.x), fxE.x, fxHx.x,
+                             fxHy.x, fxP.x);
+      }
+      if (xhi_nr && X + 1 == p.nx - 1) {
+        const PSide<float> l1 = psi_xside<float>(v0.ez.y, v0.hx.y, v0.hy.y, v0.ps.y, v0.eps.y,
+                                                 pg_of(g0, 1), q4);
+        face_flux_psi<float>(l1, psi_zero<float>(), p.fx, p.qx, prcp1(v0.eps.y), fxE.y, fxHx.y,
+                             fxHy.y, fxP.y);
+      } else if (xlo_nr && X == -2) {
+        const PSide<float> rn = psi_xside<float>(r0[0], r0[1], r0[2], r0[3], ne, gn, mq4);
+        face_flux_psi<float>(psi_zero<float>(), rn, p.fx, p.qx, prcp1(ne), fxE.y, fxHx.y,
+                             fxHy.y, fxP.y);
+      }
+    }
+    // y-faces j+1/2
+    q2 ftE, ftHx, ftHy, ftP;
+    face_flux_psi_p(psi_yside_p(v0, g0, Q4), psi_yside_p(v1, g1, MQ4), P.ky, ftE, ftHy, ftHx, ftP);
+    if (j + 1 == p.ny && yhi_nr) {
+      float e[2], hx[2], hy[2], ps[2];
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const PSide<float> lo = psi_yside<float>(GKS_COL(v0, ez, k), GKS_COL(v0, hx, k),
+                                                 GKS_COL(v0, hy, k), GKS_COL(v0, ps, k),
+                                                 GKS_COL(v0, eps, k), pg_of(g0, k), q4);
+        face_flux_psi<float>(lo, psi_zero<float>(), p.fy, p.qy, prcp1(GKS_COL(v0, eps, k)), e[k],
+                             hy[k], hx[k], ps[k]);
+      }
+      ftE = qk(e[0], e[1]); ftHx = qk(hx[0], hx[1]); ftHy = qk(hy[0], hy[1]);
+      ftP = qk(ps[0], ps[1]);
+    }
+    // update row j
+    {
+      const float lE = __shfl_up_sync(PFULL, fxE.y, 1), lHx = __shfl_up_sync(PFULL, fxHx.y, 1);
+      const float lHy = __shfl_up_sync(PFULL, fxHy.y, 1), lP = __shfl_up_sync(PFULL, fxP.y, 1);
+      q2 dE = qadd(qsub(qk(lE, fxE.x), fxE), qsub(fbE, ftE));
+      const q2 dHx = qadd(qsub(qk(lHx, fxHx.x), fxHx), qsub(fbHx, ftHx));
+      const q2 dHy = qadd(qsub(qk(lHy, fxHy.x), fxHy), qsub(fbHy, ftHy));
+      const q2 dP = qadd(qsub(qk(lP, fxP.x), fxP), qsub(fbP, ftP));
+      const int64_t ro = (int64_t)j * p.pitch;
+      if (p.src && j >= p.sy0 && j < p.sy1) {
+        if (X >= p.sx0 && X < p.sx1) dE.x -= p.src_amp * p.src[ro + X];
+        if (X + 1 >= p.sx0 && X + 1 < p.sx1) dE.y -= p.src_amp * p.src[ro + X + 1];
+      }
+      const q2 out[4] = {qfma(dE, qk(prcp1(v0.eps.x), prcp1(v0.eps.y)), v0.ez), qadd(v0.hx, dHx),
+                         qadd(v0.hy, dHy), qadd(v0.ps, dP)};
+      const bool ok0 = X >= x0 && X < xend, ok1 = X + 1 >= x0 && X + 1 < xend;
+      if (ok0 && ok1) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) *reinterpret_cast<q2 *>(p.Vout + c * p.cstride + ro + X) = out[c];
+        const q2 sum = qadd(qadd(out[0], out[1]), qadd(out[2], out[3]));
+        bad |= !(isfinite(sum.x) && isfinite(sum.y));
+      } else {
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+          if (k == 0 ? ok0 : ok1)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              const float v = k ? out[c].y : out[c].x;
+              p.Vout[c * p.cstride + ro + X + k] = v;
+              bad |= !isfinite(v);
+            }
+      }
+    }
+    v0 = v1; v1 = v2; v2 = pf; pf = pf2;
+    if (HAS_PEC) psi_mirror_p(v2);
+    g0 = g1;
+    fbE = ftE; fbHx = ftHx; fbHy = ftHy; fbP = ftP;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) r0[c] = r1[c];
+  }
+  if (__any_sync(PFULL, bad) && lane == 0) atomicOr(p.flag, 1);
+}
+#undef GKS_COL
+
 template <typename T>
 cudaError_t launch_psi_t(const CartGeom &g, const CartStepArgs &a, double gamma,
                          cudaStream_t st) {
@@ -447,6 +799,19 @@ cudaError_t launch_psi_t(const CartGeom &g, const CartStepArgs &a, double gamma,
   const int64_t nwarps = (int64_t)nstrips * nchunks;
   const int grid = (int)((nwarps + PWARPS - 1) / PWARPS);
   const bool pec = g.pec[0] || g.pec[1] || g.pec[2] || g.pec[3];
+  if constexpr (sizeof(T) == 4) {      // FP32: the paired-instruction kernel
+    PsiPackArgs P;
+    P.b = p;
+    P.kx = make_psi_kp(p.fx, p.qx);
+    P.ky = make_psi_kp(p.fy, p.qy);
+    using KP = void (*)(const PsiPackArgs, int, int);
+    static const KP kp[2][2] = {{cart2d_psi_step_kernel_p<false, false>,
+                                 cart2d_psi_step_kernel_p<false, true>},
+                                {cart2d_psi_step_kernel_p<true, false>,
+                                 cart2d_psi_step_kernel_p<true, true>}};   // [pec][limiter]
+    kp[pec ? 1 : 0][a.limiter ? 1 : 0]<<<grid, PWARPS * 32, 0, st>>>(P, nstrips, rows);
+    return cudaGetLastError();
+  }
   using K = void (*)(const PsiArgs<T>, int, int);
   static const K kern[2][2] = {{cart2d_psi_step_kernel<T, false, false>,
                                 cart2d_psi_step_kernel<T, false, true>},
