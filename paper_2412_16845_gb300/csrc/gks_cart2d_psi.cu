@@ -613,8 +613,10 @@ struct PsiPackArgs {
   PsiKP kx, ky;
 };
 
+// Three CTAs per SM (registers capped at 170, a few spills): uncapped the kernel takes 188
+// registers and runs two CTAs per SM, 18% slower.
 template <bool HAS_PEC, bool LIMIT>
-__global__ void __launch_bounds__(PWARPS * 32) cart2d_psi_step_kernel_p(const PsiPackArgs P,
+__global__ void __launch_bounds__(PWARPS * 32, 3) cart2d_psi_step_kernel_p(const PsiPackArgs P,
                                                                         int nstrips, int rows) {
   const PsiArgs<float> &p = P.b;
   const int lane = threadIdx.x & 31;
