@@ -801,8 +801,9 @@ def test_phm_equilibrium_compatibility(dim):
                                atol=1e-13, rtol=0)
 
 
-def _cleaning_wave_error(n, dim, speed):
-    """Standing cleaning wave along x: 2-D (H_x, psi) with gamma, 3-D (E_x, phi) with chi.
+def _cleaning_wave_error(n, dim, speed, potential=None):
+    """Standing cleaning wave along x: 2-D (H_x, psi) with gamma, 3-D (E_x, phi) with chi, or in
+    3-D with potential="psi" (H_x, psi) with gamma.
     Initial H_x (E_x) = sin(2 pi x); exact H_x = sin(2 pi x) cos(2 pi s t),
     psi = -cos(2 pi x) sin(2 pi s t) (s the cleaning speed)."""
     shape = (n, 4) if dim == 2 else (n, 2, 2)
@@ -814,6 +815,10 @@ def _cleaning_wave_error(n, dim, speed):
         f = np.zeros((4, mesh.ncell))
         f[1] = np.sin(2 * np.pi * x)                 # H_x
         phm, a, b = (0.0, speed), 1, 3
+    elif potential == "psi":
+        f = np.zeros((8, mesh.ncell))
+        f[3] = np.sin(2 * np.pi * x)                 # H_x
+        phm, a, b = (0.0, speed), 3, 7
     else:
         f = np.zeros((8, mesh.ncell))
         f[0] = np.sin(2 * np.pi * x)                 # E_x
@@ -830,13 +835,14 @@ def _cleaning_wave_error(n, dim, speed):
     return math.sqrt(np.mean(ea ** 2 + eb ** 2)), np.max(np.abs(others))
 
 
-@pytest.mark.parametrize("dim,speed", [(2, 0.5), (2, 1.0), (3, 0.7)])
-def test_cleaning_wave_second_order(dim, speed):
+@pytest.mark.parametrize("dim,speed,potential", [(2, 0.5, None), (2, 1.0, None), (3, 0.7, None),
+                                                 (3, 0.6, "psi")])
+def test_cleaning_wave_second_order(dim, speed, potential):
     """Sec. 2.1: the cleaning potentials carry divergence errors as waves of speed gamma (psi,
     with div B) or chi (phi, with div E).  The 1-D standing wave converges at second order and
     leaves the other components at zero."""
-    e1, o1 = _cleaning_wave_error(32, dim, speed)
-    e2, o2 = _cleaning_wave_error(64, dim, speed)
+    e1, o1 = _cleaning_wave_error(32, dim, speed, potential)
+    e2, o2 = _cleaning_wave_error(64, dim, speed, potential)
     assert math.log2(e1 / e2) >= 1.8, (e1, e2)
     assert e2 <= 2e-3
     assert max(o1, o2) <= 1e-13
