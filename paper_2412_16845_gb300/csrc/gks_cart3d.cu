@@ -134,8 +134,8 @@ __device__ __forceinline__ void face_flux(const Side8<T> &l, const Side8<T> &r, 
 // without mu uses the sums-and-differences form flux3_mu1.
 template <typename T, typename F, bool HAS_MU, int NC>
 __device__ __forceinline__ void interior_face(const Cell3<T, NC> &L, const Cell3<T, NC> &R,
-                                              T halfh, const K3<T> &K, const F3K<T> &FK, T chi,
-                                              T gam, T phi[NC]) {
+                                              T halfh, const K3<T> &K, const F3K<T> &FK,
+                                              const F8K<T> &K8, T phi[NC]) {
   T loc[NC];
   if constexpr (NC == 6) {
     if (HAS_MU)
@@ -144,8 +144,8 @@ __device__ __forceinline__ void interior_face(const Cell3<T, NC> &L, const Cell3
       flux3_mu1<T>(to_local<T, F>(L, halfh), to_local<T, F>(R, -halfh), FK,
                    rcp3x2(L.eps + R.eps), loc);
   } else {
-    flux3_phm<T, false, true>(to_local<T, F>(L, halfh), to_local<T, F>(R, -halfh), K, chi, gam,
-                              loc);
+    flux3_phm_mu1<T>(to_local<T, F>(L, halfh), to_local<T, F>(R, -halfh), K8, rcp3x2(L.eps + R.eps),
+                     loc);
   }
   to_global<T, F, NC>(loc, phi);
 }
@@ -189,6 +189,7 @@ struct Cart3DArgs {
   T inv2h[3], halfh[3];
   K3<T> K[3];
   F3K<T> FK[3];
+  F8K<T> K8[3];        // folded cleaning-flux constants (NC = 8)
   T chi, gam;          // cleaning speeds (NC = 8)
   int zchunk;
   int *flag;
@@ -382,8 +383,8 @@ __global__ void __launch_bounds__(Geo3<T, NC>::NTH, 1)
     if (z0 == 0 && zlo_nr)
       low_boundary_face<T, FrameZm, NC>(c0, p.halfh[2], p.K[2], p.chi, p.gam, fzb);
     else
-      interior_face<T, FrameZp, HAS_MU, NC>(cm1, c0, p.halfh[2], p.K[2], p.FK[2], p.chi, p.gam,
-                                            fzb);
+      interior_face<T, FrameZp, HAS_MU, NC>(cm1, c0, p.halfh[2], p.K[2], p.FK[2],
+                                            p.K8[2], fzb);
     const int gs = z0 & 1;
 #pragma unroll
     for (int a = 0; a < 3; ++a)
@@ -457,8 +458,8 @@ __global__ void __launch_bounds__(Geo3<T, NC>::NTH, 1)
         if (xlo)
           low_boundary_face<T, FrameXm, NC>(cr, p.halfh[0], p.K[0], p.chi, p.gam, fx);
         else
-          interior_face<T, FrameXp, HAS_MU, NC>(c0, cr, p.halfh[0], p.K[0], p.FK[0], p.chi,
-                                                p.gam, fx);
+          interior_face<T, FrameXp, HAS_MU, NC>(c0, cr, p.halfh[0], p.K[0], p.FK[0],
+                                                p.K8[0], fx);
       }
     }
     if (need_yface) {
@@ -472,8 +473,8 @@ __global__ void __launch_bounds__(Geo3<T, NC>::NTH, 1)
         if (ylo)
           low_boundary_face<T, FrameYm, NC>(cu, p.halfh[1], p.K[1], p.chi, p.gam, fy);
         else
-          interior_face<T, FrameYp, HAS_MU, NC>(c0, cu, p.halfh[1], p.K[1], p.FK[1], p.chi,
-                                                p.gam, fy);
+          interior_face<T, FrameYp, HAS_MU, NC>(c0, cu, p.halfh[1], p.K[1], p.FK[1],
+                                                p.K8[1], fy);
       }
     }
     if (inner) {
@@ -482,8 +483,8 @@ __global__ void __launch_bounds__(Geo3<T, NC>::NTH, 1)
       } else {
         Cell3<T, NC> c1;
         cell_from<T, NC>(s, s1, ty + 1, tx + 1, g1, c1);
-        interior_face<T, FrameZp, HAS_MU, NC>(c0, c1, p.halfh[2], p.K[2], p.FK[2], p.chi, p.gam,
-                                              fzt);
+        interior_face<T, FrameZp, HAS_MU, NC>(c0, c1, p.halfh[2], p.K[2], p.FK[2],
+                                              p.K8[2], fzt);
       }
     } else {
 #pragma unroll
@@ -544,6 +545,7 @@ cudaError_t launch3_t(const CartGeom &g, const CartStepArgs &a, double chi, doub
     p.halfh[d] = T(0.5 * g.h[d]);
     p.K[d] = make_k3<T>(a.C, g.h[d], a.c);
     p.FK[d] = make_f3k<T>(a.C, g.h[d], a.c);
+    p.K8[d] = make_f8k<T>(a.C, g.h[d], a.c, chi, gamma);
   }
   p.chi = T(chi);
   p.gam = T(gamma);
