@@ -8,7 +8,8 @@ calls it, and it shares no code, tables or helpers with the CUDA path.
 What it computes (paper: Pu, Long & Xu, "A Gas-Kinetic Scheme for Maxwell Equations",
 arXiv 2412.16845), in the paper's order and notation:
 
-* Sec. 2.1: the flux functions F_j(U) = A_j U of the Maxwell system with chi = gamma = 0.
+* Sec. 2.1: the flux functions F_j(U) = A_j U of the Maxwell system, and of the
+  divergence-cleaning (PHM) system with potentials phi, psi and speeds chi, gamma.
 * Sec. 2.2: the D3Q4 lattice (D2Q4 in 2-D) and the local equilibrium
   g_k = U/4 + F(U).u_k / (4 c^2), with the compatibility constraints sum g = U, sum u^j g = F_j.
 * Sec. 3.1: the finite-volume update U^{n+1} = U^n - dt/|Omega| sum |l_s| F_s + dt S^n, the
@@ -17,6 +18,8 @@ arXiv 2412.16845), in the paper's order and notation:
   derivative from <g_t + u.grad g0> = 0, and the time-integrated flux with C1..C5.
 * Sec. 3.1 (last paragraph): the kinetic non-reflecting boundary (incoming distributions of the
   ghost cell are zero).
+* Sec. 5.5: perfect-electric-conductor walls (mirror ghosts); Sec. 5.4: the time-harmonic dipole
+  current; Sec. 5.3: limited slopes (van Leer, a reading).
 
 Every step is written per discrete velocity, exactly as the paper states it; no closed form of
 the flux is used here (the tests derive the closed forms independently and compare).
