@@ -386,244 +386,6 @@ __global__ void __launch_bounds__(AWARPS * 32) adjoint_lambda_kernel(const AdjAr
   }
 }
 
-// ------------------------------------------------------------------ paired FP32 lambda march
-// FP32: the same march with a lane's two x-faces, its two y-faces and its two cells' sums in
-// pairs through Blackwell's paired FP32 instructions (component x: first face or column,
-// y: the second), as in the forward's cart2d_step_kernel_p.
-using a2 = float2;
-__device__ __forceinline__ a2 ak(float x, float y) { return make_float2(x, y); }
-__device__ __forceinline__ a2 aadd(a2 x, a2 y) { return __fadd2_rn(x, y); }
-__device__ __forceinline__ a2 asub(a2 x, a2 y) { return __ffma2_rn(y, make_float2(-1.f, -1.f), x); }
-__device__ __forceinline__ a2 amul(a2 x, a2 y) { return __fmul2_rn(x, y); }
-__device__ __forceinline__ a2 afma(a2 x, a2 y, a2 z) { return __ffma2_rn(x, y, z); }
-
-// FaceK constants as pairs (a14 = a1 + a4; n* negated).
-struct AdjKP {
-  a2 a14, a2_, a3, a5, a6, nq2, nq3, q5, b1, c1, c2, c3, c4, c5, c6, g0, nk3, half;
-};
-inline AdjKP make_adj_kp(const FaceK<float> &k) {
-  auto b = [](float v) { return make_float2(v, v); };
-  AdjKP q;
-  q.a14 = b(k.a1 + k.a4); q.a2_ = b(k.a2); q.a3 = b(k.a3); q.a5 = b(k.a5); q.a6 = b(k.a6);
-  q.nq2 = b(-k.q2); q.nq3 = b(-k.q3); q.q5 = b(k.q5); q.b1 = b(k.b1);
-  q.c1 = b(k.c1); q.c2 = b(k.c2); q.c3 = b(k.c3); q.c4 = b(k.c4); q.c5 = b(k.c5); q.c6 = b(k.c6);
-  q.g0 = b(k.g0); q.nk3 = b(-k.k3); q.half = b(0.5f);
-  return q;
-}
-
-struct FOutP {
-  a2 v[3];
-  a2 d[5];
-};
-
-// face_adj<float, 0> of two interior faces at once.
-__device__ __forceinline__ void face_adj_p(a2 el, a2 er, const AdjKP &k, a2 fe, a2 fa, a2 fb,
-                                           FOutP &oL, FOutP &oR) {
-  const a2 se = aadd(el, er);
-  const a2 ie = ak(fdv(2.f, se.x), fdv(2.f, se.y));
-  const a2 g = afma(k.nk3, ie, k.g0);
-  const a2 w1 = amul(g, fe);
-  const a2 SUBSB = amul(k.a14, fe), De = amul(k.a2_, fe);
-  const a2 SUxe = afma(k.half, w1, amul(k.nq3, fe)), DxB = afma(k.a3, w1, amul(k.a6, fe));
-  const a2 DUe = amul(k.nq2, fe), DAt = amul(k.a5, fe);
-  const a2 SUxa = amul(k.q5, fa), DUa = amul(k.nq2, fa), DEt = amul(k.b1, fa);
-  const a2 w2 = amul(ie, fb), w3 = amul(g, fb);
-  const a2 SUe = amul(k.c1, w2), DB = afma(k.c2, w2, amul(k.nq2, fb));
-  const a2 SUxB = afma(k.half, w3, amul(k.nq3, fb)), Dex = afma(k.c3, w3, amul(k.c6, fb));
-  const a2 SUAt = amul(amul(k.c4, ie), fb), Se = amul(k.c5, fb);
-  const a2 R4 = ak(0.25f, 0.25f);
-  // side l: differences enter with -1, reconstruction V + d/4
-  {
-    const a2 eb = aadd(asub(Se, De), amul(el, asub(SUe, DUe)));
-    const a2 hnb = asub(ak(0.f, 0.f), DUa);
-    const a2 htb = asub(SUBSB, DB);
-    oL.v[0] = eb; oL.v[1] = hnb; oL.v[2] = htb;
-    oL.d[0] = afma(R4, eb, asub(amul(el, SUxe), Dex));
-    oL.d[1] = afma(R4, hnb, SUxa);
-    oL.d[2] = afma(R4, htb, asub(SUxB, DxB));
-    oL.d[3] = asub(SUAt, DAt);
-    oL.d[4] = asub(ak(0.f, 0.f), DEt);
-  }
-  // side r: +1, V - d/4
-  {
-    const a2 eb = aadd(aadd(De, Se), amul(er, aadd(DUe, SUe)));
-    const a2 hnb = DUa;
-    const a2 htb = aadd(SUBSB, DB);
-    oR.v[0] = eb; oR.v[1] = hnb; oR.v[2] = htb;
-    oR.d[0] = afma(ak(-0.25f, -0.25f), eb, afma(er, SUxe, Dex));
-    oR.d[1] = afma(ak(-0.25f, -0.25f), hnb, SUxa);
-    oR.d[2] = afma(ak(-0.25f, -0.25f), htb, aadd(DxB, SUxB));
-    oR.d[3] = aadd(DAt, SUAt);
-    oR.d[4] = DEt;
-  }
-}
-
-struct ARowP {
-  a2 e, a, b, ep, q;
-};
-
-__device__ __forceinline__ ARowP load_arow_p(const AdjArgs<float> &p, int X, int row) {
-  const ARow<float> r = load_arow<float>(p, X, row);
-  ARowP o;
-  o.e = ak(r.e[0], r.e[1]); o.a = ak(r.a[0], r.a[1]); o.b = ak(r.b[0], r.b[1]);
-  o.ep = ak(r.ep[0], r.ep[1]);
-  return o;
-}
-__device__ __forceinline__ void finish_arow_p(ARowP &r) {
-  r.q = ak(fdv(r.e.x, r.ep.x), fdv(r.e.y, r.ep.y));
-}
-
-// adjoints gathered into the lane's two cells
-struct ACellP {
-  a2 vE, vA, vB, dEx, dEy, dAx, dAy, dBx, dBy;
-};
-__device__ __forceinline__ void add_yface_p(ACellP &c, const FOutP &o) {
-  c.vE = aadd(c.vE, o.v[0]); c.vB = aadd(c.vB, o.v[1]); c.vA = aadd(c.vA, o.v[2]);
-  c.dEy = aadd(c.dEy, o.d[0]); c.dBy = aadd(c.dBy, o.d[1]); c.dAy = aadd(c.dAy, o.d[2]);
-  c.dBx = aadd(c.dBx, o.d[3]); c.dEx = aadd(c.dEx, o.d[4]);
-}
-__device__ __forceinline__ ACellP cell_from_yface_p(const FOutP &o) {
-  ACellP c;
-  c.vE = o.v[0]; c.vB = o.v[1]; c.vA = o.v[2];
-  c.dEy = o.d[0]; c.dBy = o.d[1]; c.dAy = o.d[2]; c.dBx = o.d[3]; c.dEx = o.d[4];
-  c.dAx = ak(0.f, 0.f);
-  return c;
-}
-
-struct AdjPackArgs {
-  AdjArgs<float> b;
-  AdjKP kx, ky;
-};
-
-__global__ void __launch_bounds__(AWARPS * 32) adjoint_lambda_kernel_p(const AdjPackArgs P,
-                                                                       int nstrips, int rows) {
-  const AdjArgs<float> &p = P.b;
-  const int lane = threadIdx.x & 31;
-  const int wid = blockIdx.x * AWARPS + (threadIdx.x >> 5);
-  const int strip = wid % nstrips, chunk = wid / nstrips;
-  const int y0 = chunk * rows;
-  if (y0 >= p.ny) return;                              // whole warp leaves together
-  const int y1 = min(y0 + rows, p.ny);
-  const int x0 = strip * AWCOLS;
-  const int X = x0 - 2 + 2 * lane;
-  const int xend = min(x0 + AWCOLS, p.nx);
-  // D_x^T weights of the lane's two columns (see adjoint_lambda_kernel)
-  float cl[2], cr[2], cs[2];
-#pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    const int i = X + k;
-    cl[k] = p.perx || i - 1 >= 0 ? 1.f : 0.f;
-    cr[k] = p.perx || i + 1 < p.nx ? 1.f : 0.f;
-    cs[k] = p.perx ? 0.f : float((i == p.nx - 1 ? 1 : 0) - (i == 0 ? 1 : 0));
-  }
-  const a2 CL = ak(cl[0], cl[1]), NCR = ak(-cr[0], -cr[1]), CS = ak(cs[0], cs[1]);
-
-  ARowP cur = load_arow_p(p, X, y0 - 1);
-  ARowP nxt = load_arow_p(p, X, y0);
-  ARowP pf = load_arow_p(p, X, y0 + 1);
-  ACellP A;                                            // row j, bottom y-face gathered
-  {
-    ARowP rm = load_arow_p(p, X, y0 - 2);
-    finish_arow_p(rm);
-    finish_arow_p(cur);
-    FOutP oL, oR;
-    face_adj_p(rm.ep, cur.ep, P.ky, asub(cur.q, rm.q), asub(cur.b, rm.b), asub(cur.a, rm.a), oL,
-               oR);
-    A = cell_from_yface_p(oR);
-  }
-  finish_arow_p(nxt);
-  a2 pend[3], carry[3];                                // row j-1 output so far; +dbar_y of j-1
-#pragma unroll
-  for (int c = 0; c < 3; ++c) { pend[c] = ak(0.f, 0.f); carry[c] = ak(0.f, 0.f); }
-
-#pragma unroll 1
-  for (int j = y0 - 1; j <= y1; ++j) {
-    const ARowP pf2 = load_arow_p(p, X, j + 3);
-    // x-faces of row j: X+1/2 (component x) and X+3/2 (component y; column X+2 from the next
-    // lane)
-    {
-      const float nq = __shfl_down_sync(AFULL, cur.q.x, 1), na = __shfl_down_sync(AFULL, cur.a.x, 1);
-      const float nb = __shfl_down_sync(AFULL, cur.b.x, 1), ne = __shfl_down_sync(AFULL, cur.ep.x, 1);
-      FOutP oL, oR;
-      face_adj_p(cur.ep, ak(cur.ep.y, ne), P.kx, asub(ak(cur.q.y, nq), cur.q),
-                 asub(ak(cur.a.y, na), cur.a), asub(ak(cur.b.y, nb), cur.b), oL, oR);
-      // low sides: the lane's own columns X (face X+1/2) and X+1 (face X+3/2)
-      A.vE = aadd(A.vE, oL.v[0]); A.vA = aadd(A.vA, oL.v[1]); A.vB = aadd(A.vB, oL.v[2]);
-      A.dEx = aadd(A.dEx, oL.d[0]); A.dAx = aadd(A.dAx, oL.d[1]); A.dBx = aadd(A.dBx, oL.d[2]);
-      A.dAy = aadd(A.dAy, oL.d[3]); A.dEy = aadd(A.dEy, oL.d[4]);
-      // high side of face X+1/2 is column X+1; of face X+3/2 the next lane's column X+2, so
-      // column X receives the previous lane's second high side
-      const float l0 = __shfl_up_sync(AFULL, oR.v[0].y, 1), l1 = __shfl_up_sync(AFULL, oR.v[1].y, 1);
-      const float l2 = __shfl_up_sync(AFULL, oR.v[2].y, 1), l3 = __shfl_up_sync(AFULL, oR.d[0].y, 1);
-      const float l4 = __shfl_up_sync(AFULL, oR.d[1].y, 1), l5 = __shfl_up_sync(AFULL, oR.d[2].y, 1);
-      const float l6 = __shfl_up_sync(AFULL, oR.d[3].y, 1), l7 = __shfl_up_sync(AFULL, oR.d[4].y, 1);
-      A.vE = aadd(A.vE, ak(l0, oR.v[0].x)); A.vA = aadd(A.vA, ak(l1, oR.v[1].x));
-      A.vB = aadd(A.vB, ak(l2, oR.v[2].x)); A.dEx = aadd(A.dEx, ak(l3, oR.d[0].x));
-      A.dAx = aadd(A.dAx, ak(l4, oR.d[1].x)); A.dBx = aadd(A.dBx, ak(l5, oR.d[2].x));
-      A.dAy = aadd(A.dAy, ak(l6, oR.d[3].x)); A.dEy = aadd(A.dEy, ak(l7, oR.d[4].x));
-    }
-    // y-faces j+1/2
-    ACellP B;
-    {
-      FOutP oL, oR;
-      face_adj_p(cur.ep, nxt.ep, P.ky, asub(nxt.q, cur.q), asub(nxt.b, cur.b), asub(nxt.a, cur.a),
-                 oL, oR);
-      add_yface_p(A, oL);
-      B = cell_from_yface_p(oR);
-    }
-    // row j: lambda^{n+1} + value adjoints + D_x^T + the push from row j-1
-    a2 o[3];
-    {
-      const float lEx = __shfl_up_sync(AFULL, A.dEx.y, 1), rEx = __shfl_down_sync(AFULL, A.dEx.x, 1);
-      const float lAx = __shfl_up_sync(AFULL, A.dAx.y, 1), rAx = __shfl_down_sync(AFULL, A.dAx.x, 1);
-      const float lBx = __shfl_up_sync(AFULL, A.dBx.y, 1), rBx = __shfl_down_sync(AFULL, A.dBx.x, 1);
-      // column k: cl dbar_{k-1} - cr dbar_{k+1} + cs dbar_k
-      const a2 tE = afma(CS, A.dEx, afma(NCR, ak(A.dEx.y, rEx), amul(CL, ak(lEx, A.dEx.x))));
-      const a2 tA = afma(CS, A.dAx, afma(NCR, ak(A.dAx.y, rAx), amul(CL, ak(lAx, A.dAx.x))));
-      const a2 tB = afma(CS, A.dBx, afma(NCR, ak(A.dBx.y, rBx), amul(CL, ak(lBx, A.dBx.x))));
-      o[0] = aadd(aadd(aadd(cur.e, A.vE), carry[0]), tE);
-      o[1] = aadd(aadd(aadd(cur.a, A.vA), carry[1]), tA);
-      o[2] = aadd(aadd(aadd(cur.b, A.vB), carry[2]), tB);
-    }
-    // y-difference adjoints of row j: -> row j-1 (-), row j+1 (+), ends (clamped ghosts)
-    {
-      const bool has = p.pery || (j >= 0 && j < p.ny);
-      const a2 dy[3] = {A.dEy, A.dAy, A.dBy};
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const a2 d = has ? dy[c] : ak(0.f, 0.f);
-        pend[c] = asub(pend[c], d);
-        carry[c] = d;
-        if (!p.pery) {
-          if (j == p.ny - 1) o[c] = aadd(o[c], d);
-          if (j == 0) o[c] = asub(o[c], d);
-        }
-      }
-    }
-    // row j-1 is complete
-    const int jo = j - 1;
-    if (jo >= y0 && jo < y1) {
-      const int64_t ro = (int64_t)jo * p.pitch;
-      const bool ok0 = X >= x0 && X < xend, ok1 = X + 1 >= x0 && X + 1 < xend;
-      if (ok0 && ok1) {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) *reinterpret_cast<a2 *>(p.lout + c * p.cstride + ro + X) = pend[c];
-      } else {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          if (ok0) p.lout[c * p.cstride + ro + X] = pend[c].x;
-          if (ok1) p.lout[c * p.cstride + ro + X + 1] = pend[c].y;
-        }
-      }
-    }
-#pragma unroll
-    for (int c = 0; c < 3; ++c) pend[c] = o[c];
-    A = B;
-    cur = nxt; nxt = pf; pf = pf2;
-    finish_arow_p(nxt);
-  }
-}
-
 // ------------------------------------------------------------------ probe term and eps-gradient
 // After the march, over the box covering the design cells and the probe (32 x 8 tiles, one
 // thread per cell):
@@ -824,10 +586,7 @@ cudaError_t adjoint_t(const CartGeom &g, const AdjointArgs &a, cudaStream_t st) 
     int dev = 0, sms = 0, bps = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if constexpr (sizeof(T) == 4)
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, adjoint_lambda_kernel_p, AWARPS * 32, 0);
-    else
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, adjoint_lambda_kernel<T>, AWARPS * 32, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, adjoint_lambda_kernel<T>, AWARPS * 32, 0);
     resident = sms * (bps > 0 ? bps : 1) * AWARPS;
   }
   const int nstrips = (g.nx + AWCOLS - 1) / AWCOLS;
@@ -841,15 +600,7 @@ cudaError_t adjoint_t(const CartGeom &g, const AdjointArgs &a, cudaStream_t st) 
   const int nchunks = (g.ny + rows - 1) / rows;
   const int64_t nwarps = (int64_t)nstrips * nchunks;
   const int grid = (int)((nwarps + AWARPS - 1) / AWARPS);
-  if constexpr (sizeof(T) == 4) {     // FP32: the paired-instruction march
-    AdjPackArgs P;
-    P.b = p;
-    P.kx = make_adj_kp(p.fx);
-    P.ky = make_adj_kp(p.fy);
-    adjoint_lambda_kernel_p<<<grid, AWARPS * 32, 0, st>>>(P, nstrips, rows);
-  } else {
-    adjoint_lambda_kernel<T><<<grid, AWARPS * 32, 0, st>>>(p, nstrips, rows);
-  }
+  adjoint_lambda_kernel<T><<<grid, AWARPS * 32, 0, st>>>(p, nstrips, rows);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   // probe term and eps-gradient over the bounding box of the probe and the design cells
