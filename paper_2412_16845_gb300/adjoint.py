@@ -131,21 +131,27 @@ class DesignProblem:
         lam2 = self._buf()
         grad = torch.zeros(self.design.size, dtype=torch.float64, device="cuda")
         gks_adjoint_seed(self.ctx, self.final.data_ptr(), lam.data_ptr())
+        # the recomputed states of one segment live in K buffers reused by every segment
+        # (addresses, windows and the box taken once, not per step)
+        pool = [self._buf() for _ in range(self.K)]
+        pool_ptr = [b.data_ptr() for b in pool]
+        lam_ptr, lam2_ptr, grad_ptr = lam.data_ptr(), lam2.data_ptr(), grad.data_ptr()
+        ctx, cbox = self.ctx, self.cbox
         for (s, ckb), e in zip(reversed(self.checkpoints),
                                reversed([c[0] for c in self.checkpoints[1:]] + [self.N])):
+            k = e - s
             # recompute V^s .. V^e of this segment
-            gks_load_state(self.ctx, ckb.data_ptr(), s)
-            states = [ckb]
-            for m in range(1, e - s + 1):
-                gks_step_window(self.ctx, 1, *self._window(2 * (e - s - m)))
-                b = self._buf()
-                gks_copy_state_box(self.ctx, b.data_ptr(), *self.cbox)
-                states.append(b)
+            ck_ptr = ckb.data_ptr()
+            gks_load_state(ctx, ck_ptr, s)
+            ptrs = [ck_ptr] + pool_ptr[:k]
+            for m in range(1, k + 1):
+                gks_step_window(ctx, 1, *self._window(2 * (k - m)))
+                gks_copy_state_box(ctx, ptrs[m], *cbox)
             for n in range(e - 1, s - 1, -1):
-                gks_adjoint_step(self.ctx, states[n - s].data_ptr(), states[n - s + 1].data_ptr(),
-                                 lam.data_ptr(), lam2.data_ptr(), grad.data_ptr(), n >= 1)
-                lam, lam2 = lam2, lam
-            del states
+                gks_adjoint_step(ctx, ptrs[n - s], ptrs[n - s + 1], lam_ptr, lam2_ptr, grad_ptr,
+                                 n >= 1)
+                lam_ptr, lam2_ptr = lam2_ptr, lam_ptr
+        del pool
         return grad
 
     def value_and_grad(self, eps_design):
