@@ -38,15 +38,15 @@ __global__ void cart_to_user_kernel(const T *__restrict__ src, double *__restric
 }
 
 // Copy of a box of columns [x0, x0+w) x rows [y0, y0+h) of every component (same offsets in
-// src and dst); consecutive threads take consecutive columns of a row.
+// src and dst).  Grid x runs over the columns of a row, grid y over the rows of all components
+// (component-major), so a thread finds its row with one 32-bit division.
 template <typename T>
 __global__ void copy_box_kernel(const T *__restrict__ src, T *__restrict__ dst, int64_t cstride,
-                                int64_t pitch, int x0, int w, int64_t y0, int64_t h, int64_t n) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = i / w;
-    const int x = (int)(i - r * w);
-    const int64_t c = r / h, y = r - c * h;
+                                int64_t pitch, int x0, int w, int64_t y0, int h, int rows) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= w) return;
+  for (int r = blockIdx.y; r < rows; r += gridDim.y) {
+    const int c = r / h, y = r - c * h;
     const int64_t o = c * cstride + (y0 + y) * pitch + x0 + x;
     dst[o] = src[o];
   }
@@ -155,17 +155,18 @@ cudaError_t launch_cart_to_user(const CartGeom &g, int ncomp, const void *src, d
 
 cudaError_t launch_copy_box(const void *src, void *dst, int ncomp, int64_t cstride, int64_t pitch,
                             int x0, int x1, int64_t y0, int64_t y1, bool fp64, cudaStream_t st) {
-  const int64_t n = (int64_t)ncomp * (y1 - y0) * (x1 - x0);
-  if (n <= 0) return cudaSuccess;
-  const int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
+  const int w = x1 - x0, h = (int)(y1 - y0);
+  if (w <= 0 || h <= 0 || ncomp <= 0) return cudaSuccess;
+  const int rows = ncomp * h;
+  const dim3 grid((w + 127) / 128, std::min(rows, 65535));
   if (fp64)
-    copy_box_kernel<double><<<blocks, 256, 0, st>>>(static_cast<const double *>(src),
-                                                    static_cast<double *>(dst), cstride, pitch, x0,
-                                                    x1 - x0, y0, y1 - y0, n);
+    copy_box_kernel<double><<<grid, 128, 0, st>>>(static_cast<const double *>(src),
+                                                  static_cast<double *>(dst), cstride, pitch, x0,
+                                                  w, y0, h, rows);
   else
-    copy_box_kernel<float><<<blocks, 256, 0, st>>>(static_cast<const float *>(src),
-                                                   static_cast<float *>(dst), cstride, pitch, x0,
-                                                   x1 - x0, y0, y1 - y0, n);
+    copy_box_kernel<float><<<grid, 128, 0, st>>>(static_cast<const float *>(src),
+                                                 static_cast<float *>(dst), cstride, pitch, x0,
+                                                 w, y0, h, rows);
   return cudaGetLastError();
 }
 
