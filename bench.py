@@ -134,7 +134,7 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(seconds=12.0, block=160):
+def cpu_baseline(seconds=12.0, block=160, all_cores=False):
     """Time the FP64 oracle (unchanged) on a block of the 4096^2 workload, in a fresh process
     with single-threaded numpy/BLAS."""
     code = f"""
@@ -172,10 +172,29 @@ print(json.dumps({{"cells": b * b, "steps": steps, "seconds": el}}))
                 "sample": "failed: " + r.stderr[-300:]}
     d = json.loads(r.stdout.strip().splitlines()[-1])
     v = d["cells"] * d["steps"] / d["seconds"] / 1e9
-    return {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{d['steps']} FP64 oracle steps on a {block}x{block} block of the 4096^2 "
-                      f"cylinder workload around the source ({d['seconds']:.1f} s, numpy single "
-                      f"thread)"}
+    out = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"{d['steps']} FP64 oracle steps on a {block}x{block} block of the 4096^2 "
+                     f"cylinder workload around the source ({d['seconds']:.1f} s, numpy single "
+                     f"thread)"}
+    if all_cores:
+        # one single-threaded oracle process per host core, each on its own copy of the block,
+        # run side by side for the same time: the aggregate rate of the whole host
+        ncores = max(1, min(os.cpu_count() or 1, 64))
+        procs = [subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE,
+                                  stderr=subprocess.PIPE, text=True, env=env)
+                 for _ in range(ncores)]
+        total, ok = 0.0, True
+        for pr in procs:
+            so, _ = pr.communicate(timeout=600)
+            if pr.returncode != 0:
+                ok = False
+                continue
+            e = json.loads(so.strip().splitlines()[-1])
+            total += e["cells"] * e["steps"] / e["seconds"] / 1e9
+        if ok:
+            out["all_cores"] = {"value": total, "unit": UNIT, "cores": ncores,
+                                "sample": f"{ncores} such processes side by side"}
+    return out
 
 
 def run_reference(args, rank):
@@ -570,7 +589,7 @@ def main():
             "clocks": clocks,
         }
         if not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline()
+            line["cpu_baseline"] = cpu_baseline(all_cores=True)
         print(json.dumps(line))
     if world > 1:
         dist.barrier()
