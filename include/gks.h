@@ -10,8 +10,10 @@
  * of Sec. 3.1 (incoming distributions of ghost cells are zero).
  *
  * Conventions shared by every entry point
- *  - Fields: 2-D TM carries (Ez, Hx, Hy); 3-D carries (Ex, Ey, Ez, Hx, Hy, Hz).  The library
- *    stores the primitive state V = (E, H); the conserved state is U = (eps E, mu H).
+ *  - Fields: 2-D TM carries (Ez, Hx, Hy); 3-D carries (Ex, Ey, Ez, Hx, Hy, Hz).  With divergence
+ *    cleaning (gks_mesh_desc.chi, gamma) psi follows in 2-D, (phi, psi) in 3-D.  The library
+ *    stores the primitive state V = (E, H[, phi, psi]); the conserved state is
+ *    U = (eps E, mu H[, phi, psi]).
  *    Units: c = eps0 = mu0 = 1 (Sec. 5) unless a lattice speed is given.
  *  - User order: host arrays are [ncomp][n_cells] in user cell order.  Cartesian cells are
  *    numbered x fastest (i + nx*(j + ny*k)); tetrahedra in the order of tet_vert.  Internal
