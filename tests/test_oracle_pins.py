@@ -582,24 +582,33 @@ def test_probe_objective_against_exact_wave():
 
 # ---------------------------------------------------------------------------- PEC walls
 
-def _mirror_parity_fields(rng, mesh, modes=3):
+def _mirror_parity_fields(rng, mesh, modes=3, potentials=False):
     """Random smooth fields with the parities of the PEC mirror about every wall of the unit box:
     along axis a a component is odd (sin) if the mirror negates it (tangential E, normal H) and
-    even (cos) if it keeps it (normal E, tangential H)."""
+    even (cos) if it keeps it (normal E, tangential H).  With potentials=True the cleaning
+    potentials follow: phi odd about every wall, psi even."""
     x = mesh.centroid
-    V = np.zeros((mesh.ncell, 6))
-    for c in range(6):
+    ncomp = 8 if potentials else 6
+    V = np.zeros((mesh.ncell, ncomp))
+    for c in range(ncomp):
         for _ in range(modes):
             k = rng.integers(1, 3, size=3)
             f = rng.standard_normal() * np.ones(mesh.ncell)
             for a in range(mesh.dim):
-                # E_c is normal to the a-walls iff c == a; H_{c-3} likewise
-                normal = (c % 3) == a
-                odd = (not normal) if c < 3 else normal
+                if c == 6:
+                    odd = True
+                elif c == 7:
+                    odd = False
+                else:
+                    # E_c is normal to the a-walls iff c == a; H_{c-3} likewise
+                    normal = (c % 3) == a
+                    odd = (not normal) if c < 3 else normal
                 f = f * (np.sin if odd else np.cos)(2 * np.pi * k[a] * x[:, a])
             V[:, c] += f
     if mesh.dim == 2:
         V[:, [0, 1, 5]] = 0.0
+        if potentials:
+            V[:, 6] = 0.0
     return V
 
 
@@ -622,6 +631,26 @@ def test_pec_box_equals_periodic_for_mirror_symmetric_fields(dim, kappa):
     a, _ = go.run(per, f0, eps, None, 0.4, steps, kappa=kappa)
     b, _ = go.run(pec, f0, eps, None, 0.4, steps, kappa=kappa)
     assert np.max(np.abs(a)) > 0.1
+    assert np.max(np.abs(a - b)) <= 1e-12 * np.max(np.abs(a)), np.max(np.abs(a - b))
+
+
+@pytest.mark.parametrize("dim,cfl", [(2, 0.4), (3, 0.3)])
+def test_pec_box_equals_periodic_with_cleaning_potentials(dim, cfl):
+    """The same equivalence for the cleaning system (Sec. 2.1 with chi, gamma > 0): with phi odd
+    and psi even about every wall (the parities their equations impose, given normal E even and
+    normal B odd), the PEC box evolves as the periodic one, to rounding.  Pins the mirror of
+    the potentials and of their gradients."""
+    rng = np.random.default_rng(77 + dim)
+    n = (14, 12) if dim == 2 else (8, 6, 6)
+    per = go.cartesian_mesh(n, (0.0,) * dim, (1.0,) * dim, ("periodic",) * (2 * dim))
+    pec = go.cartesian_mesh(n, (0.0,) * dim, (1.0,) * dim, ("pec",) * (2 * dim))
+    V = _mirror_parity_fields(rng, per, potentials=True)
+    f0 = go.state_to_fields(V, dim)
+    eps = 2.0 + 0.5 * np.prod(np.cos(2 * np.pi * per.centroid[:, :dim]), axis=1)
+    phm = (0.7, 0.9)
+    a, _ = go.run(per, f0, eps, None, cfl, 10, phm=phm)
+    b, _ = go.run(pec, f0, eps, None, cfl, 10, phm=phm)
+    assert np.max(np.abs(a[-1])) > 0.01 and np.max(np.abs(a[-2])) > 0.01   # potentials carry signal
     assert np.max(np.abs(a - b)) <= 1e-12 * np.max(np.abs(a)), np.max(np.abs(a - b))
 
 
