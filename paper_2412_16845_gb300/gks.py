@@ -377,7 +377,14 @@ class GKSSolver:
         gks_set_materials(self.ctx, eps, mu)
 
     def write_fields(self, fields, t0=0.0):
-        gks_write_fields(self.ctx, _f64(fields, self.ncomp * self.ncell), t0)
+        """fields [ncomp][n_cells]; with divergence cleaning the potentials may be left out
+        (the electromagnetic rows alone), and then start at zero."""
+        f = np.asarray(fields, dtype=np.float64)
+        base = 3 if self.spec is not None and self.spec.dim == 2 else 6
+        if self.ncomp > base and f.size == base * self.ncell:
+            f = np.concatenate([f.reshape(base, self.ncell),
+                                np.zeros((self.ncomp - base, self.ncell))])
+        gks_write_fields(self.ctx, _f64(f, self.ncomp * self.ncell), t0)
 
     def set_source(self, jz_mask, A, f0, t0, s):
         gks_set_source(self.ctx, None if jz_mask is None else _f64(jz_mask, self.ncell),

@@ -47,3 +47,21 @@ def test_component_count(captured, dim, phm, ncomp):
     assert s.ncomp == ncomp
     assert d.limiter == gks.GKS_LIMITER_NONE
     assert (d.chi, d.gamma) == ((phm or (0.0, 0.0))[0], (phm or (0.0, 0.0))[1])
+
+
+def test_cleaning_fields_without_potentials_are_padded(captured, monkeypatch):
+    import numpy as np
+    seen = {}
+    monkeypatch.setattr(gks, "gks_write_fields",
+                        lambda ctx, f, t0: seen.__setitem__("f", np.array(f).ravel()))
+    s = gks.GKSSolver(_spec(phm=(0.5, 0.5)))          # 3-D: 8 components
+    n = s.ncell
+    f6 = np.arange(6 * n, dtype=float).reshape(6, n)
+    s.write_fields(f6)
+    assert seen["f"].shape == (8 * n,)
+    assert np.array_equal(seen["f"][:6 * n], f6.ravel()) and not seen["f"][6 * n:].any()
+    f8 = np.ones((8, n))
+    s.write_fields(f8)
+    assert np.array_equal(seen["f"], f8.ravel())
+    with pytest.raises(ValueError):
+        s.write_fields(np.ones((5, n)))
