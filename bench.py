@@ -178,22 +178,27 @@ print(json.dumps({{"cells": b * b, "steps": steps, "seconds": el}}))
                      f"thread)"}
     if all_cores:
         # one single-threaded oracle process per host core, each on its own copy of the block,
-        # run side by side for the same time: the aggregate rate of the whole host
+        # run side by side for the same time: the aggregate rate of the whole host (left out
+        # of the line if any process fails)
         ncores = max(1, min(os.cpu_count() or 1, 64))
-        procs = [subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE,
-                                  stderr=subprocess.PIPE, text=True, env=env)
-                 for _ in range(ncores)]
-        total, ok = 0.0, True
-        for pr in procs:
-            so, _ = pr.communicate(timeout=600)
-            if pr.returncode != 0:
-                ok = False
-                continue
-            e = json.loads(so.strip().splitlines()[-1])
-            total += e["cells"] * e["steps"] / e["seconds"] / 1e9
-        if ok:
+        procs = []
+        try:
+            procs = [subprocess.Popen([sys.executable, "-c", code], stdout=subprocess.PIPE,
+                                      stderr=subprocess.PIPE, text=True, env=env)
+                     for _ in range(ncores)]
+            total = 0.0
+            for pr in procs:
+                so, _ = pr.communicate(timeout=600)
+                if pr.returncode != 0:
+                    raise RuntimeError("oracle process failed")
+                e = json.loads(so.strip().splitlines()[-1])
+                total += e["cells"] * e["steps"] / e["seconds"] / 1e9
             out["all_cores"] = {"value": total, "unit": UNIT, "cores": ncores,
                                 "sample": f"{ncores} such processes side by side"}
+        except Exception:
+            for pr in procs:
+                if pr.poll() is None:
+                    pr.kill()
     return out
 
 
