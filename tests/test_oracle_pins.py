@@ -343,6 +343,101 @@ def test_cavity_mode_within_factor_of_table3():
     assert tab[0, 1] / 1.3 <= l1 <= tab[0, 1] * 1.3, (l1, tab[0])
 
 
+@pytest.mark.parametrize("cfl", [0.5, 0.4])
+@pytest.mark.parametrize("kappa", [0.0, 0.05, 1.0])
+def test_grid_aligned_3d_update_is_fromm(cfl, kappa):
+    """Sec. 5.1 setting (3-D grid, wave along x): for the right-moving TEM mode E_z = w,
+    H_y = -w the 3-D step is Fromm's scheme at Courant number nu, exactly:
+    w_j <- w_j - nu (w_j - w_{j-1}) - nu (1 - nu)/4 (w_{j+1} - w_j - w_{j-1} + w_{j-2}),
+    whatever kappa (the 1-D flux does not depend on tau), with the other components staying 0.
+    A dropped or mis-signed term of the 3-D face flux or of the Green-Gauss gradient along the
+    normal breaks the equality."""
+    N = 12
+    rng = np.random.default_rng(3)
+    mesh = go.cartesian_mesh((N, 1, 1), (0, 0, 0), (1, 1 / N, 1 / N), ("periodic",) * 6)
+    w = rng.standard_normal(N)
+    V = np.zeros((N, 6))
+    V[:, 2], V[:, 4] = w, -w
+    dt = cfl / N
+    Vn = go.step(mesh, V, go.material_diag(np.ones(N), None), dt,
+                 go.time_coefficients(dt, kappa * dt))
+    nu = cfl
+    wm1, wm2, wp1 = np.roll(w, 1), np.roll(w, 2), np.roll(w, -1)
+    fromm = w - nu * (w - wm1) - nu * (1 - nu) / 4 * (wp1 - w - wm1 + wm2)
+    assert np.abs(Vn[:, 2] - fromm).max() <= 1e-14
+    assert np.abs(Vn[:, 4] + fromm).max() <= 1e-14
+    assert np.abs(Vn[:, [0, 1, 3, 5]]).max() == 0.0
+
+
+def test_table1_grid_aligned_wave_is_third_order():
+    """Sec. 5.1, Table 1 (golden file): E_z = cos 2 pi (x - t), B_y = -E_z on the periodic unit
+    cube, CFL 0.5, t = 1, N = 20 .. 160.  The oracle's errors are not the printed ones: for this
+    wave the scheme is Fromm's (test above), third order at Courant number 1/2, so its L1, L2
+    and L-inf errors fall at order 3 +- 0.05 and sit below the table's second-order errors by a
+    factor that starts near 4 at N = 20 and doubles with every refinement (to within the
+    table's own order, 1.92 .. 2.02).  This is the
+    measured relation that the design doc reports; no reading of the CFL reproduces the table."""
+    tab = np.loadtxt(os.path.join(GOLDEN, "paper_table1_plane_wave.txt"))
+    errs = []
+    for N in tab[:, 0].astype(int):
+        mesh = go.cartesian_mesh((N, 1, 1), (0, 0, 0), (1, 1 / N, 1 / N), ("periodic",) * 6)
+        x = mesh.centroid[:, 0]
+        f = np.zeros((6, N))
+        f[2] = np.cos(2 * np.pi * x)
+        f[4] = -f[2]
+        out, info = go.run(mesh, f, np.ones(N), None, 0.5, 2 * N, dt=0.5 / N)
+        assert abs(info["t"] - 1.0) < 1e-12
+        e = out[2] - np.cos(2 * np.pi * (x - info["t"]))
+        errs.append((np.abs(e).mean(), np.sqrt((e * e).mean()), np.abs(e).max()))
+    errs = np.array(errs)
+    orders = np.log2(errs[:-1] / errs[1:])
+    assert np.all(np.abs(orders - 3.0) <= 0.05), orders
+    ratio = tab[:, 1:4] / errs
+    assert np.all((ratio[0] > 3.5) & (ratio[0] < 5.0)), ratio[0]
+    assert np.all(np.abs(ratio[1:] / ratio[:-1] - 2.0) <= 0.15), ratio
+
+
+def _oblique_symbol(N, cfl, kappa=0.0):
+    """The oracle's one-step amplification matrix G for the Fourier mode exp(2 pi i (x + y + z))
+    on the periodic N^3 unit cube (the step applied to the six single-component modes; the step
+    is linear and translation invariant, which the check inside confirms cell by cell)."""
+    mesh = go.cartesian_mesh((N, N, N), (0, 0, 0), (1, 1, 1), ("periodic",) * 6)
+    ph = np.exp(2j * np.pi * mesh.centroid.sum(axis=1))
+    dt = go.time_step(mesh, cfl)
+    C = go.time_coefficients(dt, kappa * dt)
+    m = go.material_diag(np.ones(mesh.ncell), None).astype(complex)
+    G = np.zeros((6, 6), complex)
+    for c in range(6):
+        V = np.zeros((mesh.ncell, 6), complex)
+        V[:, c] = ph
+        Vn = go.step(mesh, V, m, dt, C) / ph[:, None]
+        assert np.abs(Vn - Vn[0]).max() <= 1e-12
+        G[:, c] = Vn[0]
+    return G, dt
+
+
+def test_oblique_3d_plane_wave_second_order():
+    """Sec. 5.1 in three dimensions: the exact oblique plane wave E = a e^{i(k.x - |k| t)},
+    H = (k/|k|) x E with k = 2 pi (1, 1, 1) on the periodic unit cube, CFL 0.4 (the 3-D
+    workload's), t = 0.5.  The oracle's solution G^n u0 (n = t/dt steps of the mode) converges
+    at order 2 +- 0.1 from 16^3 to 32^3."""
+    k = 2 * np.pi * np.ones(3)
+    khat = k / np.linalg.norm(k)
+    a = np.array([1.0, -1.0, 0.0]) / math.sqrt(2.0)
+    u0 = np.concatenate([a, np.cross(khat, a)]).astype(complex)
+    T = 0.5
+    err = []
+    for N in (16, 32):
+        G, dt = _oblique_symbol(N, 0.4)
+        n = int(round(T / dt))
+        assert abs(n * dt - T) < 1e-12
+        exact = np.exp(-1j * np.linalg.norm(k) * T) * u0
+        err.append(np.linalg.norm(np.linalg.matrix_power(G, n) @ u0 - exact))
+    order = math.log2(err[0] / err[1])
+    assert abs(order - 2.0) <= 0.1, (err, order)
+    assert err[1] < 0.03
+
+
 def _smooth_random_fields(rng, mesh, ncomp_modes=3):
     x = mesh.centroid
     V = np.zeros((mesh.ncell, 6))
