@@ -230,6 +230,58 @@ gks_status gks_adjoint_step(gks_ctx *ctx, const void *state_n, const void *state
                             const void *adj_in, void *adj_out, double *grad_eps,
                             int32_t add_probe);
 
+/* ---- Domain split across ranks (one process per GPU).  The finite-volume update of Sec. 3.1
+ * reaches two cells along every axis (the Green-Gauss gradient of Sec. 3.1, then the face flux
+ * between two reconstructed cells), so a grid split into slabs along its slowest axis (y in
+ * 2-D, z in 3-D) advances exactly like the whole grid when every rank also holds the two
+ * layers of cells beyond each side it shares with another rank (ghost layers) and those layers
+ * are refreshed from the neighbour after every step. */
+
+/* Cells [begin, end) of the slowest axis owned by this rank; shared_lo (shared_hi) = 1 when the
+ * side below begin (at end) borders another rank, 0 when it is the grid's own boundary.  A
+ * periodic axis split over several ranks is a ring: both sides shared. */
+typedef struct gks_slab_desc {
+  int64_t begin;
+  int64_t end;
+  int32_t shared_lo;
+  int32_t shared_hi;
+} gks_slab_desc;
+
+enum { GKS_HALO_OWNED = 0, GKS_HALO_GHOST = 1 };
+
+/* Rank-local context for the slab `slab` of the grid `global` (a Cartesian description as for
+ * gks_create_mesh; c_lattice must be > 0 so that every rank steps with the same dt and C1..C5).
+ * The local grid is the owned layers plus two ghost layers beyond each shared side: along the
+ * slab axis it covers the global cells begin - 2 shared_lo .. end + 2 shared_hi - 1 (wrapped on
+ * a periodic axis).  Every user-order array of this context (materials, fields, source mask,
+ * probe cells) covers the local grid, x fastest, starting at that first layer.  The cell size,
+ * dt and C1..C5 are those of the global grid.  gks_energy sums owned cells only; the adjoint
+ * calls return GKS_E_UNSUPPORTED on a slab.  GKS_E_ARG when the slab does not fit the grid, a
+ * shared side owns fewer than two layers, a non-periodic grid edge is marked shared, or a
+ * periodic axis has one shared side only. */
+gks_status gks_create_slab(const gks_mesh_desc *global, const gks_slab_desc *slab,
+                           gks_ctx **out);
+
+/* Bytes of one side's halo buffer: ncomp components x 2 layers of the state layout. */
+gks_status gks_halo_bytes(const gks_ctx *ctx, int64_t *bytes);
+
+/* Copy two layers of `state` (device, this context's layout; NULL = the context's own current
+ * state) next to side 0 (low) or 1 (high) into the caller's device buffer buf
+ * (gks_halo_bytes): layers = GKS_HALO_OWNED the two owned layers at that side,
+ * GKS_HALO_GHOST the two ghost layers beyond it; increasing global index order.  Asynchronous
+ * on the context's stream.  GKS_E_ARG if the side is not shared. */
+gks_status gks_halo_export(gks_ctx *ctx, int32_t side, int32_t layers, const void *state,
+                           void *buf);
+
+/* The reverse: write (add = 0) or add (add = 1) buf into the two layers of `state` (NULL = the
+ * context's state) chosen as in gks_halo_export.  After each step a rank exports its owned
+ * layers to each neighbour, which imports them into its ghost layers (add = 0): rank r's high
+ * owned layers are rank r+1's low ghost layers.  The transpose of that copy, for adjoint
+ * fields, exports ghost layers and adds them into the neighbour's owned layers (add = 1).
+ * Asynchronous on the context's stream. */
+gks_status gks_halo_import(gks_ctx *ctx, int32_t side, int32_t layers, void *state,
+                           const void *buf, int32_t add);
+
 /* Energy 1/2 |Omega| sum_i (eps_i |E_i|^2 + mu_i |H_i|^2) of caller-owned device arrays, for
  * callers that cannot allocate device memory (a framework that reserved the device memory for
  * its own pool, a hot loop that cannot pay for an allocation, or code without a gks context).
@@ -243,10 +295,13 @@ gks_status gks_adjoint_step(gks_ctx *ctx, const void *state_n, const void *state
  *  out          device pointer to one double, overwritten with the energy.
  *  cuda_stream  stream the two kernels are enqueued on (asynchronous; no synchronisation).
  * Allocates nothing: the partial sums live in a fixed device array of 64 KiB that every GPU
- * loading the library keeps until the process exits.  The first call on a device looks up
- * that array's device address (with the device current); make that first call before any
+ * loading the library keeps until the process exits.  Every call looks up that array's device
+ * address on the current device (a host-side lookup, so a device reset leaves no stale address);
+ * the first call on a device also loads the library's device code there, so make it before any
  * stream capture.  All calls share the array, so calls that overlap on the GPU (on different
- * streams) race; serialise them.  GKS_E_ARG on bad arguments, GKS_E_CUDA on a launch error. */
+ * streams) race; serialise them.  GKS_E_ARG on bad arguments; GKS_E_CUDA on a launch error, and
+ * (without launching) when an earlier CUDA error is still pending on the calling thread, which
+ * is left in place for the work that caused it. */
 gks_status gks_energy_noalloc(int32_t precision, int32_t dim, int64_t n_cells, double cell_volume,
                               const void *fields, const void *eps, const void *mu, double *out,
                               void *cuda_stream);

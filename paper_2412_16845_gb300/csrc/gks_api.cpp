@@ -305,6 +305,119 @@ gks_status gks_create_mesh(const gks_mesh_desc *d, gks_ctx **out) {
   return GKS_OK;
 }
 
+gks_status gks_create_slab(const gks_mesh_desc *global, const gks_slab_desc *slab,
+                           gks_ctx **out) {
+  if (!out) return GKS_E_ARG;
+  *out = nullptr;
+  if (!global || !slab) return GKS_E_ARG;
+  if (global->kind != GKS_CARTESIAN || (global->dim != 2 && global->dim != 3)) return GKS_E_ARG;
+  // every rank must step with the same dt and lattice speed: the automatic speed would follow
+  // each slab's own materials
+  if (!finite_positive(global->c_lattice)) return GKS_E_ARG;
+  const int ax = global->dim - 1;                 // slowest axis: y in 2-D, z in 3-D
+  const int64_t n = global->n[ax];
+  const int lo_sh = slab->shared_lo, hi_sh = slab->shared_hi;
+  if ((lo_sh != 0 && lo_sh != 1) || (hi_sh != 0 && hi_sh != 1)) return GKS_E_ARG;
+  if (n < 1 || slab->begin < 0 || slab->end > n || slab->begin >= slab->end) return GKS_E_ARG;
+  const int64_t own = slab->end - slab->begin;
+  if ((lo_sh || hi_sh) && own < 2) return GKS_E_ARG;   // two owned layers go to each neighbour
+  const bool per = global->bc[2 * ax] == GKS_BC_PERIODIC;
+  if (per && lo_sh != hi_sh) return GKS_E_ARG;         // a periodic axis splits into a ring
+  if (!per && ((lo_sh && slab->begin == 0) || (hi_sh && slab->end == n))) return GKS_E_ARG;
+  if (!(global->hi[ax] > global->lo[ax]) || !std::isfinite(global->hi[ax] - global->lo[ax]))
+    return GKS_E_ARG;
+  const double h = (global->hi[ax] - global->lo[ax]) / (double)n;
+  const int64_t first = slab->begin - 2 * lo_sh;        // global index of local layer 0
+  const int64_t nloc = own + 2 * (lo_sh + hi_sh);
+  gks_mesh_desc d = *global;
+  d.n[ax] = nloc;
+  d.lo[ax] = global->lo[ax] + (double)first * h;
+  d.hi[ax] = d.lo[ax] + (double)nloc * h;
+  // a shared side's ghost layers are rewritten by gks_halo_import before every step, so the
+  // local grid's own boundary there only touches ghost cells
+  if (lo_sh || hi_sh) {
+    if (lo_sh) d.bc[2 * ax] = GKS_BC_NONREFLECTING;
+    if (hi_sh) d.bc[2 * ax + 1] = GKS_BC_NONREFLECTING;
+    if (per) d.bc[2 * ax] = d.bc[2 * ax + 1] = GKS_BC_NONREFLECTING;
+  }
+  gks_status s = gks_create_mesh(&d, out);
+  if (s != GKS_OK) return s;
+  gks_ctx *ctx = *out;
+  ctx->slab = true;
+  ctx->own0 = 2 * lo_sh;
+  ctx->own1 = ctx->own0 + (int)own;
+  ctx->shared[0] = lo_sh;
+  ctx->shared[1] = hi_sh;
+  // the same cell size (hence dt and C1..C5) as the whole grid, bit for bit
+  ctx->g.h[ax] = h;
+  double sum = 0;
+  for (int a = 0; a < ctx->dim; ++a) sum += 1.0 / ctx->g.h[a];
+  ctx->min_h = ctx->dim / sum;
+  refresh_time_step(ctx);
+  return GKS_OK;
+}
+
+namespace {
+
+// Elements of one layer of the slab axis in the state layout (a padded row in 2-D, a plane in
+// 3-D), and the first local layer of the two that a halo call moves.
+int64_t halo_layer_elems(const gks_ctx *ctx) {
+  return ctx->dim == 3 ? ctx->g.plane : ctx->g.pitch;
+}
+
+gks_status halo_check(gks_ctx *ctx, int32_t side, int32_t layers, int *first) {
+  if (!ctx->slab) return fail(ctx, GKS_E_UNSUPPORTED, "halo calls need a slab context");
+  if (side != 0 && side != 1) return fail(ctx, GKS_E_ARG, "side must be 0 (low) or 1 (high)");
+  if (!ctx->shared[side]) return fail(ctx, GKS_E_ARG, "that side is not shared with a rank");
+  if (layers == GKS_HALO_OWNED)
+    *first = side == 0 ? ctx->own0 : ctx->own1 - 2;
+  else if (layers == GKS_HALO_GHOST)
+    *first = side == 0 ? ctx->own0 - 2 : ctx->own1;
+  else
+    return fail(ctx, GKS_E_ARG, "layers must be GKS_HALO_OWNED or GKS_HALO_GHOST");
+  return GKS_OK;
+}
+
+}  // namespace
+
+gks_status gks_halo_bytes(const gks_ctx *ctx, int64_t *bytes) {
+  if (!ctx || !bytes) return GKS_E_ARG;
+  if (!ctx->slab) return GKS_E_UNSUPPORTED;
+  *bytes = (int64_t)ctx->esize * ctx->ncomp * 2 * halo_layer_elems(ctx);
+  return GKS_OK;
+}
+
+gks_status gks_halo_export(gks_ctx *ctx, int32_t side, int32_t layers, const void *state,
+                           void *buf) {
+  if (!ctx) return GKS_E_ARG;
+  int first = 0;
+  gks_status s = halo_check(ctx, side, layers, &first);
+  if (s != GKS_OK) return s;
+  if (!buf) return fail(ctx, GKS_E_ARG, "buf is NULL");
+  const int64_t L = halo_layer_elems(ctx);
+  const char *base = static_cast<const char *>(state ? state : ctx->V[ctx->cur]);
+  GKS_CUDA(gks::launch_halo_copy(base + (size_t)first * L * ctx->esize, ctx->g.cstride, buf,
+                                 2 * L, 2 * L, ctx->ncomp, false, ctx->fp64, ctx->st));
+  ctx->launches += 1;
+  return GKS_OK;
+}
+
+gks_status gks_halo_import(gks_ctx *ctx, int32_t side, int32_t layers, void *state,
+                           const void *buf, int32_t add) {
+  if (!ctx) return GKS_E_ARG;
+  int first = 0;
+  gks_status s = halo_check(ctx, side, layers, &first);
+  if (s != GKS_OK) return s;
+  if (!buf) return fail(ctx, GKS_E_ARG, "buf is NULL");
+  if (add != 0 && add != 1) return fail(ctx, GKS_E_ARG, "add must be 0 or 1");
+  const int64_t L = halo_layer_elems(ctx);
+  char *base = static_cast<char *>(state ? state : ctx->V[ctx->cur]);
+  GKS_CUDA(gks::launch_halo_copy(buf, 2 * L, base + (size_t)first * L * ctx->esize,
+                                 ctx->g.cstride, 2 * L, ctx->ncomp, add != 0, ctx->fp64, ctx->st));
+  ctx->launches += 1;
+  return GKS_OK;
+}
+
 gks_status gks_set_materials(gks_ctx *ctx, const double *eps, const double *mu) {
   if (!ctx) return GKS_E_ARG;
   if (!eps) return fail(ctx, GKS_E_ARG, "eps is NULL");
@@ -566,7 +679,17 @@ gks_status gks_energy(gks_ctx *ctx, double *out) {
   if (ctx->kind == GKS_TET)
     GKS_CUDA(gks::launch_tet_energy(ctx->tet, ctx->V[ctx->cur], ctx->eps, ctx->mu, ctx->fp64,
                                     ctx->red, ctx->red_n, ctx->red + ctx->red_n, ctx->st));
-  else
+  else if (ctx->slab) {
+    // owned layers only: the ghost layers belong to the neighbouring ranks
+    gks::CartGeom g = ctx->g;
+    const int64_t off = (int64_t)ctx->own0 * halo_layer_elems(ctx) * (int64_t)ctx->esize;
+    (ctx->dim == 3 ? g.nz : g.ny) = ctx->own1 - ctx->own0;
+    const char *V = static_cast<const char *>(ctx->V[ctx->cur]) + off;
+    const char *eps = static_cast<const char *>(ctx->eps) + off;
+    const char *mu = ctx->mu ? static_cast<const char *>(ctx->mu) + off : nullptr;
+    GKS_CUDA(gks::launch_cart_energy(g, ctx->ncomp, V, eps, mu, ctx->fp64, ctx->red,
+                                     ctx->red_n, ctx->red + ctx->red_n, ctx->st));
+  } else
     GKS_CUDA(gks::launch_cart_energy(ctx->g, ctx->ncomp, ctx->V[ctx->cur], ctx->eps, ctx->mu,
                                      ctx->fp64, ctx->red, ctx->red_n, ctx->red + ctx->red_n,
                                      ctx->st));
@@ -707,6 +830,8 @@ gks_status gks_adjoint_step(gks_ctx *ctx, const void *state_n, const void *state
   if (ctx->phm) return fail(ctx, GKS_E_UNSUPPORTED, "the adjoint does not cover divergence cleaning");
   if (ctx->limiter)
     return fail(ctx, GKS_E_UNSUPPORTED, "the limited step is not linear: no adjoint");
+  if (ctx->slab)
+    return fail(ctx, GKS_E_UNSUPPORTED, "the adjoint step runs on a whole grid, not on a slab");
   for (int k = 0; k < 4; ++k)
     if (ctx->g.pec[k])
       return fail(ctx, GKS_E_UNSUPPORTED, "the adjoint supports periodic and non-reflecting sides only");

@@ -569,18 +569,20 @@ __device__ __forceinline__ f2 psub(f2 a, f2 b) { return __ffma2_rn(b, make_float
 __device__ __forceinline__ f2 pmul(f2 a, f2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ f2 pfma(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, c); }
 
-// face_flux constants for mu = 1, each as a pair (a14 = a1 + a4, n* negated).
+// face_flux constants for mu = 1 (a14 = a1 + a4, n* negated), kept as scalars: a paired FMA
+// reads a scalar kernel parameter replicated into both halves straight from the constant bank,
+// whereas a float2 parameter costs an extra instruction per use.
 struct FaceKP {
-  f2 a14, a2, a3, a5, a6, nq2, nq3, q5, b1, c1, c2, c3, c4, c5, c6, g0, nk3, half;
+  float a14, a2, a3, a5, a6, nq2, nq3, q5, b1, c1, c2, c3, c4, c5, c6, g0, nk3, half;
 };
+__device__ __forceinline__ f2 rep(float k) { return make_float2(k, k); }
 
 inline FaceKP make_face_kp(const FaceK<float> &k) {
-  auto b = [](float v) { return make_float2(v, v); };
   FaceKP q;
-  q.a14 = b(k.a1 + k.a4); q.a2 = b(k.a2); q.a3 = b(k.a3); q.a5 = b(k.a5); q.a6 = b(k.a6);
-  q.nq2 = b(-k.q2); q.nq3 = b(-k.q3); q.q5 = b(k.q5); q.b1 = b(k.b1);
-  q.c1 = b(k.c1); q.c2 = b(k.c2); q.c3 = b(k.c3); q.c4 = b(k.c4); q.c5 = b(k.c5); q.c6 = b(k.c6);
-  q.g0 = b(k.g0); q.nk3 = b(-k.k3); q.half = b(0.5f);
+  q.a14 = k.a1 + k.a4; q.a2 = k.a2; q.a3 = k.a3; q.a5 = k.a5; q.a6 = k.a6;
+  q.nq2 = -k.q2; q.nq3 = -k.q3; q.q5 = k.q5; q.b1 = k.b1;
+  q.c1 = k.c1; q.c2 = k.c2; q.c3 = k.c3; q.c4 = k.c4; q.c5 = k.c5; q.c6 = k.c6;
+  q.g0 = k.g0; q.nk3 = -k.k3; q.half = 0.5f;
   return q;
 }
 
@@ -602,26 +604,26 @@ __device__ __forceinline__ void face_flux_p(const FSideP &l, const FSideP &r, co
   const f2 D_ex = psub(r.den, l.den), S_UAt = padd(l.dat, r.dat), S_e = padd(l.e, r.e);
   const f2 se = padd(l.eps, r.eps);
   const f2 ie = pk(rcp2(se.x), rcp2(se.y));
-  const f2 g = pfma(k.nk3, ie, k.g0);
-  f2 fe = pmul(k.a14, S_B);
-  fe = pfma(k.a2, D_e, fe);
-  fe = pfma(g, pfma(k.a3, D_xB, pmul(k.half, S_Uxe)), fe);
-  fe = pfma(k.nq2, D_Ue, fe);
-  fe = pfma(k.nq3, S_Uxe, fe);
-  fe = pfma(k.a5, D_At, fe);
-  fe = pfma(k.a6, D_xB, fe);
-  f2 fa = pmul(k.q5, S_Uxa);
-  fa = pfma(k.nq2, D_Ua, fa);
-  fa = pfma(k.b1, D_Et, fa);
-  f2 u = pmul(k.c1, S_Ue);
-  u = pfma(k.c2, D_B, u);
-  u = pfma(k.c4, S_UAt, u);
+  const f2 g = pfma(rep(k.nk3), ie, rep(k.g0));
+  f2 fe = pmul(rep(k.a14), S_B);
+  fe = pfma(rep(k.a2), D_e, fe);
+  fe = pfma(g, pfma(rep(k.a3), D_xB, pmul(rep(k.half), S_Uxe)), fe);
+  fe = pfma(rep(k.nq2), D_Ue, fe);
+  fe = pfma(rep(k.nq3), S_Uxe, fe);
+  fe = pfma(rep(k.a5), D_At, fe);
+  fe = pfma(rep(k.a6), D_xB, fe);
+  f2 fa = pmul(rep(k.q5), S_Uxa);
+  fa = pfma(rep(k.nq2), D_Ua, fa);
+  fa = pfma(rep(k.b1), D_Et, fa);
+  f2 u = pmul(rep(k.c1), S_Ue);
+  u = pfma(rep(k.c2), D_B, u);
+  u = pfma(rep(k.c4), S_UAt, u);
   f2 fb = pmul(ie, u);
-  fb = pfma(g, pfma(k.c3, D_ex, pmul(k.half, S_UxB)), fb);
-  fb = pfma(k.c5, S_e, fb);
-  fb = pfma(k.nq2, D_B, fb);
-  fb = pfma(k.nq3, S_UxB, fb);
-  fb = pfma(k.c6, D_ex, fb);
+  fb = pfma(g, pfma(rep(k.c3), D_ex, pmul(rep(k.half), S_UxB)), fb);
+  fb = pfma(rep(k.c5), S_e, fb);
+  fb = pfma(rep(k.nq2), D_B, fb);
+  fb = pfma(rep(k.nq3), S_UxB, fb);
+  fb = pfma(rep(k.c6), D_ex, fb);
   fE = fe;
   fHn = fa;
   fHt = fb;

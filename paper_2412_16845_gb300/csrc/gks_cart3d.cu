@@ -603,6 +603,7 @@ cudaError_t launch3_t(const CartGeom &g, const CartStepArgs &a, double chi, doub
 
 cudaError_t launch_cart3d_step(const CartGeom &g, const CartStepArgs &a, bool fp64,
                                cudaStream_t st) {
+  if (cart3d_side_supported(g, a, fp64)) return launch_cart3d_side(g, a, st);
   return fp64 ? launch3_t<double, 6>(g, a, 0.0, 0.0, st) : launch3_t<float, 6>(g, a, 0.0, 0.0, st);
 }
 

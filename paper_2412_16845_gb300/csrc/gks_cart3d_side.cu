@@ -1,0 +1,694 @@
+// Fused 3-D GKS step on a Cartesian grid in FP32 with mu = 1 (Sec. 3.1): the side-split face
+// flux of gks_side3.cuh, paired FP32 arithmetic, planes staged in shared memory.
+//
+// Flux.  Through the face between cells L and R along axis A the time-integrated flux is
+// F = P^l_L + P^r_R + ie (Q^l_L + Q^r_R), ie = 2/(eps_L + eps_R), where the four vectors of a
+// cell depend on that cell alone (its state, raw central differences and eps).  A cell computes
+// them once per axis; faces combine two cells' vectors.  Non-reflecting faces (Sec. 3.1, last
+// paragraph) take zero vectors for the ghost and ie = 1/eps of the cell (the ghost's eps is the
+// cell's, through the clamped loads that also give the Green-Gauss ghost copy).
+//
+// Layout of the work.  A CTA owns 64 columns x NWO rows of a chunk of z-planes.  Each of its
+// NWO row warps holds two adjacent cells per lane (columns X0 + 2l, X0 + 2l + 1) as the two
+// halves of a float2, so every flux term of both cells is one paired FP32 instruction
+// (__ffma2_rn etc.).  Two halo warps complete the tile: H0 owns the row below, H1 the row
+// above; they supply the y-face vectors of those rows and, one plane ahead, the x-face vectors
+// of the columns left and right of the tile.  Per plane:
+//   - x: the right cell's r-side vectors come from the next lane (shuffle), the flux of a lane's
+//     left face from the previous lane;
+//   - z: the l-side vectors of the plane below stay in registers (march along z), so the face
+//     below the plane completes the update of the plane below;
+//   - y: every row publishes its r-side vectors in shared memory, forms the face above it and
+//     publishes that flux for the row above (two barriers).
+// Planes arrive by TMA (cp.async.bulk.tensor) into five shared-memory slots, one plane per slot:
+// one thread issues the two tensor copies of plane k+4 (the six fields as one 4-D box, eps as a
+// 3-D box) when plane k starts; they complete on the slot's mbarrier, which every thread waits
+// for one plane later, so a whole plane of work hides the latency.  Boxes reaching past the
+// grid are zero-filled by the copy; in CTAs at the grid's edge the halo warps then write the
+// wrapped or clamped values into those entries (the periodic neighbour, or the copy of the
+// edge cell that the non-reflecting Green-Gauss ghost takes).
+#include <cuda.h>            // CUtensorMap and its enums (types only; no driver library link)
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+
+#include "gks_internal.h"
+#include "gks_side3.cuh"
+
+namespace gks {
+namespace {
+
+constexpr int NWO = 10;                 // row warps per CTA
+constexpr int NWARP = NWO + 2;          // plus the halo warps H0 (below) and H1 (above)
+constexpr int NTH = NWARP * 32;
+constexpr int TCOLS = 64;               // columns per CTA (two per lane)
+constexpr int TW = 72;                  // staged columns X0-4 .. X0+67 (16-byte chunks)
+constexpr int NR = NWO + 4;             // staged rows y0-2 .. y0+NWO+1
+constexpr int NA = 7;                   // staged arrays: Ex, Ey, Ez, Hx, Hy, Hz, eps
+constexpr int NSLOT = 5;
+constexpr unsigned FULL = 0xffffffffu;
+
+using f2 = float2;
+
+// Paired FP32 arithmetic (two cells per value).  A coefficient k is a scalar kernel parameter
+// replicated into both halves: the paired FMA then reads it straight from the constant bank,
+// whereas a float2 parameter costs an extra instruction per use.
+struct OpP {
+  static __device__ __forceinline__ f2 mul(float k, f2 x) { return __fmul2_rn(make_float2(k, k), x); }
+  static __device__ __forceinline__ f2 fma(float k, f2 x, f2 a) {
+    return __ffma2_rn(make_float2(k, k), x, a);
+  }
+  static __device__ __forceinline__ f2 add(f2 a, f2 b) { return __fadd2_rn(a, b); }
+  static __device__ __forceinline__ f2 sub(f2 a, f2 b) {
+    return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+  }
+  static __device__ __forceinline__ f2 neg(f2 a) { return __fmul2_rn(a, make_float2(-1.f, -1.f)); }
+  static __device__ __forceinline__ f2 zero() { return make_float2(0.f, 0.f); }
+};
+struct OpS {                            // scalar FP32 arithmetic
+  static __device__ __forceinline__ float mul(float k, float x) { return k * x; }
+  static __device__ __forceinline__ float fma(float k, float x, float a) { return fmaf(k, x, a); }
+  static __device__ __forceinline__ float add(float a, float b) { return a + b; }
+  static __device__ __forceinline__ float sub(float a, float b) { return a - b; }
+  static __device__ __forceinline__ float neg(float a) { return -a; }
+  static __device__ __forceinline__ float zero() { return 0.f; }
+};
+
+__device__ __forceinline__ f2 operator+(f2 a, f2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ f2 operator-(f2 a, f2 b) { return OpP::sub(a, b); }
+__device__ __forceinline__ f2 operator*(f2 a, f2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ f2 pfma(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ f2 pk(float a, float b) { return make_float2(a, b); }
+// 2 / s (the interface 1/eps_s), fast FP32 division (about 1 ulp), as the other FP32 kernels
+__device__ __forceinline__ f2 two_over(f2 s) { return pk(__fdividef(2.f, s.x), __fdividef(2.f, s.y)); }
+
+struct Side3Args {
+  const float *__restrict__ V;
+  float *__restrict__ Vout;
+  const float *__restrict__ eps;
+  const float *__restrict__ src;
+  int sx0, sx1, sy0, sy1, sz0, sz1;
+  float src_amp;
+  int nx, ny, nz;
+  int64_t pitch, plane, cstride;
+  int per[3];
+  int zchunk;
+  int *flag;
+  float k[3][kSide3K];                 // coefficient slots of the x-, y- and z-faces
+};
+
+// One staged plane in the TMA box order (array, row, column); slots start 128-byte aligned.
+struct alignas(128) PlaneSlot {
+  float a[NA][NR][TW];
+};
+
+struct SideSmem {
+  PlaneSlot V[NSLOT];                  // staged planes
+  unsigned long long bar[NSLOT];       // one mbarrier per slot
+  int err;                             // a bounded wait ran out (shared by the CTA)
+  f2 Y[NWO + 1][11][32];               // r-side y-vectors of each row (P 6, Q without Ey 5)
+  f2 F[NWO + 1][6][32];                // flux through the face above each row; [NWO]: below row 0
+  float XL[2][NWO][12];                // l-side x-vectors of column X0-1 (P 6, Q without Ex, eps)
+  float XR[2][NWO][12];                // r-side x-vectors of column X0+64
+};
+
+__device__ __forceinline__ int wrap_or_clamp(int i, int n, int periodic) {
+  if (periodic) {
+    i %= n;
+    return i < 0 ? i + n : i;
+  }
+  return i < 0 ? 0 : (i >= n ? n - 1 : i);
+}
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+constexpr unsigned kPlaneBytes = NA * NR * TW * 4;   // one staged plane (both tensor boxes)
+constexpr int kWaitLimit = 1 << 22;                 // try_wait rounds before giving up
+
+__device__ __forceinline__ void mbar_init(unsigned long long *b, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(b)), "r"(count)
+               : "memory");
+}
+// Bounded wait for the phase with parity `parity` of mbarrier b; false if the limit ran out.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *b, unsigned parity) {
+  const unsigned a = smem_u32(b);
+  for (int i = 0; i < kWaitLimit; ++i) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// One thread: the tensor copies of plane gz into slot `slot` (fields box, then eps box), both
+// completing on the slot's mbarrier.  Earlier generic-proxy reads of the slot are ordered before
+// the copies by the CTA barrier that precedes the call and the proxy fence here.
+__device__ __forceinline__ void tma_plane(SideSmem &s, const CUtensorMap *tmV,
+                                          const CUtensorMap *tmE, int slot, int x, int y,
+                                          int gz) {
+  unsigned long long *b = &s.bar[slot];
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(b)),
+               "r"(kPlaneBytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];\n" ::"r"(smem_u32(&s.V[slot].a[0][0][0])),
+      "l"(tmV), "r"(x), "r"(y), "r"(gz), "r"(0), "r"(smem_u32(b))
+      : "memory");
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(smem_u32(&s.V[slot].a[6][0][0])),
+      "l"(tmE), "r"(x), "r"(y), "r"(gz), "r"(smem_u32(b))
+      : "memory");
+}
+
+// Entries of a staged plane outside the grid (zero-filled by the copy) that the step reads:
+// on a non-reflecting axis the first ghost layer (x = -1, x = nx; y = -1, y = ny), which takes the
+// edge cell's values (the Green-Gauss ghost copy; its eps enters the boundary face's 1/eps_s),
+// copied inside the staged plane; on a periodic axis the two wrapped layers on each side, read
+// from global memory.  Deeper ghost entries only feed cells that are never stored and whose
+// face vectors are zeroed.  `nt` threads numbered `me` share the work, eight entries at a time.
+__device__ __forceinline__ void fix_plane(SideSmem &s, const Side3Args &a, int slot, int gz,
+                                          int X0, int y0, int me, int nt) {
+  // up to four tile columns and four tile rows, one byte each
+  unsigned cols = 0, rows = 0;
+  int nc = 0, nr = 0;
+  const int dx = a.per[0] ? 2 : 1, dy = a.per[1] ? 2 : 1;
+  for (int g = 1; g <= dx; ++g) {
+    const int tl = -g - (X0 - 4), th = a.nx - 1 + g - (X0 - 4);   // tile columns of x = -g, nx-1+g
+    if (tl >= 0 && tl < TW) cols |= (unsigned)tl << (8 * nc++);
+    if (th >= 0 && th < TW) cols |= (unsigned)th << (8 * nc++);
+  }
+  for (int g = 1; g <= dy; ++g) {
+    const int rl = -g - (y0 - 2), rh = a.ny - 1 + g - (y0 - 2);
+    if (rl >= 0 && rl < NR) rows |= (unsigned)rl << (8 * nr++);
+    if (rh >= 0 && rh < NR) rows |= (unsigned)rh << (8 * nr++);
+  }
+  const int n1 = NA * NR * nc, n = n1 + NA * nr * TW;
+  for (int i0 = me; i0 < n; i0 += 8 * nt) {
+    float v[8];
+    int tt[8], rr[8], aa[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int i = i0 + u * nt;
+      v[u] = 0.f;
+      aa[u] = -1;
+      if (i >= n) continue;
+      int arr, r, t;
+      if (i < n1) {
+        t = (cols >> (8 * (i % nc))) & 0xff;
+        r = (i / nc) % NR;
+        arr = i / (nc * NR);
+      } else {
+        const int j = i - n1;
+        t = j % TW;
+        r = (rows >> (8 * ((j / TW) % nr))) & 0xff;
+        arr = j / (TW * nr);
+      }
+      const int x = X0 - 4 + t, y = y0 - 2 + r;
+      const int gx = wrap_or_clamp(x, a.nx, a.per[0]), gy = wrap_or_clamp(y, a.ny, a.per[1]);
+      const int ts = gx - (X0 - 4), rs = gy - (y0 - 2);
+      if (ts >= 0 && ts < TW && rs >= 0 && rs < NR && !(a.per[0] && gx != x) &&
+          !(a.per[1] && gy != y))
+        v[u] = s.V[slot].a[arr][rs][ts];                       // clamped: inside the plane
+      else
+        v[u] = __ldg((arr < 6 ? a.V + arr * a.cstride : a.eps) + (int64_t)gz * a.plane +
+                     (int64_t)gy * a.pitch + gx);
+      tt[u] = t;
+      rr[u] = r;
+      aa[u] = arr;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (aa[u] >= 0) s.V[slot].a[aa[u]][rr[u]][tt[u]] = v[u];
+  }
+}
+
+// The own pair (both columns of the lane) of one staged row: 6 fields and eps.
+__device__ __forceinline__ void load_pair(const SideSmem &s, int slot, int r, int t, f2 v[7]) {
+#pragma unroll
+  for (int m = 0; m < NA; ++m) v[m] = *reinterpret_cast<const f2 *>(&s.V[slot].a[m][r][t]);
+}
+
+// Raw central differences of the lane's two cells in plane slot s0 (row r, tile column t of
+// the first cell), the planes below (vm) and above (vp) in registers; eps-weighted E rows.
+__device__ __forceinline__ void differences(const SideSmem &s, int s0, int r, int t,
+                                            const f2 v[7], const f2 vm[7], const f2 vp[7],
+                                            f2 d[3][6], f2 ev[3], f2 ed[3][3]) {
+#pragma unroll
+  for (int m = 0; m < 6; ++m) {
+    const float xm = s.V[s0].a[m][r][t - 1], xp = s.V[s0].a[m][r][t + 2];
+    d[0][m] = pk(v[m].y - xm, xp - v[m].x);
+    const f2 ym = *reinterpret_cast<const f2 *>(&s.V[s0].a[m][r - 1][t]);
+    const f2 yp = *reinterpret_cast<const f2 *>(&s.V[s0].a[m][r + 1][t]);
+    d[1][m] = yp - ym;
+    d[2][m] = vp[m] - vm[m];
+  }
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+    ev[m] = v[6] * v[m];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) ed[j][m] = v[6] * d[j][m];
+  }
+}
+
+// Scalar x-face vectors of one cell at tile column t, row r of plane slots (sm, s0, sp): the
+// columns left and right of the tile, computed by the halo warps.  left: the cell's l-side
+// vectors (its face at +1/2), else its r-side vectors.  out: P 6, Q without Ex 5, eps.
+__device__ __forceinline__ void halo_x_cell(const SideSmem &s, int sm, int s0, int sp, int r,
+                                            int t, const float *k, bool left, bool ghost,
+                                            float out[12]) {
+  float v[6], d[3][6], ev[3], ed[3][3];
+  const float e = s.V[s0].a[6][r][t];
+#pragma unroll
+  for (int m = 0; m < 6; ++m) {
+    v[m] = s.V[s0].a[m][r][t];
+    d[0][m] = s.V[s0].a[m][r][t + 1] - s.V[s0].a[m][r][t - 1];
+    d[1][m] = s.V[s0].a[m][r + 1][t] - s.V[s0].a[m][r - 1][t];
+    d[2][m] = s.V[sp].a[m][r][t] - s.V[sm].a[m][r][t];
+  }
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+    ev[m] = e * v[m];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) ed[j][m] = e * d[j][m];
+  }
+  float pl[6], pr[6], ql[6], qr[6];
+  side3<0, OpS>(v, d, ev, ed, k, pl, pr, ql, qr);
+#pragma unroll
+  for (int m = 0; m < 6; ++m) out[m] = ghost ? 0.f : (left ? pl[m] : pr[m]);
+#pragma unroll
+  for (int m = 1; m < 6; ++m) out[5 + m] = ghost ? 0.f : (left ? ql[m] : qr[m]);
+  out[11] = e;
+}
+
+__global__ void __launch_bounds__(NTH, 1)
+    cart3d_side_kernel(const __grid_constant__ CUtensorMap tmV,
+                       const __grid_constant__ CUtensorMap tmE, const Side3Args a) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  SideSmem &s = *reinterpret_cast<SideSmem *>(smem_raw);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int X0 = blockIdx.x * TCOLS, y0 = blockIdx.y * NWO;
+  const int z0 = blockIdx.z * a.zchunk;
+  const int z1 = min(z0 + a.zchunk, a.nz);
+  const bool owned = warp < NWO, h0 = warp == NWO, h1 = warp == NWO + 1;
+  const int r = owned ? warp + 2 : (h0 ? 1 : NWO + 2);     // tile row of this warp
+  const int y = y0 - 2 + r;                                  // its grid row
+  const int t = 4 + 2 * lane;                                // tile column of the first cell
+  const int x = X0 + 2 * lane;                               // its grid column
+  // non-reflecting ghosts (outside the grid on a non-periodic axis) carry no distributions
+  const bool yghost = !a.per[1] && (y < 0 || y >= a.ny);
+  const bool xg0 = !a.per[0] && x >= a.nx, xg1 = !a.per[0] && x + 1 >= a.nx;
+  const bool st0 = x < a.nx, st1 = x + 1 < a.nx;            // columns this lane stores
+  const float *kx = a.k[0], *ky = a.k[1], *kz = a.k[2];
+
+  // ---------------- prologue: planes z0-1 .. z0+2 staged; z-vectors of plane z0-1
+  // plane p sits in slot p mod NSLOT; it is that slot's ((p - z0 + 1) / NSLOT)-th load
+  auto slot_of = [](int p) { return (p + 2 * NSLOT) % NSLOT; };
+  auto parity_of = [z0](int p) { return (unsigned)(((p - z0 + 1) / NSLOT) & 1); };
+  auto zidx = [&a](int p) { return wrap_or_clamp(p, a.nz, a.per[2]); };
+  const bool issuer = tid == NWO * 32;                       // lane 0 of H0 issues the copies
+  const int last_plane = max(z0 + 3, z1 + 1);                // the last plane this CTA loads
+  if (tid == 0) {
+    for (int i = 0; i < NSLOT; ++i) mbar_init(&s.bar[i], 1);
+    s.err = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  if (issuer)
+    for (int p = z0 - 1; p <= z0 + 2; ++p)
+      tma_plane(s, &tmV, &tmE, slot_of(p), X0 - 4, y0 - 2, zidx(p));
+  {
+    bool ok = true;
+    for (int p = z0 - 1; p <= z0 + 2; ++p) ok &= mbar_wait(&s.bar[slot_of(p)], parity_of(p));
+    if (!ok) { s.err = 1; atomicOr(a.flag, 2); }
+    for (int p = z0 - 1; p <= z0 + 2; ++p) fix_plane(s, a, slot_of(p), zidx(p), X0, y0, tid, NTH);
+  }
+  __syncthreads();
+  if (s.err) return;                                          // nothing else is in flight
+  if (issuer) tma_plane(s, &tmV, &tmE, slot_of(z0 + 3), X0 - 4, y0 - 2, zidx(z0 + 3));
+
+  f2 Wm[7], W0[7], Wp[7];               // own pair at planes k-1, k, k+1
+  f2 Lpl[6], Lql[6];                    // l-side z-vectors of plane k-1
+  f2 B[6], Minv = pk(0.f, 0.f);         // pending update of plane k-1: V_new = B - Minv F
+  {
+    const int gz = wrap_or_clamp(z0 - 2, a.nz, a.per[2]);
+    const int gy = wrap_or_clamp(y, a.ny, a.per[1]);
+    const int c0 = wrap_or_clamp(x, a.nx, a.per[0]), c1 = wrap_or_clamp(x + 1, a.nx, a.per[0]);
+    const int64_t o = (int64_t)gz * a.plane + (int64_t)gy * a.pitch;
+#pragma unroll
+    for (int m = 0; m < NA; ++m) {
+      const float *base = (m < 6 ? a.V + m * a.cstride : a.eps) + o;
+      Wm[m] = pk(__ldg(base + c0), __ldg(base + c1));
+    }
+  }
+  load_pair(s, slot_of(z0 - 1), r, t, W0);
+  load_pair(s, slot_of(z0), r, t, Wp);
+  if (owned) {
+    f2 d[3][6], ev[3], ed[3][3], pl[6], pr[6], ql[6], qr[6];
+    differences(s, slot_of(z0 - 1), r, t, W0, Wm, Wp, d, ev, ed);
+    side3<2, OpP>(W0, d, ev, ed, kz, pl, pr, ql, qr);
+    const bool zg = !a.per[2] && z0 == 0;
+#pragma unroll
+    for (int m = 0; m < 6; ++m) {
+      Lpl[m] = zg ? pk(0.f, 0.f) : pl[m];
+      Lql[m] = zg ? pk(0.f, 0.f) : ql[m];
+      B[m] = pk(0.f, 0.f);
+    }
+  } else if (lane < NWO) {
+    // x-halo vectors of plane z0 (slots z0-1, z0, z0+1)
+    float out[12];
+    const int sm = slot_of(z0 - 1), s0 = slot_of(z0), sp = slot_of(z0 + 1);
+    if (h0) {
+      halo_x_cell(s, sm, s0, sp, lane + 2, 3, kx, true, !a.per[0] && X0 == 0, out);
+#pragma unroll
+      for (int q = 0; q < 12; ++q) s.XL[z0 & 1][lane][q] = out[q];
+    } else {
+      halo_x_cell(s, sm, s0, sp, lane + 2, 68, kx, false, !a.per[0] && X0 + TCOLS >= a.nx, out);
+#pragma unroll
+      for (int q = 0; q < 12; ++q) s.XR[z0 & 1][lane][q] = out[q];
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < NA; ++m) { Wm[m] = W0[m]; W0[m] = Wp[m]; }
+  __syncthreads();
+
+  bool bad = false;
+  const bool store_row = owned && y < a.ny;
+  // ---------------- march: plane k's x- and y-faces, the z-face below it (completing k-1)
+#pragma unroll 1
+  for (int k = z0; k <= z1; ++k) {
+    const bool last = k == z1;                 // only the z-face below plane z1 remains
+    if (issuer && !last && k + 4 <= z1 + 1)
+      tma_plane(s, &tmV, &tmE, slot_of(k + 4), X0 - 4, y0 - 2, zidx(k + 4));
+    const int s0 = slot_of(k), sp = slot_of(k + 1);
+    load_pair(s, sp, r, t, Wp);
+    f2 acc[6];
+    if (owned) {
+      f2 d[3][6], ev[3], ed[3][3];
+      differences(s, s0, r, t, W0, Wm, Wp, d, ev, ed);
+      // z: face k-1/2 = l-side of plane k-1 + r-side of plane k; completes plane k-1
+      {
+        f2 pl[6], pr[6], ql[6], qr[6];
+        side3<2, OpP>(W0, d, ev, ed, kz, pl, pr, ql, qr);
+        if (!a.per[2] && k == a.nz) {
+#pragma unroll
+          for (int m = 0; m < 6; ++m) { pr[m] = pk(0.f, 0.f); qr[m] = pk(0.f, 0.f); }
+        }
+        const f2 ie = two_over(Wm[6] + W0[6]);
+        f2 F[6];
+#pragma unroll
+        for (int m = 0; m < 6; ++m) F[m] = pfma(ie, Lql[m] + qr[m], Lpl[m] + pr[m]);
+        if (k > z0 && store_row) {
+          const int64_t o = (int64_t)(k - 1) * a.plane + (int64_t)y * a.pitch + x;
+          f2 nv[6];
+          const f2 nM = pk(-Minv.x, -Minv.y);
+#pragma unroll
+          for (int m = 0; m < 6; ++m) nv[m] = m < 3 ? pfma(nM, F[m], B[m]) : B[m] - F[m];
+          f2 sum = nv[0];
+#pragma unroll
+          for (int m = 1; m < 6; ++m) sum = sum + nv[m];
+          if (st1) {
+#pragma unroll
+            for (int m = 0; m < 6; ++m) *reinterpret_cast<f2 *>(a.Vout + m * a.cstride + o) = nv[m];
+            bad |= !(isfinite(sum.x) && isfinite(sum.y));
+          } else if (st0) {
+#pragma unroll
+            for (int m = 0; m < 6; ++m) a.Vout[m * a.cstride + o] = nv[m].x;
+            bad |= !isfinite(sum.x);
+          }
+        }
+        if (last) break;
+#pragma unroll
+        for (int m = 0; m < 6; ++m) {
+          acc[m] = pk(-F[m].x, -F[m].y);
+          Lpl[m] = pl[m];
+          Lql[m] = ql[m];
+        }
+      }
+      // x: faces x+1/2 of both cells; the second needs the r-side of the next lane's first cell
+      {
+        f2 pl[6], pr[6], ql[6], qr[6];
+        side3<0, OpP>(W0, d, ev, ed, kx, pl, pr, ql, qr);
+        if (xg0 | xg1) {                        // ghost columns past the high x side
+#pragma unroll
+          for (int m = 0; m < 6; ++m) {
+            if (xg0) { pl[m].x = 0.f; pr[m].x = 0.f; ql[m].x = 0.f; qr[m].x = 0.f; }
+            if (xg1) { pl[m].y = 0.f; pr[m].y = 0.f; ql[m].y = 0.f; qr[m].y = 0.f; }
+          }
+        }
+        const int par = k & 1;
+        float rp[6], rq[6], re;
+#pragma unroll
+        for (int m = 0; m < 6; ++m) {
+          rp[m] = __shfl_down_sync(FULL, pr[m].x, 1);
+          rq[m] = __shfl_down_sync(FULL, qr[m].x, 1);
+        }
+        re = __shfl_down_sync(FULL, W0[6].x, 1);
+        if (lane == 31) {                       // right neighbour: column X0+64 (halo warp H1)
+#pragma unroll
+          for (int m = 0; m < 6; ++m) rp[m] = s.XR[par][warp][m];
+          rq[0] = 0.f;
+#pragma unroll
+          for (int m = 1; m < 6; ++m) rq[m] = s.XR[par][warp][5 + m];
+          re = s.XR[par][warp][11];
+        }
+        const f2 ie = two_over(W0[6] + pk(W0[6].y, re));
+        f2 F[6];
+#pragma unroll
+        for (int m = 0; m < 6; ++m)
+          F[m] = pfma(ie, ql[m] + pk(qr[m].y, rq[m]), pl[m] + pk(pr[m].y, rp[m]));
+        float Fm[6];
+#pragma unroll
+        for (int m = 0; m < 6; ++m) Fm[m] = __shfl_up_sync(FULL, F[m].y, 1);
+        if (lane == 0) {                        // left face of the tile: column X0-1 (H0)
+          const float ie0 = __fdividef(2.f, s.XL[par][warp][11] + W0[6].x);
+#pragma unroll
+          for (int m = 0; m < 6; ++m) {
+            const float lq = m == 0 ? 0.f : s.XL[par][warp][5 + m];
+            Fm[m] = fmaf(ie0, lq + qr[m].x, s.XL[par][warp][m] + pr[m].x);
+          }
+        }
+#pragma unroll
+        for (int m = 0; m < 6; ++m) acc[m] = acc[m] + (F[m] - pk(Fm[m], F[m].x));
+      }
+      // y: r-side vectors published for the row below; the face above waits for the barrier
+      f2 pl[6], pr[6], ql[6], qr[6];
+      side3<1, OpP>(W0, d, ev, ed, ky, pl, pr, ql, qr);
+      if (yghost) {
+#pragma unroll
+        for (int m = 0; m < 6; ++m) { pl[m] = pr[m] = ql[m] = qr[m] = pk(0.f, 0.f); }
+      }
+#pragma unroll
+      for (int m = 0; m < 6; ++m) s.Y[warp][m][lane] = pr[m];
+      s.Y[warp][6][lane] = qr[0];
+#pragma unroll
+      for (int m = 2; m < 6; ++m) s.Y[warp][5 + m][lane] = qr[m];
+      __syncthreads();                          // B1: r-side vectors of every row
+      {
+        const f2 eu = *reinterpret_cast<const f2 *>(&s.V[s0].a[6][r + 1][t]);
+        const f2 ie = two_over(W0[6] + eu);
+        f2 Rp[6], Rq[6];
+#pragma unroll
+        for (int m = 0; m < 6; ++m) Rp[m] = s.Y[warp + 1][m][lane];
+        Rq[0] = s.Y[warp + 1][6][lane];
+        Rq[1] = pk(0.f, 0.f);
+#pragma unroll
+        for (int m = 2; m < 6; ++m) Rq[m] = s.Y[warp + 1][5 + m][lane];
+#pragma unroll
+        for (int m = 0; m < 6; ++m) {
+          const f2 F = pfma(ie, ql[m] + Rq[m], pl[m] + Rp[m]);
+          s.F[warp][m][lane] = F;
+          acc[m] = acc[m] + F;
+        }
+      }
+    } else {
+      // halo warps: the y-vectors of their row, and the x-halo columns of plane k+1; first the
+      // grid-edge entries of plane k+2, which landed at the last barrier
+      if (last) break;
+      if (k > z0) {
+        fix_plane(s, a, slot_of(k + 2), zidx(k + 2), X0, y0, tid - NWO * 32, 64);
+        asm volatile("bar.sync 1, 64;\n" ::: "memory");
+      }
+      f2 d[3][6], ev[3], ed[3][3], pl[6], pr[6], ql[6], qr[6];
+      differences(s, s0, r, t, W0, Wm, Wp, d, ev, ed);
+      side3<1, OpP>(W0, d, ev, ed, ky, pl, pr, ql, qr);
+      if (yghost) {
+#pragma unroll
+        for (int m = 0; m < 6; ++m) { pl[m] = pr[m] = ql[m] = qr[m] = pk(0.f, 0.f); }
+      }
+      if (h1) {
+#pragma unroll
+        for (int m = 0; m < 6; ++m) s.Y[NWO][m][lane] = pr[m];
+        s.Y[NWO][6][lane] = qr[0];
+#pragma unroll
+        for (int m = 2; m < 6; ++m) s.Y[NWO][5 + m][lane] = qr[m];
+      }
+      if (lane < NWO) {
+        float out[12];
+        const int sm = s0, sc = sp, sn = slot_of(k + 2);
+        if (h0) {
+          halo_x_cell(s, sm, sc, sn, lane + 2, 3, kx, true, !a.per[0] && X0 == 0, out);
+#pragma unroll
+          for (int q = 0; q < 12; ++q) s.XL[(k + 1) & 1][lane][q] = out[q];
+        } else {
+          halo_x_cell(s, sm, sc, sn, lane + 2, 68, kx, false, !a.per[0] && X0 + TCOLS >= a.nx,
+                      out);
+#pragma unroll
+          for (int q = 0; q < 12; ++q) s.XR[(k + 1) & 1][lane][q] = out[q];
+        }
+      }
+      __syncthreads();                          // B1
+      if (h0) {                                 // face below row y0
+        const f2 eu = *reinterpret_cast<const f2 *>(&s.V[s0].a[6][r + 1][t]);
+        const f2 ie = two_over(W0[6] + eu);
+#pragma unroll
+        for (int m = 0; m < 6; ++m) {
+          f2 Rq = pk(0.f, 0.f);
+          if (m == 0) Rq = s.Y[0][6][lane];
+          if (m >= 2) Rq = s.Y[0][5 + m][lane];
+          s.F[NWO][m][lane] = pfma(ie, ql[m] + Rq, pl[m] + s.Y[0][m][lane]);
+        }
+      }
+    }
+    if (k + 3 <= last_plane && !mbar_wait(&s.bar[slot_of(k + 3)], parity_of(k + 3))) {
+      s.err = 1;                                // plane k+3 never landed
+      atomicOr(a.flag, 2);
+    }
+    __syncthreads();                            // B2: face fluxes; plane k+3 visible
+    if (s.err) {                                // leave together; wait (bounded) for the copy
+      if (k + 4 <= last_plane) mbar_wait(&s.bar[slot_of(k + 4)], parity_of(k + 4));
+      break;
+    }
+    if (owned) {
+      const int below = warp == 0 ? NWO : warp - 1;
+      f2 nv_src = pk(0.f, 0.f);
+      if (a.src && y >= a.sy0 && y < a.sy1 && k >= a.sz0 && k < a.sz1) {
+        const int64_t o = (int64_t)k * a.plane + (int64_t)y * a.pitch;
+        const float s0v = (x >= a.sx0 && x < a.sx1) ? a.src[o + x] : 0.f;
+        const float s1v = (x + 1 >= a.sx0 && x + 1 < a.sx1) ? a.src[o + x + 1] : 0.f;
+        nv_src = pk(a.src_amp * s0v, a.src_amp * s1v);
+      }
+      Minv = pk(__fdividef(1.f, W0[6].x), __fdividef(1.f, W0[6].y));
+#pragma unroll
+      for (int m = 0; m < 6; ++m) {
+        f2 am = acc[m] - s.F[below][m][lane];
+        if (m == 2) am = am + nv_src;
+        B[m] = m < 3 ? pfma(pk(-Minv.x, -Minv.y), am, W0[m]) : W0[m] - am;
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < NA; ++m) { Wm[m] = W0[m]; W0[m] = Wp[m]; }
+  }
+  if (__any_sync(FULL, bad) && lane == 0) atomicOr(a.flag, 1);
+}
+
+}  // namespace
+
+namespace {
+
+// cuTensorMapEncodeTiled from the driver through the runtime (no link against the driver
+// library); null if the driver does not provide it.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+// Tensor map of `rank` dims over a [ncomp][nz][ny][pitch] FP32 array: dims (nx, ny, nz[, 6]),
+// box (TW, NR, 1[, 6]); entries past the grid read as zero.
+bool encode_map(CUtensorMap *m, const float *base, const CartGeom &g, int rank) {
+  const cuuint64_t dim[4] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)g.nz, 6};
+  const cuuint64_t stride[3] = {(cuuint64_t)g.pitch * 4, (cuuint64_t)g.plane * 4,
+                                (cuuint64_t)g.cstride * 4};
+  const cuuint32_t box[4] = {TW, NR, 1, 6};
+  const cuuint32_t estride[4] = {1, 1, 1, 1};
+  return tensor_map_encoder()(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, rank,
+                              const_cast<float *>(base), dim, stride, box, estride,
+                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+bool cart3d_side_supported(const CartGeom &g, const CartStepArgs &a, bool fp64) {
+  if (fp64 || a.mu || a.limiter) return false;
+  if (!tensor_map_encoder()) return false;
+  for (int k = 0; k < 6; ++k)
+    if (g.pec[k]) return false;
+  return g.dim == 3;
+}
+
+cudaError_t launch_cart3d_side(const CartGeom &g, const CartStepArgs &a, cudaStream_t st) {
+  Side3Args p;
+  p.V = static_cast<const float *>(a.V);
+  p.Vout = static_cast<float *>(a.Vout);
+  p.eps = static_cast<const float *>(a.eps);
+  p.src = static_cast<const float *>(a.src);
+  p.sx0 = a.src_box[0]; p.sx1 = a.src_box[1];
+  p.sy0 = a.src_box[2]; p.sy1 = a.src_box[3];
+  p.sz0 = a.src_box[4]; p.sz1 = a.src_box[5];
+  p.src_amp = float(a.src_amp);
+  p.nx = g.nx; p.ny = g.ny; p.nz = g.nz;
+  p.pitch = g.pitch; p.plane = g.plane; p.cstride = g.cstride;
+  for (int d = 0; d < 3; ++d) p.per[d] = g.periodic[d];
+  p.flag = a.flag;
+  for (int A = 0; A < 3; ++A) {
+    double k[kSide3K];
+    side3_coefficients(a.C, g.h, a.c, A, k);
+    for (int i = 0; i < kSide3K; ++i) p.k[A][i] = float(k[i]);
+  }
+  const int gx = (g.nx + TCOLS - 1) / TCOLS, gy = (g.ny + NWO - 1) / NWO;
+  const int smem = (int)sizeof(SideSmem);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(cart3d_side_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    attr = true;
+  }
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  // z chunks: one CTA per SM; pick the chunk count that fills whole waves best, counting the
+  // prologue and the closing z-face (about one plane of work) as lost
+  const int64_t tiles = (int64_t)gx * gy;
+  int zchunks = 1;
+  double best = -1.0;
+  for (int zc = 1; zc <= 64 && zc <= g.nz; ++zc) {
+    const int len = (g.nz + zc - 1) / zc;
+    const int nzc = (g.nz + len - 1) / len;
+    const int64_t ctas = tiles * nzc;
+    const double waves = (double)((ctas + sms - 1) / sms);
+    const double eff = (double)ctas / (waves * sms) * (double)g.nz / (double)(nzc * (len + 1));
+    if (eff > best + 1e-9) { best = eff; zchunks = nzc; }
+  }
+  p.zchunk = (g.nz + zchunks - 1) / zchunks;
+  zchunks = (g.nz + p.zchunk - 1) / p.zchunk;
+  CUtensorMap tmV, tmE;
+  if (!encode_map(&tmV, p.V, g, 4) || !encode_map(&tmE, p.eps, g, 3)) return cudaErrorInvalidValue;
+  dim3 grid(gx, gy, zchunks);
+  cart3d_side_kernel<<<grid, NTH, smem, st>>>(tmV, tmE, p);
+  return cudaGetLastError();
+}
+
+}  // namespace gks

@@ -129,6 +129,10 @@ cudaError_t launch_cart2d_step(const CartGeom &g, const CartStepArgs &a, bool fp
                                cudaStream_t st);
 cudaError_t launch_cart3d_step(const CartGeom &g, const CartStepArgs &a, bool fp64,
                                cudaStream_t st);
+// FP32 3-D step with mu = 1, periodic or non-reflecting sides, no limiter (gks_cart3d_side.cu):
+// the side-split flux; launch_cart3d_step dispatches to it when cart3d_side_supported().
+bool cart3d_side_supported(const CartGeom &g, const CartStepArgs &a, bool fp64);
+cudaError_t launch_cart3d_side(const CartGeom &g, const CartStepArgs &a, cudaStream_t st);
 // 2-D TM step with divergence cleaning (state Ez, Hx, Hy, psi; mu = 1).
 // Divergence-cleaning system on a 3-D grid: V = (E, H, phi, psi), 8 components.
 cudaError_t launch_cart3d_phm_step(const CartGeom &g, const CartStepArgs &a, double chi,
@@ -140,6 +144,10 @@ cudaError_t launch_user_to_cart(const CartGeom &g, int ncomp, const double *user
 cudaError_t launch_cart_to_user(const CartGeom &g, int ncomp, const void *src, double *user,
                                 bool fp64, cudaStream_t st);
 cudaError_t launch_fill(void *dst, int64_t n, double value, bool fp64, cudaStream_t st);
+// Halo layers of a slab (gks_create_slab): for every component c < ncomp,
+// dst[c * dstride + i] = src[c * sstride + i] (add: +=) for i < count.
+cudaError_t launch_halo_copy(const void *src, int64_t sstride, void *dst, int64_t dstride,
+                             int64_t count, int ncomp, bool add, bool fp64, cudaStream_t st);
 // One 2-D component (pitched layout) = a row-major FP64 box of w x h cells at (x0, y0).
 cudaError_t launch_box_to_cart(const double *box, void *dst, int x0, int w, int y0, int h,
                                int64_t pitch, bool fp64, cudaStream_t st);
@@ -196,5 +204,10 @@ struct gks_ctx {
   int64_t nd = 0;
   int dbox[4] = {0, 0, 0, 0};
   double *obj = nullptr;          // (sum, Kahan compensation)
+  // slab of a grid split across ranks (gks_create_slab): layers along the slowest axis (y in
+  // 2-D, z in 3-D); the local grid holds two ghost layers beyond each shared side
+  bool slab = false;
+  int own0 = 0, own1 = 0;         // owned layers [own0, own1) of the local grid
+  int shared[2] = {0, 0};         // the low / high side borders another rank
   std::string err;
 };

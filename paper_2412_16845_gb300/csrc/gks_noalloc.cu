@@ -8,8 +8,6 @@
 // GPU that loads the library holds until the process exits.
 #include <cuda_runtime.h>
 
-#include <mutex>
-
 #include "gks_internal.h"
 
 namespace {
@@ -64,22 +62,14 @@ __global__ void energy_finish_kernel(const double *__restrict__ partials, int nb
   if (threadIdx.x == 0) *out = red[0] * scale;
 }
 
-// Device address of g_energy_partials, looked up once per device with that device current.
-// In host code the array's name only stands for it; only this address may go to a kernel.
-constexpr int kMaxDevices = 64;
-double *g_partials_addr[kMaxDevices] = {nullptr};
-std::mutex g_setup_mutex;
-
+// Device address of g_energy_partials on the current device.  In host code the array's name
+// only stands for it; only this address may go to a kernel.  It is looked up on every call, so a
+// device reset (after which the module, and the array with it, is loaded again at a new address)
+// cannot leave a stale pointer behind.
 gks_status partials_for_current_device(double **out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return GKS_E_CUDA;
-  std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_partials_addr[dev]) {
-    void *p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_energy_partials) != cudaSuccess || !p) return GKS_E_CUDA;
-    g_partials_addr[dev] = static_cast<double *>(p);
-  }
-  *out = g_partials_addr[dev];
+  void *p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_energy_partials) != cudaSuccess || !p) return GKS_E_CUDA;
+  *out = static_cast<double *>(p);
   return GKS_OK;
 }
 
@@ -93,6 +83,9 @@ extern "C" gks_status gks_energy_noalloc(int32_t precision, int32_t dim, int64_t
   if (!fields || !eps || !out) return GKS_E_ARG;
   if (n_cells <= 0 || n_cells > kMaxCells) return GKS_E_ARG;   // beyond the scratch capacity
   if (!(cell_volume > 0.0)) return GKS_E_ARG;
+  // An error that earlier work left pending on this thread belongs to that work: leave it in
+  // place for its owner and launch nothing (launch errors of this call would be hidden by it).
+  if (cudaPeekAtLastError() != cudaSuccess) return GKS_E_CUDA;
   double *partials = nullptr;
   gks_status s = partials_for_current_device(&partials);
   if (s != GKS_OK) return s;
@@ -108,5 +101,6 @@ extern "C" gks_status gks_energy_noalloc(int32_t precision, int32_t dim, int64_t
         static_cast<const float *>(fields), static_cast<const float *>(eps),
         static_cast<const float *>(mu), n_cells, ncomp, ne, partials);
   energy_finish_kernel<<<1, kThreads, 0, st>>>(partials, blocks, 0.5 * cell_volume, out);
+  // no error was pending before the launches, so one pending now is theirs: report and clear it
   return cudaGetLastError() == cudaSuccess ? GKS_OK : GKS_E_CUDA;
 }

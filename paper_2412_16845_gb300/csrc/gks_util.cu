@@ -192,6 +192,34 @@ cudaError_t launch_fill(void *dst, int64_t n, double value, bool fp64, cudaStrea
   return cudaGetLastError();
 }
 
+template <typename T>
+__global__ void halo_copy_kernel(const T *__restrict__ src, int64_t sstride, T *__restrict__ dst,
+                                 int64_t dstride, int64_t count, int ncomp, bool add) {
+  const int c = blockIdx.y;
+  if (c >= ncomp) return;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const T v = src[c * sstride + i];
+    if (add) dst[c * dstride + i] += v;
+    else dst[c * dstride + i] = v;
+  }
+}
+
+cudaError_t launch_halo_copy(const void *src, int64_t sstride, void *dst, int64_t dstride,
+                             int64_t count, int ncomp, bool add, bool fp64, cudaStream_t st) {
+  if (count <= 0 || ncomp <= 0) return cudaSuccess;
+  const dim3 grid((unsigned)std::min<int64_t>((count + 255) / 256, 1024), (unsigned)ncomp);
+  if (fp64)
+    halo_copy_kernel<double><<<grid, 256, 0, st>>>(static_cast<const double *>(src), sstride,
+                                                   static_cast<double *>(dst), dstride, count,
+                                                   ncomp, add);
+  else
+    halo_copy_kernel<float><<<grid, 256, 0, st>>>(static_cast<const float *>(src), sstride,
+                                                  static_cast<float *>(dst), dstride, count,
+                                                  ncomp, add);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_cart_energy(const CartGeom &g, int ncomp, const void *V, const void *eps,
                                const void *mu, bool fp64, double *partials, int npart,
                                double *out, cudaStream_t st) {

@@ -35,6 +35,14 @@ class GksError(RuntimeError):
         self.status = status
 
 
+GKS_HALO_OWNED, GKS_HALO_GHOST = 0, 1
+
+
+class gks_slab_desc(ctypes.Structure):
+    _fields_ = [("begin", ctypes.c_int64), ("end", ctypes.c_int64),
+                ("shared_lo", ctypes.c_int32), ("shared_hi", ctypes.c_int32)]
+
+
 class gks_mesh_desc(ctypes.Structure):
     _fields_ = [
         ("dim", ctypes.c_int32), ("kind", ctypes.c_int32), ("precision", ctypes.c_int32),
@@ -89,6 +97,13 @@ SIGNATURES = {
     "gks_energy_noalloc": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
                                           ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "gks_create_slab": (ctypes.c_int, [ctypes.POINTER(gks_mesh_desc),
+                                       ctypes.POINTER(gks_slab_desc), ctypes.POINTER(_CTX)]),
+    "gks_halo_bytes": (ctypes.c_int, [_CTX, _I64]),
+    "gks_halo_export": (ctypes.c_int, [_CTX, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                       ctypes.c_void_p]),
+    "gks_halo_import": (ctypes.c_int, [_CTX, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                       ctypes.c_void_p, ctypes.c_int32]),
     "gks_get_info": (ctypes.c_int, [_CTX, _D, _D, _I64, _I64, _D]),
     "gks_get_launch_count": (ctypes.c_int, [_CTX, _I64]),
     "gks_last_error": (ctypes.c_char_p, [_CTX]),
@@ -138,6 +153,30 @@ def gks_create_mesh(desc: gks_mesh_desc):
     if st != GKS_OK:
         raise GksError(st, "gks_create_mesh rejected the description")
     return ctx
+
+
+def gks_create_slab(desc: gks_mesh_desc, slab: gks_slab_desc):
+    ctx = _CTX()
+    st = load_library().gks_create_slab(ctypes.byref(desc), ctypes.byref(slab), ctypes.byref(ctx))
+    if st != GKS_OK:
+        raise GksError(st, "gks_create_slab rejected the description")
+    return ctx
+
+
+def gks_halo_bytes(ctx):
+    v = ctypes.c_int64()
+    _check(ctx, load_library().gks_halo_bytes(ctx, ctypes.byref(v)))
+    return v.value
+
+
+def gks_halo_export(ctx, side, layers, state_ptr, buf_ptr):
+    _check(ctx, load_library().gks_halo_export(ctx, int(side), int(layers), state_ptr or None,
+                                               buf_ptr))
+
+
+def gks_halo_import(ctx, side, layers, state_ptr, buf_ptr, add=False):
+    _check(ctx, load_library().gks_halo_import(ctx, int(side), int(layers), state_ptr or None,
+                                               buf_ptr, 1 if add else 0))
 
 
 def gks_set_materials(ctx, eps, mu=None):

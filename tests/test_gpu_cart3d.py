@@ -65,8 +65,9 @@ def _oracle(w, steps, kappa, c):
      (0.05, 0.03, 0.04)),
 ])
 def test_random_grids(precision, kappa, case):
-    """Ragged tiles (the CTA updates 30 x 6 columns), mixed boundaries, random eps and mu,
-    scattered source, box cells, kappa in {0, 0.05, 1}; 8 steps."""
+    """Small ragged grids, mixed boundaries, random eps and mu, scattered source, box cells,
+    kappa in {0, 0.05, 1}; 8 steps.  (FP32 without mu runs the side-split kernel, whose CTA owns
+    64 columns x 10 rows; the others run the staged-plane kernel.)"""
     n, bc, with_mu, with_src, h = case
     w = _random3(n, bc, seed=sum(n), with_mu=with_mu, with_src=with_src, h=h)
     out, info = _gpu(w, 8, precision, kappa)
@@ -74,13 +75,37 @@ def test_random_grids(precision, kappa, case):
     assert rel_l2(out, ref) <= TOL[precision], rel_l2(out, ref)
 
 
+_WIDE_REF = {}
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("kappa", [0.0, 0.05])
+@pytest.mark.parametrize("case", [
+    ((66, 31, 37), ("nrbc",) * 6, False),
+    ((70, 23, 29), ("nrbc", "nrbc", "periodic", "periodic", "periodic", "periodic"), True),
+])
+def test_wide_ragged_grids(precision, kappa, case):
+    """Grids spanning several CTAs in every direction: two x-tiles with a ragged second one,
+    y > 28 rows (three to four row tiles, the last ragged), z split into several chunks; random
+    eps, a scattered source on the first grid; 4 steps against the oracle."""
+    n, bc, with_src = case
+    w = _random3(n, bc, seed=sum(n) + 11, with_src=with_src)
+    out, info = _gpu(w, 4, precision, kappa)
+    key = (n, kappa)
+    if key not in _WIDE_REF:
+        _WIDE_REF[key] = _oracle(w, 4, kappa, info["c"])
+    ref = _WIDE_REF[key]
+    assert rel_l2(out, ref) <= TOL[precision], rel_l2(out, ref)
+
+
 @pytest.mark.parametrize("n", [(1, 1, 1), (2, 3, 4), (5, 1, 3)])
 @pytest.mark.parametrize("bc", ["periodic", "nrbc"])
-def test_degenerate_grids(n, bc):
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_degenerate_grids(n, bc, precision):
     w = _random3(n, (bc,) * 6, seed=3 + sum(n))
-    out, info = _gpu(w, 5, "fp64")
+    out, info = _gpu(w, 5, precision)
     ref = _oracle(w, 5, 0.0, info["c"])
-    assert rel_l2(out, ref) <= 1e-12
+    assert rel_l2(out, ref) <= TOL[precision]
 
 
 def test_sphere_workload_reduced():

@@ -34,11 +34,23 @@ def _cases():
     w3 = wl.CartWorkload(name="e3", dim=3, n=n3, lo=(0.0,) * 3, hi=(1.0, 9 / 11, 7 / 11),
                          bc=("nrbc",) * 6, cfl=0.4, steps=0, eps=rng.uniform(1, 3, f3.shape[1]),
                          mu=None, fields0=f3)
-    return [w2, w3]
+    # many 4096-cell blocks with a partly filled last one: 300 x 301 = 90,300 cells (23 blocks)
+    # and 64^3 = 262,144 cells (64 full blocks)
+    nb = (300, 301)
+    fb = rng.standard_normal((3, nb[0] * nb[1]))
+    wb = wl.CartWorkload(name="e2b", dim=2, n=nb, lo=(0.0, 0.0), hi=(1.0, 301 / 300),
+                         bc=("nrbc",) * 4, cfl=0.5, steps=0, eps=rng.uniform(1, 3, fb.shape[1]),
+                         mu=None, fields0=fb)
+    nc = (64, 64, 64)
+    fc = rng.standard_normal((6, int(np.prod(nc))))
+    wc = wl.CartWorkload(name="e3b", dim=3, n=nc, lo=(0.0,) * 3, hi=(1.0,) * 3, bc=("nrbc",) * 6,
+                         cfl=0.4, steps=0, eps=rng.uniform(1, 3, fc.shape[1]),
+                         mu=rng.uniform(1, 2, fc.shape[1]), fields0=fc)
+    return [w2, w3, wb, wc]
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-@pytest.mark.parametrize("k", [0, 1])
+@pytest.mark.parametrize("k", [0, 1, 2, 3])
 def test_noalloc_energy_matches_gks_energy(precision, k):
     import torch
     w = _cases()[k]
