@@ -11,7 +11,10 @@ e2e        the same metric through the C ABI from host memory: gks_write_fields 
            host fields) + gks_step(K) + gks_read_fields, wall-clocked.
 roofline   the fused step kernel against the measured HBM copy bandwidth.
 cpu_baseline  the FP64 oracle on a bounded sample of the workload on the host cores.
-With N > 1 (torchrun) every rank runs its own replica of the workload (weak scaling).
+With N > 1 (torchrun) the grid is split into N slabs of its slowest axis (y in 2-D, z in 3-D),
+one per GPU, each with two ghost layers per shared side refreshed from the neighbours over NCCL
+after every step (strong scaling: the same grid on more GPUs); the 2-D headline and the 3-D leg
+run that way, the other legs only at N = 1.
 """
 from __future__ import annotations
 
@@ -61,6 +64,50 @@ def _profiled_traffic():
     if not m or not h or h.group(1) != _kernel_hash():
         return None
     return float(m.group(1))
+
+
+def sharded_steps(w, precision, steps, warmup, world, rank, stream, e2e=False):
+    """Time `steps` steps of the workload split into `world` slabs (this rank's slab), with the
+    halo exchange after every step.  Returns (ms over the timed steps, this rank's launches,
+    e2e wall seconds or None).  e2e: gks_write_fields of the slab's fields from pinned host
+    memory + steps + gks_read_fields, wall clock."""
+    import torch
+    import torch.distributed as dist
+
+    from paper_2412_16845_gb300 import gks as G
+    from paper_2412_16845_gb300 import slab
+
+    ax = w.dim - 1
+    plan = slab.partition(w.n[ax], world, rank, w.bc[2 * ax] == "periodic")
+    s = slab.SlabSolver(w, plan, precision=precision, backend="nccl", stream=stream.cuda_stream)
+    s.step(warmup)
+    torch.cuda.synchronize()
+    dist.barrier()
+    L0 = G.gks_get_launch_count(s.ctx)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    s.step(steps)
+    b.record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    ms = a.elapsed_time(b)
+    launches = G.gks_get_launch_count(s.ctx) - L0
+    wall = None
+    if e2e:
+        f = np.asarray(w.fields0)[:, s.ids]
+        hin = torch.empty(f.shape, dtype=torch.float64, pin_memory=True)
+        hin.copy_(torch.from_numpy(np.ascontiguousarray(f)))
+        hout = torch.empty(f.shape, dtype=torch.float64, pin_memory=True)
+        dist.barrier()
+        t0 = time.perf_counter()
+        G.gks_write_fields(s.ctx, hin.numpy())
+        s.step(steps)
+        G.gks_read_fields(s.ctx, hout.numpy())
+        wall = time.perf_counter() - t0
+        dist.barrier()
+    s.close()
+    return ms, launches, wall
 
 
 def max_over_ranks(x, world, device="cuda"):
@@ -172,7 +219,8 @@ print(json.dumps({{"cells": b * b, "steps": steps, "seconds": el}}))
                 "sample": "failed: " + r.stderr[-300:]}
     d = json.loads(r.stdout.strip().splitlines()[-1])
     v = d["cells"] * d["steps"] / d["seconds"] / 1e9
-    out = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+    out = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "cpu_model": cpu_model(),
+           "nproc": os.cpu_count(),
            "sample": f"{d['steps']} FP64 oracle steps on a {block}x{block} block of the 4096^2 "
                      f"cylinder workload around the source ({d['seconds']:.1f} s, numpy single "
                      f"thread)"}
@@ -202,6 +250,102 @@ print(json.dumps({{"cells": b * b, "steps": steps, "seconds": el}}))
     return out
 
 
+# reduced versions of the three timed workloads, whose FP32 GPU results the oracle leg checks
+REDUCED = {"tm2d_cylinders": (96, 60), "maxwell3d_sphere": (20, 30), "tets_sphere": (8, 25)}
+
+
+def reduced_gpu_results(stream_ptr, path):
+    """FP32 (and FP64) GPU fields of the reduced workloads, saved for the oracle leg."""
+    from paper_2412_16845_gb300 import workloads as wl
+    from paper_2412_16845_gb300.gks import GKSSolver
+    out = {}
+    n2, k2 = REDUCED["tm2d_cylinders"]
+    n3, k3 = REDUCED["maxwell3d_sphere"]
+    m4, k4 = REDUCED["tets_sphere"]
+    for prec in ("fp32", "fp64"):
+        s = GKSSolver.from_workload(wl.config2_cylinders_tm(n=n2, steps=k2), precision=prec,
+                                    stream=stream_ptr)
+        s.step(k2)
+        out[f"tm2d_{prec}"] = s.read_fields()
+        s.close()
+        s = GKSSolver.from_workload(wl.config3_sphere_3d(n=n3, steps=k3), precision=prec,
+                                    stream=stream_ptr)
+        s.step(k3)
+        out[f"maxwell3d_{prec}"] = s.read_fields()
+        s.close()
+        s = GKSSolver.from_tet_workload(wl.config4_tets(m=m4, steps=k4), precision=prec,
+                                        stream=stream_ptr)
+        s.step(k4)
+        out[f"tets_{prec}"] = s.read_fields()
+        s.close()
+    np.savez(path, **out)
+
+
+def oracle_errors(path):
+    """The oracle leg's second job: the FP64 oracle on the reduced workloads against the GPU
+    results saved at `path` (relative L2 over all components and cells, volume-weighted on
+    tets), in a fresh process like the timing."""
+    code = f"""
+import sys, json, numpy as np
+sys.path.insert(0, {ROOT!r})
+from oracle import gks_oracle as go
+from paper_2412_16845_gb300 import workloads as wl
+R = {REDUCED!r}
+g = np.load({path!r})
+def rel(a, b, w=None):
+    w = np.ones(b.shape[1]) if w is None else w
+    return float(np.sqrt(np.sum(w * (a - b) ** 2) / np.sum(w * b * b)))
+res = {{}}
+n2, k2 = R["tm2d_cylinders"]
+w = wl.config2_cylinders_tm(n=n2, steps=k2)
+m = go.cartesian_mesh(w.n, w.lo, w.hi, w.bc)
+ref, _ = go.run(m, w.fields0, w.eps, None, w.cfl, k2, jz_mask=w.jz_mask, src=w.src)
+res["tm2d_cylinders"] = {{"grid": [n2, n2], "steps": k2, "fp32": rel(g["tm2d_fp32"], ref),
+                          "fp64": rel(g["tm2d_fp64"], ref)}}
+n3, k3 = R["maxwell3d_sphere"]
+w = wl.config3_sphere_3d(n=n3, steps=k3)
+m = go.cartesian_mesh(w.n, w.lo, w.hi, w.bc)
+ref, _ = go.run(m, w.fields0, w.eps, None, w.cfl, k3)
+res["maxwell3d_sphere"] = {{"grid": [n3, n3, n3], "steps": k3,
+                            "fp32": rel(g["maxwell3d_fp32"], ref),
+                            "fp64": rel(g["maxwell3d_fp64"], ref)}}
+m4, k4 = R["tets_sphere"]
+w = wl.config4_tets(m=m4, steps=k4)
+m = go.tet_mesh(w.vert, w.tet)
+ref, _ = go.run(m, w.fields0, w.eps, None, w.cfl, k4, c=1.0)
+res["tets_sphere"] = {{"tets": int(w.tet.shape[0]), "steps": k4,
+                       "fp32": rel(g["tets_fp32"], ref, m.vol), "fp64": rel(g["tets_fp64"], ref, m.vol)}}
+print(json.dumps(res))
+"""
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = "1"
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                       timeout=900)
+    if r.returncode != 0:
+        return {"failed": r.stderr[-300:]}
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), for the baseline's record."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith(("model name", "cpu part")):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.machine()
+
+
 def run_reference(args, rank):
     """The reference arm: the FP64 oracle as it stands, on the host cores."""
     if rank != 0:
@@ -225,6 +369,71 @@ def run_reference(args, rank):
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "wall_s": el}
     print(json.dumps(line))
+
+
+def run_sharded(args, w, world, rank, local, stream):
+    """N > 1: the 2-D headline and the 3-D leg on slabs (strong scaling); one JSON line."""
+    import torch
+    from paper_2412_16845_gb300 import workloads as wl
+
+    n = args.n
+    ncell = n * n
+    sampler = ClockSampler(local)
+    if rank == 0:
+        sampler.start()
+    ms, launches, wall = sharded_steps(w, "fp32", args.steps, args.warmup, world, rank, stream,
+                                       e2e=True)
+    clocks = sampler.stop() if rank == 0 else None
+    ms = max_over_ranks(ms, world)
+    wall = max_over_ranks(wall, world)
+    value = ncell * args.steps / (ms * 1e-3) / 1e9
+    e2e = ncell * args.steps / wall / 1e9
+    three = None
+    if args.with_3d:
+        w3 = wl.config3_sphere_3d(n=args.n3, steps=500)
+        ms3, _, _ = sharded_steps(w3, "fp32", args.steps3, 3, world, rank, stream)
+        ms3 = max_over_ranks(ms3, world) / args.steps3
+        three = {"workload": f"maxwell3d_sphere_{args.n3}", "steps_timed": args.steps3,
+                 "slabs": world, "value_fp32": w3.ncell / (ms3 * 1e-3) / 1e9,
+                 "ms_per_step_fp32": ms3,
+                 "hbm_frac_fp32_per_gpu": 52 * w3.ncell / world / (ms3 * 1e-3) / 1e9 / _peaks()[0],
+                 "algorithmic_bytes_per_cell_step": 52}
+    if rank == 0:
+        hbm, how = _peaks()
+        ms_step = ms / args.steps
+        achieved = BYTES_PER_CELL_STEP["fp32"] * ncell / world / (ms_step * 1e-3) / 1e9
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"tm2d_cylinders_{n}", "grid": [n, n], "cylinders": 32,
+                       "bc": "nonreflecting", "cfl": 0.5, "source": "line, f0=20",
+                       "steps_config": 2000, "precision": "fp32",
+                       "l2": "inputs larger than L2 per GPU for N <= 3 (state+eps read+write "
+                             f"{BYTES_PER_CELL_STEP['fp32'] * ncell / world / 1e6:.0f} MB per GPU)",
+                       "parallelism": f"slabs x{world} (y), 2 ghost rows per side, NCCL "
+                                      "send/recv after every step"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "peak_source": how, "traffic": None,
+                         "kernel": "cart2d_step_kernel_p (FP32, mu = 1), per GPU, halo "
+                                   "exchange included in the time",
+                         "algorithmic_bytes_per_launch": BYTES_PER_CELL_STEP["fp32"] * ncell // world},
+            "e2e": {"value": e2e, "unit": UNIT,
+                    "h2d_bytes_per_step": 8 * 3 * ncell / args.steps,
+                    "d2h_bytes_per_step": 8 * 3 * ncell / args.steps,
+                    "definition": "per rank write_fields(pinned FP64, its slab) + step(K) with "
+                                  "halo exchange + read_fields, wall clock, slowest rank"},
+            "gpu_launches": int(launches),
+            "maxwell3d": three,
+            "clocks": clocks,
+            "note": "multi-GPU run: FP64, tets, adjoint, limiter, variants and cleaning legs "
+                    "run at N = 1 only",
+        }
+        print(json.dumps(line))
+    import torch.distributed as dist
+    dist.barrier()
+    dist.destroy_process_group()
 
 
 def main():
@@ -283,6 +492,10 @@ def main():
     def barrier():
         if world > 1:
             dist.barrier()
+
+    if world > 1:
+        run_sharded(args, w, world, rank, local, stream)
+        return
 
     # ---------------- FP32 device-resident timing
     s32 = GKSSolver.from_workload(w, precision="fp32", stream=sptr)
@@ -564,14 +777,14 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": f"tm2d_cylinders_{n}", "grid": [n, n], "cylinders": 32,
                        "bc": "nonreflecting", "cfl": 0.5, "source": "line, f0=20",
                        "steps_config": steps_cfg, "precision": "fp32",
                        "l2": "inputs larger than L2 (state+eps read+write per step "
                              f"{BYTES_PER_CELL_STEP['fp32'] * ncell / 1e6:.0f} MB > 129 MB)",
-                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+                       "parallelism": "single GPU"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "peak_source": how,
                          "traffic": _profiled_traffic(),
@@ -595,6 +808,12 @@ def main():
         }
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(all_cores=True)
+            # the same oracle leg checks the FP32 and FP64 GPU paths on reduced workloads
+            import tempfile
+            with tempfile.TemporaryDirectory() as td:
+                pth = os.path.join(td, "gpu_reduced.npz")
+                reduced_gpu_results(sptr, pth)
+                line["fp32_vs_oracle"] = oracle_errors(pth)
         print(json.dumps(line))
     if world > 1:
         dist.barrier()

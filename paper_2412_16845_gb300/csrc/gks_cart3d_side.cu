@@ -46,6 +46,9 @@ constexpr int NR = NWO + 4;             // staged rows y0-2 .. y0+NWO+1
 constexpr int NA = 7;                   // staged arrays: Ex, Ey, Ez, Hx, Hy, Hz, eps
 constexpr int NSLOT = 5;
 constexpr unsigned FULL = 0xffffffffu;
+// wrapped entries of a staged plane on periodic sides: two layers beyond each side, every row
+// for columns and every column for rows, all arrays
+constexpr int kMaxFix = NA * (4 * NR + 4 * TW);
 
 using f2 = float2;
 
@@ -109,6 +112,11 @@ struct SideSmem {
   f2 F[NWO + 1][6][32];                // flux through the face above each row; [NWO]: below row 0
   float XL[2][NWO][12];                // l-side x-vectors of column X0-1 (P 6, Q without Ex, eps)
   float XR[2][NWO][12];                // r-side x-vectors of column X0+64
+  // periodic sides: staged entries past the grid that hold wrapped cells (the TMA box leaves
+  // them zero): position in a plane slot (array, row, column) and source offset in a plane
+  unsigned short fixd[kMaxFix];
+  int fixg[kMaxFix];
+  int nfix;
 };
 
 __device__ __forceinline__ int wrap_or_clamp(int i, int n, int periodic) {
@@ -169,85 +177,106 @@ __device__ __forceinline__ void tma_plane(SideSmem &s, const CUtensorMap *tmV,
       : "memory");
 }
 
-// Entries of a staged plane outside the grid (zero-filled by the copy) that the step reads:
-// on a non-reflecting axis the first ghost layer (x = -1, x = nx; y = -1, y = ny), which takes the
-// edge cell's values (the Green-Gauss ghost copy; its eps enters the boundary face's 1/eps_s),
-// copied inside the staged plane; on a periodic axis the two wrapped layers on each side, read
-// from global memory.  Deeper ghost entries only feed cells that are never stored and whose
-// face vectors are zeroed.  `nt` threads numbered `me` share the work, eight entries at a time.
-__device__ __forceinline__ void fix_plane(SideSmem &s, const Side3Args &a, int slot, int gz,
-                                          int X0, int y0, int me, int nt) {
-  // up to four tile columns and four tile rows, one byte each
-  unsigned cols = 0, rows = 0;
+// Periodic sides: the list of staged entries that hold wrapped cells (x = -2, -1, nx, nx+1 on a
+// periodic x axis, every row; y = -2, -1, ny, ny+1 on a periodic y axis, every column; all
+// arrays).  The tensor copy leaves them zero.  Built once per CTA; non-reflecting sides need no
+// entries, their reads are clamped instead.
+__device__ __forceinline__ void build_fix_list(SideSmem &s, const Side3Args &a, int X0, int y0,
+                                               int tid) {
+  unsigned cols = 0, rows = 0;        // up to four tile columns and rows, one byte each
   int nc = 0, nr = 0;
-  const int dx = a.per[0] ? 2 : 1, dy = a.per[1] ? 2 : 1;
-  for (int g = 1; g <= dx; ++g) {
-    const int tl = -g - (X0 - 4), th = a.nx - 1 + g - (X0 - 4);   // tile columns of x = -g, nx-1+g
-    if (tl >= 0 && tl < TW) cols |= (unsigned)tl << (8 * nc++);
-    if (th >= 0 && th < TW) cols |= (unsigned)th << (8 * nc++);
-  }
-  for (int g = 1; g <= dy; ++g) {
+  for (int g = 1; g <= 2; ++g) {
+    const int tl = -g - (X0 - 4), th = a.nx - 1 + g - (X0 - 4);
     const int rl = -g - (y0 - 2), rh = a.ny - 1 + g - (y0 - 2);
-    if (rl >= 0 && rl < NR) rows |= (unsigned)rl << (8 * nr++);
-    if (rh >= 0 && rh < NR) rows |= (unsigned)rh << (8 * nr++);
+    if (a.per[0] && tl >= 0 && tl < TW) cols |= (unsigned)tl << (8 * nc++);
+    if (a.per[0] && th >= 0 && th < TW) cols |= (unsigned)th << (8 * nc++);
+    if (a.per[1] && rl >= 0 && rl < NR) rows |= (unsigned)rl << (8 * nr++);
+    if (a.per[1] && rh >= 0 && rh < NR) rows |= (unsigned)rh << (8 * nr++);
   }
   const int n1 = NA * NR * nc, n = n1 + NA * nr * TW;
-  for (int i0 = me; i0 < n; i0 += 8 * nt) {
-    float v[8];
-    int tt[8], rr[8], aa[8];
+  for (int i = tid; i < n; i += NTH) {
+    int arr, r, t;
+    if (i < n1) {
+      t = (cols >> (8 * (i % nc))) & 0xff;
+      r = (i / nc) % NR;
+      arr = i / (nc * NR);
+    } else {
+      const int j = i - n1;
+      t = j % TW;
+      r = (rows >> (8 * ((j / TW) % nr))) & 0xff;
+      arr = j / (TW * nr);
+    }
+    const int gx = wrap_or_clamp(X0 - 4 + t, a.nx, a.per[0]);
+    const int gy = wrap_or_clamp(y0 - 2 + r, a.ny, a.per[1]);
+    s.fixd[i] = (unsigned short)((arr * NR + r) * TW + t);
+    s.fixg[i] = gy * (int)a.pitch + gx;
+  }
+  if (tid == 0) s.nfix = n;
+}
+
+// Write the wrapped entries of plane gz into its slot (all threads; four loads in flight each).
+__device__ __forceinline__ void fix_plane(SideSmem &s, const Side3Args &a, int slot, int gz,
+                                          int tid) {
+  const int n = s.nfix;
+  float *dst = &s.V[slot].a[0][0][0];
+  for (int i0 = tid; i0 < n; i0 += 4 * NTH) {
+    float v[4];
+    int d[4];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int i = i0 + u * nt;
+    for (int u = 0; u < 4; ++u) {
+      const int i = i0 + u * NTH;
+      d[u] = -1;
       v[u] = 0.f;
-      aa[u] = -1;
-      if (i >= n) continue;
-      int arr, r, t;
-      if (i < n1) {
-        t = (cols >> (8 * (i % nc))) & 0xff;
-        r = (i / nc) % NR;
-        arr = i / (nc * NR);
-      } else {
-        const int j = i - n1;
-        t = j % TW;
-        r = (rows >> (8 * ((j / TW) % nr))) & 0xff;
-        arr = j / (TW * nr);
+      if (i < n) {
+        const int dd = s.fixd[i], arr = dd / (NR * TW);
+        v[u] = __ldg((arr < 6 ? a.V + arr * a.cstride : a.eps) + (int64_t)gz * a.plane + s.fixg[i]);
+        d[u] = dd;
       }
-      const int x = X0 - 4 + t, y = y0 - 2 + r;
-      const int gx = wrap_or_clamp(x, a.nx, a.per[0]), gy = wrap_or_clamp(y, a.ny, a.per[1]);
-      const int ts = gx - (X0 - 4), rs = gy - (y0 - 2);
-      if (ts >= 0 && ts < TW && rs >= 0 && rs < NR && !(a.per[0] && gx != x) &&
-          !(a.per[1] && gy != y))
-        v[u] = s.V[slot].a[arr][rs][ts];                       // clamped: inside the plane
-      else
-        v[u] = __ldg((arr < 6 ? a.V + arr * a.cstride : a.eps) + (int64_t)gz * a.plane +
-                     (int64_t)gy * a.pitch + gx);
-      tt[u] = t;
-      rr[u] = r;
-      aa[u] = arr;
     }
 #pragma unroll
-    for (int u = 0; u < 8; ++u)
-      if (aa[u] >= 0) s.V[slot].a[aa[u]][rr[u]][tt[u]] = v[u];
+    for (int u = 0; u < 4; ++u)
+      if (d[u] >= 0) dst[d[u]] = v[u];
   }
 }
 
+// Where a lane reads the staged planes.  On a non-reflecting side the reads are clamped to the
+// grid (the Green-Gauss ghost copy), so the zero-filled entries past the grid are never read;
+// on a periodic side they are the wrapped entries the fix-up list writes.
+struct Taps {
+  int r, rm, rp;          // rows of the warp's cells and of their lower / upper neighbours
+  int t0, t1;             // columns of the lane's two cells
+  int tm, tp;             // left neighbour of the first cell, right neighbour of the second
+  bool pair;              // the warp's two cells of every lane are adjacent and aligned
+};
+
 // The own pair (both columns of the lane) of one staged row: 6 fields and eps.
-__device__ __forceinline__ void load_pair(const SideSmem &s, int slot, int r, int t, f2 v[7]) {
+__device__ __forceinline__ void load_pair(const SideSmem &s, int slot, const Taps &q, f2 v[7]) {
+  if (q.pair) {
 #pragma unroll
-  for (int m = 0; m < NA; ++m) v[m] = *reinterpret_cast<const f2 *>(&s.V[slot].a[m][r][t]);
+    for (int m = 0; m < NA; ++m) v[m] = *reinterpret_cast<const f2 *>(&s.V[slot].a[m][q.r][q.t0]);
+  } else {
+#pragma unroll
+    for (int m = 0; m < NA; ++m) v[m] = pk(s.V[slot].a[m][q.r][q.t0], s.V[slot].a[m][q.r][q.t1]);
+  }
 }
 
 // Raw central differences of the lane's two cells in plane slot s0 (row r, tile column t of
 // the first cell), the planes below (vm) and above (vp) in registers; eps-weighted E rows.
-__device__ __forceinline__ void differences(const SideSmem &s, int s0, int r, int t,
+__device__ __forceinline__ void differences(const SideSmem &s, int s0, const Taps &q,
                                             const f2 v[7], const f2 vm[7], const f2 vp[7],
                                             f2 d[3][6], f2 ev[3], f2 ed[3][3]) {
 #pragma unroll
   for (int m = 0; m < 6; ++m) {
-    const float xm = s.V[s0].a[m][r][t - 1], xp = s.V[s0].a[m][r][t + 2];
+    const float xm = s.V[s0].a[m][q.r][q.tm], xp = s.V[s0].a[m][q.r][q.tp];
     d[0][m] = pk(v[m].y - xm, xp - v[m].x);
-    const f2 ym = *reinterpret_cast<const f2 *>(&s.V[s0].a[m][r - 1][t]);
-    const f2 yp = *reinterpret_cast<const f2 *>(&s.V[s0].a[m][r + 1][t]);
+    f2 ym, yp;
+    if (q.pair) {
+      ym = *reinterpret_cast<const f2 *>(&s.V[s0].a[m][q.rm][q.t0]);
+      yp = *reinterpret_cast<const f2 *>(&s.V[s0].a[m][q.rp][q.t0]);
+    } else {
+      ym = pk(s.V[s0].a[m][q.rm][q.t0], s.V[s0].a[m][q.rm][q.t1]);
+      yp = pk(s.V[s0].a[m][q.rp][q.t0], s.V[s0].a[m][q.rp][q.t1]);
+    }
     d[1][m] = yp - ym;
     d[2][m] = vp[m] - vm[m];
   }
@@ -263,15 +292,16 @@ __device__ __forceinline__ void differences(const SideSmem &s, int s0, int r, in
 // columns left and right of the tile, computed by the halo warps.  left: the cell's l-side
 // vectors (its face at +1/2), else its r-side vectors.  out: P 6, Q without Ex 5, eps.
 __device__ __forceinline__ void halo_x_cell(const SideSmem &s, int sm, int s0, int sp, int r,
-                                            int t, const float *k, bool left, bool ghost,
+                                            int rm, int rp, int t, int tm, int tp,
+                                            const float *k, bool left, bool ghost,
                                             float out[12]) {
   float v[6], d[3][6], ev[3], ed[3][3];
   const float e = s.V[s0].a[6][r][t];
 #pragma unroll
   for (int m = 0; m < 6; ++m) {
     v[m] = s.V[s0].a[m][r][t];
-    d[0][m] = s.V[s0].a[m][r][t + 1] - s.V[s0].a[m][r][t - 1];
-    d[1][m] = s.V[s0].a[m][r + 1][t] - s.V[s0].a[m][r - 1][t];
+    d[0][m] = s.V[s0].a[m][r][tp] - s.V[s0].a[m][r][tm];
+    d[1][m] = s.V[s0].a[m][rp][t] - s.V[s0].a[m][rm][t];
     d[2][m] = s.V[sp].a[m][r][t] - s.V[sm].a[m][r][t];
   }
 #pragma unroll
@@ -299,15 +329,31 @@ __global__ void __launch_bounds__(NTH, 1)
   const int z0 = blockIdx.z * a.zchunk;
   const int z1 = min(z0 + a.zchunk, a.nz);
   const bool owned = warp < NWO, h0 = warp == NWO, h1 = warp == NWO + 1;
-  const int r = owned ? warp + 2 : (h0 ? 1 : NWO + 2);     // tile row of this warp
-  const int y = y0 - 2 + r;                                  // its grid row
-  const int t = 4 + 2 * lane;                                // tile column of the first cell
-  const int x = X0 + 2 * lane;                               // its grid column
+  const int y = y0 - 2 + (owned ? warp + 2 : (h0 ? 1 : NWO + 2));   // the warp's grid row
+  const int x = X0 + 2 * lane;                               // grid column of its first cell
   // non-reflecting ghosts (outside the grid on a non-periodic axis) carry no distributions
   const bool yghost = !a.per[1] && (y < 0 || y >= a.ny);
   const bool xg0 = !a.per[0] && x >= a.nx, xg1 = !a.per[0] && x + 1 >= a.nx;
   const bool st0 = x < a.nx, st1 = x + 1 < a.nx;            // columns this lane stores
   const float *kx = a.k[0], *ky = a.k[1], *kz = a.k[2];
+  // read positions: clamped to the grid on non-reflecting sides
+  auto trow = [&](int yy) { return (a.per[1] ? yy : min(max(yy, 0), a.ny - 1)) - (y0 - 2); };
+  auto tcol = [&](int xx) { return (a.per[0] ? xx : min(max(xx, 0), a.nx - 1)) - (X0 - 4); };
+  Taps q;
+  q.r = trow(y);
+  q.rm = trow(y - 1);
+  q.rp = trow(y + 1);
+  q.t0 = tcol(x);
+  q.t1 = tcol(x + 1);
+  q.tm = tcol(x - 1);
+  q.tp = tcol(x + 2);
+  q.pair = __all_sync(FULL, q.t1 == q.t0 + 1 && (q.t0 & 1) == 0);
+  // the halo warps' x-halo cells: row y0 + lane, column X0 - 1 (H0) or X0 + 64 (H1)
+  const int hy = y0 + lane;
+  const int hr = trow(hy), hrm = trow(hy - 1), hrp = trow(hy + 1);
+  const int hx = h0 ? X0 - 1 : X0 + TCOLS;
+  const bool hghost = !a.per[0] && (hx < 0 || hx >= a.nx);
+  const int ht = tcol(hx), htm = tcol(hx - 1), htp = tcol(hx + 1);
 
   // ---------------- prologue: planes z0-1 .. z0+2 staged; z-vectors of plane z0-1
   // plane p sits in slot p mod NSLOT; it is that slot's ((p - z0 + 1) / NSLOT)-th load
@@ -321,6 +367,7 @@ __global__ void __launch_bounds__(NTH, 1)
     s.err = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
+  build_fix_list(s, a, X0, y0, tid);
   __syncthreads();
   if (issuer)
     for (int p = z0 - 1; p <= z0 + 2; ++p)
@@ -329,7 +376,7 @@ __global__ void __launch_bounds__(NTH, 1)
     bool ok = true;
     for (int p = z0 - 1; p <= z0 + 2; ++p) ok &= mbar_wait(&s.bar[slot_of(p)], parity_of(p));
     if (!ok) { s.err = 1; atomicOr(a.flag, 2); }
-    for (int p = z0 - 1; p <= z0 + 2; ++p) fix_plane(s, a, slot_of(p), zidx(p), X0, y0, tid, NTH);
+    for (int p = z0 - 1; p <= z0 + 2; ++p) fix_plane(s, a, slot_of(p), zidx(p), tid);
   }
   __syncthreads();
   if (s.err) return;                                          // nothing else is in flight
@@ -349,11 +396,11 @@ __global__ void __launch_bounds__(NTH, 1)
       Wm[m] = pk(__ldg(base + c0), __ldg(base + c1));
     }
   }
-  load_pair(s, slot_of(z0 - 1), r, t, W0);
-  load_pair(s, slot_of(z0), r, t, Wp);
+  load_pair(s, slot_of(z0 - 1), q, W0);
+  load_pair(s, slot_of(z0), q, Wp);
   if (owned) {
     f2 d[3][6], ev[3], ed[3][3], pl[6], pr[6], ql[6], qr[6];
-    differences(s, slot_of(z0 - 1), r, t, W0, Wm, Wp, d, ev, ed);
+    differences(s, slot_of(z0 - 1), q, W0, Wm, Wp, d, ev, ed);
     side3<2, OpP>(W0, d, ev, ed, kz, pl, pr, ql, qr);
     const bool zg = !a.per[2] && z0 == 0;
 #pragma unroll
@@ -366,15 +413,10 @@ __global__ void __launch_bounds__(NTH, 1)
     // x-halo vectors of plane z0 (slots z0-1, z0, z0+1)
     float out[12];
     const int sm = slot_of(z0 - 1), s0 = slot_of(z0), sp = slot_of(z0 + 1);
-    if (h0) {
-      halo_x_cell(s, sm, s0, sp, lane + 2, 3, kx, true, !a.per[0] && X0 == 0, out);
+    halo_x_cell(s, sm, s0, sp, hr, hrm, hrp, ht, htm, htp, kx, h0, hghost, out);
+    float *dst = h0 ? s.XL[z0 & 1][lane] : s.XR[z0 & 1][lane];
 #pragma unroll
-      for (int q = 0; q < 12; ++q) s.XL[z0 & 1][lane][q] = out[q];
-    } else {
-      halo_x_cell(s, sm, s0, sp, lane + 2, 68, kx, false, !a.per[0] && X0 + TCOLS >= a.nx, out);
-#pragma unroll
-      for (int q = 0; q < 12; ++q) s.XR[z0 & 1][lane][q] = out[q];
-    }
+    for (int u = 0; u < 12; ++u) dst[u] = out[u];
   }
 #pragma unroll
   for (int m = 0; m < NA; ++m) { Wm[m] = W0[m]; W0[m] = Wp[m]; }
@@ -389,11 +431,11 @@ __global__ void __launch_bounds__(NTH, 1)
     if (issuer && !last && k + 4 <= z1 + 1)
       tma_plane(s, &tmV, &tmE, slot_of(k + 4), X0 - 4, y0 - 2, zidx(k + 4));
     const int s0 = slot_of(k), sp = slot_of(k + 1);
-    load_pair(s, sp, r, t, Wp);
+    load_pair(s, sp, q, Wp);
     f2 acc[6];
     if (owned) {
       f2 d[3][6], ev[3], ed[3][3];
-      differences(s, s0, r, t, W0, Wm, Wp, d, ev, ed);
+      differences(s, s0, q, W0, Wm, Wp, d, ev, ed);
       // z: face k-1/2 = l-side of plane k-1 + r-side of plane k; completes plane k-1
       {
         f2 pl[6], pr[6], ql[6], qr[6];
@@ -493,7 +535,8 @@ __global__ void __launch_bounds__(NTH, 1)
       for (int m = 2; m < 6; ++m) s.Y[warp][5 + m][lane] = qr[m];
       __syncthreads();                          // B1: r-side vectors of every row
       {
-        const f2 eu = *reinterpret_cast<const f2 *>(&s.V[s0].a[6][r + 1][t]);
+        const f2 eu = q.pair ? *reinterpret_cast<const f2 *>(&s.V[s0].a[6][q.rp][q.t0])
+                             : pk(s.V[s0].a[6][q.rp][q.t0], s.V[s0].a[6][q.rp][q.t1]);
         const f2 ie = two_over(W0[6] + eu);
         f2 Rp[6], Rq[6];
 #pragma unroll
@@ -510,15 +553,10 @@ __global__ void __launch_bounds__(NTH, 1)
         }
       }
     } else {
-      // halo warps: the y-vectors of their row, and the x-halo columns of plane k+1; first the
-      // grid-edge entries of plane k+2, which landed at the last barrier
+      // halo warps: the y-vectors of their row, and the x-halo columns of plane k+1
       if (last) break;
-      if (k > z0) {
-        fix_plane(s, a, slot_of(k + 2), zidx(k + 2), X0, y0, tid - NWO * 32, 64);
-        asm volatile("bar.sync 1, 64;\n" ::: "memory");
-      }
       f2 d[3][6], ev[3], ed[3][3], pl[6], pr[6], ql[6], qr[6];
-      differences(s, s0, r, t, W0, Wm, Wp, d, ev, ed);
+      differences(s, s0, q, W0, Wm, Wp, d, ev, ed);
       side3<1, OpP>(W0, d, ev, ed, ky, pl, pr, ql, qr);
       if (yghost) {
 #pragma unroll
@@ -534,20 +572,15 @@ __global__ void __launch_bounds__(NTH, 1)
       if (lane < NWO) {
         float out[12];
         const int sm = s0, sc = sp, sn = slot_of(k + 2);
-        if (h0) {
-          halo_x_cell(s, sm, sc, sn, lane + 2, 3, kx, true, !a.per[0] && X0 == 0, out);
+        halo_x_cell(s, sm, sc, sn, hr, hrm, hrp, ht, htm, htp, kx, h0, hghost, out);
+        float *dst = h0 ? s.XL[(k + 1) & 1][lane] : s.XR[(k + 1) & 1][lane];
 #pragma unroll
-          for (int q = 0; q < 12; ++q) s.XL[(k + 1) & 1][lane][q] = out[q];
-        } else {
-          halo_x_cell(s, sm, sc, sn, lane + 2, 68, kx, false, !a.per[0] && X0 + TCOLS >= a.nx,
-                      out);
-#pragma unroll
-          for (int q = 0; q < 12; ++q) s.XR[(k + 1) & 1][lane][q] = out[q];
-        }
+        for (int u = 0; u < 12; ++u) dst[u] = out[u];
       }
       __syncthreads();                          // B1
       if (h0) {                                 // face below row y0
-        const f2 eu = *reinterpret_cast<const f2 *>(&s.V[s0].a[6][r + 1][t]);
+        const f2 eu = q.pair ? *reinterpret_cast<const f2 *>(&s.V[s0].a[6][q.rp][q.t0])
+                             : pk(s.V[s0].a[6][q.rp][q.t0], s.V[s0].a[6][q.rp][q.t1]);
         const f2 ie = two_over(W0[6] + eu);
 #pragma unroll
         for (int m = 0; m < 6; ++m) {
@@ -558,9 +591,13 @@ __global__ void __launch_bounds__(NTH, 1)
         }
       }
     }
-    if (k + 3 <= last_plane && !mbar_wait(&s.bar[slot_of(k + 3)], parity_of(k + 3))) {
-      s.err = 1;                                // plane k+3 never landed
-      atomicOr(a.flag, 2);
+    if (k + 3 <= last_plane) {
+      if (!mbar_wait(&s.bar[slot_of(k + 3)], parity_of(k + 3))) {
+        s.err = 1;                              // plane k+3 never landed
+        atomicOr(a.flag, 2);
+      } else if (s.nfix) {
+        fix_plane(s, a, slot_of(k + 3), zidx(k + 3), tid);   // periodic sides: wrapped cells
+      }
     }
     __syncthreads();                            // B2: face fluxes; plane k+3 visible
     if (s.err) {                                // leave together; wait (bounded) for the copy
