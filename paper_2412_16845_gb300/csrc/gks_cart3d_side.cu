@@ -117,6 +117,7 @@ struct SideSmem {
   unsigned short fixd[kMaxFix];
   int fixg[kMaxFix];
   int nfix;
+  unsigned tmem;                       // tensor-memory base of the CTA (tcgen05.alloc)
 };
 
 __device__ __forceinline__ int wrap_or_clamp(int i, int n, int periodic) {
@@ -152,6 +153,46 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *b, unsigned parity
     if (done) return true;
   }
   return false;
+}
+
+// Tensor memory as spill space.  Each row warp keeps the l-side z-vectors of the plane below
+// (24 values per thread, from one plane to the next) in its lane quarter of the SM's tensor
+// memory instead of registers: one tcgen05 store and one load per plane replace the
+// registers they would pin through the x- and y-face work.  No tensor-core instruction is
+// issued; the memory is only written and read back by the thread that owns each lane.
+constexpr unsigned kTmemCols = 128;                 // 3 row warps per lane quarter x 24 columns
+
+__device__ __forceinline__ void tmem_st24(unsigned ta, const f2 a[6], const f2 b[6]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15, %16};\n" ::"r"(ta),
+      "f"(a[0].x), "f"(a[0].y), "f"(a[1].x), "f"(a[1].y), "f"(a[2].x), "f"(a[2].y), "f"(a[3].x),
+      "f"(a[3].y), "f"(a[4].x), "f"(a[4].y), "f"(a[5].x), "f"(a[5].y), "f"(b[0].x), "f"(b[0].y),
+      "f"(b[1].x), "f"(b[1].y)
+      : "memory");
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};\n" ::"r"(ta + 16),
+      "f"(b[2].x), "f"(b[2].y), "f"(b[3].x), "f"(b[3].y), "f"(b[4].x), "f"(b[4].y), "f"(b[5].x),
+      "f"(b[5].y)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_ld24(unsigned ta, f2 a[6], f2 b[6]) {
+  asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+      "%12, %13, %14, %15}, [%16];\n"
+      : "=f"(a[0].x), "=f"(a[0].y), "=f"(a[1].x), "=f"(a[1].y), "=f"(a[2].x), "=f"(a[2].y),
+        "=f"(a[3].x), "=f"(a[3].y), "=f"(a[4].x), "=f"(a[4].y), "=f"(a[5].x), "=f"(a[5].y),
+        "=f"(b[0].x), "=f"(b[0].y), "=f"(b[1].x), "=f"(b[1].y)
+      : "r"(ta)
+      : "memory");
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n"
+      : "=f"(b[2].x), "=f"(b[2].y), "=f"(b[3].x), "=f"(b[3].y), "=f"(b[4].x), "=f"(b[4].y),
+        "=f"(b[5].x), "=f"(b[5].y)
+      : "r"(ta + 16)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 }
 
 // One thread: the tensor copies of plane gz into slot `slot` (fields box, then eps box), both
@@ -321,7 +362,8 @@ __device__ __forceinline__ void halo_x_cell(const SideSmem &s, int sm, int s0, i
 
 __global__ void __launch_bounds__(NTH, 1)
     cart3d_side_kernel(const __grid_constant__ CUtensorMap tmV,
-                       const __grid_constant__ CUtensorMap tmE, const Side3Args a) {
+                       const __grid_constant__ CUtensorMap tmE,
+                       const __grid_constant__ Side3Args a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   SideSmem &s = *reinterpret_cast<SideSmem *>(smem_raw);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -381,9 +423,20 @@ __global__ void __launch_bounds__(NTH, 1)
   __syncthreads();
   if (s.err) return;                                          // nothing else is in flight
   if (issuer) tma_plane(s, &tmV, &tmE, slot_of(z0 + 3), X0 - 4, y0 - 2, zidx(z0 + 3));
+  if (warp == NWO + 1) {                                      // H1 owns the tensor memory
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                     smem_u32(&s.tmem)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  // this warp's 24 columns in its lane quarter (row warps only)
+  const unsigned tz = s.tmem + ((unsigned)(32 * (warp & 3)) << 16) + 24u * (unsigned)(warp >> 2);
 
   f2 Wm[7], W0[7], Wp[7];               // own pair at planes k-1, k, k+1
-  f2 Lpl[6], Lql[6];                    // l-side z-vectors of plane k-1
   f2 B[6], Minv = pk(0.f, 0.f);         // pending update of plane k-1: V_new = B - Minv F
   {
     const int gz = wrap_or_clamp(z0 - 2, a.nz, a.per[2]);
@@ -405,10 +458,11 @@ __global__ void __launch_bounds__(NTH, 1)
     const bool zg = !a.per[2] && z0 == 0;
 #pragma unroll
     for (int m = 0; m < 6; ++m) {
-      Lpl[m] = zg ? pk(0.f, 0.f) : pl[m];
-      Lql[m] = zg ? pk(0.f, 0.f) : ql[m];
+      pl[m] = zg ? pk(0.f, 0.f) : pl[m];
+      ql[m] = zg ? pk(0.f, 0.f) : ql[m];
       B[m] = pk(0.f, 0.f);
     }
+    tmem_st24(tz, pl, ql);                    // l-side z-vectors of plane z0-1
   } else if (lane < NWO) {
     // x-halo vectors of plane z0 (slots z0-1, z0, z0+1)
     float out[12];
@@ -446,8 +500,13 @@ __global__ void __launch_bounds__(NTH, 1)
         }
         const f2 ie = two_over(Wm[6] + W0[6]);
         f2 F[6];
+        {
+          f2 Lpl[6], Lql[6];                    // l-side z-vectors of plane k-1
+          tmem_ld24(tz, Lpl, Lql);
 #pragma unroll
-        for (int m = 0; m < 6; ++m) F[m] = pfma(ie, Lql[m] + qr[m], Lpl[m] + pr[m]);
+          for (int m = 0; m < 6; ++m) F[m] = pfma(ie, Lql[m] + qr[m], Lpl[m] + pr[m]);
+        }
+        if (!last) tmem_st24(tz, pl, ql);
         if (k > z0 && store_row) {
           const int64_t o = (int64_t)(k - 1) * a.plane + (int64_t)y * a.pitch + x;
           f2 nv[6];
@@ -469,11 +528,7 @@ __global__ void __launch_bounds__(NTH, 1)
         }
         if (last) break;
 #pragma unroll
-        for (int m = 0; m < 6; ++m) {
-          acc[m] = pk(-F[m].x, -F[m].y);
-          Lpl[m] = pl[m];
-          Lql[m] = ql[m];
-        }
+        for (int m = 0; m < 6; ++m) acc[m] = pk(-F[m].x, -F[m].y);
       }
       // x: faces x+1/2 of both cells; the second needs the r-side of the next lane's first cell
       {
@@ -622,8 +677,18 @@ __global__ void __launch_bounds__(NTH, 1)
       }
     }
 #pragma unroll
-    for (int m = 0; m < NA; ++m) { Wm[m] = W0[m]; W0[m] = Wp[m]; }
+    for (int m = 0; m < NA; ++m) Wm[m] = W0[m];
+    load_pair(s, sp, q, W0);                   // plane k+1 (still staged) is the next W0
   }
+  // release the tensor memory once every row warp's accesses are done
+  if (owned) asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  if (warp == NWO + 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(s.tmem),
+                 "r"(kTmemCols)
+                 : "memory");
   if (__any_sync(FULL, bad) && lane == 0) atomicOr(a.flag, 1);
 }
 
