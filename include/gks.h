@@ -171,7 +171,8 @@ gks_status gks_step_window(gks_ctx *ctx, int64_t n_steps, int64_t x0, int64_t x1
                            int64_t y1);
 
 /* Wait for the stream, then copy the fields to out ([ncomp][n_cells] doubles, user order,
- * host).  GKS_E_NONFINITE if a step produced a non-finite value. */
+ * host).  GKS_E_NONFINITE if a step produced a non-finite value, GKS_E_TIMEOUT if a staged
+ * kernel's bounded wait for its tensor copies ran out. */
 gks_status gks_read_fields(gks_ctx *ctx, double *out);
 
 /* Electromagnetic energy 1/2 sum_i |Omega_i| (eps_i |E_i|^2 + mu_i |H_i|^2), accumulated in

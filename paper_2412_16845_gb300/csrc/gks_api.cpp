@@ -183,6 +183,8 @@ gks_status check_flag(gks_ctx *ctx) {
   int h = 0;
   GKS_CUDA(cudaMemcpyAsync(&h, ctx->flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
   GKS_CUDA(cudaStreamSynchronize(ctx->st));
+  // bit 1: a staged kernel's bounded wait for a tensor copy ran out; bit 0: non-finite value
+  if (h & 2) return fail(ctx, GKS_E_TIMEOUT, "a kernel's bounded wait for a staged copy ran out");
   if (h) return fail(ctx, GKS_E_NONFINITE, "a non-finite value appeared in the state");
   return GKS_OK;
 }

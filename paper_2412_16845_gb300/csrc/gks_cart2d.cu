@@ -19,6 +19,7 @@
 
 #include "gks_flux2.cuh"
 #include "gks_internal.h"
+#include "gks_tma.cuh"
 
 namespace gks {
 namespace {
@@ -883,6 +884,270 @@ __global__ void __launch_bounds__(WARPS * 32, GKS_CART2D_MINBLOCKS)
   if (__any_sync(FULL, bad) && lane == 0) atomicOr(p.flag, 1);
 }
 
+// ------------------------------------------------------------------ staged FP32 path
+// The paired march above with its rows staged in shared memory by TMA (FP32, mu = 1, no
+// limiter, no PEC wall, x not periodic).  Each warp keeps a ring of NSLOT2 rows of its strip
+// (columns x0-4 .. x0+63: Ez, Hx, Hy as one 3-D box, eps as a 2-D box, one mbarrier per row);
+// lane 0 issues the copies of row j+NSLOT2 once row j is done, so about five rows of copies
+// are in flight while a row is computed, and the lanes read their two columns from the ring
+// instead of carrying a register window.  The updated row goes back to global memory through a
+// double-buffered staging row and one tensor store (box clipped at the grid's edge).  The march
+// is unrolled by two so that the gradient, right-neighbour and face-below values alternate
+// between two register sets instead of being copied.  Rows beyond a non-reflecting y side are
+// staged from the clamped row (the Green-Gauss ghost copy); columns beyond an x side are read
+// from the clamped column, the zero-filled entries of the box are never read.
+constexpr int TW2 = 68;                 // staged columns x0-4 .. x0+63 (16-byte aligned start)
+constexpr int NSLOT2 = 8;               // staged rows per warp
+static_assert((NSLOT2 & (NSLOT2 - 1)) == 0, "the ring index masks with NSLOT2 - 1");
+constexpr int MINB2 = 4;                // CTAs per SM the register budget allows
+struct alignas(128) RowBox2 { float a[3][TW2]; };     // Ez, Hx, Hy
+struct alignas(128) EpsBox2 { float e[TW2]; };
+struct StagedRow2 { RowBox2 v; EpsBox2 e; };
+struct alignas(128) OutBox2 { float a[3][WCOLS]; };   // updated Ez, Hx, Hy of columns x0..x0+59
+struct WarpStage2 {
+  StagedRow2 row[NSLOT2];
+  OutBox2 out[2];
+  unsigned long long bar[NSLOT2];
+};
+constexpr unsigned kRowBytes2 = 4 * TW2 * 4;           // both boxes of one staged row
+
+// Where a lane reads its two columns in a staged row.
+struct Taps2 {
+  int tA, tB;           // staged columns of X and X+1 (clamped to the grid)
+  bool pair;            // every lane's two columns are adjacent (one 8-byte read)
+};
+
+__device__ __forceinline__ RowP staged_row(const StagedRow2 &R, const Taps2 &q) {
+  RowP v;
+  if (q.pair) {
+    v.ez = *reinterpret_cast<const f2 *>(&R.v.a[0][q.tA]);
+    v.hx = *reinterpret_cast<const f2 *>(&R.v.a[1][q.tA]);
+    v.hy = *reinterpret_cast<const f2 *>(&R.v.a[2][q.tA]);
+    v.eps = *reinterpret_cast<const f2 *>(&R.e.e[q.tA]);
+  } else {
+    v.ez = pk(R.v.a[0][q.tA], R.v.a[0][q.tB]);
+    v.hx = pk(R.v.a[1][q.tA], R.v.a[1][q.tB]);
+    v.hy = pk(R.v.a[2][q.tA], R.v.a[2][q.tB]);
+    v.eps = pk(R.e.e[q.tA], R.e.e[q.tB]);
+  }
+  v.xm[0] = v.xm[1] = v.ym = false;
+  return v;
+}
+
+__global__ void __launch_bounds__(WARPS * 32, MINB2)
+    cart2d_step_kernel_t(const __grid_constant__ CUtensorMap tmV,
+                         const __grid_constant__ CUtensorMap tmE,
+                         const __grid_constant__ CUtensorMap tmO, const Cart2DPackArgs P,
+                         int nstrips, int rows, int strip0, int ybeg, int yend) {
+  extern __shared__ __align__(128) unsigned char smem_t[];
+  const Cart2DKernelArgs<float> &p = P.b;
+  const int lane = threadIdx.x & 31;
+  WarpStage2 &w = reinterpret_cast<WarpStage2 *>(smem_t)[threadIdx.x >> 5];
+  const int wid = blockIdx.x * WARPS + (threadIdx.x >> 5);
+  const int strip = strip0 + wid % nstrips, chunk = wid / nstrips;
+  const int y0 = ybeg + chunk * rows;
+  if (y0 >= yend) return;                             // whole warp leaves together
+  const int y1 = min(y0 + rows, yend);
+  const int x0 = strip * WCOLS;
+  const int X = x0 - 2 + 2 * lane;
+  const int xend = min(x0 + WCOLS, p.nx);
+  const bool ylo_nr = !p.pery, yhi_nr = !p.pery;
+  const float q4 = 0.25f, mq4 = -0.25f;
+  const f2 Q4 = pk(q4, q4), MQ4 = pk(mq4, mq4), Z2 = pk(0.f, 0.f);
+  Taps2 q;
+  q.tA = min(max(X, 0), p.nx - 1) - (x0 - 4);
+  q.tB = min(max(X + 1, 0), p.nx - 1) - (x0 - 4);
+  q.pair = __all_sync(FULL, q.tB == q.tA + 1);
+  // non-reflecting x faces on the grid's edge (scalar boundary flux), per lane
+  const bool hiA = X == p.nx - 1, hiB = X + 1 == p.nx - 1, lo = X == -2;
+  const bool xedge = __any_sync(FULL, hiA || hiB || lo);
+  // cells this lane owns (the staging row holds columns x0 .. x0+59; the store clips at nx)
+  const bool okA = lane >= 1 && lane <= 30 && X < xend, okB = lane >= 1 && lane <= 30 && X + 1 < xend;
+
+  // staged rows first .. last; row r sits in slot (r - first) mod NSLOT2, whose
+  // ((r - first) / NSLOT2)-th fill it is
+  const int first = y0 - 2, last = y1 + 1;
+  auto slot = [first](int r) { return (r - first) & (NSLOT2 - 1); };
+  auto parity = [first](int r) { return (unsigned)(((r - first) / NSLOT2) & 1); };
+  auto grid_row = [&p](int r) {
+    return p.pery ? (r < 0 ? r + p.ny : (r >= p.ny ? r - p.ny : r)) : min(max(r, 0), p.ny - 1);
+  };
+  int issued = first - 1;                             // lane 0: the last row whose copy is issued
+  auto issue = [&](int r) {                           // lane 0 only
+    const int s_ = slot(r), gr = grid_row(r);
+    fence_proxy_async();
+    mbar_expect_tx(&w.bar[s_], kRowBytes2);
+    tma_load_3d(&w.row[s_].v.a[0][0], &tmV, x0 - 4, gr, 0, &w.bar[s_]);
+    tma_load_2d(&w.row[s_].e.e[0], &tmE, x0 - 4, gr, &w.bar[s_]);
+    issued = r;
+  };
+  auto wait_row = [&](int r) {                        // the whole warp; false if it ran out
+    return __all_sync(FULL, mbar_wait(&w.bar[slot(r)], parity(r)));
+  };
+  if (lane == 0) {
+    for (int i = 0; i < NSLOT2; ++i) mbar_init(&w.bar[i], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    for (int r = first; r <= min(last, first + NSLOT2 - 1); ++r) issue(r);
+  }
+  __syncwarp();
+
+  bool ok = true;
+  for (int r = first; r <= y0 + 1; ++r) ok = ok && wait_row(r);
+  GP g0, g1;
+  float r0[3], r1[3];
+  f2 fbE, fbHx, fbHy, ftE, ftHx, ftHy;
+  auto yside = [](const RowP &v, const GP &g, f2 sgn) {
+    FSideP s;
+    s.e = pfma(sgn, g.ey, v.ez); s.hn = pfma(sgn, g.by, v.hy); s.ht = pfma(sgn, g.ay, v.hx);
+    s.den = g.ey; s.dhn = g.by; s.dht = g.ay; s.dat = g.bx; s.det = g.ex;
+    s.eps = v.eps;
+    return s;
+  };
+  if (ok) {
+    const RowP vm2 = staged_row(w.row[slot(y0 - 2)], q), vm1 = staged_row(w.row[slot(y0 - 1)], q);
+    const RowP v0 = staged_row(w.row[slot(y0)], q), v1 = staged_row(w.row[slot(y0 + 1)], q);
+    GP gm1;
+    float rm1[3];
+    diffs_p<false>(vm1, vm2, v0, gm1, rm1);
+    diffs_p<false>(v0, vm1, v1, g0, r0);
+    face_flux_p(yside(vm1, gm1, Q4), yside(v0, g0, MQ4), P.fy, fbE, fbHy, fbHx);
+    if (y0 == 0 && ylo_nr) {
+      float e[2], hx[2], hy[2];
+#pragma unroll
+      for (int k = 0; k < 2; ++k)
+        low_y_boundary_flux<float>(col_of_p(v0, k), grad_of_p(g0, k), p, e[k], hx[k], hy[k]);
+      fbE = pk(e[0], e[1]); fbHx = pk(hx[0], hx[1]); fbHy = pk(hy[0], hy[1]);
+    }
+    __syncwarp();                                     // rows y0-2, y0-1 are read
+    if (lane == 0)
+      for (int r = first + NSLOT2; r <= min(last, first + NSLOT2 + 1); ++r) issue(r);
+  }
+  f2 acc = Z2;                                        // 0 * (updated values): NaN iff one is not finite
+
+  // one row: gradients of row j+1 into gn / rn, the face above row j into t*, row j updated
+  // with the face below b*
+  auto row = [&](int j, const GP &gc, GP &gn, const float (&rc)[3], float (&rn)[3], f2 bE,
+                 f2 bHx, f2 bHy, f2 &tE, f2 &tHx, f2 &tHy) -> bool {
+    if (!wait_row(j + 2)) return false;
+    const RowP v0 = staged_row(w.row[slot(j)], q);
+    const RowP v1 = staged_row(w.row[slot(j + 1)], q);
+    const RowP v2 = staged_row(w.row[slot(j + 2)], q);
+    diffs_p<false>(v1, v0, v2, gn, rn);
+    // x-faces of row j: X+1/2 (component x) and X+3/2 (component y)
+    f2 fxE, fxHx, fxHy;
+    {
+      const float nb_eps = __shfl_down_sync(FULL, v0.eps.x, 1);
+      const float gn_ex = __shfl_down_sync(FULL, gc.ex.x, 1);
+      const float gn_ax = __shfl_down_sync(FULL, gc.ax.x, 1);
+      const float gn_bx = __shfl_down_sync(FULL, gc.bx.x, 1);
+      const float gn_ay = __shfl_down_sync(FULL, gc.ay.x, 1);
+      const float gn_ey = __shfl_down_sync(FULL, gc.ey.x, 1);
+      FSideP l, r;
+      l.e = pfma(Q4, gc.ex, v0.ez); l.hn = pfma(Q4, gc.ax, v0.hx); l.ht = pfma(Q4, gc.bx, v0.hy);
+      l.den = gc.ex; l.dhn = gc.ax; l.dht = gc.bx; l.dat = gc.ay; l.det = gc.ey;
+      l.eps = v0.eps;
+      r.den = pk(gc.ex.y, gn_ex); r.dhn = pk(gc.ax.y, gn_ax); r.dht = pk(gc.bx.y, gn_bx);
+      r.dat = pk(gc.ay.y, gn_ay); r.det = pk(gc.ey.y, gn_ey);
+      r.e = pfma(MQ4, r.den, pk(v0.ez.y, rc[0]));
+      r.hn = pfma(MQ4, r.dhn, pk(v0.hx.y, rc[1]));
+      r.ht = pfma(MQ4, r.dht, pk(v0.hy.y, rc[2]));
+      r.eps = pk(v0.eps.y, nb_eps);
+      face_flux_p(l, r, P.fx, fxE, fxHx, fxHy);
+      if (xedge) {
+        if (hiA) {                      // first face on the high-x boundary
+          const Side<float> s_ = xside_scalar<float>(col_of_p(v0, 0), grad_of_p(gc, 0), q4,
+                                                     p.inv2hx, p.inv2hy);
+          tm_face_flux<float, true>(s_, s_, p.Kx, fxE.x, fxHx.x, fxHy.x);
+        }
+        if (hiB) {                      // second face on the high-x boundary
+          const Side<float> s_ = xside_scalar<float>(col_of_p(v0, 1), grad_of_p(gc, 1), q4,
+                                                     p.inv2hx, p.inv2hy);
+          tm_face_flux<float, true>(s_, s_, p.Kx, fxE.y, fxHx.y, fxHy.y);
+        }
+        if (lo) {                       // second face is the low-x boundary face of column 0
+          RowV<float> nb;
+          nb.ez = rc[0]; nb.hx = rc[1]; nb.hy = rc[2]; nb.eps = nb_eps; nb.mu = 1.f;
+          RowG<float> gg;
+          gg.ex = gn_ex; gg.ax = gn_ax; gg.bx = gn_bx; gg.ay = gn_ay; gg.ey = gn_ey; gg.by = 0.f;
+          low_boundary_flux<float>(xside_scalar<float>(nb, gg, mq4, p.inv2hx, p.inv2hy), p.Kx,
+                                   fxE.y, fxHx.y, fxHy.y);
+        }
+      }
+    }
+    // y-faces between rows j and j+1
+    face_flux_p(yside(v0, gc, Q4), yside(v1, gn, MQ4), P.fy, tE, tHy, tHx);
+    if (j + 1 == p.ny && yhi_nr) {
+      float e[2], hx[2], hy[2];
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const Side<float> s_ = yside_scalar<float>(col_of_p(v0, k), grad_of_p(gc, k), q4,
+                                                   p.inv2hx, p.inv2hy);
+        float oe, oa, ob;
+        tm_face_flux<float, true>(s_, s_, p.Ky, oe, oa, ob);
+        e[k] = oe; hx[k] = -ob; hy[k] = oa;
+      }
+      tE = pk(e[0], e[1]); tHx = pk(hx[0], hx[1]); tHy = pk(hy[0], hy[1]);
+    }
+    // update row j: left face of column X is the previous lane's second face
+    const float lE = __shfl_up_sync(FULL, fxE.y, 1);
+    const float lHx = __shfl_up_sync(FULL, fxHx.y, 1);
+    const float lHy = __shfl_up_sync(FULL, fxHy.y, 1);
+    f2 dE = padd(psub(pk(lE, fxE.x), fxE), psub(bE, tE));
+    const f2 dHx = padd(psub(pk(lHx, fxHx.x), fxHx), psub(bHx, tHx));
+    const f2 dHy = padd(psub(pk(lHy, fxHy.x), fxHy), psub(bHy, tHy));
+    if (p.src && j >= p.sy0 && j < p.sy1) {
+      const int64_t ro = (int64_t)j * p.pitch;
+      if (X >= p.sx0 && X < p.sx1) dE.x -= p.src_amp * p.src[ro + X];
+      if (X + 1 >= p.sx0 && X + 1 < p.sx1) dE.y -= p.src_amp * p.src[ro + X + 1];
+    }
+    const f2 ne = pfma(dE, pk(rcp1(v0.eps.x), rcp1(v0.eps.y)), v0.ez);
+    const f2 nhx = padd(v0.hx, dHx);
+    const f2 nhy = padd(v0.hy, dHy);
+    const f2 sum = padd(padd(ne, nhx), nhy);
+    if (okA && okB) acc = pfma(sum, Z2, acc);
+    else if (okA) acc.x = fmaf(sum.x, 0.f, acc.x);
+    // stage the row and store it; the buffer's previous store (row j-2) must have read it
+    OutBox2 &O = w.out[j & 1];
+    if (lane == 0) tma_store_wait_read<1>();
+    __syncwarp();
+    if (lane >= 1 && lane <= 30) {
+      const int c = 2 * lane - 2;
+      *reinterpret_cast<f2 *>(&O.a[0][c]) = ne;
+      *reinterpret_cast<f2 *>(&O.a[1][c]) = nhx;
+      *reinterpret_cast<f2 *>(&O.a[2][c]) = nhy;
+      fence_proxy_async();
+    }
+    __syncwarp();                                     // row j's slot is read, the row staged
+    if (lane == 0) {
+      tma_store_3d(&tmO, &O.a[0][0], x0, j, 0);
+      if (j + NSLOT2 <= last) issue(j + NSLOT2);
+    }
+    return true;
+  };
+
+  int j = y0;
+  if (ok) {
+#pragma unroll 1
+    for (; j + 1 < y1; j += 2) {
+      if (!row(j, g0, g1, r0, r1, fbE, fbHx, fbHy, ftE, ftHx, ftHy) ||
+          !row(j + 1, g1, g0, r1, r0, ftE, ftHx, ftHy, fbE, fbHx, fbHy)) {
+        ok = false;
+        break;
+      }
+    }
+    if (ok && j < y1) ok = row(j, g0, g1, r0, r1, fbE, fbHx, fbHy, ftE, ftHx, ftHy);
+  }
+  if (lane == 0) {
+    if (!ok) {
+      atomicOr(p.flag, 2);                            // a row never landed
+      for (int r = max(first, issued - NSLOT2 + 1); r <= issued; ++r)   // copies in flight
+        mbar_wait(&w.bar[slot(r)], parity(r));
+    }
+    tma_store_wait_all();                             // the staging rows outlive their stores
+  }
+  if (__any_sync(FULL, !(isfinite(acc.x) && isfinite(acc.y))) && lane == 0) atomicOr(p.flag, 1);
+}
+
 template <typename T>
 Coef<T> make_coef(const double C[5], double h, double c) {
   Coef<T> k;
@@ -891,6 +1156,56 @@ Coef<T> make_coef(const double C[5], double h, double c) {
   k.c = T(c); k.c2 = T(c * c); k.inv2c = T(0.5 / c); k.halfc = T(0.5 * c);
   k.c2half = T(0.5 * c * c);
   return k;
+}
+
+// The staged kernel covers FP32 with mu = 1, no limiter, no PEC wall and a non-periodic x
+// axis (a periodic y axis needs two rows for the wrap).
+bool staged2_supported(const CartGeom &g, const CartStepArgs &a) {
+  if (a.mu || a.limiter || g.periodic[0]) return false;
+  for (int k = 0; k < 4; ++k)
+    if (g.pec[k]) return false;
+  if (g.periodic[1] && g.ny < 2) return false;
+  return tensor_map_encoder() != nullptr;
+}
+
+// Staged launch over strips [strip0, strip0 + nstrips) and rows [wy0, wy1): about four waves
+// of warps (each marching a chunk of at least 8 rows of one strip), so that the CTA scheduler
+// evens out the SMs' progress; one wave of long chunks ran 11% slower on the 4096^2 grid.
+constexpr int kWaves2 = 4;
+cudaError_t launch_staged2(const CartGeom &g, const Cart2DPackArgs &P, int strip0, int nstrips,
+                           int wy0, int wy1, cudaStream_t st) {
+  const int smem = WARPS * (int)sizeof(WarpStage2);
+  static int per_sm = 0, sms = 0;
+  if (!per_sm) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(cart2d_step_kernel_t, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cart2d_step_kernel_t, WARPS * 32,
+                                                  smem);
+    if (sms < 1) sms = 1;
+    if (per_sm < 1) per_sm = 1;
+  }
+  const int64_t resident = (int64_t)sms * per_sm * WARPS;
+  const int wrows = wy1 - wy0;
+  const int64_t want = resident * kWaves2 / nstrips;
+  int nchunks = (int)(want > 1 ? want : 1);
+  int rows = (wrows + nchunks - 1) / nchunks;
+  if (rows < 8) rows = 8;
+  nchunks = (wrows + rows - 1) / rows;
+  const int64_t nwarps = (int64_t)nstrips * nchunks;
+  const int grid = (int)((nwarps + WARPS - 1) / WARPS);
+  CUtensorMap tmV, tmE, tmO;
+  const cuuint64_t dim[3] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, 3};
+  const cuuint64_t stride[2] = {(cuuint64_t)g.pitch * 4, (cuuint64_t)g.cstride * 4};
+  const cuuint32_t box_in[3] = {TW2, 1, 3}, box_out[3] = {WCOLS, 1, 3};
+  if (!encode_f32_map(&tmV, P.b.V, 3, dim, stride, box_in) ||
+      !encode_f32_map(&tmE, P.b.eps, 2, dim, stride, box_in) ||
+      !encode_f32_map(&tmO, P.b.Vout, 3, dim, stride, box_out))
+    return cudaErrorInvalidValue;
+  cart2d_step_kernel_t<<<grid, WARPS * 32, smem, st>>>(tmV, tmE, tmO, P, nstrips, rows, strip0,
+                                                      wy0, wy1);
+  return cudaGetLastError();
 }
 
 template <typename T>
@@ -946,6 +1261,7 @@ cudaError_t launch_t(const CartGeom &g, const CartStepArgs &a, cudaStream_t st) 
       P.b = p;
       P.fx = make_face_kp(p.fx);
       P.fy = make_face_kp(p.fy);
+      if (staged2_supported(g, a)) return launch_staged2(g, P, strip0, nstrips, wy0, wy1, st);
       using KP = void (*)(const Cart2DPackArgs, int, int, int, int, int);
       static const KP kp[2][2] = {{cart2d_step_kernel_p<false, false>,
                                    cart2d_step_kernel_p<false, true>},

@@ -27,12 +27,11 @@
 // grid are zero-filled by the copy; in CTAs at the grid's edge the halo warps then write the
 // wrapped or clamped values into those entries (the periodic neighbour, or the copy of the
 // edge cell that the non-reflecting Green-Gauss ghost takes).
-#include <cuda.h>            // CUtensorMap and its enums (types only; no driver library link)
-#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include "gks_internal.h"
 #include "gks_side3.cuh"
+#include "gks_tma.cuh"
 
 namespace gks {
 namespace {
@@ -128,32 +127,7 @@ __device__ __forceinline__ int wrap_or_clamp(int i, int n, int periodic) {
   return i < 0 ? 0 : (i >= n ? n - 1 : i);
 }
 
-__device__ __forceinline__ unsigned smem_u32(const void *p) {
-  return static_cast<unsigned>(__cvta_generic_to_shared(p));
-}
-
 constexpr unsigned kPlaneBytes = NA * NR * TW * 4;   // one staged plane (both tensor boxes)
-constexpr int kWaitLimit = 1 << 22;                 // try_wait rounds before giving up
-
-__device__ __forceinline__ void mbar_init(unsigned long long *b, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(b)), "r"(count)
-               : "memory");
-}
-// Bounded wait for the phase with parity `parity` of mbarrier b; false if the limit ran out.
-__device__ __forceinline__ bool mbar_wait(unsigned long long *b, unsigned parity) {
-  const unsigned a = smem_u32(b);
-  for (int i = 0; i < kWaitLimit; ++i) {
-    unsigned done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(a), "r"(parity)
-        : "memory");
-    if (done) return true;
-  }
-  return false;
-}
 
 // Tensor memory as spill space.  Each row warp keeps the l-side z-vectors of the plane below
 // (24 values per thread, from one plane to the next) in its lane quarter of the SM's tensor
@@ -202,20 +176,10 @@ __device__ __forceinline__ void tma_plane(SideSmem &s, const CUtensorMap *tmV,
                                           const CUtensorMap *tmE, int slot, int x, int y,
                                           int gz) {
   unsigned long long *b = &s.bar[slot];
-  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(b)),
-               "r"(kPlaneBytes)
-               : "memory");
-  asm volatile(
-      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3, %4, %5}], [%6];\n" ::"r"(smem_u32(&s.V[slot].a[0][0][0])),
-      "l"(tmV), "r"(x), "r"(y), "r"(gz), "r"(0), "r"(smem_u32(b))
-      : "memory");
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(smem_u32(&s.V[slot].a[6][0][0])),
-      "l"(tmE), "r"(x), "r"(y), "r"(gz), "r"(smem_u32(b))
-      : "memory");
+  fence_proxy_async();
+  mbar_expect_tx(b, kPlaneBytes);
+  tma_load_4d(&s.V[slot].a[0][0][0], tmV, x, y, gz, 0, b);
+  tma_load_3d(&s.V[slot].a[6][0][0], tmE, x, y, gz, b);
 }
 
 // Periodic sides: the list of staged entries that hold wrapped cells (x = -2, -1, nx, nx+1 on a
@@ -696,23 +660,6 @@ __global__ void __launch_bounds__(NTH, 1)
 
 namespace {
 
-// cuTensorMapEncodeTiled from the driver through the runtime (no link against the driver
-// library); null if the driver does not provide it.
-PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  static bool tried = false;
-  if (!tried) {
-    tried = true;
-    void *p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
-                                         &q) == cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-  }
-  return fn;
-}
-
 // Tensor map of `rank` dims over a [ncomp][nz][ny][pitch] FP32 array: dims (nx, ny, nz[, 6]),
 // box (TW, NR, 1[, 6]); entries past the grid read as zero.
 bool encode_map(CUtensorMap *m, const float *base, const CartGeom &g, int rank) {
@@ -720,12 +667,7 @@ bool encode_map(CUtensorMap *m, const float *base, const CartGeom &g, int rank) 
   const cuuint64_t stride[3] = {(cuuint64_t)g.pitch * 4, (cuuint64_t)g.plane * 4,
                                 (cuuint64_t)g.cstride * 4};
   const cuuint32_t box[4] = {TW, NR, 1, 6};
-  const cuuint32_t estride[4] = {1, 1, 1, 1};
-  return tensor_map_encoder()(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, rank,
-                              const_cast<float *>(base), dim, stride, box, estride,
-                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  return encode_f32_map(m, base, rank, dim, stride, box);
 }
 
 }  // namespace
@@ -735,7 +677,8 @@ bool cart3d_side_supported(const CartGeom &g, const CartStepArgs &a, bool fp64) 
   if (!tensor_map_encoder()) return false;
   for (int k = 0; k < 6; ++k)
     if (g.pec[k]) return false;
-  return g.dim == 3;
+  // the wrap list holds in-plane offsets as int
+  return g.dim == 3 && g.plane < (int64_t(1) << 31);
 }
 
 cudaError_t launch_cart3d_side(const CartGeom &g, const CartStepArgs &a, cudaStream_t st) {
