@@ -334,6 +334,257 @@ def numeric_terms(terms, C, h, c):
     return out
 
 
+# ==================================================================== divergence-cleaning flux
+# The same construction for the cleaning system of Sec. 2.1 (V = (E, H, phi, psi), fluxes with
+# chi and gamma) in the face frame of an arbitrary face: the folded interior-face flux with
+# mu = 1 (flux3_phm_mu1) that the 3-D cleaning kernel evaluates, written to csrc/gks_phm3.cuh.
+PHM_HEADER = os.path.join(os.path.dirname(os.path.abspath(__file__)), "csrc", "gks_phm3.cuh")
+PHM_COMP = ("En", "Et", "Ew", "Hn", "Ht", "Hw", "Ph", "Ps")
+PHM_FIELDS = (("v", "v"), ("n", "dn"), ("t", "dt"), ("w", "dw"))   # input tag, Side8 member
+
+
+def _local_flux_phm(sp):
+    """The cleaning system's face flux in the face frame (normal = local axis 0) as sympy
+    expressions: F[m] times dt / h (K_i = C_i / h), inputs per side s: V_s[m] (reconstructed
+    value) and D_s[a][m] (derivative along local axis a = n, t, w), permittivity eps_s, mu = 1."""
+    c = sp.Symbol("c", positive=True)
+    chi, gam = sp.symbols("chi gam", positive=True)
+    K = sp.symbols("K1:6")
+    el, er = sp.symbols("eps_l eps_r", positive=True)
+    blocks = (((0, 0, 0), (0, 0, 1), (0, -1, 0)),
+              ((0, 0, -1), (0, 0, 0), (1, 0, 0)),
+              ((0, 1, 0), (-1, 0, 0), (0, 0, 0)))
+
+    def flux_dir(j, V):                       # F_j of Sec. 2.1 with the cleaning terms
+        M = blocks[j]
+        E, H, ph, ps = V[:3], V[3:6], V[6], V[7]
+        out = ([sum(M[a][b] * H[b] for b in range(3)) for a in range(3)] +
+               [sum(M[b][a] * E[b] for b in range(3)) for a in range(3)] + [0, 0])
+        out[j] += chi * ph
+        out[3 + j] += gam * ps
+        out[6] = chi * E[j]
+        out[7] = gam * H[j]
+        return out
+
+    u = [[c * s for s in k] for k in ((1, 1, 1), (1, -1, -1), (-1, 1, -1), (-1, -1, 1))]
+
+    def equilibria(U, V):                     # g_k = U/4 + u_k . F(V) / (4 c^2)  (Sec. 2.2)
+        F = [flux_dir(j, V) for j in range(3)]
+        return [[U[m] / 4 + sum(uk[j] * F[j][m] for j in range(3)) / (4 * c * c)
+                 for m in range(8)] for uk in u]
+
+    def side(tag):
+        return (list(sp.symbols(f"{tag}V0:8")),
+                [list(sp.symbols(f"{tag}D{a}_0:8")) for a in range(3)])
+
+    lV, lD = side("l")
+    rV, rD = side("r")
+    ml = [el] * 3 + [1] * 5
+    mr = [er] * 3 + [1] * 5
+    gl = equilibria([ml[m] * lV[m] for m in range(8)], lV)
+    gr = equilibria([mr[m] * rV[m] for m in range(8)], rV)
+    dgl = [equilibria([ml[m] * lD[j][m] for m in range(8)], lD[j]) for j in range(3)]
+    dgr = [equilibria([mr[m] * rD[j][m] for m in range(8)], rD[j]) for j in range(3)]
+    pos, neg = (0, 1), (2, 3)
+    W0 = [sum(gl[k][m] for k in pos) + sum(gr[k][m] for k in neg) for m in range(8)]
+    dW0 = [[sum(dgl[j][k][m] for k in pos) + sum(dgr[j][k][m] for k in neg) for m in range(8)]
+           for j in range(3)]
+    ms = [(ml[m] + mr[m]) / 2 for m in range(8)]
+    V0 = [W0[m] / ms[m] for m in range(8)]
+    dV0 = [[dW0[j][m] / ms[m] for m in range(8)] for j in range(3)]
+    g0 = equilibria(W0, V0)
+    dg0 = [equilibria(dW0[j], dV0[j]) for j in range(3)]
+    W0t = [-sum(u[k][j] * dg0[j][k][m] for k in range(4) for j in range(3)) for m in range(8)]
+    gt = equilibria(W0t, [W0t[m] / ms[m] for m in range(8)])
+
+    def udg(dg, k, m):
+        return sum(u[k][j] * dg[j][k][m] for j in range(3))
+
+    T1 = [sum(u[k][0] * g0[k][m] for k in range(4)) for m in range(8)]
+    T2 = [sum(u[k][0] * udg(dg0, k, m) for k in range(4)) for m in range(8)]
+    T3 = [sum(u[k][0] * gt[k][m] for k in range(4)) for m in range(8)]
+    T4 = [sum(u[k][0] * gl[k][m] for k in pos) + sum(u[k][0] * gr[k][m] for k in neg)
+          for m in range(8)]
+    T5 = [sum(u[k][0] * udg(dgl, k, m) for k in pos) + sum(u[k][0] * udg(dgr, k, m) for k in neg)
+          for m in range(8)]
+    F = [sp.expand(K[0] * T1[m] + K[1] * T2[m] + K[2] * T3[m] + K[3] * T4[m] - K[4] * T5[m])
+         for m in range(8)]
+    return F, dict(c=c, chi=chi, gam=gam, K=K, el=el, er=er, lV=lV, lD=lD, rV=rV, rD=rD)
+
+
+def derive_phm():
+    """The folded interior-face cleaning flux with mu = 1: per output component m (local frame)
+    the list of terms (group, tag, k, A, B), each (A + B ie) group(tag_k), ie = 2/(eps_l +
+    eps_r), with group S = x_l + x_r, D = x_r - x_l, SE = eps_l x_l + eps_r x_r or
+    DE = eps_r x_r - eps_l x_l of input x = value (tag v) or derivative along n, t, w of
+    component k.  A and B are polynomials in K1..K5 = C_i / h, c, chi and gam."""
+    import sympy as sp
+
+    F, s = _local_flux_phm(sp)
+    el, er = s["el"], s["er"]
+    out = []
+    for m in range(8):
+        terms = []
+        for fi, (tag, _) in enumerate(PHM_FIELDS):
+            for k in range(8):
+                xl = s["lV"][k] if tag == "v" else s["lD"][fi - 1][k]
+                xr = s["rV"][k] if tag == "v" else s["rD"][fi - 1][k]
+                cl, cr = F[m].coeff(xl), F[m].coeff(xr)
+                zero = [sp.Integer(0)] * 4
+                al, bl, gl, dl = zero if cl == 0 else _split_coefficient(sp, cl, el, el, er)
+                ar, br, gr, dr = zero if cr == 0 else _split_coefficient(sp, cr, er, el, er)
+                for grp, A, B in (("S", (al + ar) / 2, (bl + br) / 2),
+                                  ("D", (ar - al) / 2, (br - bl) / 2),
+                                  ("SE", (gl + gr) / 2, (dl + dr) / 2),
+                                  ("DE", (gr - gl) / 2, (dr - dl) / 2)):
+                    A, B = sp.factor(sp.expand(A)), sp.factor(sp.expand(B))
+                    if A != 0 or B != 0:
+                        terms.append((grp, tag, k, A, B))
+        out.append(terms)
+    return out
+
+
+def _phm_slots(sp, terms):
+    """Coefficient slots of the folded flux: constants k[] (B = 0) and pairs (a[], b[]) for the
+    ie-dependent coefficients, shared between terms up to sign.  Returns (kslots, pslots, ref)
+    with ref[(m, i)] = (sign, kind, slot) for term i of component m."""
+    kslots, pslots, kidx, pidx, ref = [], [], {}, {}, {}
+    for m, lst in enumerate(terms):
+        for i, (_, _, _, A, B) in enumerate(lst):
+            if B == 0:
+                key, neg = sp.srepr(A), sp.srepr(sp.factor(-A))
+                if key in kidx:
+                    ref[(m, i)] = (1, "k", kidx[key])
+                elif neg in kidx:
+                    ref[(m, i)] = (-1, "k", kidx[neg])
+                else:
+                    kidx[key] = len(kslots)
+                    kslots.append(A)
+                    ref[(m, i)] = (1, "k", kidx[key])
+            else:
+                key = (sp.srepr(A), sp.srepr(B))
+                neg = (sp.srepr(sp.factor(-A)), sp.srepr(sp.factor(-B)))
+                if key in pidx:
+                    ref[(m, i)] = (1, "c", pidx[key])
+                elif neg in pidx:
+                    ref[(m, i)] = (-1, "c", pidx[neg])
+                else:
+                    pidx[key] = len(pslots)
+                    pslots.append((A, B))
+                    ref[(m, i)] = (1, "c", pidx[key])
+    return kslots, pslots, ref
+
+
+def _group_name(grp, tag, k):
+    return f"{grp}_{tag}{PHM_COMP[k]}"
+
+
+def _group_expr(grp, tag, k):
+    mem = dict(PHM_FIELDS)[tag]
+    x_l, x_r = f"l.{mem}[{k}]", f"r.{mem}[{k}]"
+    return {"S": f"{x_l} + {x_r}", "D": f"{x_r} - {x_l}",
+            "SE": f"el * {x_l} + er * {x_r}", "DE": f"er * {x_r} - el * {x_l}"}[grp]
+
+
+def emit_phm(terms) -> str:
+    import sympy as sp
+
+    kslots, pslots, ref = _phm_slots(sp, terms)
+    lines = []
+    w = lines.append
+    w("// GENERATED by paper_2412_16845_gb300/codegen.py from the D3Q4 sums of Sec. 3.1 for the")
+    w("// divergence-cleaning system of Sec. 2.1; do not edit by hand (regenerate with")
+    w("// `python -m paper_2412_16845_gb300.codegen`).")
+    w("//")
+    w("// Interior-face flux of the cleaning system with mu = 1 in the face frame (components En,")
+    w("// Et, Ew, Hn, Ht, Hw, phi, psi; times dt/h), folded: every term is a coefficient times a")
+    w("// sum S(x) = x_l + x_r, a difference D(x) = x_r - x_l or their eps-weighted forms")
+    w("// SE(x) = eps_l x_l + eps_r x_r, DE(x) = eps_r x_r - eps_l x_l of one side quantity x")
+    w("// (reconstructed value v, derivative along n, t or w).  A coefficient is a constant k[] or")
+    w("// a[] + b[] ie with ie = 2/(eps_l + eps_r), both polynomials in C_i/h, c, chi and gamma")
+    w("// folded on the host.  Included by gks_flux3.cuh after Side8.")
+    w("#pragma once")
+    w("")
+    w("#include <cmath>")
+    w("")
+    w("namespace gks {")
+    w("")
+    w("template <typename T>")
+    w("struct F8K {")
+    w(f"  T k[{len(kslots)}];")
+    w(f"  T a[{len(pslots)}], b[{len(pslots)}];")
+    w("};")
+    w("")
+    w("template <typename T>")
+    w("inline F8K<T> make_f8k(const double C[5], double h, double c, double chi, double gam) {")
+    w("  const double K1 = C[0] / h, K2 = C[1] / h, K3 = C[2] / h, K4 = C[3] / h, K5 = C[4] / h;")
+    w("  (void)K1; (void)K2; (void)K3; (void)K4; (void)K5; (void)chi; (void)gam;")
+    w("  F8K<T> f;")
+    for i, A in enumerate(kslots):
+        w(f"  f.k[{i}] = T({_cexpr(sp, A)});")
+    for i, (A, B) in enumerate(pslots):
+        w(f"  f.a[{i}] = T({_cexpr(sp, A)});")
+        w(f"  f.b[{i}] = T({_cexpr(sp, B)});")
+    w("  return f;")
+    w("}")
+    w("")
+    w("template <typename T>")
+    w("__device__ __forceinline__ void flux3_phm_mu1(const Side8<T> &l, const Side8<T> &r,")
+    w("                                              const F8K<T> &K, T ie, T out[8]) {")
+    w("  const T el = l.eps, er = r.eps;")
+    w("  (void)el; (void)er;")
+    groups = sorted({(g, t, k) for lst in terms for (g, t, k, _, _) in lst},
+                    key=lambda x: (x[0], x[1], x[2]))
+    for g, t, k in groups:
+        w(f"  const T {_group_name(g, t, k)} = {_group_expr(g, t, k)};")
+    used = sorted({ref[(m, i)][2] for m, lst in enumerate(terms) for i in range(len(lst))
+                   if ref[(m, i)][1] == "c"})
+    for j in used:
+        A, _ = pslots[j]
+        w(f"  const T c{j} = " + (f"K.b[{j}] * ie;" if A == 0 else f"K.a[{j}] + K.b[{j}] * ie;"))
+    for m, lst in enumerate(terms):
+        parts = []
+        for i, (g, t, k, _, _) in enumerate(lst):
+            sgn, kind, slot = ref[(m, i)]
+            coef = f"K.k[{slot}]" if kind == "k" else f"c{slot}"
+            op = ("-" if sgn < 0 else "") if not parts else (" - " if sgn < 0 else " + ")
+            parts.append(f"{op}{coef} * {_group_name(g, t, k)}")
+        body = "".join(parts) if parts else "T(0)"
+        w(f"  out[{m}] = {body};")
+    w("}")
+    w("")
+    w("}  // namespace gks")
+    return "\n".join(lines) + "\n"
+
+
+def phm_numeric(terms, C, h, c, chi, gam):
+    """The folded cleaning flux with numeric coefficients, as the header evaluates it: returns
+    f(l, r) for sides given as dicts of arrays v, dn, dt, dw ([8]) and eps (for the CPU tests)."""
+    import sympy as sp
+
+    K = sp.symbols("K1:6")
+    sub = {K[i]: C[i] / h for i in range(5)}
+    sub.update({sp.Symbol("c", positive=True): c, sp.Symbol("chi", positive=True): chi,
+                sp.Symbol("gam", positive=True): gam})
+    num = [[(g, dict(PHM_FIELDS)[t], k, float(sp.sympify(A).subs(sub)),
+             float(sp.sympify(B).subs(sub))) for (g, t, k, A, B) in lst] for lst in terms]
+
+    def flux(l, r):
+        ie = 2.0 / (l["eps"] + r["eps"])
+        el, er = l["eps"], r["eps"]
+        out = []
+        for lst in num:
+            acc = 0.0
+            for g, mem, k, a, b in lst:
+                xl, xr = l[mem][k], r[mem][k]
+                x = {"S": xl + xr, "D": xr - xl, "SE": el * xl + er * xr,
+                     "DE": er * xr - el * xl}[g]
+                acc = acc + (a + b * ie) * x
+            out.append(acc)
+        return out
+    return flux
+
+
 def main(argv=None) -> int:
     terms, _ = derive()
     text = emit(terms)
@@ -341,6 +592,10 @@ def main(argv=None) -> int:
         f.write(text)
     n = [sum(len(v) for v in terms[A].values()) for A in range(3)]
     print(f"wrote {HEADER}: terms per axis {n}")
+    pterms = derive_phm()
+    with open(PHM_HEADER, "w") as f:
+        f.write(emit_phm(pterms))
+    print(f"wrote {PHM_HEADER}: terms per component {[len(t) for t in pterms]}")
     return 0
 
 

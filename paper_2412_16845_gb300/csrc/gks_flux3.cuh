@@ -343,303 +343,8 @@ __device__ __forceinline__ void flux3_phm(const Side8<T> &l, const Side8<T> &r, 
   }
 }
 
-// Folded constants of flux3_phm for an interior face with mu = 1 on both sides: k[] multiply a
-// sum or difference directly, c_j = a[j] + b[j] ie (ie = 2/(eps_l + eps_r)) the others.
-template <typename T>
-struct F8K {
-  T k[30];
-  T a[19], b[19];
-};
-
-template <typename T>
-inline F8K<T> make_f8k(const double C[5], double h, double c, double chi, double gam) {
-  const double k1 = C[0] / h, k2 = C[1] / h, k3 = C[2] / h, k4 = C[3] / h, k5 = C[4] / h;
-  F8K<T> f;
-  f.k[0] = T(-1.0/2.0*(chi * chi)*k1/c);
-  f.k[1] = T(-1.0/2.0*c*k4);
-  f.k[2] = T((1.0/2.0)*chi*(k1 + k4));
-  f.k[3] = T((1.0/2.0)*k2);
-  f.k[4] = T((1.0/2.0)*c*(k2 - k5));
-  f.k[5] = T(-1.0/2.0*c*(k2 - k5));
-  f.k[6] = T(-1.0/2.0*k1/c);
-  f.k[7] = T((1.0/2.0)*(k1 + k4));
-  f.k[8] = T((1.0/2.0)*gam*k2);
-  f.k[9] = T(-1.0/2.0*(chi * chi)*k2);
-  f.k[10] = T(-1.0/2.0*((c * c)*k5 - (gam * gam)*k3)/c);
-  f.k[11] = T((1.0/2.0)*c*chi*(k2 - k5));
-  f.k[12] = T(-1.0/2.0*gam*k3);
-  f.k[13] = T(-1.0/2.0*(k1 + k4));
-  f.k[14] = T((1.0/2.0)*((c * c)*k5 - (gam * gam)*k3)/c);
-  f.k[15] = T((1.0/2.0)*gam*k3);
-  f.k[16] = T(-1.0/2.0*gam*k2);
-  f.k[17] = T(-1.0/2.0*((c * c)*k4 + (gam * gam)*k1)/c);
-  f.k[18] = T((1.0/2.0)*gam*(k1 + k4));
-  f.k[19] = T((1.0/2.0)*((c * c)*k2 - (c * c)*k5 - (gam * gam)*k3));
-  f.k[20] = T(-1.0/2.0*gam*((c * c)*k2 - (c * c)*k5 - (gam * gam)*k3)/c);
-  f.k[21] = T((1.0/2.0)*c*k5);
-  f.k[22] = T(-1.0/2.0*(gam * gam)*k3);
-  f.k[23] = T(-1.0/2.0*c*k5);
-  f.k[24] = T(-1.0/2.0*k4);
-  f.k[25] = T(-1.0/2.0*(gam * gam)*k2);
-  f.k[26] = T((1.0/2.0)*c*gam*(k2 - k5));
-  f.k[27] = T((1.0/2.0)*k4);
-  f.k[28] = T((1.0/2.0)*chi*k4);
-  f.k[29] = T(-1.0/2.0*c*chi*k5);
-  f.a[0] = T((1.0/2.0)*(c * c)*(k2 - k5));
-  f.b[0] = T(-1.0/2.0*(chi * chi)*k3);
-  f.a[1] = T(-1.0/2.0*c*chi*(k2 - k5));
-  f.b[1] = T((1.0/2.0)*(chi * chi * chi)*k3/c);
-  f.a[2] = T(0);
-  f.b[2] = T(-1.0/2.0*(chi * chi)*k3);
-  f.a[3] = T(-1.0/2.0*c*k5);
-  f.b[3] = T((1.0/2.0)*(chi * chi)*k3/c);
-  f.a[4] = T((1.0/2.0)*(c * c)*(k2 - k5));
-  f.b[4] = T(-1.0/2.0*k3);
-  f.a[5] = T(-1.0/2.0*c*(k2 - k5));
-  f.b[5] = T((1.0/2.0)*k3/c);
-  f.a[6] = T(0);
-  f.b[6] = T((1.0/2.0)*k3);
-  f.a[7] = T((1.0/2.0)*c*chi*k5);
-  f.b[7] = T(-1.0/2.0*chi*k3/c);
-  f.a[8] = T(0);
-  f.b[8] = T(-1.0/2.0*c*k2);
-  f.a[9] = T(0);
-  f.b[9] = T((1.0/2.0)*k2);
-  f.a[10] = T(0);
-  f.b[10] = T(-1.0/2.0*k1);
-  f.a[11] = T(-1.0/2.0*c*k4);
-  f.b[11] = T(-1.0/2.0*k1/c);
-  f.a[12] = T(0);
-  f.b[12] = T(-1.0/2.0*chi*k2);
-  f.a[13] = T((1.0/2.0)*c*gam*k5);
-  f.b[13] = T(-1.0/2.0*gam*k3/c);
-  f.a[14] = T(0);
-  f.b[14] = T((1.0/2.0)*chi*k3);
-  f.a[15] = T(0);
-  f.b[15] = T((1.0/2.0)*chi*k1);
-  f.a[16] = T(-1.0/2.0*c*k4);
-  f.b[16] = T(-1.0/2.0*(chi * chi)*k1/c);
-  f.a[17] = T(0);
-  f.b[17] = T((1.0/2.0)*c*chi*k2);
-  f.a[18] = T(0);
-  f.b[18] = T(-1.0/2.0*gam*k3);
-  return f;
-}
-
-// flux3_phm<T, false, true> of an interior face rewritten in sums S(x) = x_l + x_r, differences
-// D(x) = x_r - x_l and their eps-weighted forms SE(x) = eps_l x_l + eps_r x_r,
-// DE(x) = eps_r x_r - eps_l x_l of the side quantities (v reconstructed values, n/t/w the
-// derivatives along the face frame's axes; components En, Et, Ew, Hn, Ht, Hw, Ph(i), Ps(i)),
-// with the coefficients, polynomials in C_i/h, c, chi and gamma (linear in ie), folded on the
-// host.  Equal to flux3_phm term by term (checked symbolically and numerically).
-template <typename T>
-__device__ __forceinline__ void flux3_phm_mu1(const Side8<T> &l, const Side8<T> &r,
-                                              const F8K<T> &K, T ie, T out[8]) {
-  const T el = l.eps, er = r.eps;
-  const T D_nEn = r.dn[0] - l.dn[0];
-  const T D_nEt = r.dn[1] - l.dn[1];
-  const T D_nEw = r.dn[2] - l.dn[2];
-  const T D_nHn = r.dn[3] - l.dn[3];
-  const T D_nHt = r.dn[4] - l.dn[4];
-  const T D_nHw = r.dn[5] - l.dn[5];
-  const T D_nPh = r.dn[6] - l.dn[6];
-  const T D_nPs = r.dn[7] - l.dn[7];
-  const T D_tEn = r.dt[0] - l.dt[0];
-  const T D_tEt = r.dt[1] - l.dt[1];
-  const T D_tEw = r.dt[2] - l.dt[2];
-  const T D_tHn = r.dt[3] - l.dt[3];
-  const T D_tHt = r.dt[4] - l.dt[4];
-  const T D_tHw = r.dt[5] - l.dt[5];
-  const T D_tPh = r.dt[6] - l.dt[6];
-  const T D_tPs = r.dt[7] - l.dt[7];
-  const T D_vEn = r.v[0] - l.v[0];
-  const T D_vEt = r.v[1] - l.v[1];
-  const T D_vEw = r.v[2] - l.v[2];
-  const T D_vHn = r.v[3] - l.v[3];
-  const T D_vHt = r.v[4] - l.v[4];
-  const T D_vHw = r.v[5] - l.v[5];
-  const T D_vPh = r.v[6] - l.v[6];
-  const T D_vPs = r.v[7] - l.v[7];
-  const T D_wEn = r.dw[0] - l.dw[0];
-  const T D_wEt = r.dw[1] - l.dw[1];
-  const T D_wEw = r.dw[2] - l.dw[2];
-  const T D_wHn = r.dw[3] - l.dw[3];
-  const T D_wHt = r.dw[4] - l.dw[4];
-  const T D_wHw = r.dw[5] - l.dw[5];
-  const T D_wPh = r.dw[6] - l.dw[6];
-  const T D_wPs = r.dw[7] - l.dw[7];
-  const T DE_vEn = er * r.v[0] - el * l.v[0];
-  const T DE_vEt = er * r.v[1] - el * l.v[1];
-  const T DE_vEw = er * r.v[2] - el * l.v[2];
-  const T S_nHn = l.dn[3] + r.dn[3];
-  const T S_nHt = l.dn[4] + r.dn[4];
-  const T S_nHw = l.dn[5] + r.dn[5];
-  const T S_nPh = l.dn[6] + r.dn[6];
-  const T S_nPs = l.dn[7] + r.dn[7];
-  const T S_tEn = l.dt[0] + r.dt[0];
-  const T S_tEt = l.dt[1] + r.dt[1];
-  const T S_tEw = l.dt[2] + r.dt[2];
-  const T S_tHn = l.dt[3] + r.dt[3];
-  const T S_tHt = l.dt[4] + r.dt[4];
-  const T S_tHw = l.dt[5] + r.dt[5];
-  const T S_tPh = l.dt[6] + r.dt[6];
-  const T S_tPs = l.dt[7] + r.dt[7];
-  const T S_vEn = l.v[0] + r.v[0];
-  const T S_vEt = l.v[1] + r.v[1];
-  const T S_vEw = l.v[2] + r.v[2];
-  const T S_vHn = l.v[3] + r.v[3];
-  const T S_vHt = l.v[4] + r.v[4];
-  const T S_vHw = l.v[5] + r.v[5];
-  const T S_vPh = l.v[6] + r.v[6];
-  const T S_vPs = l.v[7] + r.v[7];
-  const T S_wEn = l.dw[0] + r.dw[0];
-  const T S_wEt = l.dw[1] + r.dw[1];
-  const T S_wEw = l.dw[2] + r.dw[2];
-  const T S_wHn = l.dw[3] + r.dw[3];
-  const T S_wHt = l.dw[4] + r.dw[4];
-  const T S_wHw = l.dw[5] + r.dw[5];
-  const T S_wPh = l.dw[6] + r.dw[6];
-  const T S_wPs = l.dw[7] + r.dw[7];
-  const T SE_nEn = el * l.dn[0] + er * r.dn[0];
-  const T SE_nEt = el * l.dn[1] + er * r.dn[1];
-  const T SE_nEw = el * l.dn[2] + er * r.dn[2];
-  const T SE_tEn = el * l.dt[0] + er * r.dt[0];
-  const T SE_tEt = el * l.dt[1] + er * r.dt[1];
-  const T SE_tEw = el * l.dt[2] + er * r.dt[2];
-  const T SE_vEn = el * l.v[0] + er * r.v[0];
-  const T SE_vEt = el * l.v[1] + er * r.v[1];
-  const T SE_vEw = el * l.v[2] + er * r.v[2];
-  const T SE_wEn = el * l.dw[0] + er * r.dw[0];
-  const T SE_wEt = el * l.dw[1] + er * r.dw[1];
-  const T SE_wEw = el * l.dw[2] + er * r.dw[2];
-  const T c0 = K.a[0] + K.b[0] * ie;
-  const T c1 = K.a[1] + K.b[1] * ie;
-  const T c2 = K.b[2] * ie;
-  const T c3 = K.a[3] + K.b[3] * ie;
-  const T c4 = K.a[4] + K.b[4] * ie;
-  const T c5 = K.a[5] + K.b[5] * ie;
-  const T c6 = K.b[6] * ie;
-  const T c7 = K.a[7] + K.b[7] * ie;
-  const T c8 = K.b[8] * ie;
-  const T c9 = K.b[9] * ie;
-  const T c10 = K.b[10] * ie;
-  const T c11 = K.a[11] + K.b[11] * ie;
-  const T c12 = K.b[12] * ie;
-  const T c13 = K.a[13] + K.b[13] * ie;
-  const T c14 = K.b[14] * ie;
-  const T c15 = K.b[15] * ie;
-  const T c16 = K.a[16] + K.b[16] * ie;
-  const T c17 = K.b[17] * ie;
-  const T c18 = K.b[18] * ie;
-  out[0] = K.k[0] * D_vEn +
-      K.k[1] * DE_vEn +
-      K.k[2] * S_vPh +
-      c0 * SE_nEn +
-      c1 * D_nPh +
-      c2 * SE_tEt +
-      K.k[3] * D_tEw +
-      K.k[4] * S_tHt +
-      c3 * D_tHw +
-      K.k[3] * D_wEt +
-      c2 * SE_wEw -
-      c3 * D_wHt +
-      K.k[5] * S_wHw;
-  out[1] = K.k[6] * D_vEt +
-      K.k[1] * DE_vEt +
-      K.k[7] * S_vHw +
-      c4 * SE_nEt +
-      c5 * D_nHw +
-      c6 * SE_tEn +
-      K.k[5] * S_tHn +
-      c7 * D_tPh +
-      K.k[8] * D_tPs +
-      K.k[9] * D_wEn +
-      K.k[10] * D_wHn +
-      K.k[11] * S_wPh +
-      K.k[12] * S_wPs;
-  out[2] = K.k[6] * D_vEw +
-      K.k[1] * DE_vEw +
-      K.k[13] * S_vHt +
-      c4 * SE_nEw -
-      c5 * D_nHt +
-      K.k[9] * D_tEn +
-      K.k[14] * D_tHn +
-      K.k[11] * S_tPh +
-      K.k[15] * S_tPs +
-      c6 * SE_wEn +
-      K.k[4] * S_wHn +
-      c7 * D_wPh +
-      K.k[16] * D_wPs;
-  out[3] = K.k[17] * D_vHn +
-      K.k[18] * S_vPs +
-      K.k[19] * S_nHn +
-      K.k[20] * D_nPs +
-      K.k[21] * S_tEt +
-      c8 * SE_tEt +
-      K.k[14] * D_tEw +
-      K.k[22] * S_tHt +
-      c9 * D_tHw +
-      K.k[10] * D_wEt +
-      K.k[23] * S_wEw -
-      c8 * SE_wEw +
-      c9 * D_wHt +
-      K.k[22] * S_wHw;
-  out[4] = K.k[24] * S_vEw +
-      c10 * SE_vEw +
-      c11 * D_vHt -
-      c5 * D_nEw +
-      c4 * S_nHt +
-      K.k[23] * S_tEn -
-      c8 * SE_tEn +
-      c6 * S_tHn +
-      c12 * D_tPh +
-      c13 * D_tPs -
-      c3 * D_wEn +
-      K.k[25] * D_wHn +
-      c14 * S_wPh +
-      K.k[26] * S_wPs;
-  out[5] = K.k[27] * S_vEt -
-      c10 * SE_vEt +
-      c11 * D_vHw +
-      c5 * D_nEt +
-      c4 * S_nHw +
-      c3 * D_tEn +
-      K.k[25] * D_tHn -
-      c14 * S_tPh +
-      K.k[26] * S_tPs +
-      K.k[21] * S_wEn +
-      c8 * SE_wEn +
-      c6 * S_wHn -
-      c12 * D_wPh +
-      c13 * D_wPs;
-  out[6] = K.k[28] * S_vEn +
-      c15 * SE_vEn +
-      c16 * D_vPh +
-      c1 * D_nEn +
-      c0 * S_nPh +
-      c7 * D_tEt +
-      K.k[29] * S_tEw +
-      c17 * SE_tEw -
-      c12 * D_tHt +
-      c14 * S_tHw +
-      K.k[29] * S_wEt +
-      c17 * SE_wEt +
-      c7 * D_wEw -
-      c14 * S_wHt +
-      c12 * D_wHw;
-  out[7] = K.k[18] * S_vHn +
-      K.k[17] * D_vPs +
-      K.k[20] * D_nHn +
-      K.k[19] * S_nPs +
-      K.k[16] * D_tEt +
-      c18 * SE_tEw +
-      c13 * D_tHt +
-      K.k[26] * S_tHw -
-      c18 * SE_wEt +
-      K.k[8] * D_wEw +
-      K.k[26] * S_wHt +
-      c13 * D_wHw;
-}
+// flux3_phm with mu = 1 on an interior face, folded (F8K, make_f8k, flux3_phm_mu1): generated
+// into gks_phm3.cuh, included at the end of this header.
 
 template <typename T>
 K3<T> make_k3(const double C[5], double h, double c) {
@@ -652,3 +357,5 @@ K3<T> make_k3(const double C[5], double h, double c) {
 }
 
 }  // namespace gks
+
+#include "gks_phm3.cuh"
