@@ -6,8 +6,9 @@
 //      form, gks_flux3.cuh), rotate back, times the face area -> flux scratch [6][nf].
 //   3. tet_update_kernel: every cell gathers the fluxes of its four faces (no atomics, fixed
 //      order) and applies the FV update with the source.
-// Geometry (frames, areas, offsets, volumes, face weights) stays FP64 on the device; FP32
-// kernels convert it as they read it.
+// Geometry (frames, areas, offsets, face weights) is computed in FP64 on the host and stored on
+// the device in the context's precision: an FP32 context reads it rounded to FP32 once, on the
+// host (the FP64 volumes kept for the energy are the exception).
 #include <cuda_runtime.h>
 
 #include "gks_flux3.cuh"
