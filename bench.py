@@ -281,6 +281,37 @@ def reduced_gpu_results(stream_ptr, path):
     np.savez(path, **out)
 
 
+def divergence_report(sptr):
+    """div_h H = (Hx(i+1) - Hx(i-1))/(2h) + (Hy(j+1) - Hy(j-1))/(2h) of the GPU FP64 fields on the
+    periodic 64^2 workload (oblique plane wave plus Gaussian pulse, CFL 0.5) before and after its
+    200 steps: discrete L2 norms (sqrt(sum h^2 x^2)), the same relative to the summed norms of its
+    two terms, and the largest change of sum_i |Omega_i| U_i over the run (conservation).  The
+    test suite checks these fields against the oracle's."""
+    from paper_2412_16845_gb300 import workloads as wl
+    from paper_2412_16845_gb300.gks import GKSSolver
+
+    n = 64
+    w = wl.config1_periodic_tm(n)
+    s = GKSSolver.from_workload(w, precision="fp64", stream=sptr)
+    f0 = s.read_fields()
+    s.step(200)
+    f1 = s.read_fields()
+    s.close()
+    h = 1.0 / n
+
+    def div(f):
+        hx, hy = f[1].reshape(n, n), f[2].reshape(n, n)
+        dx = (np.roll(hx, -1, axis=1) - np.roll(hx, 1, axis=1)) / (2 * h)
+        dy = (np.roll(hy, -1, axis=0) - np.roll(hy, 1, axis=0)) / (2 * h)
+        return float(np.linalg.norm(dx + dy) * h), float((np.linalg.norm(dx) + np.linalg.norm(dy)) * h)
+
+    d0, t0 = div(f0)
+    d1, t1 = div(f1)
+    return {"workload": "tm2d_periodic_64 (FP64, 200 steps)", "div_h_H_l2_initial": d0,
+            "div_h_H_l2": d1, "div_rel_to_terms_initial": d0 / t0, "div_rel_to_terms": d1 / t1,
+            "max_change_sum_vol_U": float(np.abs((f1.sum(axis=1) - f0.sum(axis=1)) * h * h).max())}
+
+
 def oracle_errors(path):
     """The oracle leg's second job: the FP64 oracle on the reduced workloads against the GPU
     results saved at `path` (relative L2 over all components and cells, volume-weighted on
@@ -399,6 +430,7 @@ def run_sharded(args, w, world, rank, local, stream):
                  "hbm_frac_fp32_per_gpu": 52 * w3.ncell / world / (ms3 * 1e-3) / 1e9 / _peaks()[0],
                  "algorithmic_bytes_per_cell_step": 52}
     if rank == 0:
+        divergence = divergence_report(sptr)
         hbm, how = _peaks()
         ms_step = ms / args.steps
         achieved = BYTES_PER_CELL_STEP["fp32"] * ncell / world / (ms_step * 1e-3) / 1e9
@@ -416,7 +448,7 @@ def run_sharded(args, w, world, rank, local, stream):
                                       "send/recv after every step"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "peak_source": how, "traffic": None,
-                         "kernel": "cart2d_step_kernel_p (FP32, mu = 1), per GPU, halo "
+                         "kernel": "cart2d_step_kernel_t (staged FP32, mu = 1), per GPU, halo "
                                    "exchange included in the time",
                          "algorithmic_bytes_per_launch": BYTES_PER_CELL_STEP["fp32"] * ncell // world},
             "e2e": {"value": e2e, "unit": UNIT,
@@ -772,6 +804,7 @@ def main():
                "grad_norm": float(g.norm())}
 
     if rank == 0:
+        divergence = divergence_report(sptr)
         hbm, how = _peaks()
         achieved = BYTES_PER_CELL_STEP["fp32"] * ncell / (ms_step * 1e-3) / 1e9
         line = {
@@ -788,7 +821,7 @@ def main():
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "peak_source": how,
                          "traffic": _profiled_traffic(),
-                         "kernel": "cart2d_step_kernel_p (FP32, mu = 1)",
+                         "kernel": "cart2d_step_kernel_t (staged FP32, mu = 1)",
                          "algorithmic_bytes_per_launch": BYTES_PER_CELL_STEP["fp32"] * ncell},
             "fp64": {"value": value64, "ms_per_step": ms64, "unit": UNIT,
                      "fp32_speedup": value / world / value64},
@@ -804,6 +837,7 @@ def main():
             "variants": variants,
             "cleaning": cleaning,
             "adjoint": adj,
+            "divergence": divergence,
             "clocks": clocks,
         }
         if not args.no_cpu_baseline:
