@@ -448,7 +448,7 @@ def run_sharded(args, w, world, rank, local, stream):
                                       "send/recv after every step"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "peak_source": how, "traffic": None,
-                         "kernel": "cart2d_step_kernel_t (staged FP32, mu = 1), per GPU, halo "
+                         "kernel": "cart2d_step_kernel_s (staged FP32, mu = 1), per GPU, halo "
                                    "exchange included in the time",
                          "algorithmic_bytes_per_launch": BYTES_PER_CELL_STEP["fp32"] * ncell // world},
             "e2e": {"value": e2e, "unit": UNIT,
@@ -821,7 +821,7 @@ def main():
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "peak_source": how,
                          "traffic": _profiled_traffic(),
-                         "kernel": "cart2d_step_kernel_t (staged FP32, mu = 1)",
+                         "kernel": "cart2d_step_kernel_s (staged FP32, mu = 1)",
                          "algorithmic_bytes_per_launch": BYTES_PER_CELL_STEP["fp32"] * ncell},
             "fp64": {"value": value64, "ms_per_step": ms64, "unit": UNIT,
                      "fp32_speedup": value / world / value64},

@@ -885,88 +885,104 @@ __global__ void __launch_bounds__(WARPS * 32, GKS_CART2D_MINBLOCKS)
 }
 
 // ------------------------------------------------------------------ staged FP32 path
-// The paired march above with its rows staged in shared memory by TMA (FP32, mu = 1, no
-// limiter, no PEC wall, x not periodic).  Each warp keeps a ring of NSLOT2 rows of its strip
-// (columns x0-4 .. x0+63: Ez, Hx, Hy as one 3-D box, eps as a 2-D box, one mbarrier per row);
-// lane 0 issues the copies of row j+NSLOT2 once row j is done, so about five rows of copies
-// are in flight while a row is computed, and the lanes read their two columns from the ring
-// instead of carrying a register window.  The updated row goes back to global memory through a
-// double-buffered staging row and one tensor store (box clipped at the grid's edge).  The march
-// is unrolled by two so that the gradient, right-neighbour and face-below values alternate
-// between two register sets instead of being copied.  Rows beyond a non-reflecting y side are
-// staged from the clamped row (the Green-Gauss ghost copy); columns beyond an x side are read
-// from the clamped column, the zero-filled entries of the box are never read.
-constexpr int TW2 = 68;                 // staged columns x0-4 .. x0+63 (16-byte aligned start)
+// FP32, mu = 1, no limiter, no PEC wall, x not periodic.  The rows of a strip are staged in
+// shared memory by TMA and the two cells of a lane lie 32 columns apart, so that no pair ever
+// has to be assembled from two lanes' registers:
+//   - a warp owns a strip of W2 = 63 columns x0 .. x0+62; lane l holds the cells A = x0+l and
+//     B = x0+32+l as the two halves of a float2 (lane 31's B is the next strip's first column,
+//     computed but not stored);
+//   - each lane evaluates the LEFT x-faces of A and B.  The 64 faces x0-1/2 .. x0+62+1/2 of the
+//     warp are exactly the faces its 63 cells need; a cell's right face is the next lane's
+//     left face (a shuffle; for lane 31's A it is lane 0's left face of B);
+//   - every value a lane needs (its own cells, the left neighbours A-1, B-1 and their
+//     left neighbours, the right neighbours, the rows above and below) is read from the staged
+//     rows, two 4-byte shared loads per pair.  Gradients of the left neighbours are recomputed
+//     from the staged rows rather than shuffled, so no lane is special;
+//   - updated cells go straight to global memory (coalesced 4-byte stores).
+// Each warp keeps a ring of NSLOT2 rows (Ez, Hx, Hy as one 3-D box and eps as a 2-D box, one
+// mbarrier per row; the box starts at the 16-byte boundary at or below x0-3).  Lane 0 issues
+// row j+NSLOT2-1 once row j is done; iteration j reads rows j-1 .. j+2.  Rows past a
+// non-reflecting y side are staged from the clamped row (the Green-Gauss ghost copy), a
+// periodic y side wraps; columns past an x side are read from the clamped column, so the
+// zero-filled entries of a box are never read.  The march is unrolled by two so that the
+// gradients and face-below fluxes alternate between two register sets.
+constexpr int W2 = 63;                  // columns updated per warp
+constexpr int TW2 = 72;                 // staged columns (x0-3 rounded down to 4, +72)
 constexpr int NSLOT2 = 8;               // staged rows per warp
 static_assert((NSLOT2 & (NSLOT2 - 1)) == 0, "the ring index masks with NSLOT2 - 1");
 constexpr int MINB2 = 4;                // CTAs per SM the register budget allows
 struct alignas(128) RowBox2 { float a[3][TW2]; };     // Ez, Hx, Hy
 struct alignas(128) EpsBox2 { float e[TW2]; };
 struct StagedRow2 { RowBox2 v; EpsBox2 e; };
-struct alignas(128) OutBox2 { float a[3][WCOLS]; };   // updated Ez, Hx, Hy of columns x0..x0+59
 struct WarpStage2 {
   StagedRow2 row[NSLOT2];
-  OutBox2 out[2];
   unsigned long long bar[NSLOT2];
 };
 constexpr unsigned kRowBytes2 = 4 * TW2 * 4;           // both boxes of one staged row
 
-// Where a lane reads its two columns in a staged row.
+// Staged columns of a lane's two cells and of their neighbours at offsets -2 .. +1, clamped to
+// the grid (non-reflecting x sides).
 struct Taps2 {
-  int tA, tB;           // staged columns of X and X+1 (clamped to the grid)
-  bool pair;            // every lane's two columns are adjacent (one 8-byte read)
+  int a[4], b[4];       // [k]: column A + k - 2 / B + k - 2
 };
 
-__device__ __forceinline__ RowP staged_row(const StagedRow2 &R, const Taps2 &q) {
+// (Ez, Hx, Hy, eps) of the pair at tap k of a staged row; 3 fields only with EPS = false.
+template <bool EPS>
+__device__ __forceinline__ RowP staged_pair(const StagedRow2 &R, const Taps2 &q, int k) {
   RowP v;
-  if (q.pair) {
-    v.ez = *reinterpret_cast<const f2 *>(&R.v.a[0][q.tA]);
-    v.hx = *reinterpret_cast<const f2 *>(&R.v.a[1][q.tA]);
-    v.hy = *reinterpret_cast<const f2 *>(&R.v.a[2][q.tA]);
-    v.eps = *reinterpret_cast<const f2 *>(&R.e.e[q.tA]);
-  } else {
-    v.ez = pk(R.v.a[0][q.tA], R.v.a[0][q.tB]);
-    v.hx = pk(R.v.a[1][q.tA], R.v.a[1][q.tB]);
-    v.hy = pk(R.v.a[2][q.tA], R.v.a[2][q.tB]);
-    v.eps = pk(R.e.e[q.tA], R.e.e[q.tB]);
-  }
+  v.ez = pk(R.v.a[0][q.a[k]], R.v.a[0][q.b[k]]);
+  v.hx = pk(R.v.a[1][q.a[k]], R.v.a[1][q.b[k]]);
+  v.hy = pk(R.v.a[2][q.a[k]], R.v.a[2][q.b[k]]);
+  v.eps = EPS ? pk(R.e.e[q.a[k]], R.e.e[q.b[k]]) : pk(0.f, 0.f);
   v.xm[0] = v.xm[1] = v.ym = false;
   return v;
 }
 
+// Raw central differences of the pair at tap k of row `mid` (rows `dn` and `up` below and
+// above): x differences of (Ez, Hx, Hy) from taps k-1 and k+1, y differences from the rows.
+__device__ __forceinline__ GP staged_diffs(const StagedRow2 &dn, const StagedRow2 &mid,
+                                           const StagedRow2 &up, const Taps2 &q, int k) {
+  GP g;
+  const RowP l = staged_pair<false>(mid, q, k - 1), r = staged_pair<false>(mid, q, k + 1);
+  const RowP d = staged_pair<false>(dn, q, k), u = staged_pair<false>(up, q, k);
+  g.ex = psub(r.ez, l.ez); g.ax = psub(r.hx, l.hx); g.bx = psub(r.hy, l.hy);
+  g.ey = psub(u.ez, d.ez); g.ay = psub(u.hx, d.hx); g.by = psub(u.hy, d.hy);
+  return g;
+}
+
 __global__ void __launch_bounds__(WARPS * 32, MINB2)
-    cart2d_step_kernel_t(const __grid_constant__ CUtensorMap tmV,
-                         const __grid_constant__ CUtensorMap tmE,
-                         const __grid_constant__ CUtensorMap tmO, const Cart2DPackArgs P,
+    cart2d_step_kernel_s(const __grid_constant__ CUtensorMap tmV,
+                         const __grid_constant__ CUtensorMap tmE, const Cart2DPackArgs P,
                          int nstrips, int rows, int strip0, int ybeg, int yend) {
-  extern __shared__ __align__(128) unsigned char smem_t[];
+  extern __shared__ __align__(128) unsigned char smem_s[];
   const Cart2DKernelArgs<float> &p = P.b;
   const int lane = threadIdx.x & 31;
-  WarpStage2 &w = reinterpret_cast<WarpStage2 *>(smem_t)[threadIdx.x >> 5];
+  WarpStage2 &w = reinterpret_cast<WarpStage2 *>(smem_s)[threadIdx.x >> 5];
   const int wid = blockIdx.x * WARPS + (threadIdx.x >> 5);
   const int strip = strip0 + wid % nstrips, chunk = wid / nstrips;
   const int y0 = ybeg + chunk * rows;
   if (y0 >= yend) return;                             // whole warp leaves together
   const int y1 = min(y0 + rows, yend);
-  const int x0 = strip * WCOLS;
-  const int X = x0 - 2 + 2 * lane;
-  const int xend = min(x0 + WCOLS, p.nx);
+  const int x0 = strip * W2;
+  const int xs = (x0 - 3) & ~3;                       // first staged column (16-byte aligned)
+  const int A = x0 + lane, B = x0 + 32 + lane;
   const bool ylo_nr = !p.pery, yhi_nr = !p.pery;
   const float q4 = 0.25f, mq4 = -0.25f;
   const f2 Q4 = pk(q4, q4), MQ4 = pk(mq4, mq4), Z2 = pk(0.f, 0.f);
   Taps2 q;
-  q.tA = min(max(X, 0), p.nx - 1) - (x0 - 4);
-  q.tB = min(max(X + 1, 0), p.nx - 1) - (x0 - 4);
-  q.pair = __all_sync(FULL, q.tB == q.tA + 1);
-  // non-reflecting x faces on the grid's edge (scalar boundary flux), per lane
-  const bool hiA = X == p.nx - 1, hiB = X + 1 == p.nx - 1, lo = X == -2;
-  const bool xedge = __any_sync(FULL, hiA || hiB || lo);
-  // cells this lane owns (the staging row holds columns x0 .. x0+59; the store clips at nx)
-  const bool okA = lane >= 1 && lane <= 30 && X < xend, okB = lane >= 1 && lane <= 30 && X + 1 < xend;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    q.a[k] = min(max(A + k - 2, 0), p.nx - 1) - xs;
+    q.b[k] = min(max(B + k - 2, 0), p.nx - 1) - xs;
+  }
+  // boundary x faces (scalar flux): the left face of column 0 is the low-x face of column 0;
+  // the left face of column nx is the high-x face of column nx - 1
+  const bool loA = A == 0, loB = B == 0, hiA = A == p.nx, hiB = B == p.nx;
+  const bool xedge = __any_sync(FULL, loA || loB || hiA || hiB);
+  const int xend = min(x0 + W2, p.nx);
+  const bool stA = A < xend, stB = lane < 31 && B < xend;   // cells this lane stores
 
-  // staged rows first .. last; row r sits in slot (r - first) mod NSLOT2, whose
-  // ((r - first) / NSLOT2)-th fill it is
-  const int first = y0 - 2, last = y1 + 1;
+  const int first = y0 - 2, last = y1 + 1;            // staged rows
   auto slot = [first](int r) { return (r - first) & (NSLOT2 - 1); };
   auto parity = [first](int r) { return (unsigned)(((r - first) / NSLOT2) & 1); };
   auto grid_row = [&p](int r) {
@@ -977,8 +993,8 @@ __global__ void __launch_bounds__(WARPS * 32, MINB2)
     const int s_ = slot(r), gr = grid_row(r);
     fence_proxy_async();
     mbar_expect_tx(&w.bar[s_], kRowBytes2);
-    tma_load_3d(&w.row[s_].v.a[0][0], &tmV, x0 - 4, gr, 0, &w.bar[s_]);
-    tma_load_2d(&w.row[s_].e.e[0], &tmE, x0 - 4, gr, &w.bar[s_]);
+    tma_load_3d(&w.row[s_].v.a[0][0], &tmV, xs, gr, 0, &w.bar[s_]);
+    tma_load_2d(&w.row[s_].e.e[0], &tmE, xs, gr, &w.bar[s_]);
     issued = r;
   };
   auto wait_row = [&](int r) {                        // the whole warp; false if it ran out
@@ -991,11 +1007,6 @@ __global__ void __launch_bounds__(WARPS * 32, MINB2)
   }
   __syncwarp();
 
-  bool ok = true;
-  for (int r = first; r <= y0 + 1; ++r) ok = ok && wait_row(r);
-  GP g0, g1;
-  float r0[3], r1[3];
-  f2 fbE, fbHx, fbHy, ftE, ftHx, ftHy;
   auto yside = [](const RowP &v, const GP &g, f2 sgn) {
     FSideP s;
     s.e = pfma(sgn, g.ey, v.ez); s.hn = pfma(sgn, g.by, v.hy); s.ht = pfma(sgn, g.ay, v.hx);
@@ -1003,13 +1014,24 @@ __global__ void __launch_bounds__(WARPS * 32, MINB2)
     s.eps = v.eps;
     return s;
   };
+  auto xside = [](const RowP &v, const GP &g, f2 sgn) {
+    FSideP s;
+    s.e = pfma(sgn, g.ex, v.ez); s.hn = pfma(sgn, g.ax, v.hx); s.ht = pfma(sgn, g.bx, v.hy);
+    s.den = g.ex; s.dhn = g.ax; s.dht = g.bx; s.dat = g.ay; s.det = g.ey;
+    s.eps = v.eps;
+    return s;
+  };
+
+  bool ok = true;
+  for (int r = first; r <= y0 + 1; ++r) ok = ok && wait_row(r);
+  GP g0, g1;                                          // own gradients of the current / next row
+  f2 fbE, fbHx, fbHy, ftE, ftHx, ftHy;                // y-face fluxes below / above the row
   if (ok) {
-    const RowP vm2 = staged_row(w.row[slot(y0 - 2)], q), vm1 = staged_row(w.row[slot(y0 - 1)], q);
-    const RowP v0 = staged_row(w.row[slot(y0)], q), v1 = staged_row(w.row[slot(y0 + 1)], q);
-    GP gm1;
-    float rm1[3];
-    diffs_p<false>(vm1, vm2, v0, gm1, rm1);
-    diffs_p<false>(v0, vm1, v1, g0, r0);
+    const StagedRow2 &Rm2 = w.row[slot(y0 - 2)], &Rm1 = w.row[slot(y0 - 1)];
+    const StagedRow2 &R0 = w.row[slot(y0)], &R1 = w.row[slot(y0 + 1)];
+    const GP gm1 = staged_diffs(Rm2, Rm1, R0, q, 2);
+    g0 = staged_diffs(Rm1, R0, R1, q, 2);
+    const RowP vm1 = staged_pair<true>(Rm1, q, 2), v0 = staged_pair<true>(R0, q, 2);
     face_flux_p(yside(vm1, gm1, Q4), yside(v0, g0, MQ4), P.fy, fbE, fbHy, fbHx);
     if (y0 == 0 && ylo_nr) {
       float e[2], hx[2], hy[2];
@@ -1018,62 +1040,49 @@ __global__ void __launch_bounds__(WARPS * 32, MINB2)
         low_y_boundary_flux<float>(col_of_p(v0, k), grad_of_p(g0, k), p, e[k], hx[k], hy[k]);
       fbE = pk(e[0], e[1]); fbHx = pk(hx[0], hx[1]); fbHy = pk(hy[0], hy[1]);
     }
-    __syncwarp();                                     // rows y0-2, y0-1 are read
-    if (lane == 0)
-      for (int r = first + NSLOT2; r <= min(last, first + NSLOT2 + 1); ++r) issue(r);
+    __syncwarp();                                     // row y0-2 is read
+    if (lane == 0 && first + NSLOT2 <= last) issue(first + NSLOT2);
   }
   f2 acc = Z2;                                        // 0 * (updated values): NaN iff one is not finite
 
-  // one row: gradients of row j+1 into gn / rn, the face above row j into t*, row j updated
-  // with the face below b*
-  auto row = [&](int j, const GP &gc, GP &gn, const float (&rc)[3], float (&rn)[3], f2 bE,
-                 f2 bHx, f2 bHy, f2 &tE, f2 &tHx, f2 &tHy) -> bool {
+  // one row: own gradients of row j+1 into gn, the y-face above row j into t*, row j updated
+  // with the y-face below b*
+  auto row = [&](int j, const GP &gc, GP &gn, f2 bE, f2 bHx, f2 bHy, f2 &tE, f2 &tHx,
+                 f2 &tHy) -> bool {
     if (!wait_row(j + 2)) return false;
-    const RowP v0 = staged_row(w.row[slot(j)], q);
-    const RowP v1 = staged_row(w.row[slot(j + 1)], q);
-    const RowP v2 = staged_row(w.row[slot(j + 2)], q);
-    diffs_p<false>(v1, v0, v2, gn, rn);
-    // x-faces of row j: X+1/2 (component x) and X+3/2 (component y)
+    const StagedRow2 &Rm = w.row[slot(j - 1)], &R0 = w.row[slot(j)];
+    const StagedRow2 &R1 = w.row[slot(j + 1)], &R2 = w.row[slot(j + 2)];
+    gn = staged_diffs(R0, R1, R2, q, 2);
+    const RowP v0 = staged_pair<true>(R0, q, 2), v1 = staged_pair<true>(R1, q, 2);
+    // left x-faces of A and B: l side the left neighbours (their gradients recomputed from the
+    // staged rows), r side the lane's own cells
+    const RowP vl = staged_pair<true>(R0, q, 1);
+    const GP gl = staged_diffs(Rm, R0, R1, q, 1);
     f2 fxE, fxHx, fxHy;
-    {
-      const float nb_eps = __shfl_down_sync(FULL, v0.eps.x, 1);
-      const float gn_ex = __shfl_down_sync(FULL, gc.ex.x, 1);
-      const float gn_ax = __shfl_down_sync(FULL, gc.ax.x, 1);
-      const float gn_bx = __shfl_down_sync(FULL, gc.bx.x, 1);
-      const float gn_ay = __shfl_down_sync(FULL, gc.ay.x, 1);
-      const float gn_ey = __shfl_down_sync(FULL, gc.ey.x, 1);
-      FSideP l, r;
-      l.e = pfma(Q4, gc.ex, v0.ez); l.hn = pfma(Q4, gc.ax, v0.hx); l.ht = pfma(Q4, gc.bx, v0.hy);
-      l.den = gc.ex; l.dhn = gc.ax; l.dht = gc.bx; l.dat = gc.ay; l.det = gc.ey;
-      l.eps = v0.eps;
-      r.den = pk(gc.ex.y, gn_ex); r.dhn = pk(gc.ax.y, gn_ax); r.dht = pk(gc.bx.y, gn_bx);
-      r.dat = pk(gc.ay.y, gn_ay); r.det = pk(gc.ey.y, gn_ey);
-      r.e = pfma(MQ4, r.den, pk(v0.ez.y, rc[0]));
-      r.hn = pfma(MQ4, r.dhn, pk(v0.hx.y, rc[1]));
-      r.ht = pfma(MQ4, r.dht, pk(v0.hy.y, rc[2]));
-      r.eps = pk(v0.eps.y, nb_eps);
-      face_flux_p(l, r, P.fx, fxE, fxHx, fxHy);
-      if (xedge) {
-        if (hiA) {                      // first face on the high-x boundary
-          const Side<float> s_ = xside_scalar<float>(col_of_p(v0, 0), grad_of_p(gc, 0), q4,
-                                                     p.inv2hx, p.inv2hy);
-          tm_face_flux<float, true>(s_, s_, p.Kx, fxE.x, fxHx.x, fxHy.x);
-        }
-        if (hiB) {                      // second face on the high-x boundary
-          const Side<float> s_ = xside_scalar<float>(col_of_p(v0, 1), grad_of_p(gc, 1), q4,
-                                                     p.inv2hx, p.inv2hy);
-          tm_face_flux<float, true>(s_, s_, p.Kx, fxE.y, fxHx.y, fxHy.y);
-        }
-        if (lo) {                       // second face is the low-x boundary face of column 0
-          RowV<float> nb;
-          nb.ez = rc[0]; nb.hx = rc[1]; nb.hy = rc[2]; nb.eps = nb_eps; nb.mu = 1.f;
-          RowG<float> gg;
-          gg.ex = gn_ex; gg.ax = gn_ax; gg.bx = gn_bx; gg.ay = gn_ay; gg.ey = gn_ey; gg.by = 0.f;
-          low_boundary_flux<float>(xside_scalar<float>(nb, gg, mq4, p.inv2hx, p.inv2hy), p.Kx,
-                                   fxE.y, fxHx.y, fxHy.y);
-        }
+    face_flux_p(xside(vl, gl, Q4), xside(v0, gc, MQ4), P.fx, fxE, fxHx, fxHy);
+    if (xedge) {
+      if (loA)                          // low-x face of column 0 (cell A)
+        low_boundary_flux<float>(xside_scalar<float>(col_of_p(v0, 0), grad_of_p(gc, 0), mq4,
+                                                     p.inv2hx, p.inv2hy),
+                                 p.Kx, fxE.x, fxHx.x, fxHy.x);
+      if (hiA) {                        // high-x face of column nx - 1 (left neighbour of A)
+        const Side<float> s_ = xside_scalar<float>(col_of_p(vl, 0), grad_of_p(gl, 0), q4,
+                                                   p.inv2hx, p.inv2hy);
+        tm_face_flux<float, true>(s_, s_, p.Kx, fxE.x, fxHx.x, fxHy.x);
+      }
+      if (hiB) {                        // the same for B
+        const Side<float> s_ = xside_scalar<float>(col_of_p(vl, 1), grad_of_p(gl, 1), q4,
+                                                   p.inv2hx, p.inv2hy);
+        tm_face_flux<float, true>(s_, s_, p.Kx, fxE.y, fxHx.y, fxHy.y);
       }
     }
+    // right faces: the next lane's left faces; for lane 31's A, lane 0's left face of B
+    auto right = [lane](f2 f) {
+      const float a = __shfl_down_sync(FULL, f.x, 1), b = __shfl_sync(FULL, f.y, 0);
+      const float c = __shfl_down_sync(FULL, f.y, 1);
+      return pk(lane == 31 ? b : a, c);
+    };
+    const f2 frE = right(fxE), frHx = right(fxHx), frHy = right(fxHy);
     // y-faces between rows j and j+1
     face_flux_p(yside(v0, gc, Q4), yside(v1, gn, MQ4), P.fy, tE, tHy, tHx);
     if (j + 1 == p.ny && yhi_nr) {
@@ -1088,40 +1097,30 @@ __global__ void __launch_bounds__(WARPS * 32, MINB2)
       }
       tE = pk(e[0], e[1]); tHx = pk(hx[0], hx[1]); tHy = pk(hy[0], hy[1]);
     }
-    // update row j: left face of column X is the previous lane's second face
-    const float lE = __shfl_up_sync(FULL, fxE.y, 1);
-    const float lHx = __shfl_up_sync(FULL, fxHx.y, 1);
-    const float lHy = __shfl_up_sync(FULL, fxHy.y, 1);
-    f2 dE = padd(psub(pk(lE, fxE.x), fxE), psub(bE, tE));
-    const f2 dHx = padd(psub(pk(lHx, fxHx.x), fxHx), psub(bHx, tHx));
-    const f2 dHy = padd(psub(pk(lHy, fxHy.x), fxHy), psub(bHy, tHy));
+    // update row j
+    f2 dE = padd(psub(fxE, frE), psub(bE, tE));
+    const f2 dHx = padd(psub(fxHx, frHx), psub(bHx, tHx));
+    const f2 dHy = padd(psub(fxHy, frHy), psub(bHy, tHy));
+    const int64_t ro = (int64_t)j * p.pitch;
     if (p.src && j >= p.sy0 && j < p.sy1) {
-      const int64_t ro = (int64_t)j * p.pitch;
-      if (X >= p.sx0 && X < p.sx1) dE.x -= p.src_amp * p.src[ro + X];
-      if (X + 1 >= p.sx0 && X + 1 < p.sx1) dE.y -= p.src_amp * p.src[ro + X + 1];
+      if (A >= p.sx0 && A < p.sx1) dE.x -= p.src_amp * p.src[ro + A];
+      if (B >= p.sx0 && B < p.sx1) dE.y -= p.src_amp * p.src[ro + B];
     }
     const f2 ne = pfma(dE, pk(rcp1(v0.eps.x), rcp1(v0.eps.y)), v0.ez);
     const f2 nhx = padd(v0.hx, dHx);
     const f2 nhy = padd(v0.hy, dHy);
+    float *o = p.Vout + ro;
+    if (stA) {
+      o[A] = ne.x; o[p.cstride + A] = nhx.x; o[2 * p.cstride + A] = nhy.x;
+    }
+    if (stB) {
+      o[B] = ne.y; o[p.cstride + B] = nhx.y; o[2 * p.cstride + B] = nhy.y;
+    }
     const f2 sum = padd(padd(ne, nhx), nhy);
-    if (okA && okB) acc = pfma(sum, Z2, acc);
-    else if (okA) acc.x = fmaf(sum.x, 0.f, acc.x);
-    // stage the row and store it; the buffer's previous store (row j-2) must have read it
-    OutBox2 &O = w.out[j & 1];
-    if (lane == 0) tma_store_wait_read<1>();
-    __syncwarp();
-    if (lane >= 1 && lane <= 30) {
-      const int c = 2 * lane - 2;
-      *reinterpret_cast<f2 *>(&O.a[0][c]) = ne;
-      *reinterpret_cast<f2 *>(&O.a[1][c]) = nhx;
-      *reinterpret_cast<f2 *>(&O.a[2][c]) = nhy;
-      fence_proxy_async();
-    }
-    __syncwarp();                                     // row j's slot is read, the row staged
-    if (lane == 0) {
-      tma_store_3d(&tmO, &O.a[0][0], x0, j, 0);
-      if (j + NSLOT2 <= last) issue(j + NSLOT2);
-    }
+    if (stB) acc = pfma(sum, Z2, acc);                 // stB implies stA
+    else if (stA) acc.x = fmaf(sum.x, 0.f, acc.x);
+    __syncwarp();                                     // row j-1 is read
+    if (lane == 0 && j + NSLOT2 - 1 <= last) issue(j + NSLOT2 - 1);
     return true;
   };
 
@@ -1129,21 +1128,18 @@ __global__ void __launch_bounds__(WARPS * 32, MINB2)
   if (ok) {
 #pragma unroll 1
     for (; j + 1 < y1; j += 2) {
-      if (!row(j, g0, g1, r0, r1, fbE, fbHx, fbHy, ftE, ftHx, ftHy) ||
-          !row(j + 1, g1, g0, r1, r0, ftE, ftHx, ftHy, fbE, fbHx, fbHy)) {
+      if (!row(j, g0, g1, fbE, fbHx, fbHy, ftE, ftHx, ftHy) ||
+          !row(j + 1, g1, g0, ftE, ftHx, ftHy, fbE, fbHx, fbHy)) {
         ok = false;
         break;
       }
     }
-    if (ok && j < y1) ok = row(j, g0, g1, r0, r1, fbE, fbHx, fbHy, ftE, ftHx, ftHy);
+    if (ok && j < y1) ok = row(j, g0, g1, fbE, fbHx, fbHy, ftE, ftHx, ftHy);
   }
-  if (lane == 0) {
-    if (!ok) {
-      atomicOr(p.flag, 2);                            // a row never landed
-      for (int r = max(first, issued - NSLOT2 + 1); r <= issued; ++r)   // copies in flight
-        mbar_wait(&w.bar[slot(r)], parity(r));
-    }
-    tma_store_wait_all();                             // the staging rows outlive their stores
+  if (lane == 0 && !ok) {
+    atomicOr(p.flag, 2);                              // a row never landed
+    for (int r = max(first, issued - NSLOT2 + 1); r <= issued; ++r)   // copies in flight
+      mbar_wait(&w.bar[slot(r)], parity(r));
   }
   if (__any_sync(FULL, !(isfinite(acc.x) && isfinite(acc.y))) && lane == 0) atomicOr(p.flag, 1);
 }
@@ -1168,24 +1164,27 @@ bool staged2_supported(const CartGeom &g, const CartStepArgs &a) {
   return tensor_map_encoder() != nullptr;
 }
 
-// Staged launch over strips [strip0, strip0 + nstrips) and rows [wy0, wy1): about four waves
-// of warps (each marching a chunk of at least 8 rows of one strip), so that the CTA scheduler
-// evens out the SMs' progress; one wave of long chunks ran 11% slower on the 4096^2 grid.
+// Staged launch over the window's columns [wx0, wx1) (strips of W2 columns) and rows [wy0, wy1):
+// about four waves of warps (each marching a chunk of at least 8 rows of one strip), so that the
+// CTA scheduler evens out the SMs' progress; one wave of long chunks ran 11% slower on the
+// 4096^2 grid.
 constexpr int kWaves2 = 4;
-cudaError_t launch_staged2(const CartGeom &g, const Cart2DPackArgs &P, int strip0, int nstrips,
-                           int wy0, int wy1, cudaStream_t st) {
+cudaError_t launch_staged2(const CartGeom &g, const Cart2DPackArgs &P, int wx0, int wx1, int wy0,
+                           int wy1, cudaStream_t st) {
   const int smem = WARPS * (int)sizeof(WarpStage2);
   static int per_sm = 0, sms = 0;
   if (!per_sm) {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaFuncSetAttribute(cart2d_step_kernel_t, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cart2d_step_kernel_t, WARPS * 32,
+    cudaFuncSetAttribute(cart2d_step_kernel_s, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cart2d_step_kernel_s, WARPS * 32,
                                                   smem);
     if (sms < 1) sms = 1;
     if (per_sm < 1) per_sm = 1;
   }
+  const int strip0 = wx0 / W2;
+  const int nstrips = (wx1 - 1) / W2 - strip0 + 1;
   const int64_t resident = (int64_t)sms * per_sm * WARPS;
   const int wrows = wy1 - wy0;
   const int64_t want = resident * kWaves2 / nstrips;
@@ -1195,16 +1194,15 @@ cudaError_t launch_staged2(const CartGeom &g, const Cart2DPackArgs &P, int strip
   nchunks = (wrows + rows - 1) / rows;
   const int64_t nwarps = (int64_t)nstrips * nchunks;
   const int grid = (int)((nwarps + WARPS - 1) / WARPS);
-  CUtensorMap tmV, tmE, tmO;
+  CUtensorMap tmV, tmE;
   const cuuint64_t dim[3] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, 3};
   const cuuint64_t stride[2] = {(cuuint64_t)g.pitch * 4, (cuuint64_t)g.cstride * 4};
-  const cuuint32_t box_in[3] = {TW2, 1, 3}, box_out[3] = {WCOLS, 1, 3};
-  if (!encode_f32_map(&tmV, P.b.V, 3, dim, stride, box_in) ||
-      !encode_f32_map(&tmE, P.b.eps, 2, dim, stride, box_in) ||
-      !encode_f32_map(&tmO, P.b.Vout, 3, dim, stride, box_out))
+  const cuuint32_t box[3] = {TW2, 1, 3};
+  if (!encode_f32_map(&tmV, P.b.V, 3, dim, stride, box) ||
+      !encode_f32_map(&tmE, P.b.eps, 2, dim, stride, box))
     return cudaErrorInvalidValue;
-  cart2d_step_kernel_t<<<grid, WARPS * 32, smem, st>>>(tmV, tmE, tmO, P, nstrips, rows, strip0,
-                                                      wy0, wy1);
+  cart2d_step_kernel_s<<<grid, WARPS * 32, smem, st>>>(tmV, tmE, P, nstrips, rows, strip0, wy0,
+                                                      wy1);
   return cudaGetLastError();
 }
 
@@ -1261,7 +1259,7 @@ cudaError_t launch_t(const CartGeom &g, const CartStepArgs &a, cudaStream_t st) 
       P.b = p;
       P.fx = make_face_kp(p.fx);
       P.fy = make_face_kp(p.fy);
-      if (staged2_supported(g, a)) return launch_staged2(g, P, strip0, nstrips, wy0, wy1, st);
+      if (staged2_supported(g, a)) return launch_staged2(g, P, wx0, wx1, wy0, wy1, st);
       using KP = void (*)(const Cart2DPackArgs, int, int, int, int, int);
       static const KP kp[2][2] = {{cart2d_step_kernel_p<false, false>,
                                    cart2d_step_kernel_p<false, true>},

@@ -1,11 +1,11 @@
 """GPU parity of the staged 2-D TM step (FP32, mu = 1, non-reflecting or periodic-y sides: rows
-staged in shared memory by tensor copies, rows written back by tensor stores) against the FP64
-oracle, relative L2 <= 2e-5.
+staged in shared memory by tensor copies, a lane's two cells 32 columns apart, 63 columns per
+warp) against the FP64 oracle, relative L2 <= 2e-5.
 
 Shapes span the strip and chunk structure of that kernel: widths below, at and past one
-60-column strip and ragged against it, heights of one or two rows and heights that split a
-strip into several row chunks with an odd last chunk; sources, periodic y (with the two-row
-wrap), rectangular cells."""
+63-column strip and ragged against it, high-x boundary faces on either half of a lane's pair,
+heights of one or two rows and heights that split a strip into several row chunks with an odd
+last chunk; sources, periodic y (with the two-row wrap), rectangular cells."""
 import numpy as np
 import pytest
 
@@ -42,10 +42,12 @@ def _workload(nx, ny, ybc, seed, with_src, hy_ratio=1.0):
 
 
 @pytest.mark.parametrize("nx,ny,ybc,src,hy", [
-    (61, 47, "nrbc", True, 1.0),      # two strips, the second one column wide; 6 row chunks
-    (59, 9, "nrbc", False, 0.7),      # one strip, its last lane pair past the grid
-    (60, 2, "nrbc", True, 1.0),       # exactly one strip, two rows
-    (121, 130, "nrbc", True, 1.3),    # three strips, many chunks, odd last chunk
+    (64, 47, "nrbc", True, 1.0),      # two strips, the second one column wide; 6 row chunks
+    (59, 9, "nrbc", False, 0.7),      # one strip, its last cells past the grid
+    (63, 2, "nrbc", True, 1.0),       # exactly one strip, two rows
+    (127, 130, "nrbc", True, 1.3),    # three strips, many chunks, odd last chunk
+    (33, 40, "nrbc", True, 1.0),      # high-x face on the second half of lane 1's pair
+    (32, 5, "nrbc", False, 1.0),      # high-x face on the second half of lane 0's pair
     (1, 7, "nrbc", False, 1.0),       # one column: both x faces on the same cell
     (3, 1, "nrbc", True, 1.0),        # one row: both y faces on the same cell
     (200, 3, "periodic", True, 1.0),  # periodic y on three rows (wrap of two rows)
