@@ -57,9 +57,11 @@ def _gpu(vert, tet, eps, mu, f, mask, steps, prec, kappa, src=(1.0, 20.0, 0.02, 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 @pytest.mark.parametrize("kappa", [0.0, 0.05])
-@pytest.mark.parametrize("case", [(3, False, False), (4, True, True)])
+@pytest.mark.parametrize("case", [(3, False, False), (4, True, True), (5, False, True)])
 def test_random_tet_meshes(precision, kappa, case):
-    """Jittered Kuhn meshes, random eps (and mu), scattered source, 10 steps."""
+    """Jittered Kuhn meshes, random eps (and mu), scattered source, 10 steps.  The meshes hold
+    162, 384 and 750 tets: one, two and three 256-thread blocks per pass, the last one partly
+    full."""
     m, with_mu, with_src = case
     vert, tet, eps, mu, f, mask = _rand_tets(m, 40 + m, with_mu=with_mu, with_src=with_src)
     out, info = _gpu(vert, tet, eps, mu, f, mask, 10, precision, kappa)
