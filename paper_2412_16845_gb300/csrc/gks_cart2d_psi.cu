@@ -427,24 +427,22 @@ __device__ __forceinline__ q2 qsub(q2 a, q2 b) { return __ffma2_rn(b, make_float
 __device__ __forceinline__ q2 qmul(q2 a, q2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ q2 qfma(q2 a, q2 b, q2 c) { return __ffma2_rn(a, b, c); }
 
-// FaceK and FacePsiK constants (a14 = a1 + a4; n* negated) as scalars: a paired FMA reads a
-// scalar kernel parameter replicated into both halves straight from the constant bank, whereas
-// a float2 parameter costs an extra instruction per use.
+// FaceK and FacePsiK constants as pairs (a14 = a1 + a4; n* negated).
 struct PsiKP {
-  float a14, a2, a3, a5, a6, nq2, nq3, q5, b1, c1, c2, c3, c4, c5, c6, g0, nk3, half;
-  float pe1, pe2, pa1, pa2, pa3, pa4, pa5, pa6, h0, nh1, pp5, pz1, pz2;
+  q2 a14, a2, a3, a5, a6, nq2, nq3, q5, b1, c1, c2, c3, c4, c5, c6, g0, nk3, half;
+  q2 pe1, pe2, pa1, pa2, pa3, pa4, pa5, pa6, h0, nh1, pp5, pz1, pz2;
 };
-__device__ __forceinline__ q2 qrep(float k) { return make_float2(k, k); }
 
 inline PsiKP make_psi_kp(const FaceK<float> &k, const FacePsiK<float> &q) {
+  auto b = [](float v) { return make_float2(v, v); };
   PsiKP r;
-  r.a14 = k.a1 + k.a4; r.a2 = k.a2; r.a3 = k.a3; r.a5 = k.a5; r.a6 = k.a6;
-  r.nq2 = -k.q2; r.nq3 = -k.q3; r.q5 = k.q5; r.b1 = k.b1;
-  r.c1 = k.c1; r.c2 = k.c2; r.c3 = k.c3; r.c4 = k.c4; r.c5 = k.c5; r.c6 = k.c6;
-  r.g0 = k.g0; r.nk3 = -k.k3; r.half = 0.5f;
-  r.pe1 = q.pe1; r.pe2 = q.pe2; r.pa1 = q.pa1; r.pa2 = q.pa2; r.pa3 = q.pa3;
-  r.pa4 = q.pa4; r.pa5 = q.pa5; r.pa6 = q.pa6; r.h0 = q.h0; r.nh1 = -q.h1;
-  r.pp5 = q.pp5; r.pz1 = q.pz1; r.pz2 = q.pz2;
+  r.a14 = b(k.a1 + k.a4); r.a2 = b(k.a2); r.a3 = b(k.a3); r.a5 = b(k.a5); r.a6 = b(k.a6);
+  r.nq2 = b(-k.q2); r.nq3 = b(-k.q3); r.q5 = b(k.q5); r.b1 = b(k.b1);
+  r.c1 = b(k.c1); r.c2 = b(k.c2); r.c3 = b(k.c3); r.c4 = b(k.c4); r.c5 = b(k.c5); r.c6 = b(k.c6);
+  r.g0 = b(k.g0); r.nk3 = b(-k.k3); r.half = b(0.5f);
+  r.pe1 = b(q.pe1); r.pe2 = b(q.pe2); r.pa1 = b(q.pa1); r.pa2 = b(q.pa2); r.pa3 = b(q.pa3);
+  r.pa4 = b(q.pa4); r.pa5 = b(q.pa5); r.pa6 = b(q.pa6); r.h0 = b(q.h0); r.nh1 = b(-q.h1);
+  r.pp5 = b(q.pp5); r.pz1 = b(q.pz1); r.pz2 = b(q.pz2);
   return r;
 }
 
@@ -466,52 +464,52 @@ __device__ __forceinline__ void face_flux_psi_p(const PSideP &l, const PSideP &r
   const q2 D_ex = qsub(r.den, l.den), S_UAt = qadd(l.dat, r.dat), S_e = qadd(l.e, r.e);
   const q2 se = qadd(l.eps, r.eps);
   const q2 ie = qk(prcp2(se.x), prcp2(se.y));
-  const q2 g = qfma(qrep(k.nk3), ie, qrep(k.g0));
+  const q2 g = qfma(k.nk3, ie, k.g0);
   // Maxwell part (mu = 1)
-  q2 fe = qmul(qrep(k.a14), S_B);
-  fe = qfma(qrep(k.a2), D_e, fe);
-  fe = qfma(g, qfma(qrep(k.a3), D_xB, qmul(qrep(k.half), S_Uxe)), fe);
-  fe = qfma(qrep(k.nq2), D_Ue, fe);
-  fe = qfma(qrep(k.nq3), S_Uxe, fe);
-  fe = qfma(qrep(k.a5), D_At, fe);
-  fe = qfma(qrep(k.a6), D_xB, fe);
-  q2 fa = qmul(qrep(k.q5), S_Uxa);
-  fa = qfma(qrep(k.nq2), D_Ua, fa);
-  fa = qfma(qrep(k.b1), D_Et, fa);
-  q2 u = qmul(qrep(k.c1), S_Ue);
-  u = qfma(qrep(k.c2), D_B, u);
-  u = qfma(qrep(k.c4), S_UAt, u);
+  q2 fe = qmul(k.a14, S_B);
+  fe = qfma(k.a2, D_e, fe);
+  fe = qfma(g, qfma(k.a3, D_xB, qmul(k.half, S_Uxe)), fe);
+  fe = qfma(k.nq2, D_Ue, fe);
+  fe = qfma(k.nq3, S_Uxe, fe);
+  fe = qfma(k.a5, D_At, fe);
+  fe = qfma(k.a6, D_xB, fe);
+  q2 fa = qmul(k.q5, S_Uxa);
+  fa = qfma(k.nq2, D_Ua, fa);
+  fa = qfma(k.b1, D_Et, fa);
+  q2 u = qmul(k.c1, S_Ue);
+  u = qfma(k.c2, D_B, u);
+  u = qfma(k.c4, S_UAt, u);
   q2 fb = qmul(ie, u);
-  fb = qfma(g, qfma(qrep(k.c3), D_ex, qmul(qrep(k.half), S_UxB)), fb);
-  fb = qfma(qrep(k.c5), S_e, fb);
-  fb = qfma(qrep(k.nq2), D_B, fb);
-  fb = qfma(qrep(k.nq3), S_UxB, fb);
-  fb = qfma(qrep(k.c6), D_ex, fb);
+  fb = qfma(g, qfma(k.c3, D_ex, qmul(k.half, S_UxB)), fb);
+  fb = qfma(k.c5, S_e, fb);
+  fb = qfma(k.nq2, D_B, fb);
+  fb = qfma(k.nq3, S_UxB, fb);
+  fb = qfma(k.c6, D_ex, fb);
   // gamma terms and psi's own transport
   const q2 S_p = qadd(l.p, r.p), D_p = qsub(r.p, l.p);
   const q2 S_np = qadd(l.dnp, r.dnp), D_np = qsub(r.dnp, l.dnp);
   const q2 S_tp = qadd(l.dtp, r.dtp), D_tp = qsub(r.dtp, l.dtp);
   const q2 S_tt = qadd(l.dtt, r.dtt), D_tt = qsub(r.dtt, l.dtt);
   const q2 S_hn = qadd(l.hn, r.hn), D_hn_n = qsub(r.dhn, l.dhn);
-  const q2 H = qfma(qrep(k.nh1), ie, qrep(k.h0));
-  fe = qfma(qrep(k.pe1), S_tp, fe);
-  fe = qfma(qrep(k.pe2), D_At, fe);
-  fa = qfma(qrep(k.pa1), S_p, fa);
-  fa = qfma(qrep(k.pa2), S_Uxa, fa);
-  fa = qfma(qrep(k.pa3), S_tt, fa);
-  fa = qfma(qrep(k.pa4), D_Ua, fa);
-  fa = qfma(qrep(k.pa5), D_np, fa);
-  fa = qfma(qrep(k.pa6), D_Et, fa);
+  const q2 H = qfma(k.nh1, ie, k.h0);
+  fe = qfma(k.pe1, S_tp, fe);
+  fe = qfma(k.pe2, D_At, fe);
+  fa = qfma(k.pa1, S_p, fa);
+  fa = qfma(k.pa2, S_Uxa, fa);
+  fa = qfma(k.pa3, S_tt, fa);
+  fa = qfma(k.pa4, D_Ua, fa);
+  fa = qfma(k.pa5, D_np, fa);
+  fa = qfma(k.pa6, D_Et, fa);
   fb = qfma(H, D_tp, fb);
   const q2 Edet = qfma(l.eps, l.det, qmul(r.eps, r.det));
-  q2 fp = qmul(qrep(k.pa1), S_hn);
-  fp = qfma(qrep(k.pa2), S_np, fp);
-  fp = qfma(qrep(k.pa4), D_p, fp);
-  fp = qfma(qrep(k.pa5), D_hn_n, fp);
+  q2 fp = qmul(k.pa1, S_hn);
+  fp = qfma(k.pa2, S_np, fp);
+  fp = qfma(k.pa4, D_p, fp);
+  fp = qfma(k.pa5, D_hn_n, fp);
   fp = qfma(H, D_tt, fp);
-  fp = qfma(qmul(qrep(k.pp5), ie), Edet, fp);
-  fp = qfma(qrep(k.pz1), D_p, fp);
-  fp = qfma(qrep(k.pz2), S_np, fp);
+  fp = qfma(qmul(k.pp5, ie), Edet, fp);
+  fp = qfma(k.pz1, D_p, fp);
+  fp = qfma(k.pz2, S_np, fp);
   fE = fe;
   fHn = fa;
   fHt = fb;
