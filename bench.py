@@ -50,18 +50,22 @@ def _peaks():
     return 6800.0, "fallback"
 
 
-def _kernel_hash():
-    return hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
+KERNEL_SRC_3D = os.path.join(ROOT, "paper_2412_16845_gb300", "csrc", "gks_cart3d_side.cu")
+PROFILE_3D = os.path.join(ROOT, "profiles", "cart3d_side_step_maxwell3d_sphere_fp32.md")
 
 
-def _profiled_traffic():
-    """DRAM bytes per launch from the committed ncu summary, if it matches the current kernel."""
-    if not os.path.exists(PROFILE):
+def _kernel_hash(src=KERNEL_SRC):
+    return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+
+
+def _profiled_traffic(profile=PROFILE, src=KERNEL_SRC):
+    """DRAM bytes per launch from a committed ncu summary, if it matches the current kernel."""
+    if not os.path.exists(profile):
         return None
-    txt = open(PROFILE).read()
+    txt = open(profile).read()
     m = re.search(r"dram_bytes_per_launch\s*=\s*([0-9.eE+]+)", txt)
     h = re.search(r"kernel_source_sha256_16\s*=\s*([0-9a-f]+)", txt)
-    if not m or not h or h.group(1) != _kernel_hash():
+    if not m or not h or h.group(1) != _kernel_hash(src):
         return None
     return float(m.group(1))
 
@@ -279,6 +283,32 @@ def reduced_gpu_results(stream_ptr, path):
         out[f"tets_{prec}"] = s.read_fields()
         s.close()
     np.savez(path, **out)
+
+
+# The 3-D FP32 step kernel (cart3d_side_kernel) is bound by instruction issue: its ncu summary
+# (profiles/cart3d_side_step_maxwell3d_sphere_fp32.md) counts 608 thread-instructions per cell at
+# 160^3, where 20% of the 64-column tiles lie past the grid, i.e. about 520 per cell on a grid of
+# whole tiles such as 256^3.  The issue peak is 152 SMs x 4 schedulers x 32 threads x 2.07 GHz.
+INSTR_PER_CELL_3D = 520
+ISSUE_PEAK_T = 152 * 4 * 32 * 2.07e9 / 1e12          # T thread-instructions/s
+
+
+def roofline_3d(ncell, ms):
+    """Roofline object of the 3-D FP32 step: issue-bound (thread-instructions per second against
+    the issue peak), with the HBM fraction of its 52 algorithmic bytes per cell alongside."""
+    hbm, how = _peaks()
+    gcells = ncell / (ms * 1e-3) / 1e9
+    achieved = gcells * 1e9 * INSTR_PER_CELL_3D / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": ISSUE_PEAK_T,
+            "unit": "T thread-instructions/s", "frac": achieved / ISSUE_PEAK_T,
+            "peak_source": "152 SMs x 4 schedulers x 32 lanes x 2.07 GHz",
+            "instructions_per_cell": INSTR_PER_CELL_3D,
+            "instructions_source": "ncu, profiles/cart3d_side_step_maxwell3d_sphere_fp32.md",
+            "kernel": "cart3d_side_kernel (FP32, mu = 1)",
+            "hbm": {"achieved": 52 * gcells, "peak": hbm, "unit": "GB/s",
+                    "frac": 52 * gcells / hbm, "peak_source": how,
+                    "traffic": _profiled_traffic(PROFILE_3D, KERNEL_SRC_3D) if ncell == 256 ** 3
+                    else None}}
 
 
 def divergence_report(sptr):
@@ -635,7 +665,8 @@ def main():
                  "value_fp64": n3 / (ms3_64 * 1e-3) / 1e9, "ms_per_step_fp64": ms3_64,
                  "fp32_speedup": ms3_64 / ms3, "fp32_vs_fp64_rel_l2_after_500": err3,
                  "hbm_frac_fp32": 52 * n3 / (ms3 * 1e-3) / 1e9 / _peaks()[0],
-                 "algorithmic_bytes_per_cell_step": 52}
+                 "algorithmic_bytes_per_cell_step": 52,
+                 "roofline": roofline_3d(n3, ms3)}
 
     # ---------------- tetrahedral sphere workload (64^3 x 6 Kuhn tets, jittered): FP32 and FP64
     tets = None
