@@ -159,6 +159,30 @@ def test_phm_3d(precision, kappa, case):
     assert rel_l2(out, ref) <= TOL[precision], rel_l2(out, ref)
 
 
+_WIDE_PHM_REF = {}
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("kappa", [0.0, 0.05])
+@pytest.mark.parametrize("case", [
+    (65, 23, 19, ("nrbc",) * 6, (1.0, 1.0), True),
+    (61, 31, 17, ("nrbc", "nrbc", "periodic", "periodic", "periodic", "periodic"), (0.7, 0.4),
+     False),
+])
+def test_phm_3d_wide_ragged_grids(precision, kappa, case):
+    """The cleaning kernel on grids spanning several CTAs in every direction: three x-tiles of
+    its 30-column interior with a ragged last one, y over 20 rows (three or four 10-row tiles,
+    the last ragged), z split into several chunks; a scattered source on the first grid; 4 steps
+    against the oracle."""
+    nx, ny, nz, bc, phm, with_src = case
+    w = _w3(nx, ny, nz, bc, phm, seed=nx + 3 * ny + nz, with_src=with_src)
+    out, info = _gpu(w, 4, precision, kappa)
+    key = (nx, ny, nz, kappa)
+    if key not in _WIDE_PHM_REF:
+        _WIDE_PHM_REF[key] = oracle_cart_run(w, 4, kappa=kappa, c=info["c"])[0]
+    assert rel_l2(out, _WIDE_PHM_REF[key]) <= TOL[precision], rel_l2(out, _WIDE_PHM_REF[key])
+
+
 def test_phm_3d_energy_includes_potentials():
     """gks_energy with cleaning: 1/2 sum |Omega| (eps |E|^2 + |H|^2 + phi^2 + psi^2)."""
     w = _w3(10, 9, 8, ("nrbc",) * 6, (0.5, 0.5), seed=4)
