@@ -11,6 +11,7 @@
 
 #include "gks_flux2.cuh"
 #include "gks_internal.h"
+#include "gks_tma.cuh"
 
 namespace gks {
 namespace {
@@ -767,7 +768,298 @@ __global__ void __launch_bounds__(PWARPS * 32, 3) cart2d_psi_step_kernel_p(const
   }
   if (__any_sync(PFULL, bad) && lane == 0) atomicOr(p.flag, 1);
 }
+// ------------------------------------------------------------------ staged FP32 path
+// The staged march of the 2-D TM step (gks_cart2d.cu: rows staged per warp by TMA, a lane's two
+// cells 32 columns apart, 63 columns per warp, left x-faces per lane, every neighbour read from
+// the staged rows, coalesced stores) with psi as a fourth field: FP32, no limiter, no PEC wall,
+// x not periodic.  (With the limiter the register-window kernel below is faster: the left
+// neighbours' limited slopes would be recomputed here rather than shuffled.)
+constexpr int PW2 = 63;                 // columns updated per warp
+constexpr int PTW2 = 72;                // staged columns (x0-3 rounded down to 4, +72)
+constexpr int PNSLOT2 = 8;              // staged rows per warp
+static_assert((PNSLOT2 & (PNSLOT2 - 1)) == 0, "the ring index masks with PNSLOT2 - 1");
+struct alignas(128) PRowBox2 { float a[4][PTW2]; };   // Ez, Hx, Hy, psi
+struct alignas(128) PEpsBox2 { float e[PTW2]; };
+struct PStagedRow2 { PRowBox2 v; PEpsBox2 e; };
+struct PWarpStage2 {
+  PStagedRow2 row[PNSLOT2];
+  unsigned long long bar[PNSLOT2];
+};
+constexpr unsigned kPRowBytes2 = 5 * PTW2 * 4;         // both boxes of one staged row
+
+struct PTaps2 {
+  int a[4], b[4];       // [k]: staged column of A + k - 2 / B + k - 2 (clamped to the grid)
+};
+
+template <bool EPS>
+__device__ __forceinline__ PRowP pstaged_pair(const PStagedRow2 &R, const PTaps2 &q, int k) {
+  PRowP v;
+  v.ez = qk(R.v.a[0][q.a[k]], R.v.a[0][q.b[k]]);
+  v.hx = qk(R.v.a[1][q.a[k]], R.v.a[1][q.b[k]]);
+  v.hy = qk(R.v.a[2][q.a[k]], R.v.a[2][q.b[k]]);
+  v.ps = qk(R.v.a[3][q.a[k]], R.v.a[3][q.b[k]]);
+  v.eps = EPS ? qk(R.e.e[q.a[k]], R.e.e[q.b[k]]) : qk(0.f, 0.f);
+  v.xm[0] = v.xm[1] = v.ym = false;
+  return v;
+}
+
+// Raw central differences of the pair at tap k of row `mid` (rows `dn` and `up` below and above).
+__device__ __forceinline__ PGP pstaged_diffs(const PStagedRow2 &dn, const PStagedRow2 &mid,
+                                             const PStagedRow2 &up, const PTaps2 &q, int k) {
+  PGP g;
+  const PRowP l = pstaged_pair<false>(mid, q, k - 1), r = pstaged_pair<false>(mid, q, k + 1);
+  const PRowP d = pstaged_pair<false>(dn, q, k), u = pstaged_pair<false>(up, q, k);
+  g.ex = qsub(r.ez, l.ez); g.ax = qsub(r.hx, l.hx); g.bx = qsub(r.hy, l.hy);
+  g.px = qsub(r.ps, l.ps);
+  g.ey = qsub(u.ez, d.ez); g.ay = qsub(u.hx, d.hx); g.by = qsub(u.hy, d.hy);
+  g.py = qsub(u.ps, d.ps);
+  return g;
+}
+
+// x-face side of the pair (normal x: hn = Hx, ht = Hy).
+__device__ __forceinline__ PSideP psi_xside_p(const PRowP &v, const PGP &g, q2 sgn) {
+  PSideP s;
+  s.e = qfma(sgn, g.ex, v.ez); s.hn = qfma(sgn, g.ax, v.hx); s.ht = qfma(sgn, g.bx, v.hy);
+  s.p = qfma(sgn, g.px, v.ps);
+  s.den = g.ex; s.dhn = g.ax; s.dht = g.bx; s.dnp = g.px;
+  s.dat = g.ay; s.det = g.ey; s.dtp = g.py; s.dtt = g.by;
+  s.eps = v.eps;
+  return s;
+}
+
+// Two CTAs per SM: the psi component's flux keeps more values live than the TM step's (at 3
+// CTAs per SM, 168 registers, the kernel spills 356 B per thread and runs 28% slower than at 2).
+__global__ void __launch_bounds__(PWARPS * 32, 2)
+    cart2d_psi_step_kernel_s(const __grid_constant__ CUtensorMap tmV,
+                             const __grid_constant__ CUtensorMap tmE, const PsiPackArgs P,
+                             int nstrips, int rows) {
+  extern __shared__ __align__(128) unsigned char smem_ps[];
+  const PsiArgs<float> &p = P.b;
+  const int lane = threadIdx.x & 31;
+  PWarpStage2 &w = reinterpret_cast<PWarpStage2 *>(smem_ps)[threadIdx.x >> 5];
+  const int wid = blockIdx.x * PWARPS + (threadIdx.x >> 5);
+  const int strip = wid % nstrips, chunk = wid / nstrips;
+  const int y0 = chunk * rows;
+  if (y0 >= p.ny) return;                             // whole warp leaves together
+  const int y1 = min(y0 + rows, p.ny);
+  const int x0 = strip * PW2;
+  const int xs = (x0 - 3) & ~3;                       // first staged column (16-byte aligned)
+  const int A = x0 + lane, B = x0 + 32 + lane;
+  const bool ylo_nr = !p.pery, yhi_nr = !p.pery;
+  const float q4 = 0.25f, mq4 = -0.25f;
+  const q2 Q4 = qk(q4, q4), MQ4 = qk(mq4, mq4), Z2 = qk(0.f, 0.f);
+  PTaps2 q;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    q.a[k] = min(max(A + k - 2, 0), p.nx - 1) - xs;
+    q.b[k] = min(max(B + k - 2, 0), p.nx - 1) - xs;
+  }
+  // boundary x faces (scalar flux): the left face of column 0 is its low-x face, the left face
+  // of column nx is the high-x face of column nx - 1
+  const bool loA = A == 0, hiA = A == p.nx, hiB = B == p.nx;
+  const bool xedge = __any_sync(PFULL, loA || hiA || hiB);
+  const int xend = min(x0 + PW2, p.nx);
+  const bool stA = A < xend, stB = lane < 31 && B < xend;
+
+  const int first = y0 - 2, last = y1 + 1;            // staged rows
+  auto slot = [first](int r) { return (r - first) & (PNSLOT2 - 1); };
+  auto parity = [first](int r) { return (unsigned)(((r - first) / PNSLOT2) & 1); };
+  auto grid_row = [&p](int r) {
+    return p.pery ? (r < 0 ? r + p.ny : (r >= p.ny ? r - p.ny : r)) : min(max(r, 0), p.ny - 1);
+  };
+  int issued = first - 1;                             // lane 0: the last row whose copy is issued
+  auto issue = [&](int r) {                           // lane 0 only
+    const int s_ = slot(r), gr = grid_row(r);
+    fence_proxy_async();
+    mbar_expect_tx(&w.bar[s_], kPRowBytes2);
+    tma_load_3d(&w.row[s_].v.a[0][0], &tmV, xs, gr, 0, &w.bar[s_]);
+    tma_load_2d(&w.row[s_].e.e[0], &tmE, xs, gr, &w.bar[s_]);
+    issued = r;
+  };
+  auto wait_row = [&](int r) {                        // the whole warp; false if it ran out
+    return __all_sync(PFULL, mbar_wait(&w.bar[slot(r)], parity(r)));
+  };
+  if (lane == 0) {
+    for (int i = 0; i < PNSLOT2; ++i) mbar_init(&w.bar[i], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    for (int r = first; r <= min(last, first + PNSLOT2 - 1); ++r) issue(r);
+  }
+  __syncwarp();
+
+  bool ok = true;
+  for (int r = first; r <= y0 + 1; ++r) ok = ok && wait_row(r);
+  PGP g0, g1;
+  q2 fbE, fbHx, fbHy, fbP, ftE, ftHx, ftHy, ftP;
+  if (ok) {
+    const PStagedRow2 &Rm2 = w.row[slot(y0 - 2)], &Rm1 = w.row[slot(y0 - 1)];
+    const PStagedRow2 &R0 = w.row[slot(y0)], &R1 = w.row[slot(y0 + 1)];
+    const PGP gm1 = pstaged_diffs(Rm2, Rm1, R0, q, 2);
+    g0 = pstaged_diffs(Rm1, R0, R1, q, 2);
+    const PRowP vm1 = pstaged_pair<true>(Rm1, q, 2), v0 = pstaged_pair<true>(R0, q, 2);
+    face_flux_psi_p(psi_yside_p(vm1, gm1, Q4), psi_yside_p(v0, g0, MQ4), P.ky, fbE, fbHy, fbHx,
+                    fbP);
+    if (y0 == 0 && ylo_nr) {
+      float e[2], hx[2], hy[2], ps[2];
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const PSide<float> up = psi_yside<float>(GKS_COL(v0, ez, k), GKS_COL(v0, hx, k),
+                                                 GKS_COL(v0, hy, k), GKS_COL(v0, ps, k),
+                                                 GKS_COL(v0, eps, k), pg_of(g0, k), mq4);
+        face_flux_psi<float>(psi_zero<float>(), up, p.fy, p.qy, prcp1(GKS_COL(v0, eps, k)), e[k],
+                             hy[k], hx[k], ps[k]);
+      }
+      fbE = qk(e[0], e[1]); fbHx = qk(hx[0], hx[1]); fbHy = qk(hy[0], hy[1]);
+      fbP = qk(ps[0], ps[1]);
+    }
+    __syncwarp();                                     // row y0-2 is read
+    if (lane == 0 && first + PNSLOT2 <= last) issue(first + PNSLOT2);
+  }
+  q2 acc = Z2;                                        // 0 * (updated values): NaN iff one is not finite
+
+  auto row = [&](int j, const PGP &gc, PGP &gn, q2 bE, q2 bHx, q2 bHy, q2 bP, q2 &tE, q2 &tHx,
+                 q2 &tHy, q2 &tP) -> bool {
+    if (!wait_row(j + 2)) return false;
+    const PStagedRow2 &Rm = w.row[slot(j - 1)], &R0 = w.row[slot(j)];
+    const PStagedRow2 &R1 = w.row[slot(j + 1)], &R2 = w.row[slot(j + 2)];
+    gn = pstaged_diffs(R0, R1, R2, q, 2);
+    const PRowP v0 = pstaged_pair<true>(R0, q, 2), v1 = pstaged_pair<true>(R1, q, 2);
+    // left x-faces of A and B: l side the left neighbours, r side the lane's own cells
+    const PRowP vl = pstaged_pair<true>(R0, q, 1);
+    const PGP gl = pstaged_diffs(Rm, R0, R1, q, 1);
+    q2 fxE, fxHx, fxHy, fxP;
+    face_flux_psi_p(psi_xside_p(vl, gl, Q4), psi_xside_p(v0, gc, MQ4), P.kx, fxE, fxHx, fxHy, fxP);
+    if (xedge) {
+      if (loA) {                        // low-x face of column 0 (cell A)
+        const PSide<float> rn = psi_xside<float>(v0.ez.x, v0.hx.x, v0.hy.x, v0.ps.x, v0.eps.x,
+                                                 pg_of(gc, 0), mq4);
+        face_flux_psi<float>(psi_zero<float>(), rn, p.fx, p.qx, prcp1(v0.eps.x), fxE.x, fxHx.x,
+                             fxHy.x, fxP.x);
+      }
+      if (hiA) {                        // high-x face of column nx - 1 (left neighbour of A)
+        const PSide<float> l0 = psi_xside<float>(vl.ez.x, vl.hx.x, vl.hy.x, vl.ps.x, vl.eps.x,
+                                                 pg_of(gl, 0), q4);
+        face_flux_psi<float>(l0, psi_zero<float>(), p.fx, p.qx, prcp1(vl.eps.x), fxE.x, fxHx.x,
+                             fxHy.x, fxP.x);
+      }
+      if (hiB) {
+        const PSide<float> l1 = psi_xside<float>(vl.ez.y, vl.hx.y, vl.hy.y, vl.ps.y, vl.eps.y,
+                                                 pg_of(gl, 1), q4);
+        face_flux_psi<float>(l1, psi_zero<float>(), p.fx, p.qx, prcp1(vl.eps.y), fxE.y, fxHx.y,
+                             fxHy.y, fxP.y);
+      }
+    }
+    // right faces: the next lane's left faces; for lane 31's A, lane 0's left face of B
+    auto right = [lane](q2 f) {
+      const float a = __shfl_down_sync(PFULL, f.x, 1), b = __shfl_sync(PFULL, f.y, 0);
+      const float c = __shfl_down_sync(PFULL, f.y, 1);
+      return qk(lane == 31 ? b : a, c);
+    };
+    const q2 frE = right(fxE), frHx = right(fxHx), frHy = right(fxHy), frP = right(fxP);
+    // y-faces between rows j and j+1
+    face_flux_psi_p(psi_yside_p(v0, gc, Q4), psi_yside_p(v1, gn, MQ4), P.ky, tE, tHy, tHx, tP);
+    if (j + 1 == p.ny && yhi_nr) {
+      float e[2], hx[2], hy[2], ps[2];
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const PSide<float> lo = psi_yside<float>(GKS_COL(v0, ez, k), GKS_COL(v0, hx, k),
+                                                 GKS_COL(v0, hy, k), GKS_COL(v0, ps, k),
+                                                 GKS_COL(v0, eps, k), pg_of(gc, k), q4);
+        face_flux_psi<float>(lo, psi_zero<float>(), p.fy, p.qy, prcp1(GKS_COL(v0, eps, k)), e[k],
+                             hy[k], hx[k], ps[k]);
+      }
+      tE = qk(e[0], e[1]); tHx = qk(hx[0], hx[1]); tHy = qk(hy[0], hy[1]); tP = qk(ps[0], ps[1]);
+    }
+    // update row j
+    q2 dE = qadd(qsub(fxE, frE), qsub(bE, tE));
+    const q2 dHx = qadd(qsub(fxHx, frHx), qsub(bHx, tHx));
+    const q2 dHy = qadd(qsub(fxHy, frHy), qsub(bHy, tHy));
+    const q2 dP = qadd(qsub(fxP, frP), qsub(bP, tP));
+    const int64_t ro = (int64_t)j * p.pitch;
+    if (p.src && j >= p.sy0 && j < p.sy1) {
+      if (A >= p.sx0 && A < p.sx1) dE.x -= p.src_amp * p.src[ro + A];
+      if (B >= p.sx0 && B < p.sx1) dE.y -= p.src_amp * p.src[ro + B];
+    }
+    const q2 out[4] = {qfma(dE, qk(prcp1(v0.eps.x), prcp1(v0.eps.y)), v0.ez), qadd(v0.hx, dHx),
+                       qadd(v0.hy, dHy), qadd(v0.ps, dP)};
+    float *o = p.Vout + ro;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      if (stA) o[c * p.cstride + A] = out[c].x;
+      if (stB) o[c * p.cstride + B] = out[c].y;
+    }
+    const q2 sum = qadd(qadd(out[0], out[1]), qadd(out[2], out[3]));
+    if (stB) acc = qfma(sum, Z2, acc);                 // stB implies stA
+    else if (stA) acc.x = fmaf(sum.x, 0.f, acc.x);
+    __syncwarp();                                     // row j-1 is read
+    if (lane == 0 && j + PNSLOT2 - 1 <= last) issue(j + PNSLOT2 - 1);
+    return true;
+  };
+
+  int j = y0;
+  if (ok) {
+#pragma unroll 1
+    for (; j + 1 < y1; j += 2) {
+      if (!row(j, g0, g1, fbE, fbHx, fbHy, fbP, ftE, ftHx, ftHy, ftP) ||
+          !row(j + 1, g1, g0, ftE, ftHx, ftHy, ftP, fbE, fbHx, fbHy, fbP)) {
+        ok = false;
+        break;
+      }
+    }
+    if (ok && j < y1) ok = row(j, g0, g1, fbE, fbHx, fbHy, fbP, ftE, ftHx, ftHy, ftP);
+  }
+  if (lane == 0 && !ok) {
+    atomicOr(p.flag, 2);                              // a row never landed
+    for (int r = max(first, issued - PNSLOT2 + 1); r <= issued; ++r)   // copies in flight
+      mbar_wait(&w.bar[slot(r)], parity(r));
+  }
+  if (__any_sync(PFULL, !(isfinite(acc.x) && isfinite(acc.y))) && lane == 0) atomicOr(p.flag, 1);
+}
+
 #undef GKS_COL
+
+// The staged kernel covers FP32 without the limiter, without PEC walls and with a non-periodic
+// x axis (a periodic y axis needs two rows for the wrap); about four waves of chunks of at least
+// 8 rows.
+bool psi_staged_supported(const CartGeom &g, const CartStepArgs &a) {
+  if (a.limiter || g.periodic[0]) return false;
+  for (int k = 0; k < 4; ++k)
+    if (g.pec[k]) return false;
+  if (g.periodic[1] && g.ny < 2) return false;
+  return tensor_map_encoder() != nullptr;
+}
+
+cudaError_t launch_psi_staged(const CartGeom &g, const PsiPackArgs &P, cudaStream_t st) {
+  const int smem = PWARPS * (int)sizeof(PWarpStage2);
+  static int per_sm = 0, sms = 0;
+  if (!per_sm) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaFuncSetAttribute(cart2d_psi_step_kernel_s, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cart2d_psi_step_kernel_s, PWARPS * 32,
+                                                  smem);
+    if (sms < 1) sms = 1;
+    if (per_sm < 1) per_sm = 1;
+  }
+  const int nstrips = (g.nx + PW2 - 1) / PW2;
+  const int64_t want = (int64_t)sms * per_sm * PWARPS * 4 / nstrips;
+  int nchunks = (int)(want > 1 ? want : 1);
+  int rows = (g.ny + nchunks - 1) / nchunks;
+  if (rows < 8) rows = 8;
+  nchunks = (g.ny + rows - 1) / rows;
+  const int64_t nwarps = (int64_t)nstrips * nchunks;
+  const int grid = (int)((nwarps + PWARPS - 1) / PWARPS);
+  CUtensorMap tmV, tmE;
+  const cuuint64_t dim[3] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, 4};
+  const cuuint64_t stride[2] = {(cuuint64_t)g.pitch * 4, (cuuint64_t)g.cstride * 4};
+  const cuuint32_t box[3] = {PTW2, 1, 4};
+  if (!encode_f32_map(&tmV, P.b.V, 3, dim, stride, box) ||
+      !encode_f32_map(&tmE, P.b.eps, 2, dim, stride, box))
+    return cudaErrorInvalidValue;
+  cart2d_psi_step_kernel_s<<<grid, PWARPS * 32, smem, st>>>(tmV, tmE, P, nstrips, rows);
+  return cudaGetLastError();
+}
 
 template <typename T>
 cudaError_t launch_psi_t(const CartGeom &g, const CartStepArgs &a, double gamma,
@@ -806,6 +1098,7 @@ cudaError_t launch_psi_t(const CartGeom &g, const CartStepArgs &a, double gamma,
     P.b = p;
     P.kx = make_psi_kp(p.fx, p.qx);
     P.ky = make_psi_kp(p.fy, p.qy);
+    if (psi_staged_supported(g, a)) return launch_psi_staged(g, P, st);
     using KP = void (*)(const PsiPackArgs, int, int);
     static const KP kp[2][2] = {{cart2d_psi_step_kernel_p<false, false>,
                                  cart2d_psi_step_kernel_p<false, true>},

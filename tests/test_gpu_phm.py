@@ -68,6 +68,26 @@ def test_phm_2d(precision, kappa, case):
     assert rel_l2(out, ref) <= TOL[precision], rel_l2(out, ref)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("case", [
+    (127, 130, ("nrbc", "nrbc", "periodic", "periodic"), 1.0, True),   # strips, chunks, wrap
+    (64, 47, ("nrbc",) * 4, 0.7, True),       # two strips, the second one column wide
+    (33, 9, ("nrbc",) * 4, 1.3, False),       # high-x face on the second half of lane 1's pair
+    (63, 2, ("nrbc",) * 4, 0.5, True),        # one strip, two rows
+    (1, 5, ("nrbc",) * 4, 0.8, False),        # one column
+    (200, 3, ("nrbc", "nrbc", "periodic", "periodic"), 1.0, False),   # periodic y on 3 rows
+])
+def test_phm_2d_staged_shapes(precision, case):
+    """Shapes spanning the staged FP32 cleaning kernel's strips (63 columns, a lane's two cells
+    32 apart) and row chunks, against the oracle (FP64 runs the scalar kernel on the same
+    cases); kappa = 0.05, 12 steps."""
+    nx, ny, bc, gamma, with_src = case
+    w = _w(nx, ny, bc, gamma, seed=nx + 5 * ny, with_src=with_src, chi=0.4)
+    out, info = _gpu(w, 12, precision, 0.05)
+    ref, _ = oracle_cart_run(w, 12, kappa=0.05, c=info["c"])
+    assert rel_l2(out, ref) <= TOL[precision], rel_l2(out, ref)
+
+
 def test_phm_cleaning_wave_against_exact():
     """The standing cleaning wave of Sec. 2.1 (H_x = sin(2 pi x) initially, psi = 0, gamma =
     0.5) on the GPU: H_x = sin(2 pi x) cos(2 pi gamma t), psi = -cos(2 pi x) sin(2 pi gamma t)
