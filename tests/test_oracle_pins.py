@@ -375,8 +375,8 @@ def test_table1_grid_aligned_wave_is_third_order():
     wave the scheme is Fromm's (test above), third order at Courant number 1/2, so its L1, L2
     and L-inf errors fall at order 3 +- 0.05 and sit below the table's second-order errors by a
     factor that starts near 4 at N = 20 and doubles with every refinement (to within the
-    table's own order, 1.92 .. 2.02).  This is the
-    measured relation that the design doc reports; no reading of the CFL reproduces the table."""
+    table's own order, 1.92 .. 2.02).  No reading of the CFL reproduces the table; this pins
+    the measured relation instead."""
     tab = np.loadtxt(os.path.join(GOLDEN, "paper_table1_plane_wave.txt"))
     errs = []
     for N in tab[:, 0].astype(int):
