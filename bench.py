@@ -422,7 +422,7 @@ def run_reference(args, rank):
     v = res["value"]
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": None, "higher_is_better": True, "scaling": "strong",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "tm2d_cylinders_4096 (block sample)", "grid": [4096, 4096],
                        "cfl": 0.5, "steps_config": 2000},
