@@ -885,9 +885,9 @@ __global__ void __launch_bounds__(WARPS * 32, GKS_CART2D_MINBLOCKS)
 }
 
 // ------------------------------------------------------------------ staged FP32 path
-// FP32, mu = 1, no limiter, no PEC wall, x not periodic.  The rows of a strip are staged in
-// shared memory by TMA and the two cells of a lane lie 32 columns apart, so that no pair ever
-// has to be assembled from two lanes' registers:
+// FP32, mu = 1, no limiter, x not periodic (non-reflecting or PEC sides).  The rows of a strip
+// are staged in shared memory by TMA and the two cells of a lane lie 32 columns apart, so that no
+// pair ever has to be assembled from two lanes' registers:
 //   - a warp owns a strip of W2 = 63 columns x0 .. x0+62; lane l holds the cells A = x0+l and
 //     B = x0+32+l as the two halves of a float2 (lane 31's B is the next strip's first column,
 //     computed but not stored);
@@ -903,8 +903,9 @@ __global__ void __launch_bounds__(WARPS * 32, GKS_CART2D_MINBLOCKS)
 // mbarrier per row; the box starts at the 16-byte boundary at or below x0-3).  Lane 0 issues
 // row j+NSLOT2-1 once row j is done; iteration j reads rows j-1 .. j+2.  Rows past a
 // non-reflecting y side are staged from the clamped row (the Green-Gauss ghost copy), a
-// periodic y side wraps; columns past an x side are read from the clamped column, so the
-// zero-filled entries of a box are never read.  The march is unrolled by two so that the
+// periodic y side wraps; columns past a non-reflecting x side are read from the clamped column,
+// so the zero-filled entries of a box are never read.  On PEC sides the rows and columns past the
+// wall hold mirror images (fix_row).  The march is unrolled by two so that the
 // gradients and face-below fluxes alternate between two register sets.
 constexpr int W2 = 63;                  // columns updated per warp
 constexpr int TW2 = 72;                 // staged columns (x0-3 rounded down to 4, +72)
@@ -950,6 +951,8 @@ __device__ __forceinline__ GP staged_diffs(const StagedRow2 &dn, const StagedRow
   return g;
 }
 
+// HAS_PEC: some side is a PEC wall (the mirror-image bookkeeping is compiled in only then).
+template <bool HAS_PEC>
 __global__ void __launch_bounds__(WARPS * 32, MINB2)
     cart2d_step_kernel_s(const __grid_constant__ CUtensorMap tmV,
                          const __grid_constant__ CUtensorMap tmE, const Cart2DPackArgs P,
@@ -966,27 +969,71 @@ __global__ void __launch_bounds__(WARPS * 32, MINB2)
   const int x0 = strip * W2;
   const int xs = (x0 - 3) & ~3;                       // first staged column (16-byte aligned)
   const int A = x0 + lane, B = x0 + 32 + lane;
-  const bool ylo_nr = !p.pery, yhi_nr = !p.pery;
+  const bool pxl = HAS_PEC && p.pec[0], pxh = HAS_PEC && p.pec[1];
+  const bool pyl = HAS_PEC && p.pec[2], pyh = HAS_PEC && p.pec[3];
+  const bool ylo_nr = !p.pery && !pyl, yhi_nr = !p.pery && !pyh;
   const float q4 = 0.25f, mq4 = -0.25f;
   const f2 Q4 = pk(q4, q4), MQ4 = pk(mq4, mq4), Z2 = pk(0.f, 0.f);
+  // staged column read for grid column c: a non-reflecting side clamps to the edge cell (the
+  // Green-Gauss ghost copy); a PEC side reads its two mirror-image columns, which fix_row writes
+  // into the staged row, and nothing further out
+  auto tap = [&p, pxl, pxh, xs](int c) {
+    c = c < 0 ? (pxl ? max(c, -2) : 0) : c;
+    c = c >= p.nx ? (pxh ? min(c, p.nx + 1) : p.nx - 1) : c;
+    return c - xs;
+  };
   Taps2 q;
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    q.a[k] = min(max(A + k - 2, 0), p.nx - 1) - xs;
-    q.b[k] = min(max(B + k - 2, 0), p.nx - 1) - xs;
+    q.a[k] = tap(A + k - 2);
+    q.b[k] = tap(B + k - 2);
   }
-  // boundary x faces (scalar flux): the left face of column 0 is the low-x face of column 0;
-  // the left face of column nx is the high-x face of column nx - 1
-  const bool loA = A == 0, loB = B == 0, hiA = A == p.nx, hiB = B == p.nx;
+  // boundary x faces (scalar flux) on non-reflecting sides: the left face of column 0 is the
+  // low-x face of column 0; the left face of column nx is the high-x face of column nx - 1.
+  // PEC wall faces are interior faces against the mirror-image columns.
+  const bool loA = !pxl && A == 0, loB = !pxl && B == 0;
+  const bool hiA = !pxh && A == p.nx, hiB = !pxh && B == p.nx;
   const bool xedge = __any_sync(FULL, loA || loB || hiA || hiB);
+  // PEC x walls: lane g < 4 writes ghost column gc = (-2, -1, nx, nx+1)[g] of each staged row from
+  // its mirror column (Ez and Hx negated), if the warp stages that column
+  int gcol = lane == 0 ? -2 : lane == 1 ? -1 : lane == 2 ? p.nx : p.nx + 1;
+  const int gmir = lane < 2 ? min(-1 - gcol, p.nx - 1) : max(2 * p.nx - 1 - gcol, 0);
+  const bool gact = lane < 4 && (lane < 2 ? pxl : pxh) && gcol - xs >= 0 && gcol - xs < TW2;
+  const bool xfix = HAS_PEC && __any_sync(FULL, gact);
   const int xend = min(x0 + W2, p.nx);
   const bool stA = A < xend, stB = lane < 31 && B < xend;   // cells this lane stores
 
   const int first = y0 - 2, last = y1 + 1;            // staged rows
   auto slot = [first](int r) { return (r - first) & (NSLOT2 - 1); };
   auto parity = [first](int r) { return (unsigned)(((r - first) / NSLOT2) & 1); };
-  auto grid_row = [&p](int r) {
-    return p.pery ? (r < 0 ? r + p.ny : (r >= p.ny ? r - p.ny : r)) : min(max(r, 0), p.ny - 1);
+  auto grid_row = [&p, pyl, pyh](int r) {
+    if (p.pery) return r < 0 ? r + p.ny : (r >= p.ny ? r - p.ny : r);
+    if (r < 0) return pyl ? min(-1 - r, p.ny - 1) : 0;
+    if (r >= p.ny) return pyh ? max(2 * p.ny - 1 - r, 0) : p.ny - 1;
+    return r;
+  };
+  // mirror images on PEC walls, written into a staged row once it has landed (whole warp): a row
+  // past a PEC y wall negates Ez and Hy; then the ghost columns past a PEC x wall take their
+  // mirror columns with Ez and Hx negated (corner ghosts get both)
+  auto fix_row = [&](int r) {
+    if constexpr (!HAS_PEC) return;
+    const bool yg = (r < 0 && pyl) || (r >= p.ny && pyh);
+    if (!yg && !xfix) return;
+    StagedRow2 &R = w.row[slot(r)];
+    if (yg)
+      for (int c = lane; c < TW2; c += 32) {
+        R.v.a[0][c] = -R.v.a[0][c];
+        R.v.a[2][c] = -R.v.a[2][c];
+      }
+    __syncwarp();
+    if (gact) {
+      const int t = gcol - xs, m = gmir - xs;
+      R.v.a[0][t] = -R.v.a[0][m];
+      R.v.a[1][t] = -R.v.a[1][m];
+      R.v.a[2][t] = R.v.a[2][m];
+      R.e.e[t] = R.e.e[m];
+    }
+    __syncwarp();
   };
   int issued = first - 1;                             // lane 0: the last row whose copy is issued
   auto issue = [&](int r) {                           // lane 0 only
@@ -1023,7 +1070,10 @@ __global__ void __launch_bounds__(WARPS * 32, MINB2)
   };
 
   bool ok = true;
-  for (int r = first; r <= y0 + 1; ++r) ok = ok && wait_row(r);
+  for (int r = first; r <= y0 + 1; ++r) {
+    ok = ok && wait_row(r);
+    if (ok) fix_row(r);
+  }
   GP g0, g1;                                          // own gradients of the current / next row
   f2 fbE, fbHx, fbHy, ftE, ftHx, ftHy;                // y-face fluxes below / above the row
   if (ok) {
@@ -1050,6 +1100,7 @@ __global__ void __launch_bounds__(WARPS * 32, MINB2)
   auto row = [&](int j, const GP &gc, GP &gn, f2 bE, f2 bHx, f2 bHy, f2 &tE, f2 &tHx,
                  f2 &tHy) -> bool {
     if (!wait_row(j + 2)) return false;
+    fix_row(j + 2);
     const StagedRow2 &Rm = w.row[slot(j - 1)], &R0 = w.row[slot(j)];
     const StagedRow2 &R1 = w.row[slot(j + 1)], &R2 = w.row[slot(j + 2)];
     gn = staged_diffs(R0, R1, R2, q, 2);
@@ -1154,12 +1205,10 @@ Coef<T> make_coef(const double C[5], double h, double c) {
   return k;
 }
 
-// The staged kernel covers FP32 with mu = 1, no limiter, no PEC wall and a non-periodic x
-// axis (a periodic y axis needs two rows for the wrap).
+// The staged kernel covers FP32 with mu = 1, no limiter and a non-periodic x axis (a periodic
+// y axis needs two rows for the wrap); non-reflecting and PEC sides.
 bool staged2_supported(const CartGeom &g, const CartStepArgs &a) {
   if (a.mu || a.limiter || g.periodic[0]) return false;
-  for (int k = 0; k < 4; ++k)
-    if (g.pec[k]) return false;
   if (g.periodic[1] && g.ny < 2) return false;
   return tensor_map_encoder() != nullptr;
 }
@@ -1177,8 +1226,11 @@ cudaError_t launch_staged2(const CartGeom &g, const Cart2DPackArgs &P, int wx0, 
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaFuncSetAttribute(cart2d_step_kernel_s, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cart2d_step_kernel_s, WARPS * 32,
+    cudaFuncSetAttribute(cart2d_step_kernel_s<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         smem);
+    cudaFuncSetAttribute(cart2d_step_kernel_s<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cart2d_step_kernel_s<false>, WARPS * 32,
                                                   smem);
     if (sms < 1) sms = 1;
     if (per_sm < 1) per_sm = 1;
@@ -1201,8 +1253,9 @@ cudaError_t launch_staged2(const CartGeom &g, const Cart2DPackArgs &P, int wx0, 
   if (!encode_f32_map(&tmV, P.b.V, 3, dim, stride, box) ||
       !encode_f32_map(&tmE, P.b.eps, 2, dim, stride, box))
     return cudaErrorInvalidValue;
-  cart2d_step_kernel_s<<<grid, WARPS * 32, smem, st>>>(tmV, tmE, P, nstrips, rows, strip0, wy0,
-                                                      wy1);
+  const bool pec = g.pec[0] || g.pec[1] || g.pec[2] || g.pec[3];
+  auto kern = pec ? cart2d_step_kernel_s<true> : cart2d_step_kernel_s<false>;
+  kern<<<grid, WARPS * 32, smem, st>>>(tmV, tmE, P, nstrips, rows, strip0, wy0, wy1);
   return cudaGetLastError();
 }
 

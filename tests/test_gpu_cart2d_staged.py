@@ -1,11 +1,12 @@
-"""GPU parity of the staged 2-D TM step (FP32, mu = 1, non-reflecting or periodic-y sides: rows
-staged in shared memory by tensor copies, a lane's two cells 32 columns apart, 63 columns per
+"""GPU parity of the staged 2-D TM step (FP32, mu = 1; non-reflecting, PEC or periodic-y sides:
+rows staged in shared memory by tensor copies, a lane's two cells 32 columns apart, 63 columns per
 warp) against the FP64 oracle, relative L2 <= 2e-5.
 
 Shapes span the strip and chunk structure of that kernel: widths below, at and past one
 63-column strip and ragged against it, high-x boundary faces on either half of a lane's pair,
 heights of one or two rows and heights that split a strip into several row chunks with an odd
-last chunk; sources, periodic y (with the two-row wrap), rectangular cells."""
+last chunk; PEC walls on either axis (mirror rows and columns in the staged rows); sources,
+periodic y (with the two-row wrap), rectangular cells."""
 import numpy as np
 import pytest
 
@@ -23,7 +24,7 @@ def _built():
     build.build()
 
 
-def _workload(nx, ny, ybc, seed, with_src, hy_ratio=1.0):
+def _workload(nx, ny, ybc, seed, with_src, hy_ratio=1.0, xbc="nrbc"):
     rng = np.random.default_rng(seed)
     hi = (1.0, hy_ratio * ny / nx)
     x, y = wl.cell_centres_2d(nx, ny, hi=hi)
@@ -37,7 +38,7 @@ def _workload(nx, ny, ybc, seed, with_src, hy_ratio=1.0):
         mask = np.zeros(nx * ny)
         mask[rng.choice(nx * ny, size=k, replace=False)] = rng.uniform(-3, 3, k)
     return wl.CartWorkload(name="staged", dim=2, n=(nx, ny), lo=(0.0, 0.0), hi=hi,
-                           bc=("nrbc", "nrbc", ybc, ybc), cfl=0.5, steps=0, eps=eps, mu=None,
+                           bc=(xbc, xbc, ybc, ybc), cfl=0.5, steps=0, eps=eps, mu=None,
                            fields0=f, jz_mask=mask, src=(1.0, 20.0, 0.02, 0.02), c_lattice=0.0)
 
 
@@ -56,6 +57,30 @@ def _workload(nx, ny, ybc, seed, with_src, hy_ratio=1.0):
 ])
 def test_staged_step_matches_the_oracle(nx, ny, ybc, src, hy):
     w = _workload(nx, ny, ybc, seed=nx + 1000 * ny, with_src=src, hy_ratio=hy)
+    steps = 17
+    s = GKSSolver.from_workload(w, precision="fp32")
+    s.step(steps)
+    out = s.read_fields()
+    c = s.info()["c"]
+    s.close()
+    mesh = go.cartesian_mesh(w.n, w.lo, w.hi, w.bc)
+    ref, _ = go.run(mesh, w.fields0, w.eps, None, w.cfl, steps, c=c, jz_mask=w.jz_mask,
+                    src=w.src if w.jz_mask is not None else None)
+    assert rel_l2(out, ref) <= 2e-5, rel_l2(out, ref)
+
+
+@pytest.mark.parametrize("nx,ny,xbc,ybc,src", [
+    (64, 47, "pec", "pec", True),          # closed box: mirror rows and columns, corners
+    (33, 9, "pec", "nrbc", False),         # PEC x walls, high wall on lane 1's second cell
+    (63, 2, "nrbc", "pec", True),          # PEC y walls on two rows
+    (2, 7, "pec", "pec", False),           # two columns: the mirrors span the whole grid
+    (127, 130, "pec", "periodic", True),   # three strips, chunks, periodic y
+    (32, 5, "pec", "nrbc", False),         # high wall on lane 0's second cell
+])
+def test_staged_step_pec_walls(nx, ny, xbc, ybc, src):
+    """PEC walls (Sec. 5.5) through the staged kernel: rows and columns past a wall are mirror
+    images written into the staged rows, the wall faces interior faces against them."""
+    w = _workload(nx, ny, ybc, seed=nx + 77 * ny, with_src=src, xbc=xbc)
     steps = 17
     s = GKSSolver.from_workload(w, precision="fp32")
     s.step(steps)
