@@ -592,9 +592,17 @@ struct FSideP {
   f2 e, hn, ht, den, dhn, dht, dat, det, eps;
 };
 
-// face_flux<float, false> for two faces at once.
+// face_flux<float, false> for two faces at once.  The interface factor g multiplies two
+// differences per flux; it is folded into their coefficients (g a3 + a6, g/2 - q3, g c3 + c6),
+// and each sum is taken in two independent halves.
 __device__ __forceinline__ void face_flux_p(const FSideP &l, const FSideP &r, const FaceKP &k,
                                             f2 &fE, f2 &fHn, f2 &fHt) {
+  const f2 se = padd(l.eps, r.eps);
+  const f2 ie = pk(rcp2(se.x), rcp2(se.y));
+  const f2 g = pfma(rep(k.nk3), ie, rep(k.g0));
+  const f2 cX = pfma(g, rep(k.a3), rep(k.a6));        // of D_xB in fE
+  const f2 cU = pfma(g, rep(k.half), rep(k.nq3));     // of S_Uxe in fE and of S_UxB in fHt
+  const f2 cD = pfma(g, rep(k.c3), rep(k.c6));        // of D_ex in fHt
   const f2 Ue_l = pmul(l.eps, l.e), Ue_r = pmul(r.eps, r.e);
   const f2 Uxe_l = pmul(l.eps, l.den), Uxe_r = pmul(r.eps, r.den);
   const f2 S_B = padd(l.ht, r.ht), D_e = psub(r.e, l.e);
@@ -603,31 +611,22 @@ __device__ __forceinline__ void face_flux_p(const FSideP &l, const FSideP &r, co
   const f2 S_Uxa = padd(l.dhn, r.dhn), D_Ua = psub(r.hn, l.hn), D_Et = psub(r.det, l.det);
   const f2 S_Ue = padd(Ue_l, Ue_r), D_B = psub(r.ht, l.ht), S_UxB = padd(l.dht, r.dht);
   const f2 D_ex = psub(r.den, l.den), S_UAt = padd(l.dat, r.dat), S_e = padd(l.e, r.e);
-  const f2 se = padd(l.eps, r.eps);
-  const f2 ie = pk(rcp2(se.x), rcp2(se.y));
-  const f2 g = pfma(rep(k.nk3), ie, rep(k.g0));
-  f2 fe = pmul(rep(k.a14), S_B);
-  fe = pfma(rep(k.a2), D_e, fe);
-  fe = pfma(g, pfma(rep(k.a3), D_xB, pmul(rep(k.half), S_Uxe)), fe);
-  fe = pfma(rep(k.nq2), D_Ue, fe);
-  fe = pfma(rep(k.nq3), S_Uxe, fe);
-  fe = pfma(rep(k.a5), D_At, fe);
-  fe = pfma(rep(k.a6), D_xB, fe);
+  f2 fe1 = pfma(rep(k.a2), D_e, pmul(rep(k.a14), S_B));
+  fe1 = pfma(rep(k.nq2), D_Ue, fe1);
+  f2 fe2 = pfma(cX, D_xB, pmul(rep(k.a5), D_At));
+  fe2 = pfma(cU, S_Uxe, fe2);
   f2 fa = pmul(rep(k.q5), S_Uxa);
   fa = pfma(rep(k.nq2), D_Ua, fa);
   fa = pfma(rep(k.b1), D_Et, fa);
   f2 u = pmul(rep(k.c1), S_Ue);
   u = pfma(rep(k.c2), D_B, u);
   u = pfma(rep(k.c4), S_UAt, u);
-  f2 fb = pmul(ie, u);
-  fb = pfma(g, pfma(rep(k.c3), D_ex, pmul(rep(k.half), S_UxB)), fb);
-  fb = pfma(rep(k.c5), S_e, fb);
-  fb = pfma(rep(k.nq2), D_B, fb);
-  fb = pfma(rep(k.nq3), S_UxB, fb);
-  fb = pfma(rep(k.c6), D_ex, fb);
-  fE = fe;
+  const f2 fb1 = pfma(ie, u, pmul(rep(k.nq2), D_B));
+  f2 fb2 = pfma(cD, D_ex, pmul(rep(k.c5), S_e));
+  fb2 = pfma(cU, S_UxB, fb2);
+  fE = padd(fe1, fe2);
   fHn = fa;
-  fHt = fb;
+  fHt = padd(fb1, fb2);
 }
 
 // Two columns of one row as pairs, plus the PEC mirror flags (as in Row2).
