@@ -30,15 +30,43 @@ int blocks_for(int64_t n) {
   return (int)(b < 1 ? 1 : b);
 }
 
+// The twelve gradient weights n|l|/|Omega| of a cell (its four faces): vector loads.
+__device__ __forceinline__ void load_cell_w(const float *p, float w[kTetCellW]) {
+#pragma unroll
+  for (int k = 0; k < kTetCellW / 4; ++k) {
+    const float4 v = __ldg(reinterpret_cast<const float4 *>(p) + k);
+    w[4 * k] = v.x; w[4 * k + 1] = v.y; w[4 * k + 2] = v.z; w[4 * k + 3] = v.w;
+  }
+}
+__device__ __forceinline__ void load_cell_w(const double *p, double w[kTetCellW]) {
+#pragma unroll
+  for (int k = 0; k < kTetCellW / 2; ++k) {
+    const double2 v = __ldg(reinterpret_cast<const double2 *>(p) + k);
+    w[2 * k] = v.x; w[2 * k + 1] = v.y;
+  }
+}
+
 template <typename T>
 __global__ void tet_gradient_kernel(const T *__restrict__ V, const int32_t *__restrict__ cnb,
                                     const T *__restrict__ cw, int64_t nt, int pec,
                                     T *__restrict__ G) {
   const int64_t i = blockIdx.x * (int64_t)TB + threadIdx.x;
   if (i >= nt) return;
-  T vi[6];
+  // every load is issued before the arithmetic: the four neighbour indices in one vector load,
+  // then the 24 neighbour values (a wall face reads the cell itself), so that the gathers are in
+  // flight together
+  const int4 nb4 = __ldg(reinterpret_cast<const int4 *>(cnb) + i);
+  const int32_t nb[4] = {nb4.x, nb4.y, nb4.z, nb4.w};
+  T vi[6], vn[4][6], w[kTetCellW];
 #pragma unroll
   for (int c = 0; c < 6; ++c) vi[c] = V[c * nt + i];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int64_t j = nb[k] >= 0 ? (int64_t)nb[k] : i;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) vn[k][c] = V[c * nt + j];
+  }
+  load_cell_w(cw + kTetCellW * i, w);
   T g[3][6];
 #pragma unroll
   for (int a = 0; a < 3; ++a)
@@ -46,17 +74,16 @@ __global__ void tet_gradient_kernel(const T *__restrict__ V, const int32_t *__re
     for (int c = 0; c < 6; ++c) g[a][c] = T(0);
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    const int32_t nb = cnb[4 * i + k];
     T vf[6];
-    if (nb >= 0) {
+    if (nb[k] >= 0) {
 #pragma unroll
-      for (int c = 0; c < 6; ++c) vf[c] = T(0.5) * (vi[c] + V[c * nt + nb]);
+      for (int c = 0; c < 6; ++c) vf[c] = T(0.5) * (vi[c] + vn[k][c]);
     } else if (pec) {
       // PEC wall: face value (V + P V)/2 of the mirror ghost P V = (-E + 2 (E.n) n, H - 2 (H.n) n),
       // i.e. the normal part of E and the tangential part of H
-      const T *w = cw + kTetCellW * i + 3 * k;
-      const T inv = T(1) / sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
-      const T n[3] = {w[0] * inv, w[1] * inv, w[2] * inv};
+      const T *wk = w + 3 * k;
+      const T inv = T(1) / sqrt(wk[0] * wk[0] + wk[1] * wk[1] + wk[2] * wk[2]);
+      const T n[3] = {wk[0] * inv, wk[1] * inv, wk[2] * inv};
       const T en = vi[0] * n[0] + vi[1] * n[1] + vi[2] * n[2];
       const T hn = vi[3] * n[0] + vi[4] * n[1] + vi[5] * n[2];
 #pragma unroll
@@ -70,9 +97,9 @@ __global__ void tet_gradient_kernel(const T *__restrict__ V, const int32_t *__re
     }
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      const T w = cw[kTetCellW * i + 3 * k + a];
+      const T wa = w[3 * k + a];
 #pragma unroll
-      for (int c = 0; c < 6; ++c) g[a][c] += vf[c] * w;
+      for (int c = 0; c < 6; ++c) g[a][c] += vf[c] * wa;
     }
   }
 #pragma unroll
