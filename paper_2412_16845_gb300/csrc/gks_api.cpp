@@ -137,9 +137,14 @@ gks_status setup_tets(gks_ctx *ctx, const gks_mesh_desc *d) {
   std::vector<double> cw((size_t)h.nt * gks::kTetCellW), cu((size_t)h.nt * gks::kTetCellU);
   for (int64_t f = 0; f < h.nf; ++f) {
     double *q = &fgeo[(size_t)f * gks::kTetFaceGeo];
-    for (int k = 0; k < 9; ++k) q[k] = h.fT[9 * f + k];
-    for (int a = 0; a < 3; ++a) { q[9 + a] = h.fdL[3 * f + a]; q[12 + a] = h.fdR[3 * f + a]; }
-    q[15] = h.farea[f];
+    // the frame's rows t, w follow from n and 1/(1 + n_1) (zero for n_1 = -1, which gives the
+    // special frame diag(-1, -1, 1) from the same expressions)
+    const double *T = &h.fT[9 * f];
+    for (int k = 0; k < 3; ++k) q[k] = T[k];
+    q[3] = T[0] == -1.0 ? 0.0 : gks::frame_inv_one_plus(T[0], T[1], T[2]);
+    for (int a = 0; a < 3; ++a) { q[4 + a] = h.fdL[3 * f + a]; q[7 + a] = h.fdR[3 * f + a]; }
+    q[10] = h.farea[f];
+    q[11] = 0.0;
   }
   for (int64_t i = 0; i < h.nt; ++i) {
     for (int k = 0; k < 12; ++k) cw[(size_t)i * gks::kTetCellW + k] = h.cw[12 * i + k];

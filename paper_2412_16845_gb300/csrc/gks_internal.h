@@ -66,11 +66,15 @@ struct TetHost {
 gks_status build_tet_geometry(const double *vert, int64_t nv, const int64_t *tet, int64_t nt,
                               TetHost &g, std::string &err);
 void face_frame(const double n[3], double T[9]);
+// 1 / (1 + n_1) of the face frame, with 1 + n_1 formed as (n_2^2 + n_3^2) / (1 - n_1) for n_1 < 0
+inline double frame_inv_one_plus(double n1, double n2, double n3) {
+  return 1.0 / (n1 >= 0.0 ? 1.0 + n1 : (n2 * n2 + n3 * n3) / (1.0 - n1));
+}
 
 // Device copies of the tet geometry plus the per-step scratch (gradients, face fluxes).  The
 // geometry is computed in FP64 on the host; the step kernels read it in the context's precision
 // (rounded once on the host for FP32 contexts), packed per face and per cell.
-constexpr int kTetFaceGeo = 16;   // per face: frame rows (n, t, w) 9, x_s - x_L 3, x_s - x_R 3, |l|
+constexpr int kTetFaceGeo = 12;   // per face: n 3, 1/(1+n_1) of the frame, x_s - x_L 3, x_s - x_R 3, |l|, pad
 constexpr int kTetCellW = 12;     // per cell, gradient pass: n |l| / |Omega| of its 4 faces
 constexpr int kTetCellU = 4;      // per cell, update pass: sign_k / |Omega| of its 4 faces
 struct TetDev {

@@ -108,7 +108,7 @@ __global__ void tet_gradient_kernel(const T *__restrict__ V, const int32_t *__re
     for (int c = 0; c < 6; ++c) G[(6 * a + c) * nt + i] = g[a][c];
 }
 
-// The packed geometry of one face (16 values, 64 or 128 bytes, aligned): vector loads.
+// The packed geometry of one face (12 values, 48 or 96 bytes, aligned): vector loads.
 __device__ __forceinline__ void load_face_geo(const float *p, float q[kTetFaceGeo]) {
 #pragma unroll
   for (int k = 0; k < kTetFaceGeo / 4; ++k) {
@@ -191,7 +191,15 @@ __global__ void __launch_bounds__(TB, (sizeof(T) == 4 && !HAS_MU) ? 4 : 1)
   if (f >= nf) return;
   T q[kTetFaceGeo];
   load_face_geo(fgeo + kTetFaceGeo * f, q);
-  const T *Tm = q, *dl = q + 9, *dr = q + 12;
+  // frame rows (n, t, w) from n and 1/(1 + n_1)
+  T Tm[9];
+  {
+    const T n1 = q[0], n2 = q[1], n3 = q[2], a = q[2] * q[3];
+    Tm[0] = n1; Tm[1] = n2; Tm[2] = n3;
+    Tm[3] = -n2; Tm[4] = n1 + n3 * a; Tm[5] = -n2 * a;
+    Tm[6] = -n3; Tm[7] = -n2 * a; Tm[8] = T(1) - n3 * a;
+  }
+  const T *dl = q + 4, *dr = q + 7;
   const int32_t L = fL[f], R = fR[f];
   const Side3<T> l = tet_side<T>(V, G, eps, mu, nt, L, Tm, dl);
   T loc[6];
@@ -210,7 +218,7 @@ __global__ void __launch_bounds__(TB, (sizeof(T) == 4 && !HAS_MU) ? 4 : 1)
   } else {
     flux3<T, true>(l, l, K, loc);
   }
-  const T area = q[15];
+  const T area = q[10];
   // back to global components: Phi = T'^T Phi_local, times |l_s|
 #pragma unroll
   for (int b = 0; b < 2; ++b)

@@ -61,8 +61,7 @@ void face_frame(const double n[3], double T[9]) {
     for (int k = 0; k < 9; ++k) T[k] = d[k];
     return;
   }
-  const double one_p = n1 >= 0.0 ? 1.0 + n1 : (n2 * n2 + n3 * n3) / (1.0 - n1);
-  const double inv = 1.0 / one_p;
+  const double inv = frame_inv_one_plus(n1, n2, n3);
   T[0] = n1; T[1] = n2; T[2] = n3;
   T[3] = -n2; T[4] = n1 + n3 * n3 * inv; T[5] = -n2 * n3 * inv;
   T[6] = -n3; T[7] = -n2 * n3 * inv; T[8] = 1.0 - n3 * n3 * inv;

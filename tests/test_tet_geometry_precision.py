@@ -1,5 +1,6 @@
-"""The FP32 tet path reads its geometry (frames, face-centroid offsets, areas, face weights,
-update weights) rounded to FP32 once on the host.  This measures what that rounding alone does
+"""The FP32 tet path reads its geometry (face normals and the frame's 1/(1 + n_1), from which
+the kernel forms the frame rows in FP32; face-centroid offsets, areas, face weights, update
+weights) rounded to FP32 once on the host.  This measures what that rounding alone does
 to the method: the FP64 oracle run on the jittered Kuhn-tet sphere workload with every
 geometric quantity rounded to FP32 (same dt, computed from the FP64 geometry as the library
 does) stays within 1e-6 relative L2 of the run on the FP64 geometry after 30 steps (measured
