@@ -178,8 +178,8 @@ __device__ __forceinline__ Side3<T> pec_ghost(const Side3<T> &l) {
   return g;
 }
 
-// FP32 with mu = 1: capped at 64 registers (8 bytes of spills) for 4 CTAs per SM; the gathers'
-// latency is hidden by more resident warps (3.7% faster than at 72 registers).
+// FP32 with mu = 1: capped at 64 registers (no spills) for 4 CTAs per SM; the gathers' latency is
+// hidden by more resident warps (3.7% faster than at 72 registers).
 template <typename T, bool HAS_MU>
 __global__ void __launch_bounds__(TB, (sizeof(T) == 4 && !HAS_MU) ? 4 : 1)
     tet_face_kernel(const T *__restrict__ V, const T *__restrict__ G,
