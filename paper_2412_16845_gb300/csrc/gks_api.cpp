@@ -143,12 +143,12 @@ gks_status setup_tets(gks_ctx *ctx, const gks_mesh_desc *d) {
     for (int k = 0; k < 3; ++k) q[k] = T[k];
     q[3] = T[0] == -1.0 ? 0.0 : gks::frame_inv_one_plus(T[0], T[1], T[2]);
     for (int a = 0; a < 3; ++a) { q[4 + a] = h.fdL[3 * f + a]; q[7 + a] = h.fdR[3 * f + a]; }
-    q[10] = h.farea[f];
-    q[11] = 0.0;
   }
   for (int64_t i = 0; i < h.nt; ++i) {
     for (int k = 0; k < 12; ++k) cw[(size_t)i * gks::kTetCellW + k] = h.cw[12 * i + k];
-    for (int k = 0; k < 4; ++k) cu[(size_t)i * gks::kTetCellU + k] = h.csign[4 * i + k] * h.ivol[i];
+    for (int k = 0; k < 4; ++k)   // the face area enters here, not in the face pass
+      cu[(size_t)i * gks::kTetCellU + k] =
+          h.csign[4 * i + k] * h.farea[h.cface[4 * i + k]] * h.ivol[i];
   }
   if ((s = upload_vec(ctx, h.perm, &g.perm)) != GKS_OK || (s = upload_vec(ctx, h.vol, &g.vol)) != GKS_OK ||
       (s = upload_vec(ctx, h.cnb, &g.cnb)) != GKS_OK || (s = upload_vec(ctx, h.cface, &g.cface)) != GKS_OK ||

@@ -74,9 +74,9 @@ inline double frame_inv_one_plus(double n1, double n2, double n3) {
 // Device copies of the tet geometry plus the per-step scratch (gradients, face fluxes).  The
 // geometry is computed in FP64 on the host; the step kernels read it in the context's precision
 // (rounded once on the host for FP32 contexts), packed per face and per cell.
-constexpr int kTetFaceGeo = 12;   // per face: n 3, 1/(1+n_1) of the frame, x_s - x_L 3, x_s - x_R 3, |l|, pad
+constexpr int kTetFaceGeo = 10;   // per face: n 3, 1/(1+n_1) of the frame, x_s - x_L 3, x_s - x_R 3
 constexpr int kTetCellW = 12;     // per cell, gradient pass: n |l| / |Omega| of its 4 faces
-constexpr int kTetCellU = 4;      // per cell, update pass: sign_k / |Omega| of its 4 faces
+constexpr int kTetCellU = 4;      // per cell, update pass: sign_k |l_k| / |Omega| of its 4 faces
 struct TetDev {
   int64_t nt = 0, nf = 0;
   int64_t *perm = nullptr;

@@ -108,12 +108,12 @@ __global__ void tet_gradient_kernel(const T *__restrict__ V, const int32_t *__re
     for (int c = 0; c < 6; ++c) G[(6 * a + c) * nt + i] = g[a][c];
 }
 
-// The packed geometry of one face (12 values, 48 or 96 bytes, aligned): vector loads.
+// The packed geometry of one face (10 values, 40 or 80 bytes): 8- or 16-byte vector loads.
 __device__ __forceinline__ void load_face_geo(const float *p, float q[kTetFaceGeo]) {
 #pragma unroll
-  for (int k = 0; k < kTetFaceGeo / 4; ++k) {
-    const float4 v = __ldg(reinterpret_cast<const float4 *>(p) + k);
-    q[4 * k] = v.x; q[4 * k + 1] = v.y; q[4 * k + 2] = v.z; q[4 * k + 3] = v.w;
+  for (int k = 0; k < kTetFaceGeo / 2; ++k) {
+    const float2 v = __ldg(reinterpret_cast<const float2 *>(p) + k);
+    q[2 * k] = v.x; q[2 * k + 1] = v.y;
   }
 }
 __device__ __forceinline__ void load_face_geo(const double *p, double q[kTetFaceGeo]) {
@@ -218,14 +218,13 @@ __global__ void __launch_bounds__(TB, (sizeof(T) == 4 && !HAS_MU) ? 4 : 1)
   } else {
     flux3<T, true>(l, l, K, loc);
   }
-  const T area = q[10];
-  // back to global components: Phi = T'^T Phi_local, times |l_s|
+  // back to global components: Phi = T'^T Phi_local (|l_s| enters through the update weights)
 #pragma unroll
   for (int b = 0; b < 2; ++b)
 #pragma unroll
     for (int a = 0; a < 3; ++a)
       F[(3 * b + a) * nf + f] =
-          area * (Tm[a] * loc[3 * b] + Tm[3 + a] * loc[3 * b + 1] + Tm[6 + a] * loc[3 * b + 2]);
+          Tm[a] * loc[3 * b] + Tm[3 + a] * loc[3 * b + 1] + Tm[6 + a] * loc[3 * b + 2];
 }
 
 // The four update weights sign_k / |Omega| of a cell: one vector load (FP32) or two (FP64).
