@@ -378,6 +378,20 @@ __global__ void __launch_bounds__(NTH, 1)
   if (issuer)
     for (int p = z0 - 1; p <= z0 + 2; ++p)
       tma_plane(s, &tmV, &tmE, slot_of(p), X0 - 4, y0 - 2, zidx(p));
+  // own pair at plane z0-2 (wrapped or clamped, always inside the grid), loaded while the
+  // staged planes are in flight
+  f2 Wm[7];
+  {
+    const int gz = wrap_or_clamp(z0 - 2, a.nz, a.per[2]);
+    const int gy = wrap_or_clamp(y, a.ny, a.per[1]);
+    const int c0 = wrap_or_clamp(x, a.nx, a.per[0]), c1 = wrap_or_clamp(x + 1, a.nx, a.per[0]);
+    const int64_t o = (int64_t)gz * a.plane + (int64_t)gy * a.pitch;
+#pragma unroll
+    for (int m = 0; m < NA; ++m) {
+      const float *base = (m < 6 ? a.V + m * a.cstride : a.eps) + o;
+      Wm[m] = pk(__ldg(base + c0), __ldg(base + c1));
+    }
+  }
   {
     bool ok = true;
     for (int p = z0 - 1; p <= z0 + 2; ++p) ok &= mbar_wait(&s.bar[slot_of(p)], parity_of(p));
@@ -400,19 +414,8 @@ __global__ void __launch_bounds__(NTH, 1)
   // this warp's 24 columns in its lane quarter (row warps only)
   const unsigned tz = s.tmem + ((unsigned)(32 * (warp & 3)) << 16) + 24u * (unsigned)(warp >> 2);
 
-  f2 Wm[7], W0[7], Wp[7];               // own pair at planes k-1, k, k+1
+  f2 W0[7], Wp[7];                      // own pair at planes k, k+1 (Wm: k-1)
   f2 B[6], Minv = pk(0.f, 0.f);         // pending update of plane k-1: V_new = B - Minv F
-  {
-    const int gz = wrap_or_clamp(z0 - 2, a.nz, a.per[2]);
-    const int gy = wrap_or_clamp(y, a.ny, a.per[1]);
-    const int c0 = wrap_or_clamp(x, a.nx, a.per[0]), c1 = wrap_or_clamp(x + 1, a.nx, a.per[0]);
-    const int64_t o = (int64_t)gz * a.plane + (int64_t)gy * a.pitch;
-#pragma unroll
-    for (int m = 0; m < NA; ++m) {
-      const float *base = (m < 6 ? a.V + m * a.cstride : a.eps) + o;
-      Wm[m] = pk(__ldg(base + c0), __ldg(base + c1));
-    }
-  }
   load_pair(s, slot_of(z0 - 1), q, W0);
   load_pair(s, slot_of(z0), q, Wp);
   if (owned) {
@@ -714,8 +717,11 @@ cudaError_t launch_cart3d_side(const CartGeom &g, const CartStepArgs &a, cudaStr
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (sms <= 0) sms = 1;
   }
-  // z chunks: one CTA per SM; pick the chunk count that fills whole waves best, counting the
-  // prologue and the closing z-face (about one plane of work) as lost
+  // z chunks: one CTA per SM; pick the chunk count that fills whole waves best.  A CTA's fixed
+  // cost -- staging its first four planes with nothing to overlap them, the z-vectors of the
+  // plane below its chunk and the closing z-face -- counts as 2.7 planes of work: the value that
+  // fits measured step times at 256^3 over 1 to 32 chunks (7 chunks, 0.511 ms; 16, 0.529 ms)
+  constexpr double kChunkCost = 2.7;
   const int64_t tiles = (int64_t)gx * gy;
   int zchunks = 1;
   double best = -1.0;
@@ -724,7 +730,8 @@ cudaError_t launch_cart3d_side(const CartGeom &g, const CartStepArgs &a, cudaStr
     const int nzc = (g.nz + len - 1) / len;
     const int64_t ctas = tiles * nzc;
     const double waves = (double)((ctas + sms - 1) / sms);
-    const double eff = (double)ctas / (waves * sms) * (double)g.nz / (double)(nzc * (len + 1));
+    const double eff =
+        (double)ctas / (waves * sms) * (double)g.nz / ((double)nzc * (len + kChunkCost));
     if (eff > best + 1e-9) { best = eff; zchunks = nzc; }
   }
   p.zchunk = (g.nz + zchunks - 1) / zchunks;
