@@ -120,8 +120,8 @@ def test_sphere_workload_reduced():
 
 def test_full_size_sphere_sampled_fp32():
     """The 256^3 FP32 workload in the benchmark's launch configuration: after 20 steps, one more
-    step is checked at 150 sampled cells (plus faces and corners) against the oracle applied to
-    the GPU's own state."""
+    step is checked at 150 sampled cells (plus faces, corners and one whole z-column) against
+    the oracle applied to the GPU's own state."""
     n = 256
     w = wl.config3_sphere_3d(n=n, steps=21)
     s = GKSSolver.from_workload(w, precision="fp32")
@@ -134,6 +134,9 @@ def test_full_size_sphere_sampled_fp32():
     rng = np.random.default_rng(5)
     cells = list(rng.choice(n ** 3, size=150, replace=False))
     cells += [0, n - 1, n * n - 1, n ** 3 - 1, n * n * (n // 2) + n * (n // 2) + 30]
+    # a whole z-column at a corner of the side-split kernel's 64-column, 10-row tiles: it crosses
+    # every boundary between the z-chunks the launch splits the grid into
+    cells += [n * n * z + n * 10 + 64 for z in range(n)]
     ref = oracle_block_step(w, before, cells, info["dt"], 0.0, info["t"])
     scale = np.abs(before).max()
     assert np.abs(after[:, cells] - ref).max() <= 2e-6 * scale
