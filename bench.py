@@ -460,7 +460,6 @@ def run_sharded(args, w, world, rank, local, stream):
                  "hbm_frac_fp32_per_gpu": 52 * w3.ncell / world / (ms3 * 1e-3) / 1e9 / _peaks()[0],
                  "algorithmic_bytes_per_cell_step": 52}
     if rank == 0:
-        divergence = divergence_report(sptr)
         hbm, how = _peaks()
         ms_step = ms / args.steps
         achieved = BYTES_PER_CELL_STEP["fp32"] * ncell / world / (ms_step * 1e-3) / 1e9

@@ -53,3 +53,30 @@ def test_single_rank_is_identity():
     assert bench.max_over_ranks(12.5, 1, device="cpu") == 12.5
     assert bench.job_throughput(4096 * 4096, 2000, 400.0, 1) == pytest.approx(
         4096 * 4096 * 2000 / 0.4 / 1e9)
+
+
+def test_bench_functions_read_only_defined_globals():
+    """Every name a function of bench.py reads from the module scope exists there (or is a
+    builtin).  The multi-GPU legs run only under torchrun on several GPUs, so a stray name in
+    them would otherwise first show as a crash of the scaling run."""
+    import builtins
+    import symtable
+
+    sys.path.insert(0, ROOT)
+    import bench
+    path = os.path.join(ROOT, "bench.py")
+    with open(path) as f:
+        table = symtable.symtable(f.read(), path, "exec")
+    missing = []
+
+    def visit(t):
+        for child in t.get_children():
+            if child.get_type() == "function":
+                for sym in child.get_symbols():
+                    if (sym.is_global() and sym.is_referenced() and not hasattr(bench, sym.get_name())
+                            and not hasattr(builtins, sym.get_name())):
+                        missing.append((child.get_name(), sym.get_name()))
+            visit(child)
+
+    visit(table)
+    assert not missing, missing
