@@ -91,3 +91,55 @@ def test_limiter_needs_a_cartesian_grid(lib):
     d = _desc(kind=gks.GKS_TET, dim=3, limiter=gks.GKS_LIMITER_VAN_LEER)
     assert lib.gks_create_mesh(ctypes.byref(d), ctypes.byref(ctx)) == gks.GKS_E_UNSUPPORTED
     assert not ctx.value
+
+
+def _tet_desc(vert, tet, tet_bc=None):
+    """A tet-mesh description over host arrays (kept alive by the caller)."""
+    d = _desc(kind=gks.GKS_TET, dim=3)
+    d.n_vert = vert.shape[0]
+    d.vert_xyz = vert.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    d.n_tet = tet.shape[0]
+    d.tet_vert = tet.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    d.tet_bc = gks.GKS_BC_NONREFLECTING if tet_bc is None else tet_bc
+    return d
+
+
+@pytest.mark.parametrize("case", ["vertex_id", "non_finite", "degenerate", "three_owners",
+                                  "wall_kind"])
+def test_create_rejects_bad_tet_meshes(lib, case):
+    """The host builds the FP64 geometry before any device memory exists, and rejects a mesh
+    whose vertex ids leave the vertex list, whose coordinates are not finite, with a tet of zero
+    volume, with a face of three tets, or with an unknown wall kind."""
+    import numpy as np
+    vert = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1], [0, 0, -1], [1, 1, 1]], float)
+    tet = np.array([[0, 1, 2, 3], [0, 1, 2, 4]], np.int64)
+    bc = None
+    if case == "vertex_id":
+        tet[1, 3] = 6
+    elif case == "non_finite":
+        vert[5, 0] = np.inf
+    elif case == "degenerate":
+        vert[4] = [0.5, 0.5, 0.0]                   # in the plane of face (0, 1, 2)
+    elif case == "three_owners":
+        tet = np.array([[0, 1, 2, 3], [0, 1, 2, 4], [0, 1, 2, 5]], np.int64)
+    else:
+        bc = gks.GKS_BC_PERIODIC
+    d = _tet_desc(vert, tet, bc)
+    ctx = ctypes.c_void_p()
+    assert lib.gks_create_mesh(ctypes.byref(d), ctypes.byref(ctx)) == gks.GKS_E_ARG
+    assert not ctx.value
+
+
+@pytest.mark.parametrize("args", [
+    (7, 2, 10, 1.0), (gks.GKS_FP32, 4, 10, 1.0), (gks.GKS_FP32, 2, 0, 1.0),
+    (gks.GKS_FP32, 2, 33554432 + 1, 1.0), (gks.GKS_FP64, 3, 10, 0.0),
+    (gks.GKS_FP64, 3, 10, float("nan")),
+])
+def test_noalloc_energy_rejects_bad_arguments(lib, args):
+    """gks_energy_noalloc checks its precision, dimension, cell count (at most the fixed scratch's
+    33,554,432 cells) and cell volume before it touches the device."""
+    precision, dim, n, vol = args
+    fake = ctypes.c_void_p(256)                     # never dereferenced: rejected first
+    out = ctypes.c_void_p(512)
+    assert lib.gks_energy_noalloc(precision, dim, ctypes.c_int64(n), ctypes.c_double(vol), fake,
+                                  fake, None, out, None) == gks.GKS_E_ARG
