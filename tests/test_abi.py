@@ -143,3 +143,35 @@ def test_noalloc_energy_rejects_bad_arguments(lib, args):
     out = ctypes.c_void_p(512)
     assert lib.gks_energy_noalloc(precision, dim, ctypes.c_int64(n), ctypes.c_double(vol), fake,
                                   fake, None, out, None) == gks.GKS_E_ARG
+
+
+@pytest.mark.parametrize("case", ["auto_speed", "flag", "empty", "past_end", "thin", "ring",
+                                  "edge", "tets"])
+def test_create_slab_rejects_bad_slabs(lib, case):
+    """A rank-local slab needs the whole grid's lattice speed, 0/1 sharing flags, a non-empty
+    range inside the grid, two owned layers for each neighbour, both sides shared on a periodic
+    axis, no shared side at a non-periodic grid edge, and a Cartesian grid."""
+    d = _desc(c_lattice=1.0)                         # 8 x 8; slab axis y
+    d.bc[2] = d.bc[3] = gks.GKS_BC_NONREFLECTING     # (the zero-filled sides are periodic)
+    s = gks.gks_slab_desc(begin=2, end=6, shared_lo=1, shared_hi=1)
+    if case == "auto_speed":
+        d.c_lattice = 0.0
+    elif case == "flag":
+        s.shared_hi = 2
+    elif case == "empty":
+        s.end = 2
+    elif case == "past_end":
+        s.end = 9
+    elif case == "thin":
+        s.end = 3
+    elif case == "ring":
+        d.bc[2] = d.bc[3] = gks.GKS_BC_PERIODIC
+        s.shared_hi = 0
+    elif case == "edge":
+        s.begin = 0
+    else:
+        d.kind = gks.GKS_TET
+    ctx = ctypes.c_void_p()
+    assert lib.gks_create_slab(ctypes.byref(d), ctypes.byref(s), ctypes.byref(ctx)) == \
+        gks.GKS_E_ARG
+    assert not ctx.value
